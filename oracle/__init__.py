@@ -1,0 +1,231 @@
+"""AirGS splatting oracle -- TEST INFRASTRUCTURE ONLY.
+
+A plain FP64 CPU restatement of the splatting path of AirGS (arXiv 2512.20943):
+decode/apply of streamed updates (Sec. II Eq. 3, Sec. III-B Eq. 5, Sec. III-C),
+EWA projection and SH colour of the Gaussian primitive of Sec. II, 16x16 tile
+binning with a stable (tile, depth) order, front-to-back blending, the
+per-Gaussian blend weight behind usage-frequency pruning (Sec. III-C), the L1
+part of Eq. 1, and the analytic adjoint.  The arithmetic lives in
+``airgs_oracle.cpp``; this module only marshals numpy arrays.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It shares no code with the CUDA path.
+
+Parity pins live in ``tests/test_oracle_*.py``.  The one function without an
+external pin is the end-to-end image quality of the paper's trained scenes
+(parity unpinned: the paper's dataset is not available).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "airgs_oracle.cpp")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+# Rasterizer settings used by every definition (3DGS values; see module doc).
+DEFAULT_SETTINGS = dict(
+    dilation=0.3,
+    alpha_max=0.99,
+    alpha_min=1.0 / 255.0,
+    T_min=1e-4,
+    bg=(0.0, 0.0, 0.0),
+    tol_px=1e-3,
+    tol_rel=1e-5,
+    tol_stop=1e-3,
+)
+
+QUAT_COMPOSE = 0
+QUAT_ADD = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with g++ (plain -O2, single-threaded)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-o", _LIB_PATH + ".tmp", _SRC]
+        subprocess.run(cmd, check=True)
+        os.replace(_LIB_PATH + ".tmp", _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.c_void_p
+        lib.orc_sh_eval.argtypes = [ctypes.c_int, P, P, P]
+        lib.orc_decode_apply.argtypes = [ctypes.c_int64, P, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, P, P, P, P]
+        lib.orc_project.argtypes = [ctypes.c_int64, ctypes.c_int] + [P] * 7 + [P] * 10
+        lib.orc_bin_sort.argtypes = [ctypes.c_int64, P, P, P, P, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int64]
+        lib.orc_bin_sort.restype = ctypes.c_int64
+        lib.orc_render.argtypes = [ctypes.c_int64, ctypes.c_int] + [P] * 5 + [ctypes.c_int, P, P] + [P] * 8
+        lib.orc_render_backward.argtypes = [ctypes.c_int64, ctypes.c_int] + [P] * 5 + [ctypes.c_int, P, P] + [P] * 6
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def settings_array(**kw) -> np.ndarray:
+    s = dict(DEFAULT_SETTINGS)
+    s.update(kw)
+    return np.array(
+        [s["dilation"], s["alpha_max"], s["alpha_min"], s["T_min"], *s["bg"], s["tol_px"], s["tol_rel"], s["tol_stop"]],
+        dtype=np.float64,
+    )
+
+
+def camera_array(cam: dict) -> np.ndarray:
+    """Flatten a camera dict (width, height, fx, fy, cx, cy, near, viewmat 4x4)."""
+    vm = np.asarray(cam["viewmat"], dtype=np.float64).reshape(4, 4)
+    return np.concatenate(
+        [
+            np.array([cam["width"], cam["height"], cam["fx"], cam["fy"], cam["cx"], cam["cy"], cam.get("near", 0.2)],
+                     dtype=np.float64),
+            vm.reshape(-1),
+        ]
+    )
+
+
+def sh_eval(degree: int, direction, with_grad: bool = False):
+    """Real SH basis (3DGS sign convention) at a unit direction."""
+    lib = _load()
+    K = (degree + 1) ** 2
+    d = _f64(direction)
+    Y = np.zeros(K)
+    dY = np.zeros((K, 3)) if with_grad else None
+    if lib.orc_sh_eval(degree, _p(d), _p(Y), _p(dY)) != 0:
+        raise ValueError("bad degree")
+    return (Y, dY) if with_grad else Y
+
+
+def decode_apply(update_map, lo, hi, base_means, base_quats, quat_mode: int = QUAT_COMPOSE):
+    """Decode a [7, H, W] uint16 map and apply it to base means/quats."""
+    lib = _load()
+    m = np.ascontiguousarray(update_map, dtype=np.uint16)
+    assert m.ndim == 3 and m.shape[0] == 7
+    bm, bq = _f64(base_means), _f64(base_quats)
+    N = bm.shape[0]
+    om, oq = np.zeros((N, 3)), np.zeros((N, 4))
+    rc = lib.orc_decode_apply(N, _p(m), m.shape[2], m.shape[1], _p(_f64(lo)), _p(_f64(hi)), quat_mode, _p(bm),
+                              _p(bq), _p(om), _p(oq))
+    if rc != 0:
+        raise ValueError("N exceeds the map's pixel count")
+    return om, oq
+
+
+def _params(g):
+    return (_f64(g["means"]), _f64(g["log_scales"]), _f64(g["quats"]), _f64(g["opacity_logit"]), _f64(g["sh"]))
+
+
+def project(g: dict, cam: dict, **settings):
+    lib = _load()
+    means, ls, qs, ol, sh = _params(g)
+    N = means.shape[0]
+    deg = int(g["sh_degree"])
+    out = dict(
+        mean2d=np.zeros((N, 2)), conic=np.zeros((N, 3)), radius=np.zeros(N, np.int32), depth=np.zeros(N),
+        rect=np.zeros((N, 4), np.int32), rgb=np.zeros((N, 3)), clamp=np.zeros(N, np.uint8), opacity=np.zeros(N),
+        visible=np.zeros(N, np.uint8), ambig=np.zeros(N, np.uint8),
+    )
+    rc = lib.orc_project(N, deg, _p(means), _p(ls), _p(qs), _p(ol), _p(sh), _p(camera_array(cam)),
+                         _p(settings_array(**settings)), _p(out["mean2d"]), _p(out["conic"]), _p(out["radius"]),
+                         _p(out["depth"]), _p(out["rect"]), _p(out["rgb"]), _p(out["clamp"]), _p(out["opacity"]),
+                         _p(out["visible"]), _p(out["ambig"]))
+    if rc != 0:
+        raise ValueError("bad sh degree")
+    return out
+
+
+def bin_sort(mean2d, radius, depth, visible, width: int, height: int):
+    """Tile lists for given centres, radii, depths (any precision, widened)."""
+    lib = _load()
+    m2 = _f64(mean2d)
+    N = m2.shape[0]
+    r = np.ascontiguousarray(radius, dtype=np.int32)
+    d = _f64(depth)
+    vis = np.ascontiguousarray(visible, dtype=np.uint8)
+    ntiles = ((width + 15) // 16) * ((height + 15) // 16)
+    ranges = np.zeros((ntiles, 2), np.int64)
+    n = lib.orc_bin_sort(N, _p(m2), _p(r), _p(d), _p(vis), width, height, _p(ranges), None, 0)
+    lst = np.zeros(max(n, 1), np.int32)
+    lib.orc_bin_sort(N, _p(m2), _p(r), _p(d), _p(vis), width, height, _p(ranges), _p(lst), n)
+    return ranges, lst[:n]
+
+
+def _cams(cams):
+    return np.ascontiguousarray(np.stack([camera_array(c) for c in cams]), dtype=np.float64)
+
+
+def render(g: dict, cams, **settings):
+    """Forward over several views.  Returns a dict with per-view lists of
+    rgb [3,H,W], T [H,W], n_contrib [H,W], ambig [H,W], and the per-Gaussian
+    importance weight/count and ambiguity flags, and the evaluated pair count."""
+    lib = _load()
+    means, ls, qs, ol, sh = _params(g)
+    N = means.shape[0]
+    sizes = [(int(c["height"]), int(c["width"])) for c in cams]
+    tot = sum(h * w for h, w in sizes)
+    rgb = np.zeros(3 * tot)
+    T = np.zeros(tot)
+    nc = np.zeros(tot, np.int32)
+    amb = np.zeros(tot, np.uint8)
+    w = np.zeros(N)
+    cnt = np.zeros(N, np.int64)
+    gamb = np.zeros(N, np.uint8)
+    pairs = np.zeros(1, np.int64)
+    rc = lib.orc_render(N, int(g["sh_degree"]), _p(means), _p(ls), _p(qs), _p(ol), _p(sh), len(cams), _p(_cams(cams)),
+                        _p(settings_array(**settings)), _p(rgb), _p(T), _p(nc), _p(w), _p(cnt), _p(amb), _p(gamb),
+                        _p(pairs))
+    if rc != 0:
+        raise ValueError("bad sh degree")
+    out = dict(rgb=[], T=[], n_contrib=[], ambig=[], importance_w=w, importance_cnt=cnt, gauss_ambig=gamb,
+               pairs=int(pairs[0]))
+    off = 0
+    for h, wd in sizes:
+        hw = h * wd
+        out["rgb"].append(rgb[3 * off:3 * (off + hw)].reshape(3, h, wd))
+        out["T"].append(T[off:off + hw].reshape(h, wd))
+        out["n_contrib"].append(nc[off:off + hw].reshape(h, wd))
+        out["ambig"].append(amb[off:off + hw].reshape(h, wd).astype(bool))
+        off += hw
+    return out
+
+
+def render_backward(g: dict, cams, dL_drgb, **settings):
+    """Analytic gradients of sum(dL_drgb * rgb) w.r.t. the raw parameters.
+    dL_drgb is a list of [3,H,W] arrays, one per view."""
+    lib = _load()
+    means, ls, qs, ol, sh = _params(g)
+    N = means.shape[0]
+    K = sh.shape[1]
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float64).reshape(-1) for x in dL_drgb]))
+    gm, gl, gq, go, gs = np.zeros((N, 3)), np.zeros((N, 3)), np.zeros((N, 4)), np.zeros(N), np.zeros((N, K, 3))
+    rc = lib.orc_render_backward(N, int(g["sh_degree"]), _p(means), _p(ls), _p(qs), _p(ol), _p(sh), len(cams),
+                                 _p(_cams(cams)), _p(settings_array(**settings)), _p(flat), _p(gm), _p(gl), _p(gq),
+                                 _p(go), _p(gs))
+    if rc != 0:
+        raise ValueError("bad sh degree")
+    return dict(means=gm, log_scales=gl, quats=gq, opacity_logit=go, sh=gs)
+
+
+def l1_loss_grad(rgb_views, target_views):
+    """L1 part of Eq. 1: mean |C - target| over views, pixels and channels, and
+    its gradient sign(C - target) / (3 sum_v H_v W_v), sign(0) = 0."""
+    n = sum(np.asarray(r).size for r in rgb_views)
+    loss = sum(np.abs(np.asarray(r, np.float64) - np.asarray(t, np.float64)).sum()
+               for r, t in zip(rgb_views, target_views)) / n
+    grads = [np.sign(np.asarray(r, np.float64) - np.asarray(t, np.float64)) / n for r, t in zip(rgb_views, target_views)]
+    return loss, grads
