@@ -1,0 +1,232 @@
+/*
+ * airgs.h -- C ABI of the AirGS splatting library (sm_103a).
+ *
+ * The library evaluates the data-parallel path of AirGS (arXiv 2512.20943):
+ *   - decode and apply of a frame's streamed Gaussian update, shipped as a
+ *     multi-channel 16-bit 2D map with one Gaussian per pixel and one attribute
+ *     per channel (Sec. II, Eq. 3), applied to the previous frame
+ *     (GS_{t+1} = GS_t + d_{t+1}, Sec. III-B, Eq. 5) or to the anchor
+ *     (GS_t = GC_k + D_t, Sec. III-C);
+ *   - rendering of Gaussians G = {mu, alpha, c, SH, R, S}, Sigma = R S S^T R^T
+ *     (Sec. II) with a differentiable tile-based splatting rasterizer: EWA
+ *     projection, SH colour, 16x16 tile binning, a stable (tile, depth) order
+ *     and front-to-back alpha blending with
+ *       alpha = min(alpha_max, o exp(-1/2 d^T Sigma'^-1 d)),
+ *     pairs with alpha < alpha_min skipped, and a pixel stopped before the
+ *     Gaussian that would take T below T_min;
+ *   - the adjoint of the rasterizer (the "differentiable splatting renderer" of
+ *     Sec. II) with the L1 term of Eq. 1;
+ *   - the per-Gaussian blend weight sum(alpha_i T_i) and blended-pair count,
+ *     the usage frequency behind the adaptive pruning of Sec. III-C.
+ *
+ * Conventions
+ *   - Every pointer argument named as "device" is CUDA device memory owned by
+ *     the caller; the library never frees it.  Host pointers are read during
+ *     the call only.
+ *   - All work is enqueued on the context's stream and is asynchronous, except
+ *     where a call says it synchronises.  The caller must keep device inputs
+ *     alive and unmodified until the stream has passed the call.
+ *   - Gaussian parameters are float32, structure of arrays: means [N][3],
+ *     log_scales [N][3], quats [N][4] (w, x, y, z; any norm), opacity_logit [N],
+ *     sh [N][K][3] with K = (sh_degree + 1)^2, sh_degree 0..3.
+ *   - Images are float32 planar: view v occupies [3][H_v][W_v] starting at
+ *     3 * sum_{u<v} H_u W_u in the output buffer; single-channel outputs
+ *     (T, n_contrib) start at sum_{u<v} H_u W_u.
+ *   - Pixel (x, y) is sampled at (x + 0.5, y + 0.5).  Cameras look down +z with
+ *     x right and y down.
+ *   - Return value: AIRGS_OK or a negative AIRGS_E_* code; airgs_last_error()
+ *     describes the failure.  No C++ exception crosses this boundary.
+ */
+#ifndef AIRGS_H
+#define AIRGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AIRGS_OK 0
+#define AIRGS_E_ARG (-1)      /* invalid argument (sizes, degree, null pointer) */
+#define AIRGS_E_OOM (-2)      /* device allocation failed */
+#define AIRGS_E_CAPACITY (-3) /* a size limit was exceeded */
+#define AIRGS_E_TIMEOUT (-4)  /* a bounded device wait gave up */
+#define AIRGS_E_CUDA (-5)     /* a CUDA runtime call failed */
+#define AIRGS_E_STATE (-6)    /* call out of order (no anchor, state released) */
+
+/* apply_frame_update modes */
+#define AIRGS_DELTA_PREV 0   /* apply d_t to the current frame state */
+#define AIRGS_DELTA_ANCHOR 1 /* apply D_t to the anchor */
+#define AIRGS_QUAT_ADD 2     /* flag: q = q_base + dq instead of normalize(dq (x) q_base) */
+
+#define AIRGS_UPDATE_CHANNELS 7 /* dx, dy, dz, qw, qx, qy, qz */
+#define AIRGS_MAX_VIEWS 256
+
+typedef struct airgs_ctx airgs_ctx;     /* opaque: device state, scratch, stream */
+typedef struct airgs_state airgs_state; /* opaque: what render saved for render_backward */
+
+/* Rasterizer settings (3DGS values by default). */
+typedef struct {
+  float dilation;  /* added to the 2D covariance diagonal (0.3) */
+  float alpha_max; /* 0.99 */
+  float alpha_min; /* 1/255 */
+  float T_min;     /* 1e-4 */
+  float bg[3];     /* background colour, added as T_final * bg (black) */
+  int blend_variant;          /* -1: autotuned per workload, else a fixed kernel variant */
+  const char* autotune_cache; /* nullable path of a text cache of autotune choices */
+} airgs_config;
+
+typedef struct {
+  int width, height;
+  float fx, fy, cx, cy;
+  float viewmat[16]; /* world -> camera, row-major 4x4 */
+  float near_plane;  /* z <= near_plane is culled (0.2) */
+} airgs_camera;
+
+typedef struct {
+  int64_t n;
+  int sh_degree;
+  const float* means;         /* device [n][3] */
+  const float* log_scales;    /* device [n][3] */
+  const float* quats;         /* device [n][4] */
+  const float* opacity_logit; /* device [n] */
+  const float* sh;            /* device [n][K][3] */
+} airgs_gaussians;
+
+/* Per-call counters, filled by airgs_state_stats. */
+typedef struct {
+  int64_t n_instances;   /* (tile, Gaussian) list entries over all views */
+  int64_t n_tiles;       /* 16x16 tiles over all views */
+  int64_t n_pixels;      /* pixels over all views */
+  int64_t pairs_forward; /* (pixel, list entry) pairs evaluated by the forward, up to termination */
+  int64_t pairs_backward;/* pairs replayed by the backward (list positions < n_contrib) */
+  int blend_variant;     /* kernel variant the forward ran */
+} airgs_stats;
+
+/* Fill *cfg with the defaults above. */
+void airgs_default_config(airgs_config* cfg);
+
+/* Create a context bound to the current CUDA device and to `stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  cfg may be NULL. */
+int airgs_create(airgs_ctx** out, const airgs_config* cfg, void* stream);
+int airgs_destroy(airgs_ctx* ctx);
+int airgs_set_stream(airgs_ctx* ctx, void* stream);
+/* Block until the context's stream is idle, then report any device-side
+ * status (AIRGS_E_CAPACITY, AIRGS_E_TIMEOUT) raised since the last sync. */
+int airgs_sync(airgs_ctx* ctx);
+/* Message of the last failure on this context ("" if none).  Valid until the
+ * next call on the context. */
+const char* airgs_last_error(const airgs_ctx* ctx);
+
+/* set_anchor: copy the canonical Gaussian set GC_k of a keyframe (Sec. II
+ * Eq. 2, Sec. III-C) into the context; the current frame state is reset to the
+ * anchor.  Pointers are device [n]... arrays as in airgs_gaussians; copied
+ * before return (asynchronously on the stream). */
+int airgs_set_anchor(airgs_ctx* ctx, int64_t n, int sh_degree, const float* means, const float* log_scales,
+                     const float* quats, const float* opacity_logit, const float* sh);
+
+/* apply_frame_update: decode one frame's update map and apply it (Sec. II
+ * Eq. 3; Sec. III-B Eq. 5; Sec. III-C d_t / D_t).
+ *   map     device uint16 [7][map_h][map_w], channel c of Gaussian i at pixel i
+ *           (row-major); pixels >= n are ignored.  Requires n <= map_w * map_h.
+ *   lo, hi  host float[7]: channel c decodes as lo[c] + u (hi[c] - lo[c]) / 65535.
+ *   mode    AIRGS_DELTA_PREV (base = current frame) or AIRGS_DELTA_ANCHOR
+ *           (base = anchor), optionally | AIRGS_QUAT_ADD.
+ * Result: means = base_means + (dx, dy, dz); quats = normalize(dq (x) base_q)
+ * (Hamilton product) or base_q + dq.  Scales, opacity and SH stay the
+ * anchor's.  frame_id is recorded only. */
+int airgs_apply_frame_update(airgs_ctx* ctx, const uint16_t* map, int map_w, int map_h, const float* lo,
+                             const float* hi, int mode, int64_t frame_id);
+
+/* Copy the current frame's means [n][3] and quats [n][4] into device buffers. */
+int airgs_get_frame_state(airgs_ctx* ctx, float* means_out, float* quats_out);
+
+/* render: forward over n_views cameras (host array) of the current frame
+ * state.  Outputs (device, caller-owned):
+ *   rgb_out         float [sum 3 H W]   C + T_final bg, planar per view (required)
+ *   T_out           float [sum H W]     final transmittance (nullable)
+ *   n_contrib_out   int32 [sum H W]     1 + list position of the last blended Gaussian (nullable)
+ *   importance_w    float [n]           += sum over blended pairs of alpha_i T_i (nullable)
+ *   importance_cnt  uint32 [n]          += number of blended pairs (nullable)
+ *   saved           if not NULL, receives a state for render_backward; the
+ *                   state reads rgb_out again, so rgb_out must stay unmodified
+ *                   until the state is released.
+ * Synchronises once on the stream to size the tile lists. */
+int airgs_render(airgs_ctx* ctx, const airgs_camera* cams, int n_views, float* rgb_out, float* T_out,
+                 int32_t* n_contrib_out, float* importance_w, uint32_t* importance_cnt, airgs_state** saved);
+
+/* render_gaussians: as airgs_render, for a caller-owned Gaussian set (the
+ * training path); the parameters must stay unmodified while a saved state
+ * refers to them. */
+int airgs_render_gaussians(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* cams, int n_views,
+                           float* rgb_out, float* T_out, int32_t* n_contrib_out, float* importance_w,
+                           uint32_t* importance_cnt, airgs_state** saved);
+
+/* render_backward: adjoint of the render that produced `saved`, given
+ * dL/d(rgb) laid out like rgb_out (device).  Gradients with respect to the raw
+ * parameters (means, log_scales, quats, opacity_logit, sh) are written to the
+ * device buffers g_* (overwritten; shapes as the parameters).  importance_w /
+ * importance_cnt (nullable) accumulate as in render, computed during the
+ * backward replay. */
+int airgs_render_backward(airgs_ctx* ctx, airgs_state* saved, const float* dL_drgb, float* g_means,
+                          float* g_log_scales, float* g_quats, float* g_opacity_logit, float* g_sh,
+                          float* importance_w, uint32_t* importance_cnt);
+
+/* render_backward_l1: as render_backward with dL/d(rgb) taken from the L1 term
+ * of Eq. 1, L = mean |rgb - target| over views, pixels and channels
+ * (gradient sign(rgb - target) / (3 sum H W), sign(0) = 0), fused into the
+ * backward.  target is laid out like rgb_out; loss_out (device float, nullable)
+ * receives L (overwritten). */
+int airgs_render_backward_l1(airgs_ctx* ctx, airgs_state* saved, const float* target, float* loss_out,
+                             float* g_means, float* g_log_scales, float* g_quats, float* g_opacity_logit,
+                             float* g_sh, float* importance_w, uint32_t* importance_cnt);
+
+/* gaussian_importance: the per-Gaussian blend weight and blended-pair count of
+ * the current frame over n_views cameras, without colour output (the usage
+ * frequency of Sec. III-C).  w_out [n] float and cnt_out [n] uint32 are
+ * overwritten (device). */
+int airgs_gaussian_importance(airgs_ctx* ctx, const airgs_camera* cams, int n_views, float* w_out,
+                              uint32_t* cnt_out);
+
+/* Release a state returned by a render call (its device memory is returned to
+ * the context's pool once the stream passes this point). */
+int airgs_release_state(airgs_ctx* ctx, airgs_state* state);
+
+/* Counters of the render that produced `state` (synchronises on the stream). */
+int airgs_state_stats(airgs_ctx* ctx, const airgs_state* state, airgs_stats* out);
+
+/* Inspection of a state for parity tests (device outputs, caller-owned):
+ *   view-local projection of each Gaussian: mean2d [n][2], depth [n],
+ *   radius [n] (0 when culled);
+ *   the view's tile lists: ranges [tiles][2] int64 (start, end) relative to the
+ *   view's first entry, ids [entries] int32 (Gaussian index per list entry).
+ * airgs_state_view_info returns the view's tile count and list length. */
+int airgs_state_view_info(airgs_ctx* ctx, const airgs_state* state, int view, int64_t* n_tiles,
+                          int64_t* n_entries);
+int airgs_state_projection(airgs_ctx* ctx, const airgs_state* state, int view, float* mean2d, float* depth,
+                           int32_t* radius);
+int airgs_state_tile_lists(airgs_ctx* ctx, const airgs_state* state, int view, int64_t* ranges, int32_t* ids);
+
+/* Stable LSD radix sort of (key, value) pairs by the key bits [0, key_bits),
+ * the sort the tile ordering uses: keys_in/vals_in are device uint32 [n];
+ * results go to keys_out/vals_out (device, distinct from the inputs).
+ * Allocates its scratch from the context's pool. */
+int airgs_sort_pairs(airgs_ctx* ctx, const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                     uint32_t* vals_out, int64_t n, int key_bits);
+
+/* Autotune the blend kernel variant for this workload shape (n Gaussians of
+ * the current frame, the given cameras) by timing every variant; the choice
+ * is cached per (n, total pixels, n_views) and written to the config's cache
+ * path if set.  Returns the chosen variant in *variant. */
+int airgs_autotune(airgs_ctx* ctx, const airgs_camera* cams, int n_views, int* variant);
+
+/* Number of blend kernel variants and a short name of each. */
+int airgs_blend_variant_count(void);
+const char* airgs_blend_variant_name(int variant);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AIRGS_H */

@@ -1,0 +1,117 @@
+// Internal device-side definitions shared by the AirGS kernels (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace airgs {
+
+constexpr int kTile = 16;            // 16x16 pixel tiles
+constexpr int kTilePixels = kTile * kTile;
+constexpr float kLog2e = 1.4426950408889634f;  // 1 / ln 2
+constexpr float kLn2 = 0.6931471805599453f;
+
+// One camera as the kernels see it.
+struct CamDev {
+  float R[9];       // world -> camera rotation, row-major
+  float t[3];       // world -> camera translation
+  float campos[3];  // camera centre in world space, -R^T t
+  float fx, fy, cx, cy;
+  float znear;
+  float limx, limy;  // frustum guard 1.3 tan(fov/2) on x/z, y/z
+  int W, H, TW, TH;  // image size and tile grid
+  int64_t tile_base; // first global tile id of this view
+  int64_t pix_base;  // first pixel of this view in concatenated outputs
+};
+
+// Rasterizer constants of a launch.
+struct RasterParams {
+  float dilation, alpha_max, alpha_min, T_min;
+  float bg[3];
+};
+
+// Per (view, Gaussian) projection record, three 16-byte words:
+//   a = {mx, my, a2, b2}
+//   b = {c2, opacity, r, g}
+//   c = {b, depth, radius (int bits), flags (int bits)}
+// with (a2, b2, c2) = log2(e) * (-A/2, -B, -C/2) for the conic (A, B, C) of
+// Sigma'^-1, so that  power * log2(e) = a2 dx^2 + b2 dx dy + c2 dy^2.
+struct __align__(16) ProjRec {
+  float4 a, b, c;
+};
+constexpr int kFlagVisible = 1;
+constexpr int kFlagClampShift = 1;  // bits 1..3: colour channel clamped at 0
+constexpr int kFlagGuardX = 16;     // x/z outside the frustum guard
+constexpr int kFlagGuardY = 32;
+
+// Per (view, Gaussian) gradient record accumulated by the blend backward:
+//   a = {dL/dmx, dL/dmy, dL/dA, dL/dB}
+//   b = {dL/dC, dL/dopacity, dL/dr, dL/dg}
+//   c = {dL/db, 0, 0, 0}
+struct __align__(16) GradRec {
+  float4 a, b, c;
+};
+
+// ------------------------------------------------------------------ exact-replay arithmetic
+// The forward and the backward evaluate every (pixel, Gaussian) pair through
+// these helpers, with explicit rounding intrinsics, so that the backward's
+// replay takes exactly the forward's skip / blend / stop decisions and
+// reproduces its running sums bit for bit.
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Terms that depend only on the pixel row: b2 dy and c2 dy^2.
+__device__ __forceinline__ void row_terms(float my, float py, float b2, float c2, float& dy, float& b2dy,
+                                          float& c2dy2) {
+  dy = __fsub_rn(my, py);
+  b2dy = __fmul_rn(b2, dy);
+  c2dy2 = __fmul_rn(__fmul_rn(c2, dy), dy);
+}
+
+// log2(e) * power for a pixel column offset dx.
+__device__ __forceinline__ float power2_of(float dx, float a2, float b2dy, float c2dy2) {
+  return __fmaf_rn(__fmaf_rn(a2, dx, b2dy), dx, c2dy2);
+}
+
+__device__ __forceinline__ float alpha_of(float o, float G, float alpha_max) { return fminf(alpha_max, __fmul_rn(o, G)); }
+
+__device__ __forceinline__ float transmit(float T, float alpha) { return __fmul_rn(T, __fsub_rn(1.0f, alpha)); }
+
+// Tile rectangle of a footprint centred at (mx, my) with integer radius r: the
+// tiles whose 16-pixel span meets [m - r, m + r], computed exactly from
+// floor(m) (floor((m +- r)/16) = floor((floor(m) +- r)/16) for integer r).
+__device__ __forceinline__ void tile_rect(float mx, float my, int r, int TW, int TH, int& x0, int& y0, int& x1,
+                                          int& y1) {
+  const float lim = 1048576.0f;
+  int fx = (int)floorf(fminf(fmaxf(mx, -lim), lim));
+  int fy = (int)floorf(fminf(fmaxf(my, -lim), lim));
+  int rr = min(r, 1048576);
+  // arithmetic shift = floor division by 16 for negative values too
+  x0 = min(max((fx - rr) >> 4, 0), TW);
+  x1 = min(max(((fx + rr) >> 4) + 1, 0), TW);
+  y0 = min(max((fy - rr) >> 4, 0), TH);
+  y1 = min(max(((fy + rr) >> 4) + 1, 0), TH);
+}
+
+// View that owns a global tile id (binary search over tile_base).
+__device__ __forceinline__ int view_of_tile(const int64_t* tile_base, int n_views, int64_t tile) {
+  int lo = 0, hi = n_views - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (tile_base[mid] <= tile)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
+               : "memory");
+}
+
+}  // namespace airgs

@@ -1,0 +1,783 @@
+// C ABI of the AirGS splatting library: context, device memory, and the
+// render / backward / update pipelines built from the kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <new>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "airgs.h"
+#include "airgs_internal.cuh"
+#include "kernels.h"
+
+using namespace airgs;
+
+struct airgs_ctx {
+  airgs_config cfg;
+  std::string autotune_path;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 148;
+  cudaMemPool_t pool = nullptr;
+  // anchor GC_k and the current frame state
+  int64_t n = 0;
+  int sh_degree = -1;
+  float *a_means = nullptr, *a_log_scales = nullptr, *a_quats = nullptr, *a_opacity = nullptr, *a_sh = nullptr;
+  float *c_means = nullptr, *c_quats = nullptr;
+  int64_t frame_id = -1;
+  uint64_t* h_pinned = nullptr;  // small pinned host buffer for counters
+  std::string last_error;
+  std::map<std::string, int> tuned;  // autotune choices
+};
+
+struct airgs_state {
+  int n_views = 0;
+  int64_t n = 0;
+  int sh_degree = 0;
+  const float *means = nullptr, *log_scales = nullptr, *quats = nullptr, *opacity = nullptr, *sh = nullptr;
+  std::vector<CamDev> h_cams;
+  CamDev* d_cams = nullptr;
+  ProjRec* proj = nullptr;     // [V][N]
+  uint32_t* ids = nullptr;     // sorted instance values
+  uint2* ranges = nullptr;     // [tiles]
+  int32_t* ncontrib = nullptr; // [pixels]
+  int* work = nullptr;         // [2] work counters (forward, backward)
+  unsigned long long* pairs = nullptr;  // [2] pair counters (forward, backward)
+  const float* rgb = nullptr;  // caller's forward output
+  int64_t n_inst = 0, n_tiles = 0, n_pixels = 0;
+  int variant = 0;
+  std::vector<void*> owned;    // device allocations to free on release
+};
+
+// ------------------------------------------------------------------ helpers
+namespace {
+
+int fail(airgs_ctx* ctx, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->last_error = buf;
+  return code;
+}
+
+#define CK(expr)                                                                                  \
+  do {                                                                                            \
+    cudaError_t e_ = (expr);                                                                      \
+    if (e_ != cudaSuccess) return fail(ctx, AIRGS_E_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+template <class T>
+int dalloc(airgs_ctx* ctx, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMallocFromPoolAsync((void**)p, count * sizeof(T), ctx->pool, ctx->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, AIRGS_E_OOM, "device allocation of %zu bytes failed: %s", count * sizeof(T),
+                cudaGetErrorString(e));
+  }
+  return AIRGS_OK;
+}
+
+void dfree(airgs_ctx* ctx, void* p) {
+  if (p) cudaFreeAsync(p, ctx->stream);
+}
+
+void free_anchor(airgs_ctx* ctx) {
+  for (float** p : {&ctx->a_means, &ctx->a_log_scales, &ctx->a_quats, &ctx->a_opacity, &ctx->a_sh, &ctx->c_means,
+                    &ctx->c_quats}) {
+    dfree(ctx, *p);
+    *p = nullptr;
+  }
+  ctx->n = 0;
+  ctx->sh_degree = -1;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+int build_cams(airgs_ctx* ctx, const airgs_camera* cams, int n_views, std::vector<CamDev>& out, int64_t& n_tiles,
+               int64_t& n_pixels) {
+  if (!cams || n_views <= 0 || n_views > AIRGS_MAX_VIEWS)
+    return fail(ctx, AIRGS_E_ARG, "n_views must be in [1, %d]", AIRGS_MAX_VIEWS);
+  out.resize(n_views);
+  n_tiles = 0;
+  n_pixels = 0;
+  for (int v = 0; v < n_views; ++v) {
+    const airgs_camera& c = cams[v];
+    if (c.width <= 0 || c.height <= 0 || c.width > 65536 || c.height > 65536 || !(c.fx > 0) || !(c.fy > 0))
+      return fail(ctx, AIRGS_E_ARG, "camera %d: bad size or focal length", v);
+    CamDev& d = out[v];
+    for (int r = 0; r < 3; ++r) {
+      for (int k = 0; k < 3; ++k) d.R[3 * r + k] = c.viewmat[4 * r + k];
+      d.t[r] = c.viewmat[4 * r + 3];
+    }
+    for (int k = 0; k < 3; ++k)
+      d.campos[k] = -(d.R[k] * d.t[0] + d.R[3 + k] * d.t[1] + d.R[6 + k] * d.t[2]);
+    d.fx = c.fx;
+    d.fy = c.fy;
+    d.cx = c.cx;
+    d.cy = c.cy;
+    d.znear = c.near_plane;
+    d.limx = 1.3f * (float)c.width / (2.f * c.fx);
+    d.limy = 1.3f * (float)c.height / (2.f * c.fy);
+    d.W = c.width;
+    d.H = c.height;
+    d.TW = (c.width + kTile - 1) / kTile;
+    d.TH = (c.height + kTile - 1) / kTile;
+    d.tile_base = n_tiles;
+    d.pix_base = n_pixels;
+    n_tiles += (int64_t)d.TW * d.TH;
+    n_pixels += (int64_t)c.width * c.height;
+  }
+  if (n_tiles >= (1ll << 31)) return fail(ctx, AIRGS_E_CAPACITY, "too many tiles (%lld)", (long long)n_tiles);
+  return AIRGS_OK;
+}
+
+int check_gaussians(airgs_ctx* ctx, const airgs_gaussians* g) {
+  if (!g || g->n < 0 || g->n >= (1ll << 31)) return fail(ctx, AIRGS_E_ARG, "Gaussian count out of range");
+  if (g->sh_degree < 0 || g->sh_degree > 3) return fail(ctx, AIRGS_E_ARG, "sh_degree must be 0..3");
+  if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logit || !g->sh))
+    return fail(ctx, AIRGS_E_ARG, "null Gaussian parameter pointer");
+  if (g->n > 0 && !aligned16(g->quats)) return fail(ctx, AIRGS_E_ARG, "quats must be 16-byte aligned");
+  return AIRGS_OK;
+}
+
+RasterParams raster_params(const airgs_config& c) {
+  RasterParams rp;
+  rp.dilation = c.dilation;
+  rp.alpha_max = c.alpha_max;
+  rp.alpha_min = c.alpha_min;
+  rp.T_min = c.T_min;
+  for (int k = 0; k < 3; ++k) rp.bg[k] = c.bg[k];
+  return rp;
+}
+
+int bits_for(int64_t count) {
+  int b = 0;
+  while ((1ll << b) < count) ++b;
+  return std::max(b, 1);
+}
+
+void release_state(airgs_ctx* ctx, airgs_state* s) {
+  if (!s) return;
+  for (void* p : s->owned) dfree(ctx, p);
+  delete s;
+}
+
+std::string tune_key(int64_t n, int64_t pixels, int views) {
+  std::ostringstream os;
+  os << n << ":" << pixels << ":" << views;
+  return os.str();
+}
+
+int choose_variant(airgs_ctx* ctx, int64_t n, int64_t pixels, int views) {
+  if (ctx->cfg.blend_variant >= 0 && ctx->cfg.blend_variant < blend_variant_count()) return ctx->cfg.blend_variant;
+  auto it = ctx->tuned.find(tune_key(n, pixels, views));
+  if (it != ctx->tuned.end()) return it->second;
+  return 1;  // two pixels per thread unless tuned otherwise
+}
+
+// Forward pipeline: project -> depth sort -> emit -> tile sort -> ranges -> blend.
+int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* cams, int n_views, float* rgb_out,
+                float* T_out, int32_t* nc_out, float* imp_w, uint32_t* imp_cnt, airgs_state** saved,
+                int forced_variant) {
+  if (saved) *saved = nullptr;
+  int rc = check_gaussians(ctx, g);
+  if (rc) return rc;
+  if (!rgb_out) return fail(ctx, AIRGS_E_ARG, "rgb_out is required");
+  if ((imp_w == nullptr) != (imp_cnt == nullptr))
+    return fail(ctx, AIRGS_E_ARG, "importance_w and importance_cnt go together");
+  airgs_state* s = new (std::nothrow) airgs_state();
+  if (!s) return fail(ctx, AIRGS_E_OOM, "host allocation failed");
+  struct Guard {
+    airgs_ctx* c;
+    airgs_state* s;
+    bool keep = false;
+    ~Guard() {
+      if (!keep) release_state(c, s);
+    }
+  } guard{ctx, s};
+
+  rc = build_cams(ctx, cams, n_views, s->h_cams, s->n_tiles, s->n_pixels);
+  if (rc) return rc;
+  const int64_t N = g->n, V = n_views;
+  s->n_views = n_views;
+  s->n = N;
+  s->sh_degree = g->sh_degree;
+  s->means = g->means;
+  s->log_scales = g->log_scales;
+  s->quats = g->quats;
+  s->opacity = g->opacity_logit;
+  s->sh = g->sh;
+  s->rgb = rgb_out;
+  s->variant = forced_variant >= 0 ? forced_variant : choose_variant(ctx, N, s->n_pixels, n_views);
+  cudaStream_t st = ctx->stream;
+
+#define ALLOC(ptr, count)                      \
+  do {                                         \
+    int r_ = dalloc(ctx, &(ptr), (count));     \
+    if (r_) return r_;                         \
+    s->owned.push_back((void*)(ptr));          \
+  } while (0)
+  ALLOC(s->d_cams, V);
+  ALLOC(s->proj, V * N);
+  ALLOC(s->ranges, s->n_tiles);
+  ALLOC(s->ncontrib, s->n_pixels);
+  ALLOC(s->work, 2);
+  ALLOC(s->pairs, 2);
+  CK(cudaMemcpyAsync(s->d_cams, s->h_cams.data(), V * sizeof(CamDev), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(s->work, 0, 2 * sizeof(int), st));
+  CK(cudaMemsetAsync(s->pairs, 0, 2 * sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(s->ranges, 0, s->n_tiles * sizeof(uint2), st));
+  RasterParams rp = raster_params(ctx->cfg);
+
+  // temporaries of the ordering stage
+  std::vector<void*> tmp;
+  struct TmpGuard {
+    airgs_ctx* c;
+    std::vector<void*>& t;
+    ~TmpGuard() {
+      for (void* p : t) dfree(c, p);
+    }
+  } tguard{ctx, tmp};
+#define TALLOC(ptr, count)                     \
+  do {                                         \
+    int r_ = dalloc(ctx, &(ptr), (count));     \
+    if (r_) return r_;                         \
+    tmp.push_back((void*)(ptr));               \
+  } while (0)
+
+  int64_t n_inst = 0;
+  if (N > 0) {
+    uint32_t *dkeys, *tiles, *keys_b, *vals_a, *vals_b, *counts_sorted, *rs_scratch;
+    uint64_t* chunk;
+    TALLOC(dkeys, V * N);
+    TALLOC(tiles, V * N);
+    TALLOC(keys_b, V * N);
+    TALLOC(vals_a, V * N);
+    TALLOC(vals_b, V * N);
+    TALLOC(counts_sorted, V * N);
+    TALLOC(rs_scratch, radix_scratch_bytes(N, n_views, ctx->num_sms) / sizeof(uint32_t) + 1);
+    int64_t n_chunks = (V * N + 1023) / 1024;
+    TALLOC(chunk, n_chunks + 1);
+    CK(launch_project(st, N, g->sh_degree, g->means, g->log_scales, g->quats, g->opacity_logit, g->sh, s->d_cams,
+                      n_views, rp, s->proj, dkeys, tiles));
+    bool in_b = false;
+    CK(radix_sort_pairs(st, ctx->num_sms, dkeys, vals_a, keys_b, vals_b, N, n_views, 32, true, rs_scratch, &in_b));
+    const uint32_t* order = in_b ? vals_b : vals_a;
+    int64_t nc2 = 0;
+    CK(launch_count_gather(st, V * N, N, order, tiles, counts_sorted, chunk, &nc2));
+    CK(launch_scan_spans(st, chunk, nc2, chunk + n_chunks));
+    CK(cudaMemcpyAsync(ctx->h_pinned, chunk + n_chunks, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    n_inst = (int64_t)ctx->h_pinned[0];
+    if (n_inst >= (int64_t)0xFFFFFFFFll)
+      return fail(ctx, AIRGS_E_CAPACITY, "%lld tile instances exceed the 32-bit list limit", (long long)n_inst);
+    s->n_inst = n_inst;
+    if (n_inst > 0) {
+      uint32_t *ikeys_a, *ikeys_b, *ivals_b, *ivals_a, *rs2;
+      TALLOC(ikeys_a, n_inst);
+      TALLOC(ikeys_b, n_inst);
+      TALLOC(ivals_b, n_inst);
+      ALLOC(ivals_a, n_inst);  // may end up holding the sorted values
+      TALLOC(rs2, radix_scratch_bytes(n_inst, 1, ctx->num_sms) / sizeof(uint32_t) + 1);
+      CK(launch_emit(st, V * N, N, order, counts_sorted, chunk, s->proj, s->d_cams, ikeys_a, ivals_a));
+      bool in_b2 = false;
+      CK(radix_sort_pairs(st, ctx->num_sms, ikeys_a, ivals_a, ikeys_b, ivals_b, n_inst, 1, bits_for(s->n_tiles),
+                          false, rs2, &in_b2));
+      const uint32_t* skeys = in_b2 ? ikeys_b : ikeys_a;
+      if (in_b2) {
+        // keep the sorted values: move ivals_b into the state, ivals_a to the temporaries
+        s->owned.back() = ivals_b;
+        tmp.erase(std::find(tmp.begin(), tmp.end(), (void*)ivals_b));
+        tmp.push_back(ivals_a);
+        s->ids = ivals_b;
+      } else {
+        s->ids = ivals_a;
+      }
+      CK(launch_tile_ranges(st, n_inst, skeys, s->ranges));
+    }
+  }
+
+  BlendArgs a;
+  a.proj = s->proj;
+  a.n = N;
+  a.ids = s->ids;
+  a.ranges = s->ranges;
+  a.cams = s->d_cams;
+  a.n_views = n_views;
+  a.n_tiles = s->n_tiles;
+  a.rp = rp;
+  a.work_counter = s->work;
+  a.pair_counter = s->pairs;
+  FwdOut o;
+  o.rgb = rgb_out;
+  o.T = T_out;
+  o.ncontrib = s->ncontrib;
+  o.ncontrib_user = nc_out;
+  o.imp_w = imp_w;
+  o.imp_cnt = imp_cnt;
+  CK(launch_blend_fwd(st, s->variant, ctx->num_sms, a, o));
+#undef ALLOC
+#undef TALLOC
+  if (saved) {
+    guard.keep = true;
+    *saved = s;
+  }
+  return AIRGS_OK;
+}
+
+int backward_impl(airgs_ctx* ctx, airgs_state* s, const float* dL, const float* target, float* loss_out,
+                  float* g_means, float* g_log_scales, float* g_quats, float* g_opacity, float* g_sh, float* imp_w,
+                  uint32_t* imp_cnt) {
+  if (!s) return fail(ctx, AIRGS_E_STATE, "null state");
+  if (!dL && !target) return fail(ctx, AIRGS_E_ARG, "dL_drgb or target required");
+  if (s->n > 0 && (!g_means || !g_log_scales || !g_quats || !g_opacity || !g_sh))
+    return fail(ctx, AIRGS_E_ARG, "null gradient pointer");
+  if (s->n > 0 && !aligned16(g_quats)) return fail(ctx, AIRGS_E_ARG, "g_quats must be 16-byte aligned");
+  if ((imp_w == nullptr) != (imp_cnt == nullptr))
+    return fail(ctx, AIRGS_E_ARG, "importance_w and importance_cnt go together");
+  cudaStream_t st = ctx->stream;
+  if (loss_out) CK(cudaMemsetAsync(loss_out, 0, sizeof(float), st));
+  if (s->n == 0) return AIRGS_OK;
+  GradRec* grad = nullptr;
+  int rc = dalloc(ctx, &grad, (size_t)s->n_views * s->n);
+  if (rc) return rc;
+  struct G {
+    airgs_ctx* c;
+    void* p;
+    ~G() { dfree(c, p); }
+  } gguard{ctx, grad};
+  CK(cudaMemsetAsync(grad, 0, (size_t)s->n_views * s->n * sizeof(GradRec), st));
+  CK(cudaMemsetAsync(s->work + 1, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(s->pairs + 1, 0, sizeof(unsigned long long), st));
+  BlendArgs a;
+  a.proj = s->proj;
+  a.n = s->n;
+  a.ids = s->ids;
+  a.ranges = s->ranges;
+  a.cams = s->d_cams;
+  a.n_views = s->n_views;
+  a.n_tiles = s->n_tiles;
+  a.rp = raster_params(ctx->cfg);
+  a.work_counter = s->work + 1;
+  a.pair_counter = s->pairs + 1;
+  BwdIn in;
+  in.rgb = s->rgb;
+  in.dL = dL;
+  in.target = target;
+  in.inv_norm = (float)(1.0 / (3.0 * (double)s->n_pixels));
+  in.loss = loss_out;
+  in.ncontrib = s->ncontrib;
+  in.grad = grad;
+  in.imp_w = imp_w;
+  in.imp_cnt = imp_cnt;
+  if (s->n_inst > 0) CK(launch_blend_bwd(st, s->variant, ctx->num_sms, a, in));
+  CK(launch_project_bwd(st, s->n, s->sh_degree, s->means, s->log_scales, s->quats, s->opacity, s->sh, s->d_cams,
+                        s->n_views, s->proj, grad, g_means, g_log_scales, g_quats, g_opacity, g_sh));
+  return AIRGS_OK;
+}
+
+airgs_gaussians frame_gaussians(const airgs_ctx* ctx) {
+  airgs_gaussians g;
+  g.n = ctx->n;
+  g.sh_degree = ctx->sh_degree;
+  g.means = ctx->c_means;
+  g.log_scales = ctx->a_log_scales;
+  g.quats = ctx->c_quats;
+  g.opacity_logit = ctx->a_opacity;
+  g.sh = ctx->a_sh;
+  return g;
+}
+
+__global__ void k_extract_projection(const ProjRec* proj, int64_t n, float* mean2d, float* depth, int32_t* radius) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  ProjRec r = proj[i];
+  if (mean2d) {
+    mean2d[2 * i] = r.a.x;
+    mean2d[2 * i + 1] = r.a.y;
+  }
+  if (depth) depth[i] = r.c.y;
+  if (radius) radius[i] = __float_as_int(r.c.z);
+}
+
+void load_tune_cache(airgs_ctx* ctx) {
+  if (ctx->autotune_path.empty()) return;
+  std::ifstream f(ctx->autotune_path);
+  std::string key;
+  int v;
+  while (f >> key >> v)
+    if (v >= 0 && v < blend_variant_count()) ctx->tuned[key] = v;
+}
+
+void save_tune_cache(airgs_ctx* ctx) {
+  if (ctx->autotune_path.empty()) return;
+  std::ofstream f(ctx->autotune_path, std::ios::trunc);
+  for (auto& kv : ctx->tuned) f << kv.first << " " << kv.second << "\n";
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ ABI
+extern "C" {
+
+void airgs_default_config(airgs_config* c) {
+  if (!c) return;
+  c->dilation = 0.3f;
+  c->alpha_max = 0.99f;
+  c->alpha_min = 1.0f / 255.0f;
+  c->T_min = 1e-4f;
+  c->bg[0] = c->bg[1] = c->bg[2] = 0.f;
+  c->blend_variant = -1;
+  c->autotune_cache = nullptr;
+}
+
+int airgs_create(airgs_ctx** out, const airgs_config* cfg, void* stream) {
+  if (!out) return AIRGS_E_ARG;
+  *out = nullptr;
+  airgs_ctx* ctx = new (std::nothrow) airgs_ctx();
+  if (!ctx) return AIRGS_E_OOM;
+  airgs_default_config(&ctx->cfg);
+  if (cfg) {
+    ctx->cfg = *cfg;
+    if (cfg->autotune_cache) ctx->autotune_path = cfg->autotune_cache;
+    ctx->cfg.autotune_cache = nullptr;
+  }
+  if (!(ctx->cfg.alpha_max > 0 && ctx->cfg.alpha_max < 1) || !(ctx->cfg.alpha_min >= 0) || !(ctx->cfg.T_min >= 0) ||
+      !(ctx->cfg.dilation >= 0)) {
+    delete ctx;
+    return AIRGS_E_ARG;
+  }
+  ctx->stream = (cudaStream_t)stream;
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (e == cudaSuccess) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = ctx->device;
+    e = cudaMemPoolCreate(&ctx->pool, &props);
+  }
+  if (e == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    e = cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_pinned, 64);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+    delete ctx;
+    return AIRGS_E_CUDA;
+  }
+  load_tune_cache(ctx);
+  *out = ctx;
+  return AIRGS_OK;
+}
+
+int airgs_destroy(airgs_ctx* ctx) {
+  if (!ctx) return AIRGS_E_ARG;
+  free_anchor(ctx);
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+  if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+  delete ctx;
+  return AIRGS_OK;
+}
+
+int airgs_set_stream(airgs_ctx* ctx, void* stream) {
+  if (!ctx) return AIRGS_E_ARG;
+  ctx->stream = (cudaStream_t)stream;
+  return AIRGS_OK;
+}
+
+int airgs_sync(airgs_ctx* ctx) {
+  if (!ctx) return AIRGS_E_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  return AIRGS_OK;
+}
+
+const char* airgs_last_error(const airgs_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+int airgs_set_anchor(airgs_ctx* ctx, int64_t n, int sh_degree, const float* means, const float* log_scales,
+                     const float* quats, const float* opacity_logit, const float* sh) {
+  if (!ctx) return AIRGS_E_ARG;
+  airgs_gaussians g{n, sh_degree, means, log_scales, quats, opacity_logit, sh};
+  int rc = check_gaussians(ctx, &g);
+  if (rc) return rc;
+  free_anchor(ctx);
+  int K = (sh_degree + 1) * (sh_degree + 1);
+  if ((rc = dalloc(ctx, &ctx->a_means, 3 * n)) || (rc = dalloc(ctx, &ctx->a_log_scales, 3 * n)) ||
+      (rc = dalloc(ctx, &ctx->a_quats, 4 * n)) || (rc = dalloc(ctx, &ctx->a_opacity, n)) ||
+      (rc = dalloc(ctx, &ctx->a_sh, (size_t)K * 3 * n)) || (rc = dalloc(ctx, &ctx->c_means, 3 * n)) ||
+      (rc = dalloc(ctx, &ctx->c_quats, 4 * n))) {
+    free_anchor(ctx);
+    return rc;
+  }
+  cudaStream_t st = ctx->stream;
+  if (n > 0) {
+    CK(cudaMemcpyAsync(ctx->a_means, means, 12 * n, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ctx->a_log_scales, log_scales, 12 * n, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ctx->a_quats, quats, 16 * n, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ctx->a_opacity, opacity_logit, 4 * n, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ctx->a_sh, sh, (size_t)K * 12 * n, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ctx->c_means, means, 12 * n, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ctx->c_quats, quats, 16 * n, cudaMemcpyDeviceToDevice, st));
+  }
+  ctx->n = n;
+  ctx->sh_degree = sh_degree;
+  ctx->frame_id = -1;
+  return AIRGS_OK;
+}
+
+int airgs_apply_frame_update(airgs_ctx* ctx, const uint16_t* map, int map_w, int map_h, const float* lo,
+                             const float* hi, int mode, int64_t frame_id) {
+  if (!ctx) return AIRGS_E_ARG;
+  if (ctx->sh_degree < 0) return fail(ctx, AIRGS_E_STATE, "set_anchor first");
+  if (!map || !lo || !hi || map_w <= 0 || map_h <= 0) return fail(ctx, AIRGS_E_ARG, "bad update map arguments");
+  if ((int64_t)map_w * map_h < ctx->n)
+    return fail(ctx, AIRGS_E_ARG, "map has %lld pixels for %lld Gaussians", (long long)map_w * map_h,
+                (long long)ctx->n);
+  int base = mode & 1, quat_add = (mode & AIRGS_QUAT_ADD) ? 1 : 0;
+  if (mode & ~3) return fail(ctx, AIRGS_E_ARG, "unknown mode bits");
+  const float* bm = base == AIRGS_DELTA_ANCHOR ? ctx->a_means : ctx->c_means;
+  const float* bq = base == AIRGS_DELTA_ANCHOR ? ctx->a_quats : ctx->c_quats;
+  CK(launch_decode_apply(ctx->stream, ctx->n, map, (int64_t)map_w * map_h, lo, hi, quat_add, bm, bq, ctx->c_means,
+                         ctx->c_quats));
+  ctx->frame_id = frame_id;
+  return AIRGS_OK;
+}
+
+int airgs_get_frame_state(airgs_ctx* ctx, float* means_out, float* quats_out) {
+  if (!ctx) return AIRGS_E_ARG;
+  if (ctx->sh_degree < 0) return fail(ctx, AIRGS_E_STATE, "set_anchor first");
+  if (ctx->n == 0) return AIRGS_OK;
+  if (means_out) CK(cudaMemcpyAsync(means_out, ctx->c_means, 12 * ctx->n, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (quats_out) CK(cudaMemcpyAsync(quats_out, ctx->c_quats, 16 * ctx->n, cudaMemcpyDeviceToDevice, ctx->stream));
+  return AIRGS_OK;
+}
+
+int airgs_render(airgs_ctx* ctx, const airgs_camera* cams, int n_views, float* rgb_out, float* T_out,
+                 int32_t* n_contrib_out, float* importance_w, uint32_t* importance_cnt, airgs_state** saved) {
+  if (!ctx) return AIRGS_E_ARG;
+  if (ctx->sh_degree < 0) return fail(ctx, AIRGS_E_STATE, "set_anchor first");
+  airgs_gaussians g = frame_gaussians(ctx);
+  return render_impl(ctx, &g, cams, n_views, rgb_out, T_out, n_contrib_out, importance_w, importance_cnt, saved, -1);
+}
+
+int airgs_render_gaussians(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* cams, int n_views,
+                           float* rgb_out, float* T_out, int32_t* n_contrib_out, float* importance_w,
+                           uint32_t* importance_cnt, airgs_state** saved) {
+  if (!ctx) return AIRGS_E_ARG;
+  return render_impl(ctx, g, cams, n_views, rgb_out, T_out, n_contrib_out, importance_w, importance_cnt, saved, -1);
+}
+
+int airgs_render_backward(airgs_ctx* ctx, airgs_state* saved, const float* dL_drgb, float* g_means,
+                          float* g_log_scales, float* g_quats, float* g_opacity_logit, float* g_sh,
+                          float* importance_w, uint32_t* importance_cnt) {
+  if (!ctx) return AIRGS_E_ARG;
+  if (!dL_drgb) return fail(ctx, AIRGS_E_ARG, "dL_drgb is required");
+  return backward_impl(ctx, saved, dL_drgb, nullptr, nullptr, g_means, g_log_scales, g_quats, g_opacity_logit, g_sh,
+                       importance_w, importance_cnt);
+}
+
+int airgs_render_backward_l1(airgs_ctx* ctx, airgs_state* saved, const float* target, float* loss_out,
+                             float* g_means, float* g_log_scales, float* g_quats, float* g_opacity_logit,
+                             float* g_sh, float* importance_w, uint32_t* importance_cnt) {
+  if (!ctx) return AIRGS_E_ARG;
+  if (!target) return fail(ctx, AIRGS_E_ARG, "target is required");
+  return backward_impl(ctx, saved, nullptr, target, loss_out, g_means, g_log_scales, g_quats, g_opacity_logit, g_sh,
+                       importance_w, importance_cnt);
+}
+
+int airgs_gaussian_importance(airgs_ctx* ctx, const airgs_camera* cams, int n_views, float* w_out,
+                              uint32_t* cnt_out) {
+  if (!ctx) return AIRGS_E_ARG;
+  if (ctx->sh_degree < 0) return fail(ctx, AIRGS_E_STATE, "set_anchor first");
+  if (!w_out || !cnt_out) return fail(ctx, AIRGS_E_ARG, "w_out and cnt_out are required");
+  std::vector<CamDev> tmp;
+  int64_t nt = 0, np = 0;
+  int rc = build_cams(ctx, cams, n_views, tmp, nt, np);
+  if (rc) return rc;
+  if (ctx->n > 0) {
+    CK(cudaMemsetAsync(w_out, 0, 4 * ctx->n, ctx->stream));
+    CK(cudaMemsetAsync(cnt_out, 0, 4 * ctx->n, ctx->stream));
+  }
+  float* rgb = nullptr;
+  rc = dalloc(ctx, &rgb, 3 * np);
+  if (rc) return rc;
+  airgs_gaussians g = frame_gaussians(ctx);
+  rc = render_impl(ctx, &g, cams, n_views, rgb, nullptr, nullptr, w_out, cnt_out, nullptr, -1);
+  dfree(ctx, rgb);
+  return rc;
+}
+
+int airgs_release_state(airgs_ctx* ctx, airgs_state* state) {
+  if (!ctx) return AIRGS_E_ARG;
+  release_state(ctx, state);
+  return AIRGS_OK;
+}
+
+int airgs_state_stats(airgs_ctx* ctx, const airgs_state* s, airgs_stats* out) {
+  if (!ctx || !s || !out) return AIRGS_E_ARG;
+  CK(cudaMemcpyAsync(ctx->h_pinned, s->pairs, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  out->n_instances = s->n_inst;
+  out->n_tiles = s->n_tiles;
+  out->n_pixels = s->n_pixels;
+  out->pairs_forward = (int64_t)ctx->h_pinned[0];
+  out->pairs_backward = (int64_t)ctx->h_pinned[1];
+  out->blend_variant = s->variant;
+  return AIRGS_OK;
+}
+
+int airgs_state_view_info(airgs_ctx* ctx, const airgs_state* s, int view, int64_t* n_tiles, int64_t* n_entries) {
+  if (!ctx || !s || view < 0 || view >= s->n_views) return AIRGS_E_ARG;
+  const CamDev& c = s->h_cams[view];
+  int64_t nt = (int64_t)c.TW * c.TH;
+  if (n_tiles) *n_tiles = nt;
+  if (n_entries) {
+    std::vector<uint2> r(nt);
+    CK(cudaMemcpyAsync(r.data(), s->ranges + c.tile_base, nt * sizeof(uint2), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    int64_t cnt = 0;
+    for (auto& x : r) cnt += (int64_t)x.y - x.x;
+    *n_entries = cnt;
+  }
+  return AIRGS_OK;
+}
+
+int airgs_state_projection(airgs_ctx* ctx, const airgs_state* s, int view, float* mean2d, float* depth,
+                           int32_t* radius) {
+  if (!ctx || !s || view < 0 || view >= s->n_views) return AIRGS_E_ARG;
+  if (s->n == 0) return AIRGS_OK;
+  k_extract_projection<<<(unsigned)((s->n + 255) / 256), 256, 0, ctx->stream>>>(s->proj + (size_t)view * s->n, s->n,
+                                                                                  mean2d, depth, radius);
+  CK(cudaGetLastError());
+  return AIRGS_OK;
+}
+
+int airgs_state_tile_lists(airgs_ctx* ctx, const airgs_state* s, int view, int64_t* ranges, int32_t* ids) {
+  if (!ctx || !s || view < 0 || view >= s->n_views) return AIRGS_E_ARG;
+  const CamDev& c = s->h_cams[view];
+  int64_t nt = (int64_t)c.TW * c.TH;
+  std::vector<uint2> r(nt);
+  CK(cudaMemcpyAsync(r.data(), s->ranges + c.tile_base, nt * sizeof(uint2), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  // the view's entries are contiguous (tile ids are view-major)
+  int64_t first = -1;
+  for (auto& x : r)
+    if (x.y > x.x) {
+      first = x.x;
+      break;
+    }
+  std::vector<int64_t> rel(2 * nt, 0);
+  int64_t total = 0;
+  for (int64_t t = 0; t < nt; ++t) {
+    if (r[t].y > r[t].x) {
+      rel[2 * t] = (int64_t)r[t].x - first;
+      rel[2 * t + 1] = (int64_t)r[t].y - first;
+      total = std::max(total, rel[2 * t + 1]);
+    } else {
+      rel[2 * t] = rel[2 * t + 1] = total;  // empty tile: an empty range at the current end
+    }
+  }
+  if (ranges) {
+    CK(cudaMemcpyAsync(ranges, rel.data(), rel.size() * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
+  }
+  if (ids && total > 0)
+    CK(cudaMemcpyAsync(ids, s->ids + first, total * sizeof(uint32_t), cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return AIRGS_OK;
+}
+
+int airgs_sort_pairs(airgs_ctx* ctx, const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                     uint32_t* vals_out, int64_t n, int key_bits) {
+  if (!ctx) return AIRGS_E_ARG;
+  if (n < 0 || n >= (1ll << 32) || key_bits < 1 || key_bits > 32 || !keys_in || !vals_in || !keys_out || !vals_out)
+    return fail(ctx, AIRGS_E_ARG, "bad sort arguments");
+  if (n == 0) return AIRGS_OK;
+  cudaStream_t st = ctx->stream;
+  uint32_t *ka, *va, *kb, *vb, *scr;
+  int rc;
+  if ((rc = dalloc(ctx, &ka, n)) || (rc = dalloc(ctx, &va, n)) || (rc = dalloc(ctx, &kb, n)) ||
+      (rc = dalloc(ctx, &vb, n)) ||
+      (rc = dalloc(ctx, &scr, radix_scratch_bytes(n, 1, ctx->num_sms) / sizeof(uint32_t) + 1)))
+    return rc;
+  bool in_b = false;
+  cudaError_t e = cudaMemcpyAsync(ka, keys_in, 4 * n, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(va, vals_in, 4 * n, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = radix_sort_pairs(st, ctx->num_sms, ka, va, kb, vb, n, 1, key_bits, false, scr, &in_b);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(keys_out, in_b ? kb : ka, 4 * n, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(vals_out, in_b ? vb : va, 4 * n, cudaMemcpyDeviceToDevice, st);
+  for (void* p : {(void*)ka, (void*)va, (void*)kb, (void*)vb, (void*)scr}) dfree(ctx, p);
+  if (e != cudaSuccess) return fail(ctx, AIRGS_E_CUDA, "sort: %s", cudaGetErrorString(e));
+  return AIRGS_OK;
+}
+
+int airgs_autotune(airgs_ctx* ctx, const airgs_camera* cams, int n_views, int* variant) {
+  if (!ctx) return AIRGS_E_ARG;
+  if (ctx->sh_degree < 0) return fail(ctx, AIRGS_E_STATE, "set_anchor first");
+  std::vector<CamDev> tmp;
+  int64_t nt = 0, np = 0;
+  int rc = build_cams(ctx, cams, n_views, tmp, nt, np);
+  if (rc) return rc;
+  airgs_gaussians g = frame_gaussians(ctx);
+  float *rgb = nullptr, *dL = nullptr, *gm = nullptr, *gl = nullptr, *gq = nullptr, *go = nullptr, *gs = nullptr;
+  int K = (ctx->sh_degree + 1) * (ctx->sh_degree + 1);
+  int64_t n = std::max<int64_t>(ctx->n, 1);
+  if ((rc = dalloc(ctx, &rgb, 3 * np)) || (rc = dalloc(ctx, &dL, 3 * np)) || (rc = dalloc(ctx, &gm, 3 * n)) ||
+      (rc = dalloc(ctx, &gl, 3 * n)) || (rc = dalloc(ctx, &gq, 4 * n)) || (rc = dalloc(ctx, &go, n)) ||
+      (rc = dalloc(ctx, &gs, (size_t)K * 3 * n)))
+    return rc;
+  CK(cudaMemsetAsync(dL, 0, 12 * np, ctx->stream));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int best = 0;
+  float best_ms = 1e30f;
+  for (int v = 0; v < blend_variant_count() && rc == AIRGS_OK; ++v) {
+    float ms_sum = 0.f;
+    for (int rep = 0; rep < 3 && rc == AIRGS_OK; ++rep) {
+      // one forward + backward with this variant (the first repetition warms up)
+      airgs_state* s = nullptr;
+      cudaEventRecord(e0, ctx->stream);
+      rc = render_impl(ctx, &g, cams, n_views, rgb, nullptr, nullptr, nullptr, nullptr, &s, v);
+      if (rc == AIRGS_OK) rc = backward_impl(ctx, s, dL, nullptr, nullptr, gm, gl, gq, go, gs, nullptr, nullptr);
+      cudaEventRecord(e1, ctx->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) ms_sum += ms;
+      release_state(ctx, s);
+    }
+    if (rc == AIRGS_OK && ms_sum < best_ms) {
+      best_ms = ms_sum;
+      best = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (void* p : {(void*)rgb, (void*)dL, (void*)gm, (void*)gl, (void*)gq, (void*)go, (void*)gs}) dfree(ctx, p);
+  if (rc) return rc;
+  ctx->tuned[tune_key(ctx->n, np, n_views)] = best;
+  save_tune_cache(ctx);
+  if (variant) *variant = best;
+  return AIRGS_OK;
+}
+
+int airgs_blend_variant_count(void) { return blend_variant_count(); }
+const char* airgs_blend_variant_name(int variant) { return blend_variant_name(variant); }
+
+}  // extern "C"

@@ -1,0 +1,81 @@
+// Host-side launchers of the AirGS kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "airgs_internal.cuh"
+
+#define AIRGS_MAX_VIEWS_DEV 256
+
+namespace airgs {
+
+cudaError_t launch_decode_apply(cudaStream_t st, int64_t n, const uint16_t* map, int64_t plane, const float* lo,
+                                const float* hi, int quat_add, const float* base_means, const float* base_quats,
+                                float* out_means, float* out_quats);
+
+cudaError_t launch_project(cudaStream_t st, int64_t n, int sh_degree, const float* means, const float* log_scales,
+                           const float* quats, const float* opacity_logit, const float* sh, const CamDev* cams,
+                           int n_views, const RasterParams& rp, ProjRec* proj, uint32_t* depth_keys,
+                           uint32_t* tiles_touched);
+
+size_t radix_scratch_bytes(int64_t seg_len, int n_seg, int num_sms);
+cudaError_t radix_sort_pairs(cudaStream_t st, int num_sms, uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b,
+                             uint32_t* vals_b, int64_t seg_len, int n_seg, int key_bits, bool identity_vals,
+                             uint32_t* scratch, bool* result_in_b);
+
+cudaError_t launch_count_gather(cudaStream_t st, int64_t total, int64_t n, const uint32_t* order,
+                                const uint32_t* tiles_touched, uint32_t* counts_sorted, uint64_t* chunk_sums,
+                                int64_t* n_chunks);
+cudaError_t launch_scan_spans(cudaStream_t st, uint64_t* sums, int64_t n_chunks, uint64_t* total_out);
+cudaError_t launch_emit(cudaStream_t st, int64_t total, int64_t n, const uint32_t* order,
+                        const uint32_t* counts_sorted, const uint64_t* chunk_offsets, const ProjRec* proj,
+                        const CamDev* cams, uint32_t* keys, uint32_t* vals);
+cudaError_t launch_tile_ranges(cudaStream_t st, int64_t n_inst, const uint32_t* keys, uint2* ranges);
+
+struct BlendArgs {
+  const ProjRec* proj;  // [V][N]
+  int64_t n;
+  const uint32_t* ids;  // sorted instance values (Gaussian ids)
+  const uint2* ranges;  // [tiles] (start, end)
+  const CamDev* cams;
+  int n_views;
+  int64_t n_tiles;
+  RasterParams rp;
+  int* work_counter;
+  unsigned long long* pair_counter;
+};
+
+struct FwdOut {
+  float* rgb;        // planar per view
+  float* T;          // nullable
+  int32_t* ncontrib; // state copy (required)
+  int32_t* ncontrib_user;  // nullable
+  float* imp_w;      // nullable
+  uint32_t* imp_cnt; // nullable
+};
+
+struct BwdIn {
+  const float* rgb;     // final colour of the forward (C + T bg)
+  const float* dL;      // dL/drgb (nullable when l1)
+  const float* target;  // L1 target (nullable)
+  float inv_norm;       // 1 / (3 sum H W)
+  float* loss;          // L1 accumulator (nullable)
+  const int32_t* ncontrib;
+  GradRec* grad;        // [V][N]
+  float* imp_w;
+  uint32_t* imp_cnt;
+};
+
+int blend_variant_count();
+const char* blend_variant_name(int v);
+cudaError_t launch_blend_fwd(cudaStream_t st, int variant, int num_sms, const BlendArgs& a, const FwdOut& o);
+cudaError_t launch_blend_bwd(cudaStream_t st, int variant, int num_sms, const BlendArgs& a, const BwdIn& in);
+
+cudaError_t launch_project_bwd(cudaStream_t st, int64_t n, int sh_degree, const float* means,
+                               const float* log_scales, const float* quats, const float* opacity_logit,
+                               const float* sh, const CamDev* cams, int n_views, const ProjRec* proj,
+                               const GradRec* grad, float* g_means, float* g_log_scales, float* g_quats,
+                               float* g_opacity, float* g_sh);
+
+}  // namespace airgs

@@ -1,0 +1,55 @@
+"""The C-ABI library loads on a machine without a GPU and exports every
+function include/airgs.h declares; the Python binding declares the same set."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions(path):
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(airgs_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_2512_20943_b300 import build
+    return build.build()
+
+
+def test_library_exports_every_declared_function(lib_path):
+    names = header_functions(os.path.join(ROOT, "include", "airgs.h"))
+    assert len(names) >= 20
+    lib = ctypes.CDLL(lib_path)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_declares_the_header(lib_path):
+    from paper_2512_20943_b300 import _abi
+    names = header_functions(os.path.join(ROOT, "include", "airgs.h"))
+    assert sorted(_abi.SIGNATURES) == names
+    _abi.load_library()  # resolves every symbol with its signature
+
+
+def test_variant_table_without_gpu(lib_path):
+    from paper_2512_20943_b300 import _abi
+    lib = _abi.load_library()
+    n = lib.airgs_blend_variant_count()
+    assert n >= 3
+    assert all(lib.airgs_blend_variant_name(i) for i in range(n))
+
+
+def test_create_without_gpu_fails_cleanly(lib_path):
+    """Without a device airgs_create reports an error code instead of crashing."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2512_20943_b300 import _abi
+    lib = _abi.load_library()
+    ctx = ctypes.c_void_p()
+    assert lib.airgs_create(ctypes.byref(ctx), None, None) != 0

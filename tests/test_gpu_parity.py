@@ -1,0 +1,268 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bars: tile lists bit-exact (when the oracle bins the GPU's own single-precision
+centres, radii and depths), RGB within 1e-3 absolute, gradients within 1e-3
+relative (per tensor L2, plus 1e-3 of the largest magnitude elementwise),
+importance counts exact; pixels whose blend passes within the oracle's
+tolerance of a threshold (alpha_min, T_min, power = 0, near-equal depths) are
+excluded from exact comparisons and must be rare.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic
+from tests._helpers import (RGB_ATOL, assert_grad_close, params, small_sh3_scene, to_cuda, views_np)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rast():
+    from paper_2512_20943_b300 import Rasterizer
+    return Rasterizer()
+
+
+def render_gpu(rast, g, cams, **kw):
+    t = to_cuda(g)
+    res = rast.render_gaussians(*params(t), cams, **kw)
+    torch.cuda.synchronize()
+    return t, res
+
+
+def scenes():
+    g1, c1 = synthetic.plain_forward_scene()
+    g2, c2 = small_sh3_scene()
+    return {"plain_2k": (g1, c1), "sh3_ragged": (g2, c2)}
+
+
+@pytest.mark.parametrize("name", ["plain_2k", "sh3_ragged"])
+def test_projection_matches_oracle(rast, name):
+    g, cams = scenes()[name]
+    t, res = render_gpu(rast, g, cams, save=True)
+    for v, cam in enumerate(cams):
+        m2, d, r = (x.cpu().numpy() for x in rast.state_projection(res.state, v))
+        ref = oracle.project(synthetic.widen(g), cam)
+        ok = (ref["ambig"] == 0) & (ref["visible"] == 1)
+        assert ok.sum() > 0.5 * ref["visible"].sum()
+        assert np.array_equal(r[ok], ref["radius"][ok])
+        assert np.abs(m2[ok] - ref["mean2d"][ok]).max() < 1e-3
+        assert np.abs(d[ok] - ref["depth"][ok]).max() < 1e-5 * np.abs(ref["depth"]).max()
+        # culled exactly where the oracle culls
+        unamb = ref["ambig"] == 0
+        assert np.array_equal(r[unamb] > 0, ref["visible"][unamb] == 1)
+    res.state.release()
+
+
+@pytest.mark.parametrize("name", ["plain_2k", "sh3_ragged"])
+def test_tile_lists_bit_exact(rast, name):
+    """The GPU's binning and stable (tile, depth, index) ordering equal the
+    oracle's when the oracle is given the GPU's own centres, radii and depths."""
+    g, cams = scenes()[name]
+    t, res = render_gpu(rast, g, cams, save=True)
+    for v, cam in enumerate(cams):
+        m2, d, r = (x.cpu().numpy() for x in rast.state_projection(res.state, v))
+        ranges, ids = (x.cpu().numpy() for x in rast.state_tile_lists(res.state, v))
+        ref_ranges, ref_ids = oracle.bin_sort(m2.astype(np.float64), r, d.astype(np.float64), r > 0, cam["width"],
+                                              cam["height"])
+        assert np.array_equal(ranges, ref_ranges)
+        assert np.array_equal(ids, ref_ids)
+        assert len(ids) > 0
+    res.state.release()
+
+
+@pytest.mark.parametrize("name", ["plain_2k", "sh3_ragged"])
+def test_tile_lists_match_fp64_sets(rast, name):
+    g, cams = scenes()[name]
+    t, res = render_gpu(rast, g, cams, save=True)
+    for v, cam in enumerate(cams):
+        ranges, ids = (x.cpu().numpy() for x in rast.state_tile_lists(res.state, v))
+        ref = oracle.project(synthetic.widen(g), cam)
+        ref_ranges, ref_ids = oracle.bin_sort(ref["mean2d"], ref["radius"], ref["depth"], ref["visible"],
+                                              cam["width"], cam["height"])
+        amb = set(np.nonzero(ref["ambig"])[0].tolist())
+        for tile in range(len(ranges)):
+            a = [i for i in ids[ranges[tile, 0]:ranges[tile, 1]] if i not in amb]
+            b = [i for i in ref_ids[ref_ranges[tile, 0]:ref_ranges[tile, 1]] if i not in amb]
+            assert a == b, tile
+    res.state.release()
+
+
+@pytest.mark.parametrize("name", ["plain_2k", "sh3_ragged"])
+def test_forward_matches_oracle(rast, name):
+    g, cams = scenes()[name]
+    t, res = render_gpu(rast, g, cams, T=True, n_contrib=True)
+    ref = oracle.render(synthetic.widen(g), cams)
+    rgb, T, nc = views_np(res.rgb, cams), views_np(res.T, cams, 1), views_np(res.n_contrib, cams, 1)
+    for v in range(len(cams)):
+        ok = ~ref["ambig"][v]
+        assert ok.mean() > 0.97
+        assert np.abs(rgb[v] - ref["rgb"][v])[:, ok].max() < RGB_ATOL
+        assert np.abs(T[v] - ref["T"][v])[ok].max() < RGB_ATOL
+        assert np.array_equal(nc[v][ok], ref["n_contrib"][v][ok])
+        assert (rgb[v] >= 0).all() and ((T[v] >= 0) & (T[v] <= 1)).all()
+    assert max(r.max() for r in ref["rgb"]) > 0.2  # not an empty image
+
+
+def test_importance_matches_oracle(rast):
+    g, cams = small_sh3_scene()
+    t, res = render_gpu(rast, g, cams, importance=True, save=True)
+    ref = oracle.render(synthetic.widen(g), cams)
+    ok = ref["gauss_ambig"] == 0
+    w = res.importance_w.cpu().numpy()
+    c = res.importance_cnt.cpu().numpy()
+    assert ok.mean() > 0.8
+    assert np.array_equal(c[ok], ref["importance_cnt"][ok])
+    assert np.abs(w - ref["importance_w"])[ok].max() < 1e-3 * max(1.0, ref["importance_w"].max())
+    # the backward replay accumulates the same usage frequency
+    iw = torch.zeros_like(res.importance_w)
+    ic = torch.zeros_like(res.importance_cnt)
+    rast.render_backward(res.state, torch.zeros_like(res.rgb), importance=(iw, ic))
+    torch.cuda.synchronize()
+    assert np.array_equal(ic.cpu().numpy(), c)
+    assert np.abs(iw.cpu().numpy() - w).max() < 1e-4 * max(1.0, w.max())
+    # gaussian_importance over the context's frame state
+    rast.set_anchor(*params(t))
+    w2, c2 = rast.gaussian_importance(cams)
+    torch.cuda.synchronize()
+    assert np.array_equal(c2.cpu().numpy(), c)
+    res.state.release()
+
+
+def masked_dL(cams, ref, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for v, c in enumerate(cams):
+        d = rng.standard_normal((3, c["height"], c["width"]))
+        d[:, ref["ambig"][v]] = 0.0  # no loss on pixels with a near-threshold decision
+        out.append(d)
+    return out
+
+
+@pytest.mark.parametrize("name", ["plain_2k", "sh3_ragged"])
+def test_backward_matches_oracle(rast, name):
+    g, cams = scenes()[name]
+    ref = oracle.render(synthetic.widen(g), cams)
+    dL = masked_dL(cams, ref, 5)
+    t, res = render_gpu(rast, g, cams, save=True)
+    flat = torch.from_numpy(np.concatenate([d.reshape(-1) for d in dL]).astype(np.float32)).cuda()
+    gr = rast.render_backward(res.state, flat)
+    torch.cuda.synchronize()
+    ref_g = oracle.render_backward(synthetic.widen(g), cams, dL)
+    for k in ("means", "log_scales", "quats", "opacity_logit", "sh"):
+        assert_grad_close(gr[k].cpu().numpy(), ref_g[k], k)
+    res.state.release()
+
+
+def test_l1_fused_equals_explicit_gradient(rast):
+    g, cams = small_sh3_scene()
+    tgt = synthetic.target_images(cams, 1)
+    target = torch.from_numpy(np.concatenate([x.reshape(-1) for x in tgt])).cuda()
+    t, res = render_gpu(rast, g, cams, save=True)
+    loss, gr = rast.render_backward_l1(res.state, target)
+    n = res.rgb.numel()
+    dL = torch.sign(res.rgb - target) / n
+    gr2 = rast.render_backward(res.state, dL.contiguous())
+    torch.cuda.synchronize()
+    ref_loss = float(torch.abs(res.rgb.double() - target.double()).mean())
+    assert abs(float(loss) - ref_loss) < 1e-5 * ref_loss
+    for k in gr:
+        a, b = gr[k].cpu().numpy(), gr2[k].cpu().numpy()
+        assert np.abs(a - b).max() <= 1e-5 * max(np.abs(b).max(), 1e-30), k
+    # and against the oracle's L1 definition
+    ref = oracle.render(synthetic.widen(g), cams)
+    ref_loss2, _ = oracle.l1_loss_grad(ref["rgb"], [x.astype(np.float64) for x in tgt])
+    assert abs(float(loss) - ref_loss2) < 1e-4
+    res.state.release()
+
+
+def test_decode_apply_matches_oracle(rast):
+    N = 3000
+    g = synthetic.gaussians(N, 3, sh_degree=1)
+    t = to_cuda(g)
+    rast.set_anchor(*params(t))
+    m1, lo, hi = synthetic.update_map(N, 1001, size=64)
+    m2, _, _ = synthetic.update_map(N, 1002, size=64)
+    for mode_name in ("prev", "anchor", "add"):
+        rast.set_anchor(*params(t))
+        from paper_2512_20943_b300 import AIRGS_DELTA_ANCHOR, AIRGS_DELTA_PREV
+        mode = AIRGS_DELTA_ANCHOR if mode_name == "anchor" else AIRGS_DELTA_PREV
+        qa = mode_name == "add"
+        rast.apply_frame_update(torch.from_numpy(m1.view(np.int16)).cuda().view(torch.uint16), lo, hi, mode=mode,
+                                quat_add=qa)
+        rast.apply_frame_update(torch.from_numpy(m2.view(np.int16)).cuda().view(torch.uint16), lo, hi, mode=mode,
+                                quat_add=qa)
+        means, quats = (x.cpu().numpy() for x in rast.frame_state())
+        w = synthetic.widen(g)
+        qm = oracle.QUAT_ADD if qa else oracle.QUAT_COMPOSE
+        lo64, hi64 = lo.astype(np.float64), hi.astype(np.float64)
+        if mode_name == "anchor":
+            rm, rq = oracle.decode_apply(m2, lo64, hi64, w["means"], w["quats"], qm)
+        else:
+            am, aq = oracle.decode_apply(m1, lo64, hi64, w["means"], w["quats"], qm)
+            rm, rq = oracle.decode_apply(m2, lo64, hi64, am, aq, qm)
+        assert np.abs(means - rm).max() < 2e-6 * max(1, np.abs(rm).max())
+        assert np.abs(quats - rq).max() < 2e-6
+
+
+@pytest.mark.parametrize("n,bits", [(1, 8), (4095, 13), (4096, 32), (4097, 16), (1_000_003, 24), (3_000_000, 32)])
+def test_radix_sort_stable_bit_exact(rast, n, bits):
+    rng = np.random.default_rng(n)
+    keys = rng.integers(0, 1 << min(bits, 20), n, dtype=np.uint64).astype(np.uint32)  # many duplicates
+    if bits > 20:
+        keys = (keys.astype(np.uint64) << np.uint64(bits - 20)).astype(np.uint32)
+    vals = np.arange(n, dtype=np.uint32)
+    kt = torch.from_numpy(keys.view(np.int32)).cuda()
+    vt = torch.from_numpy(vals.view(np.int32)).cuda()
+    ko, vo = rast.sort_pairs(kt, vt, bits)
+    torch.cuda.synchronize()
+    order = np.argsort(keys, kind="stable")
+    assert np.array_equal(ko.cpu().numpy().view(np.uint32), keys[order])
+    assert np.array_equal(vo.cpu().numpy().view(np.uint32), vals[order])
+
+
+def test_permutation_invariance_gpu(rast):
+    g, cams = small_sh3_scene()
+    perm = np.random.default_rng(4).permutation(g["means"].shape[0])
+    gp = dict(g)
+    for k in ("means", "log_scales", "quats", "opacity_logit", "sh"):
+        gp[k] = np.ascontiguousarray(g[k][perm])
+    _, a = render_gpu(rast, g, cams)
+    _, b = render_gpu(rast, gp, cams)
+    # same lists up to relabelling, same arithmetic: identical images
+    assert torch.equal(a.rgb, b.rgb)
+
+
+def test_degenerate_inputs(rast):
+    from paper_2512_20943_b300 import AirGSError
+    # no Gaussians
+    g = synthetic.gaussians(0, 0, sh_degree=0)
+    cams = [synthetic.camera((0, 0, -4.0), 40, 30, fov_x_deg=60)]
+    _, res = render_gpu(rast, g, cams, T=True)
+    assert float(res.rgb.abs().max()) == 0.0 and float(res.T.min()) == 1.0
+    # everything behind the camera
+    g = synthetic.gaussians(50, 1, sh_degree=0)
+    g["means"][:, 2] = -10.0
+    _, res = render_gpu(rast, g, cams, T=True)
+    assert float(res.rgb.abs().max()) == 0.0
+    # a 1x1 image and a 17x1 strip
+    g = synthetic.gaussians(200, 2, mean_mode="uniform", mean_scale=(1, 1, 1), log_scale=(-2.5, 0.3), sh_degree=0)
+    cams = [synthetic.camera((0, 0, -4.0), 1, 1, fx=1.0), synthetic.camera((0, 0, -4.0), 17, 1, fx=17.0)]
+    _, res = render_gpu(rast, g, cams)
+    ref = oracle.render(synthetic.widen(g), cams)
+    rgb = views_np(res.rgb, cams)
+    for v in range(2):
+        ok = ~ref["ambig"][v]
+        assert np.abs(rgb[v] - ref["rgb"][v])[:, ok].max() < RGB_ATOL
+    # argument errors are reported, not crashed on
+    with pytest.raises(AirGSError):
+        rast.render_gaussians(*params(to_cuda(g)), [])
+
+
+def test_frame_update_map_too_small_is_an_error(rast):
+    from paper_2512_20943_b300 import AirGSError
+    g = synthetic.gaussians(100, 0, sh_degree=0)
+    rast.set_anchor(*params(to_cuda(g)))
+    with pytest.raises(AirGSError):
+        rast.apply_frame_update(torch.zeros((7, 5, 5), dtype=torch.uint16, device="cuda"), np.zeros(7), np.ones(7))
