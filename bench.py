@@ -1,0 +1,433 @@
+#!/usr/bin/env python
+"""Benchmark of the AirGS splatting path on B300.
+
+Workload (streaming training): a 300k-Gaussian SH-degree-3 anchor (means
+N(0,1)*(3,2,3), log-scales N(-4,0.7), SH N(0,0.2)); each step takes frame t's
+7-channel 16-bit 768x768 update map (position offset N(0,0.01), rotation
+delta near identity), decodes and applies it on the device (previous-frame
+mode), renders 8 views (views 8t mod 20 ... of a 20-camera 120-degree arc at
+1352x1014) in one batch, and back-propagates the L1 loss against random
+targets through the hand-written adjoint, accumulating the per-Gaussian blend
+weight (usage frequency).  Metric: fwd+bwd Mpix/s = 8 * 1352 * 1014 / step
+time.  Synthetic data (the paper's captures are not available).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs an independent
+replica of the workload (the path has no data-path exchange here); the time is
+the max over ranks and the value the pixels of all ranks over that time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic  # noqa: E402
+
+METRIC = "fwd+bwd Mpix/s @300k Gaussians SH3"
+UNIT = "Mpix/s"
+N_GAUSS = 300_000
+VIEWS_PER_STEP = 8
+WIDTH, HEIGHT = 1352, 1014
+MAP_SIZE = 768
+
+# Algorithmic work per unit (see the design notes): flops per evaluated
+# (pixel, Gaussian) pair of the blend forward and of the backward replay, and
+# bytes per Gaussian of the projection.
+FLOPS_PER_PAIR_FWD = 20
+FLOPS_PER_PAIR_BWD = 65
+FP32_LANES_PER_SM = 128
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        loaded = [s for s in sm if mx and s > 0.3 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- distributed
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier_max(world, value, device=None):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- workload
+class Workload:
+    def __init__(self, n_frames, device, seed=0):
+        import torch
+        self.g, arc = synthetic.streaming_scene(N_GAUSS, seed)
+        self.arc = arc
+        # the 20 arc cameras followed by the first 8 again, so that any 8
+        # consecutive views (mod 20) are one contiguous run of cameras/targets
+        self.cams28 = arc + arc[:VIEWS_PER_STEP]
+        tg = synthetic.target_images(arc, 1)
+        tg = tg + tg[:VIEWS_PER_STEP]
+        self.view_px = WIDTH * HEIGHT
+        self.targets_host = np.concatenate([t.reshape(-1) for t in tg])
+        self.targets = torch.from_numpy(self.targets_host).to(device)
+        self.maps_host = []
+        for t in range(n_frames):
+            m, lo, hi = synthetic.update_map(N_GAUSS, 1000 + t, size=MAP_SIZE)
+            self.maps_host.append(m)
+        self.lo, self.hi = lo, hi
+        self.maps = [torch.from_numpy(m.view(np.int16)).to(device).view(torch.uint16) for m in self.maps_host]
+        self.params = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in self.g.items()
+                       if k != "sh_degree"}
+
+    def views(self, frame):
+        s = (VIEWS_PER_STEP * frame) % len(self.arc)
+        return s, self.cams28[s:s + VIEWS_PER_STEP]
+
+    def target_slice(self, frame):
+        s, _ = self.views(frame)
+        n = 3 * self.view_px
+        return self.targets[s * n:(s + VIEWS_PER_STEP) * n]
+
+
+def train_step(rast, wl, frame, imp, map_tensor=None, target=None):
+    """One step of the path: decode/apply frame `frame`, batched render of its
+    8 views, fused L1 backward with importance accumulation."""
+    from paper_2512_20943_b300 import AIRGS_DELTA_PREV
+    m = wl.maps[frame] if map_tensor is None else map_tensor
+    rast.apply_frame_update(m, wl.lo, wl.hi, mode=AIRGS_DELTA_PREV, frame_id=frame)
+    _, cams = wl.views(frame)
+    res = rast.render(cams, save=True)
+    tgt = wl.target_slice(frame) if target is None else target
+    loss, grads = rast.render_backward_l1(res.state, tgt, importance=imp)
+    res.state.release()
+    return loss, grads
+
+
+# ---------------------------------------------------------------- CPU baseline (oracle)
+def oracle_sample(wl_g, arc, view, frame_map, lo, hi, crop):
+    """fwd+bwd of the oracle on a centred crop x crop window of one view,
+    after decoding/applying one frame; returns (seconds, pixels)."""
+    import oracle
+    g = synthetic.widen(wl_g)
+    t0 = time.perf_counter()
+    m, q = oracle.decode_apply(frame_map, lo.astype(np.float64), hi.astype(np.float64), g["means"], g["quats"])
+    g["means"], g["quats"] = m, q
+    cam = dict(arc[view])
+    cam["cx"] = cam["cx"] - (cam["width"] - crop) / 2.0
+    cam["cy"] = cam["cy"] - (cam["height"] - crop) / 2.0
+    cam["width"] = cam["height"] = crop
+    out = oracle.render(g, [cam])
+    tgt = np.random.default_rng(1).uniform(0, 1, (3, crop, crop))
+    _, dL = oracle.l1_loss_grad(out["rgb"], [tgt])
+    oracle.render_backward(g, [cam], dL)
+    return time.perf_counter() - t0, crop * crop
+
+
+def cpu_baseline_line(crop=512):
+    g, arc = synthetic.streaming_scene(N_GAUSS, 0)
+    m, lo, hi = synthetic.update_map(N_GAUSS, 1000, size=MAP_SIZE)
+    secs, px = oracle_sample(g, arc, 0, m, lo, hi, crop)
+    return {"value": px / secs / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"frame 0 decode/apply + fwd+bwd (L1) of view 0 cropped to the central {crop}x{crop} "
+                      f"window, 300k Gaussians SH3, FP64 single-threaded; {secs:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    crop = 256
+    g, arc = synthetic.streaming_scene(N_GAUSS, 0)
+    times, pix = [], 0
+    for step in range(args.warmup + args.steps):
+        m, lo, hi = synthetic.update_map(N_GAUSS, 1000 + step, size=MAP_SIZE)
+        view = (VIEWS_PER_STEP * step) % len(arc)
+        secs, px = oracle_sample(g, arc, view, m, lo, hi, crop)
+        if step >= args.warmup:
+            times.append(secs)
+            pix += px
+    total = sum(times)
+    value = pix / total / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "streaming training, 300k Gaussians SH3, 8 views 1352x1014 per step, "
+                               "768x768 uint16 update maps; each reference step is one view cropped to 256x256",
+                   "global_batch": 1, "seq_len": crop * crop, "parallelism": "none"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"per step: decode/apply one frame + fwd+bwd of one view cropped to {crop}x{crop}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- ours
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    device = torch.device("cuda", torch.cuda.current_device())
+    from paper_2512_20943_b300 import RasterConfig, Rasterizer
+
+    n_frames = args.warmup + args.steps
+    wl = Workload(n_frames, device)
+    stream = torch.cuda.Stream()
+    rast = Rasterizer(RasterConfig(), stream=stream)
+    p = wl.params
+    with torch.cuda.stream(stream):
+        rast.set_anchor(p["means"], p["log_scales"], p["quats"], p["opacity_logit"], p["sh"])
+        imp_w = torch.zeros(N_GAUSS, dtype=torch.float32, device=device)
+        imp_c = torch.zeros(N_GAUSS, dtype=torch.int32, device=device)
+    if args.autotune:
+        with torch.cuda.stream(stream):
+            rast.autotune(wl.views(0)[1])
+
+    # warm-up
+    with torch.cuda.stream(stream):
+        for t in range(args.warmup):
+            train_step(rast, wl, t, (imp_w, imp_c))
+    stream.synchronize()
+
+    # timed region: per-step CUDA events on the library's stream
+    rast.set_profiling(True)
+    rast.stage_times()  # clear
+    sampler = ClockSampler(device.index)
+    launches0 = Rasterizer.kernel_launch_count()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    wall0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            train_step(rast, wl, args.warmup + k, (imp_w, imp_c))
+            ev[k][1].record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    launches = Rasterizer.kernel_launch_count() - launches0
+    stages = rast.stage_times()
+    rast.set_profiling(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    total_ms = barrier_max(world, total_ms, device)
+    px_step = VIEWS_PER_STEP * WIDTH * HEIGHT
+    value = world * px_step * args.steps / (total_ms / 1e3) / 1e6
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(rast, wl, args, device, stream, (imp_w, imp_c), world)
+
+    # roofline of the dominant kernel
+    peaks, peak_kind = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    n_sms = torch.cuda.get_device_properties(device).multi_processor_count
+    fp32_peak = n_sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FMA = 2 flops
+    ms = stages["ms"]
+    nl = stages["launches"]
+    dom = max(ms, key=lambda k: ms[k])
+    stage_lines = {}
+    for name in ms:
+        if nl[name] == 0:
+            continue
+        stage_lines[name] = {"ms_per_launch": ms[name] / nl[name], "launches": nl[name],
+                             "share": ms[name] / max(1e-9, sum(ms.values()))}
+    fwd_tflops = stages["pairs_forward"] * FLOPS_PER_PAIR_FWD / (ms["blend_fwd"] / 1e3) / 1e12 if ms["blend_fwd"] else 0
+    bwd_tflops = stages["pairs_backward"] * FLOPS_PER_PAIR_BWD / (ms["blend_bwd"] / 1e3) / 1e12 if ms["blend_bwd"] else 0
+    stage_lines.get("blend_fwd", {})["tflops"] = fwd_tflops
+    stage_lines.get("blend_bwd", {})["tflops"] = bwd_tflops
+    stage_lines.get("blend_fwd", {})["pairs_per_launch"] = stages["pairs_forward"] / max(1, nl["blend_fwd"])
+    stage_lines.get("blend_bwd", {})["pairs_per_launch"] = stages["pairs_backward"] / max(1, nl["blend_bwd"])
+    proj_bytes = N_GAUSS * (236 + VIEWS_PER_STEP * 56)
+    if ms["project_sh"]:
+        stage_lines["project_sh"]["gbs"] = proj_bytes / (ms["project_sh"] / nl["project_sh"] / 1e3) / 1e9
+    if dom == "blend_bwd":
+        roof = {"bound": "alu", "achieved": bwd_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": bwd_tflops / fp32_peak, "traffic": None, "kernel": "k_blend_bwd",
+                "peak_source": f"derived: {n_sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz ({peak_kind} max clock)",
+                "work": f"{FLOPS_PER_PAIR_BWD} flops per replayed pair"}
+    elif dom == "blend_fwd":
+        roof = {"bound": "alu", "achieved": fwd_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": fwd_tflops / fp32_peak, "traffic": None, "kernel": "k_blend_fwd",
+                "peak_source": f"derived: {n_sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz ({peak_kind} max clock)",
+                "work": f"{FLOPS_PER_PAIR_FWD} flops per evaluated pair"}
+    else:
+        gbs = stage_lines.get(dom, {}).get("gbs")
+        roof = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": (gbs / peaks["hbm_gbs"]) if gbs else None, "traffic": None, "kernel": dom}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "streaming training: 300k-Gaussian SH3 anchor, per step one 7x768x768 uint16 "
+                               "update map decoded+applied, 8 views 1352x1014 rendered in one batch, fused L1 "
+                               "backward with importance accumulation",
+                   "global_batch": VIEWS_PER_STEP * world, "seq_len": WIDTH * HEIGHT,
+                   "parallelism": f"replicas x{world}" if world > 1 else "none",
+                   "l2": "inputs larger than L2 (per step: 8.3 MB map + 131 MB targets + 236 B x 300k params "
+                         "+ 115 MB projection records)"},
+        "wall_s_timed": wall,
+        "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "roofline": roof,
+        "stages": stage_lines,
+        "pairs_per_step": {"forward": stages["pairs_forward"] / args.steps,
+                           "backward": stages["pairs_backward"] / args.steps},
+    }
+    if e2e is not None:
+        line["e2e"] = e2e
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_line()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_e2e(rast, wl, args, device, stream, imp, world):
+    """Same step through the public API with host inputs: the frame's update
+    map and the 8 target images are copied from pinned host memory each step,
+    and the loss is read back."""
+    import torch
+    map_h = [torch.from_numpy(m.view(np.int16)).view(torch.uint16).pin_memory() for m in wl.maps_host]
+    n = 3 * wl.view_px * VIEWS_PER_STEP
+    tg_h = torch.from_numpy(wl.targets_host).pin_memory()
+    map_d = torch.empty(map_h[0].shape, dtype=torch.uint16, device=device)
+    tg_d = torch.empty(n, dtype=torch.float32, device=device)
+    loss_h = torch.empty(1, dtype=torch.float32).pin_memory()
+    h2d = map_h[0].numel() * 2 + n * 4
+
+    def step(k):
+        s, _ = wl.views(k)
+        map_d.copy_(map_h[k], non_blocking=True)
+        tg_d.copy_(tg_h[s * 3 * wl.view_px:s * 3 * wl.view_px + n], non_blocking=True)
+        loss, _ = train_step(rast, wl, k, imp, map_tensor=map_d, target=tg_d)
+        loss_h.copy_(loss, non_blocking=True)
+        stream.synchronize()
+        return float(loss_h[0])
+
+    with torch.cuda.stream(stream):
+        for k in range(min(args.warmup, len(map_h))):
+            step(k)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            step((args.warmup + k) % len(map_h))
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+    secs = barrier_max(world, secs, device)
+    value = world * VIEWS_PER_STEP * WIDTH * HEIGHT * args.steps / secs / 1e6
+    return {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4,
+            "ms_per_step": 1e3 * secs / args.steps}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--autotune", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

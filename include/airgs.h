@@ -221,6 +221,22 @@ int airgs_sort_pairs(airgs_ctx* ctx, const uint32_t* keys_in, const uint32_t* va
  * path if set.  Returns the chosen variant in *variant. */
 int airgs_autotune(airgs_ctx* ctx, const airgs_camera* cams, int n_views, int* variant);
 
+/* Per-stage device timing.  With profiling on, each pipeline stage (decode,
+ * projection, depth sort, scan+emit, tile sort, ranges, blend forward, blend
+ * backward, projection backward) is bracketed by CUDA events on the context's
+ * stream, and the blend kernels also add their evaluated pairs to a context
+ * counter.  airgs_stage_times synchronises, writes the summed milliseconds and
+ * the number of timed launches of each stage since the previous readout into
+ * ms[AIRGS_NUM_STAGES] / launches[AIRGS_NUM_STAGES], the forward and backward
+ * pair totals into pairs[2] (each nullable), and clears them. */
+#define AIRGS_NUM_STAGES 9
+int airgs_set_profiling(airgs_ctx* ctx, int enabled);
+int airgs_stage_times(airgs_ctx* ctx, double* ms, int64_t* launches, int64_t* pairs);
+const char* airgs_stage_name(int stage);
+
+/* Process-wide number of kernel launches the library has issued. */
+int64_t airgs_kernel_launch_count(void);
+
 /* Number of blend kernel variants and a short name of each. */
 int airgs_blend_variant_count(void);
 const char* airgs_blend_variant_name(int variant);

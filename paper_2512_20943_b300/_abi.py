@@ -27,6 +27,7 @@ AIRGS_DELTA_PREV = 0
 AIRGS_DELTA_ANCHOR = 1
 AIRGS_QUAT_ADD = 2
 AIRGS_MAX_VIEWS = 256
+AIRGS_NUM_STAGES = 9
 
 
 class airgs_config(ctypes.Structure):
@@ -108,6 +109,10 @@ SIGNATURES = {
     "airgs_state_tile_lists": (I, [CTX, STATE, I, P, P]),
     "airgs_sort_pairs": (I, [CTX, P, P, P, P, I64, I]),
     "airgs_autotune": (I, [CTX, ctypes.POINTER(airgs_camera), I, ctypes.POINTER(I)]),
+    "airgs_set_profiling": (I, [CTX, I]),
+    "airgs_stage_times": (I, [CTX, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64), ctypes.POINTER(I64)]),
+    "airgs_stage_name": (ctypes.c_char_p, [I]),
+    "airgs_kernel_launch_count": (I64, []),
     "airgs_blend_variant_count": (I, []),
     "airgs_blend_variant_name": (ctypes.c_char_p, [I]),
 }

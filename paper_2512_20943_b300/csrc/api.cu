@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -20,6 +21,25 @@
 
 using namespace airgs;
 
+static std::atomic<int64_t> g_launches{0};
+void airgs::count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// Stages timed with CUDA events on the context's stream when profiling is on.
+enum Stage {
+  ST_DECODE = 0,
+  ST_PROJECT,
+  ST_DEPTH_SORT,
+  ST_EMIT,
+  ST_TILE_SORT,
+  ST_RANGES,
+  ST_BLEND_FWD,
+  ST_BLEND_BWD,
+  ST_PROJECT_BWD,
+  ST_COUNT
+};
+static const char* kStageNames[ST_COUNT] = {"decode_apply", "project_sh",  "depth_sort",  "scan_emit",  "tile_sort",
+                                            "tile_ranges",  "blend_fwd",   "blend_bwd",   "project_bwd"};
+
 struct airgs_ctx {
   airgs_config cfg;
   std::string autotune_path;
@@ -36,6 +56,11 @@ struct airgs_ctx {
   uint64_t* h_pinned = nullptr;  // small pinned host buffer for counters
   std::string last_error;
   std::map<std::string, int> tuned;  // autotune choices
+  // profiling: (stage, start, end) event triples awaiting readout
+  bool profiling = false;
+  unsigned long long* d_pair_total = nullptr;  // [2] forward, backward pairs while profiling
+  std::vector<cudaEvent_t> event_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
 };
 
 struct airgs_state {
@@ -174,6 +199,37 @@ void release_state(airgs_ctx* ctx, airgs_state* s) {
   delete s;
 }
 
+cudaEvent_t take_event(airgs_ctx* ctx) {
+  if (!ctx->event_pool.empty()) {
+    cudaEvent_t e = ctx->event_pool.back();
+    ctx->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// RAII stage timer: records a start event now and an end event at scope exit.
+struct StageScope {
+  airgs_ctx* ctx;
+  int stage;
+  cudaEvent_t e0 = nullptr;
+  StageScope(airgs_ctx* c, int s) : ctx(c), stage(s) {
+    if (ctx->profiling) {
+      e0 = take_event(ctx);
+      cudaEventRecord(e0, ctx->stream);
+    }
+  }
+  ~StageScope() {
+    if (ctx->profiling && e0) {
+      cudaEvent_t e1 = take_event(ctx);
+      cudaEventRecord(e1, ctx->stream);
+      ctx->pending.push_back({stage, {e0, e1}});
+    }
+  }
+};
+
 std::string tune_key(int64_t n, int64_t pixels, int views) {
   std::ostringstream os;
   os << n << ":" << pixels << ":" << views;
@@ -270,14 +326,23 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
     TALLOC(rs_scratch, radix_scratch_bytes(N, n_views, ctx->num_sms) / sizeof(uint32_t) + 1);
     int64_t n_chunks = (V * N + 1023) / 1024;
     TALLOC(chunk, n_chunks + 1);
+    {
+    StageScope sc(ctx, ST_PROJECT);
     CK(launch_project(st, N, g->sh_degree, g->means, g->log_scales, g->quats, g->opacity_logit, g->sh, s->d_cams,
                       n_views, rp, s->proj, dkeys, tiles));
+    }
     bool in_b = false;
-    CK(radix_sort_pairs(st, ctx->num_sms, dkeys, vals_a, keys_b, vals_b, N, n_views, 32, true, rs_scratch, &in_b));
+    {
+      StageScope sc(ctx, ST_DEPTH_SORT);
+      CK(radix_sort_pairs(st, ctx->num_sms, dkeys, vals_a, keys_b, vals_b, N, n_views, 32, true, rs_scratch, &in_b));
+    }
     const uint32_t* order = in_b ? vals_b : vals_a;
     int64_t nc2 = 0;
-    CK(launch_count_gather(st, V * N, N, order, tiles, counts_sorted, chunk, &nc2));
-    CK(launch_scan_spans(st, chunk, nc2, chunk + n_chunks));
+    {
+      StageScope sc(ctx, ST_EMIT);
+      CK(launch_count_gather(st, V * N, N, order, tiles, counts_sorted, chunk, &nc2));
+      CK(launch_scan_spans(st, chunk, nc2, chunk + n_chunks));
+    }
     CK(cudaMemcpyAsync(ctx->h_pinned, chunk + n_chunks, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     n_inst = (int64_t)ctx->h_pinned[0];
@@ -291,10 +356,16 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
       TALLOC(ivals_b, n_inst);
       ALLOC(ivals_a, n_inst);  // may end up holding the sorted values
       TALLOC(rs2, radix_scratch_bytes(n_inst, 1, ctx->num_sms) / sizeof(uint32_t) + 1);
-      CK(launch_emit(st, V * N, N, order, counts_sorted, chunk, s->proj, s->d_cams, ikeys_a, ivals_a));
+      {
+        StageScope sc(ctx, ST_EMIT);
+        CK(launch_emit(st, V * N, N, order, counts_sorted, chunk, s->proj, s->d_cams, ikeys_a, ivals_a));
+      }
       bool in_b2 = false;
-      CK(radix_sort_pairs(st, ctx->num_sms, ikeys_a, ivals_a, ikeys_b, ivals_b, n_inst, 1, bits_for(s->n_tiles),
-                          false, rs2, &in_b2));
+      {
+        StageScope sc(ctx, ST_TILE_SORT);
+        CK(radix_sort_pairs(st, ctx->num_sms, ikeys_a, ivals_a, ikeys_b, ivals_b, n_inst, 1, bits_for(s->n_tiles),
+                            false, rs2, &in_b2));
+      }
       const uint32_t* skeys = in_b2 ? ikeys_b : ikeys_a;
       if (in_b2) {
         // keep the sorted values: move ivals_b into the state, ivals_a to the temporaries
@@ -305,6 +376,7 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
       } else {
         s->ids = ivals_a;
       }
+      StageScope sc(ctx, ST_RANGES);
       CK(launch_tile_ranges(st, n_inst, skeys, s->ranges));
     }
   }
@@ -320,6 +392,7 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
   a.rp = rp;
   a.work_counter = s->work;
   a.pair_counter = s->pairs;
+  a.pair_total = ctx->profiling ? ctx->d_pair_total : nullptr;
   FwdOut o;
   o.rgb = rgb_out;
   o.T = T_out;
@@ -327,7 +400,10 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
   o.ncontrib_user = nc_out;
   o.imp_w = imp_w;
   o.imp_cnt = imp_cnt;
-  CK(launch_blend_fwd(st, s->variant, ctx->num_sms, a, o));
+  {
+    StageScope sc(ctx, ST_BLEND_FWD);
+    CK(launch_blend_fwd(st, s->variant, ctx->num_sms, a, o));
+  }
 #undef ALLOC
 #undef TALLOC
   if (saved) {
@@ -372,6 +448,7 @@ int backward_impl(airgs_ctx* ctx, airgs_state* s, const float* dL, const float* 
   a.rp = raster_params(ctx->cfg);
   a.work_counter = s->work + 1;
   a.pair_counter = s->pairs + 1;
+  a.pair_total = ctx->profiling ? ctx->d_pair_total + 1 : nullptr;
   BwdIn in;
   in.rgb = s->rgb;
   in.dL = dL;
@@ -382,7 +459,11 @@ int backward_impl(airgs_ctx* ctx, airgs_state* s, const float* dL, const float* 
   in.grad = grad;
   in.imp_w = imp_w;
   in.imp_cnt = imp_cnt;
-  if (s->n_inst > 0) CK(launch_blend_bwd(st, s->variant, ctx->num_sms, a, in));
+  if (s->n_inst > 0) {
+    StageScope sc(ctx, ST_BLEND_BWD);
+    CK(launch_blend_bwd(st, s->variant, ctx->num_sms, a, in));
+  }
+  StageScope sc(ctx, ST_PROJECT_BWD);
   CK(launch_project_bwd(st, s->n, s->sh_degree, s->means, s->log_scales, s->quats, s->opacity, s->sh, s->d_cams,
                         s->n_views, s->proj, grad, g_means, g_log_scales, g_quats, g_opacity, g_sh));
   return AIRGS_OK;
@@ -489,8 +570,11 @@ int airgs_create(airgs_ctx** out, const airgs_config* cfg, void* stream) {
 int airgs_destroy(airgs_ctx* ctx) {
   if (!ctx) return AIRGS_E_ARG;
   free_anchor(ctx);
+  dfree(ctx, ctx->d_pair_total);
   cudaStreamSynchronize(ctx->stream);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+  for (auto& p : ctx->pending) ctx->event_pool.insert(ctx->event_pool.end(), {p.second.first, p.second.second});
+  for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   delete ctx;
   return AIRGS_OK;
@@ -553,6 +637,7 @@ int airgs_apply_frame_update(airgs_ctx* ctx, const uint16_t* map, int map_w, int
   if (mode & ~3) return fail(ctx, AIRGS_E_ARG, "unknown mode bits");
   const float* bm = base == AIRGS_DELTA_ANCHOR ? ctx->a_means : ctx->c_means;
   const float* bq = base == AIRGS_DELTA_ANCHOR ? ctx->a_quats : ctx->c_quats;
+  StageScope sc(ctx, ST_DECODE);
   CK(launch_decode_apply(ctx->stream, ctx->n, map, (int64_t)map_w * map_h, lo, hi, quat_add, bm, bq, ctx->c_means,
                          ctx->c_quats));
   ctx->frame_id = frame_id;
@@ -776,6 +861,52 @@ int airgs_autotune(airgs_ctx* ctx, const airgs_camera* cams, int n_views, int* v
   if (variant) *variant = best;
   return AIRGS_OK;
 }
+
+int airgs_set_profiling(airgs_ctx* ctx, int enabled) {
+  if (!ctx) return AIRGS_E_ARG;
+  if (enabled && !ctx->d_pair_total) {
+    int rc = dalloc(ctx, &ctx->d_pair_total, 2);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(ctx->d_pair_total, 0, 2 * sizeof(unsigned long long), ctx->stream));
+  }
+  ctx->profiling = enabled != 0;
+  return AIRGS_OK;
+}
+
+int airgs_stage_times(airgs_ctx* ctx, double* ms, int64_t* launches, int64_t* pairs) {
+  if (!ctx) return AIRGS_E_ARG;
+  if (pairs) {
+    pairs[0] = pairs[1] = 0;
+    if (ctx->d_pair_total) {
+      CK(cudaMemcpyAsync(ctx->h_pinned + 2, ctx->d_pair_total, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                         ctx->stream));
+      CK(cudaMemsetAsync(ctx->d_pair_total, 0, 2 * sizeof(unsigned long long), ctx->stream));
+    }
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (pairs && ctx->d_pair_total) {
+    pairs[0] = (int64_t)ctx->h_pinned[2];
+    pairs[1] = (int64_t)ctx->h_pinned[3];
+  }
+  for (int k = 0; k < ST_COUNT; ++k) {
+    if (ms) ms[k] = 0.0;
+    if (launches) launches[k] = 0;
+  }
+  for (auto& p : ctx->pending) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, p.second.first, p.second.second);
+    if (ms) ms[p.first] += t;
+    if (launches) launches[p.first] += 1;
+    ctx->event_pool.push_back(p.second.first);
+    ctx->event_pool.push_back(p.second.second);
+  }
+  ctx->pending.clear();
+  return AIRGS_OK;
+}
+
+const char* airgs_stage_name(int stage) { return (stage >= 0 && stage < ST_COUNT) ? kStageNames[stage] : ""; }
+
+int64_t airgs_kernel_launch_count(void) { return g_launches.load(); }
 
 int airgs_blend_variant_count(void) { return blend_variant_count(); }
 const char* airgs_blend_variant_name(int variant) { return blend_variant_name(variant); }

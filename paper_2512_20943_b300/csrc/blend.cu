@@ -170,7 +170,10 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_blend_fwd(BlendArgs a, Fwd
   }
   // evaluated-pair statistics
   for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
-  if ((tid & 31) == 0 && pairs) atomicAdd(a.pair_counter, pairs);
+  if ((tid & 31) == 0 && pairs) {
+    atomicAdd(a.pair_counter, pairs);
+    if (a.pair_total) atomicAdd(a.pair_total, pairs);
+  }
 }
 
 // ------------------------------------------------------------------ 16-slot warp transpose reduction
@@ -389,7 +392,10 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_blend_bwd(BlendArgs a, Bwd
     }
   }
   for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
-  if (lane == 0 && pairs) atomicAdd(a.pair_counter, pairs);
+  if (lane == 0 && pairs) {
+    atomicAdd(a.pair_counter, pairs);
+    if (a.pair_total) atomicAdd(a.pair_total, pairs);
+  }
   if (L1 && in.loss) {
     for (int o = 16; o > 0; o >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, o);
     if (lane == 0) s_loss[warp] = loss_acc;
@@ -420,6 +426,7 @@ static cudaError_t fwd_launch(cudaStream_t st, int grid_per_sm, int num_sms, con
   grid = (int)(a.n_tiles < (int64_t)grid ? a.n_tiles : (int64_t)grid);
   if (grid <= 0) return cudaSuccess;
   k_blend_fwd<PX, IMP><<<grid, kTilePixels / PX, 0, st>>>(a, o);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -444,6 +451,7 @@ static cudaError_t bwd_launch(cudaStream_t st, int num_sms, const BlendArgs& a, 
   int grid = (int)(a.n_tiles < g64 ? a.n_tiles : g64);
   if (grid <= 0) return cudaSuccess;
   k_blend_bwd<PX, L1, IMP><<<grid, kTilePixels / PX, 0, st>>>(a, in);
+  count_launches(1);
   return cudaGetLastError();
 }
 

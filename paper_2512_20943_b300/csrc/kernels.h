@@ -10,6 +10,9 @@
 
 namespace airgs {
 
+// Process-wide count of kernel launches issued by the library.
+void count_launches(int n);
+
 cudaError_t launch_decode_apply(cudaStream_t st, int64_t n, const uint16_t* map, int64_t plane, const float* lo,
                                 const float* hi, int quat_add, const float* base_means, const float* base_quats,
                                 float* out_means, float* out_quats);
@@ -44,6 +47,7 @@ struct BlendArgs {
   RasterParams rp;
   int* work_counter;
   unsigned long long* pair_counter;
+  unsigned long long* pair_total;  // nullable: cumulative counter of the context
 };
 
 struct FwdOut {

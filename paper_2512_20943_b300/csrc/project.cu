@@ -224,6 +224,7 @@ cudaError_t launch_decode_apply(cudaStream_t st, int64_t n, const uint16_t* map,
   }
   int blocks = (int)((n + 255) / 256);
   k_decode_apply<<<blocks, 256, 0, st>>>(n, map, plane, dp, quat_add, base_means, base_quats, out_means, out_quats);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -251,6 +252,7 @@ cudaError_t launch_project(cudaStream_t st, int64_t n, int sh_degree, const floa
                                            depth_keys, tiles_touched);
       break;
   }
+  count_launches(1);
   return cudaGetLastError();
 }
 

@@ -266,6 +266,7 @@ cudaError_t launch_project_bwd(cudaStream_t st, int64_t n, int sh_degree, const 
     default: AIRGS_PB(3); break;
   }
 #undef AIRGS_PB
+  count_launches(1);
   return cudaGetLastError();
 }
 

@@ -383,6 +383,7 @@ cudaError_t radix_sort_pairs(cudaStream_t st, int num_sms, uint32_t* keys_a, uin
     k_rs_spine<<<n_seg, 1024, 0, st>>>(scratch, g.ctas_seg);
     k_rs_downsweep<<<grid, RS_THREADS, 0, st>>>(ki, (pass == 0 && identity_vals) ? nullptr : vi, ko, vo, g, shift,
                                                  scratch);
+    count_launches(3);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     uint32_t* t = ki;
@@ -403,11 +404,13 @@ cudaError_t launch_count_gather(cudaStream_t st, int64_t total, int64_t n, const
   if (total == 0) return cudaSuccess;
   k_count_gather<<<(unsigned)*n_chunks, EM_THREADS, 0, st>>>(total, n, order, tiles_touched, counts_sorted,
                                                              chunk_sums);
+  count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_scan_spans(cudaStream_t st, uint64_t* sums, int64_t n_chunks, uint64_t* total_out) {
   k_scan_spans<<<1, 1024, 0, st>>>(sums, n_chunks, total_out);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -418,12 +421,14 @@ cudaError_t launch_emit(cudaStream_t st, int64_t total, int64_t n, const uint32_
   int64_t n_chunks = (total + EM_CHUNK - 1) / EM_CHUNK;
   k_emit<<<(unsigned)n_chunks, EM_THREADS, 0, st>>>(total, n, order, counts_sorted, chunk_offsets, proj, cams, keys,
                                                      vals);
+  count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tile_ranges(cudaStream_t st, int64_t n_inst, const uint32_t* keys, uint2* ranges) {
   if (n_inst == 0) return cudaSuccess;
   k_tile_ranges<<<(unsigned)((n_inst + 255) / 256), 256, 0, st>>>(n_inst, keys, ranges);
+  count_launches(1);
   return cudaGetLastError();
 }
 

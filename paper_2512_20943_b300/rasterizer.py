@@ -345,6 +345,26 @@ class Rasterizer:
         self._check(self.lib.airgs_autotune(self.ctx, camera_array(cams), len(cams), ctypes.byref(v)))
         return v.value
 
+    def set_profiling(self, enabled: bool = True):
+        """Time each pipeline stage with CUDA events on the context's stream."""
+        self._check(self.lib.airgs_set_profiling(self.ctx, 1 if enabled else 0))
+
+    def stage_times(self) -> dict:
+        """Per-stage device milliseconds and launch counts since the previous
+        readout, and the forward/backward evaluated-pair totals (synchronises)."""
+        n = _abi.AIRGS_NUM_STAGES
+        ms = (ctypes.c_double * n)()
+        launches = (ctypes.c_int64 * n)()
+        pairs = (ctypes.c_int64 * 2)()
+        self._check(self.lib.airgs_stage_times(self.ctx, ms, launches, pairs))
+        names = [self.lib.airgs_stage_name(i).decode() for i in range(n)]
+        return dict(ms={names[i]: ms[i] for i in range(n)}, launches={names[i]: launches[i] for i in range(n)},
+                    pairs_forward=pairs[0], pairs_backward=pairs[1])
+
+    @staticmethod
+    def kernel_launch_count() -> int:
+        return int(load_library().airgs_kernel_launch_count())
+
     @staticmethod
     def variant_names():
         lib = load_library()
