@@ -215,6 +215,28 @@ int airgs_state_tile_lists(airgs_ctx* ctx, const airgs_state* state, int view, i
 int airgs_sort_pairs(airgs_ctx* ctx, const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
                      uint32_t* vals_out, int64_t n, int key_bits);
 
+/* Allocation-free variant of airgs_sort_pairs, for callers that cannot
+ * allocate device memory while they run (cudaMalloc / cudaFree can
+ * synchronise the whole device and stall other streams; engine plug-ins and
+ * real-time loops often run under a memory budget owned by their host).  The
+ * paper has no counterpart: this is a service of the library, not a step of
+ * the method.
+ *   keys_in, vals_in    device uint32 [n], read only
+ *   keys_out, vals_out  device uint32 [n], the pairs stably sorted by key bits
+ *                       [0, key_bits); must not overlap the inputs
+ *   stream              cudaStream_t the work is enqueued on (NULL = legacy)
+ * Needs no context and calls no allocator: its scratch is a fixed device
+ * array of 2 * AIRGS_NOALLOC_SORT_MAX_PAIRS + 262144 uint32 words (about 9 MB)
+ * that every GPU loading the library holds until the process exits.  The
+ * first call on a device looks up that array's device address (make it before
+ * any stream capture).  All calls share the array: calls that overlap on the
+ * GPU (other streams, other threads) race and must be serialised by the
+ * caller.  Returns AIRGS_E_CAPACITY if n > AIRGS_NOALLOC_SORT_MAX_PAIRS,
+ * AIRGS_E_ARG for bad arguments, AIRGS_E_CUDA if a launch fails. */
+#define AIRGS_NOALLOC_SORT_MAX_PAIRS (1 << 20)
+int airgs_sort_pairs_noalloc(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                             uint32_t* vals_out, int64_t n, int key_bits, void* stream);
+
 /* Autotune the blend kernel variant for this workload shape (n Gaussians of
  * the current frame, the given cameras) by timing every variant; the choice
  * is cached per (n, total pixels, n_views) and written to the config's cache

@@ -28,6 +28,7 @@ AIRGS_DELTA_ANCHOR = 1
 AIRGS_QUAT_ADD = 2
 AIRGS_MAX_VIEWS = 256
 AIRGS_NUM_STAGES = 9
+AIRGS_NOALLOC_SORT_MAX_PAIRS = 1 << 20
 
 
 class airgs_config(ctypes.Structure):
@@ -108,6 +109,7 @@ SIGNATURES = {
     "airgs_state_projection": (I, [CTX, STATE, I, P, P, P]),
     "airgs_state_tile_lists": (I, [CTX, STATE, I, P, P]),
     "airgs_sort_pairs": (I, [CTX, P, P, P, P, I64, I]),
+    "airgs_sort_pairs_noalloc": (I, [P, P, P, P, I64, I, P]),
     "airgs_autotune": (I, [CTX, ctypes.POINTER(airgs_camera), I, ctypes.POINTER(I)]),
     "airgs_set_profiling": (I, [CTX, I]),
     "airgs_stage_times": (I, [CTX, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64), ctypes.POINTER(I64)]),

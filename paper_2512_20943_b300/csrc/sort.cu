@@ -397,6 +397,20 @@ cudaError_t radix_sort_pairs(cudaStream_t st, int num_sms, uint32_t* keys_a, uin
   return cudaSuccess;
 }
 
+// One 8-bit pass (bits [shift, shift + 8)) of the same radix sort over a single
+// segment, reading (keys_in, vals_in) and writing (keys_out, vals_out);
+// `counts` must hold radix_scratch_bytes(n, 1, num_sms) bytes.
+cudaError_t radix_sort_pass(cudaStream_t st, int num_sms, const uint32_t* keys_in, const uint32_t* vals_in,
+                            uint32_t* keys_out, uint32_t* vals_out, int64_t n, int shift, uint32_t* counts) {
+  if (n == 0) return cudaSuccess;
+  SortGeom g = make_geom(n, 1, num_sms);
+  k_rs_upsweep<<<g.ctas_seg, RS_THREADS, 0, st>>>(keys_in, g, shift, counts);
+  k_rs_spine<<<1, 1024, 0, st>>>(counts, g.ctas_seg);
+  k_rs_downsweep<<<g.ctas_seg, RS_THREADS, 0, st>>>(keys_in, vals_in, keys_out, vals_out, g, shift, counts);
+  count_launches(3);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_count_gather(cudaStream_t st, int64_t total, int64_t n, const uint32_t* order,
                                 const uint32_t* tiles_touched, uint32_t* counts_sorted, uint64_t* chunk_sums,
                                 int64_t* n_chunks) {
