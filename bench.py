@@ -253,7 +253,7 @@ def run_ours(args):
     n_frames = args.warmup + args.steps
     wl = Workload(n_frames, device)
     stream = torch.cuda.Stream()
-    rast = Rasterizer(RasterConfig(), stream=stream)
+    rast = Rasterizer(RasterConfig(blend_variant=args.variant), stream=stream)
     p = wl.params
     with torch.cuda.stream(stream):
         rast.set_anchor(p["means"], p["log_scales"], p["quats"], p["opacity_logit"], p["sh"])
@@ -301,6 +301,13 @@ def run_ours(args):
     px_step = VIEWS_PER_STEP * WIDTH * HEIGHT
     value = world * px_step * args.steps / (total_ms / 1e3) / 1e6
 
+    # one untimed render to read the variant and list sizes the timed steps used
+    with torch.cuda.stream(stream):
+        res = rast.render(wl.views(args.warmup)[1], save=True)
+        st = rast.stats(res.state)
+        res.state.release()
+    probe = {"variant": Rasterizer.variant_names()[st["blend_variant"]], "n_instances": st["n_instances"]}
+
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -320,12 +327,23 @@ def run_ours(args):
             continue
         stage_lines[name] = {"ms_per_launch": ms[name] / nl[name], "launches": nl[name],
                              "share": ms[name] / max(1e-9, sum(ms.values()))}
-    fwd_tflops = stages["pairs_forward"] * FLOPS_PER_PAIR_FWD / (ms["blend_fwd"] / 1e3) / 1e12 if ms["blend_fwd"] else 0
-    bwd_tflops = stages["pairs_backward"] * FLOPS_PER_PAIR_BWD / (ms["blend_bwd"] / 1e3) / 1e12 if ms["blend_bwd"] else 0
-    stage_lines.get("blend_fwd", {})["tflops"] = fwd_tflops
-    stage_lines.get("blend_bwd", {})["tflops"] = bwd_tflops
-    stage_lines.get("blend_fwd", {})["pairs_per_launch"] = stages["pairs_forward"] / max(1, nl["blend_fwd"])
-    stage_lines.get("blend_bwd", {})["pairs_per_launch"] = stages["pairs_backward"] / max(1, nl["blend_bwd"])
+    # Blend work: the definition's pairs (list entries up to termination) and the
+    # lane evaluations the kernel actually issued (the culling variants decide
+    # most definition pairs per 8x4 block without per-pair arithmetic).  The
+    # roofline uses the issued evaluations when the variant counts them.
+    def tflops(n, flops, name):
+        return n * flops / (ms[name] / 1e3) / 1e12 if ms[name] else 0.0
+    fwd_units = stages["issued_forward"] or stages["pairs_forward"]
+    bwd_units = stages["issued_backward"] or stages["pairs_backward"]
+    fwd_tflops = tflops(fwd_units, FLOPS_PER_PAIR_FWD, "blend_fwd")
+    bwd_tflops = tflops(bwd_units, FLOPS_PER_PAIR_BWD, "blend_bwd")
+    for name, units, defn, flops in (("blend_fwd", fwd_units, stages["pairs_forward"], FLOPS_PER_PAIR_FWD),
+                                     ("blend_bwd", bwd_units, stages["pairs_backward"], FLOPS_PER_PAIR_BWD)):
+        if name in stage_lines:
+            stage_lines[name]["tflops_issued"] = tflops(units, flops, name)
+            stage_lines[name]["tflops_definition_pairs"] = tflops(defn, flops, name)
+            stage_lines[name]["issued_evals_per_launch"] = units / max(1, nl[name])
+            stage_lines[name]["definition_pairs_per_launch"] = defn / max(1, nl[name])
     proj_bytes = N_GAUSS * (236 + VIEWS_PER_STEP * 56)
     if ms["project_sh"]:
         stage_lines["project_sh"]["gbs"] = proj_bytes / (ms["project_sh"] / nl["project_sh"] / 1e3) / 1e9
@@ -333,12 +351,12 @@ def run_ours(args):
         roof = {"bound": "alu", "achieved": bwd_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": bwd_tflops / fp32_peak, "traffic": None, "kernel": "k_blend_bwd",
                 "peak_source": f"derived: {n_sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz ({peak_kind} max clock)",
-                "work": f"{FLOPS_PER_PAIR_BWD} flops per replayed pair"}
+                "work": f"{FLOPS_PER_PAIR_BWD} flops per issued (pixel, Gaussian) evaluation of the replay"}
     elif dom == "blend_fwd":
         roof = {"bound": "alu", "achieved": fwd_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": fwd_tflops / fp32_peak, "traffic": None, "kernel": "k_blend_fwd",
                 "peak_source": f"derived: {n_sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz ({peak_kind} max clock)",
-                "work": f"{FLOPS_PER_PAIR_FWD} flops per evaluated pair"}
+                "work": f"{FLOPS_PER_PAIR_FWD} flops per issued (pixel, Gaussian) evaluation"}
     else:
         gbs = stage_lines.get(dom, {}).get("gbs")
         roof = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -361,8 +379,12 @@ def run_ours(args):
         "clocks": clocks,
         "roofline": roof,
         "stages": stage_lines,
+        "blend_variant": probe["variant"],
+        "instances_per_step": probe["n_instances"],
         "pairs_per_step": {"forward": stages["pairs_forward"] / args.steps,
-                           "backward": stages["pairs_backward"] / args.steps},
+                           "backward": stages["pairs_backward"] / args.steps,
+                           "issued_forward": stages["issued_forward"] / args.steps,
+                           "issued_backward": stages["issued_backward"] / args.steps},
     }
     if e2e is not None:
         line["e2e"] = e2e
@@ -420,7 +442,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--autotune", action="store_true", help="time every blend variant first and keep the fastest")
+    ap.add_argument("--variant", type=int, default=-1, help="blend kernel variant (-1: autotuned choice or default)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -249,8 +249,11 @@ int airgs_autotune(airgs_ctx* ctx, const airgs_camera* cams, int n_views, int* v
  * stream, and the blend kernels also add their evaluated pairs to a context
  * counter.  airgs_stage_times synchronises, writes the summed milliseconds and
  * the number of timed launches of each stage since the previous readout into
- * ms[AIRGS_NUM_STAGES] / launches[AIRGS_NUM_STAGES], the forward and backward
- * pair totals into pairs[2] (each nullable), and clears them. */
+ * ms[AIRGS_NUM_STAGES] / launches[AIRGS_NUM_STAGES], and into pairs[4] (each
+ * nullable) the forward and backward pair totals of the definition (list
+ * entries up to termination / below n_contrib) followed by the forward and
+ * backward lane evaluations the culling kernels actually issued (0 for
+ * variants that do not count them); then clears them. */
 #define AIRGS_NUM_STAGES 9
 int airgs_set_profiling(airgs_ctx* ctx, int enabled);
 int airgs_stage_times(airgs_ctx* ctx, double* ms, int64_t* launches, int64_t* pairs);

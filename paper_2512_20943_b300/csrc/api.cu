@@ -58,7 +58,7 @@ struct airgs_ctx {
   std::map<std::string, int> tuned;  // autotune choices
   // profiling: (stage, start, end) event triples awaiting readout
   bool profiling = false;
-  unsigned long long* d_pair_total = nullptr;  // [2] forward, backward pairs while profiling
+  unsigned long long* d_pair_total = nullptr;  // [4] forward, backward pairs; forward, backward issued evaluations
   std::vector<cudaEvent_t> event_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
 };
@@ -240,7 +240,7 @@ int choose_variant(airgs_ctx* ctx, int64_t n, int64_t pixels, int views) {
   if (ctx->cfg.blend_variant >= 0 && ctx->cfg.blend_variant < blend_variant_count()) return ctx->cfg.blend_variant;
   auto it = ctx->tuned.find(tune_key(n, pixels, views));
   if (it != ctx->tuned.end()) return it->second;
-  return 1;  // two pixels per thread unless tuned otherwise
+  return 4;  // warp-per-tile with block culling unless tuned otherwise
 }
 
 // Forward pipeline: project -> depth sort -> emit -> tile sort -> ranges -> blend.
@@ -393,6 +393,7 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
   a.work_counter = s->work;
   a.pair_counter = s->pairs;
   a.pair_total = ctx->profiling ? ctx->d_pair_total : nullptr;
+  a.exec_total = ctx->profiling ? ctx->d_pair_total + 2 : nullptr;
   FwdOut o;
   o.rgb = rgb_out;
   o.T = T_out;
@@ -449,6 +450,7 @@ int backward_impl(airgs_ctx* ctx, airgs_state* s, const float* dL, const float* 
   a.work_counter = s->work + 1;
   a.pair_counter = s->pairs + 1;
   a.pair_total = ctx->profiling ? ctx->d_pair_total + 1 : nullptr;
+  a.exec_total = ctx->profiling ? ctx->d_pair_total + 3 : nullptr;
   BwdIn in;
   in.rgb = s->rgb;
   in.dL = dL;
@@ -555,7 +557,7 @@ int airgs_create(airgs_ctx** out, const airgs_config* cfg, void* stream) {
     uint64_t thr = UINT64_MAX;
     e = cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &thr);
   }
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_pinned, 64);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_pinned, 128);
   if (e != cudaSuccess) {
     cudaGetLastError();
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
@@ -865,9 +867,9 @@ int airgs_autotune(airgs_ctx* ctx, const airgs_camera* cams, int n_views, int* v
 int airgs_set_profiling(airgs_ctx* ctx, int enabled) {
   if (!ctx) return AIRGS_E_ARG;
   if (enabled && !ctx->d_pair_total) {
-    int rc = dalloc(ctx, &ctx->d_pair_total, 2);
+    int rc = dalloc(ctx, &ctx->d_pair_total, 4);
     if (rc) return rc;
-    CK(cudaMemsetAsync(ctx->d_pair_total, 0, 2 * sizeof(unsigned long long), ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_pair_total, 0, 4 * sizeof(unsigned long long), ctx->stream));
   }
   ctx->profiling = enabled != 0;
   return AIRGS_OK;
@@ -876,18 +878,16 @@ int airgs_set_profiling(airgs_ctx* ctx, int enabled) {
 int airgs_stage_times(airgs_ctx* ctx, double* ms, int64_t* launches, int64_t* pairs) {
   if (!ctx) return AIRGS_E_ARG;
   if (pairs) {
-    pairs[0] = pairs[1] = 0;
+    pairs[0] = pairs[1] = pairs[2] = pairs[3] = 0;
     if (ctx->d_pair_total) {
-      CK(cudaMemcpyAsync(ctx->h_pinned + 2, ctx->d_pair_total, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost,
+      CK(cudaMemcpyAsync(ctx->h_pinned + 2, ctx->d_pair_total, 4 * sizeof(uint64_t), cudaMemcpyDeviceToHost,
                          ctx->stream));
-      CK(cudaMemsetAsync(ctx->d_pair_total, 0, 2 * sizeof(unsigned long long), ctx->stream));
+      CK(cudaMemsetAsync(ctx->d_pair_total, 0, 4 * sizeof(unsigned long long), ctx->stream));
     }
   }
   CK(cudaStreamSynchronize(ctx->stream));
-  if (pairs && ctx->d_pair_total) {
-    pairs[0] = (int64_t)ctx->h_pinned[2];
-    pairs[1] = (int64_t)ctx->h_pinned[3];
-  }
+  if (pairs && ctx->d_pair_total)
+    for (int k = 0; k < 4; ++k) pairs[k] = (int64_t)ctx->h_pinned[2 + k];
   for (int k = 0; k < ST_COUNT; ++k) {
     if (ms) ms[k] = 0.0;
     if (launches) launches[k] = 0;

@@ -1,0 +1,464 @@
+// Warp-per-tile blend kernels with exact block culling (sm_103a).
+//
+// A warp owns one 16x16 tile, split into eight 8x4 pixel blocks; block k
+// (bx = k & 1, by = k >> 1) gives lane l the pixel (8 bx + (l & 7), 4 by + (l >> 3)).
+// Most (pixel, Gaussian) pairs of a tile list cannot contribute: a Gaussian is
+// listed for every tile its 3-sigma square touches, but it blends only where
+// alpha = o G >= alpha_min, i.e. inside the ellipse
+//     Q(d) = -log2(e) power(d) <= L,   L = log2(o / alpha_min).
+// When a batch is staged, each Gaussian's axis-aligned bounding box of that
+// ellipse (half-widths sqrt(L (M^-1)_xx), sqrt(L (M^-1)_yy) for Q = d^T M d),
+// widened by a safety margin far above the single-precision error of the
+// per-pair test, is intersected with the eight blocks; the warp then evaluates
+// only the blocks the box meets, with warp-uniform branches.  Pairs in skipped
+// blocks are pairs whose alpha is below alpha_min, which the definition skips:
+// results are bit-identical to the unculled variants.  Blocks whose pixels
+// all stopped (forward) or whose pixels' n_contrib lie behind the current list
+// position (backward) are skipped the same way.
+//
+// Per-pixel arithmetic uses the exact-replay helpers of airgs_internal.cuh; the
+// backward reduces each Gaussian's ten sums once per tile with the 20-shuffle
+// transpose butterfly and three red.global.add.v4.f32.
+#include "airgs_internal.cuh"
+#include "kernels.h"
+
+namespace airgs {
+
+constexpr int NG = 8;          // 8x4 blocks per tile
+constexpr int CBATCH = 64;     // records staged per batch (two per lane)
+constexpr unsigned kAll = 0xffffffffu;
+
+__device__ __forceinline__ int cull_fetch(int* counter) {
+  int it = 0;
+  if ((threadIdx.x & 31) == 0) it = atomicAdd(counter, 1);
+  return __shfl_sync(kAll, it, 0);
+}
+
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Blocks of the tile at (X0, Y0) that the Gaussian's alpha >= alpha_min box meets.
+__device__ __forceinline__ unsigned block_mask(float4 ga, float4 gb, float log2_amin, float X0, float Y0) {
+  const float mx = ga.x, my = ga.y;
+  const float ap = -ga.z, bp = -ga.w, cp = -gb.x;  // Q = ap dx^2 + bp dx dy + cp dy^2
+  const float L = lg2_approx(gb.y) - log2_amin + 1e-3f;
+  if (L <= 0.f) return 0u;        // o below alpha_min: never blends
+  if (!(L > 0.f)) return 0xFFu;   // NaN opacity: leave it to the per-pair test
+  const float det = ap * cp - 0.25f * bp * bp;
+  if (!(det > 0.f)) return 0xFFu; // degenerate conic: no culling
+  const float hx = sqrtf(L * cp / det) * 1.0001f + 0.01f;
+  const float hy = sqrtf(L * ap / det) * 1.0001f + 0.01f;
+  unsigned xm = 0, m = 0;
+#pragma unroll
+  for (int bx = 0; bx < 2; ++bx) {
+    const float lo = X0 + 8.f * bx + 0.5f, hi = lo + 7.f;
+    if (mx + hx >= lo && mx - hx <= hi) xm |= 1u << bx;
+  }
+#pragma unroll
+  for (int by = 0; by < 4; ++by) {
+    const float lo = Y0 + 4.f * by + 0.5f, hi = lo + 3.f;
+    if (my + hy >= lo && my - hy <= hi) m |= xm << (2 * by);
+  }
+  return m;
+}
+
+// ------------------------------------------------------------------ forward
+template <bool IMP>
+__global__ void __launch_bounds__(32) k_blend_fwd_cull(BlendArgs a, FwdOut out) {
+  __shared__ float4 s_a[CBATCH];
+  __shared__ float4 s_b[CBATCH];
+  __shared__ float s_c[CBATCH];
+  __shared__ uint32_t s_id[CBATCH];
+  __shared__ unsigned s_mask[CBATCH];
+  __shared__ int64_t s_tile_base[AIRGS_MAX_VIEWS_DEV];
+
+  const int lane = threadIdx.x;
+  for (int v = lane; v < a.n_views; v += 32) s_tile_base[v] = a.cams[v].tile_base;
+  __syncwarp();
+  const float alpha_max = a.rp.alpha_max, alpha_min = a.rp.alpha_min, T_min = a.rp.T_min;
+  const float log2_amin = log2f(alpha_min);
+  const int lx = lane & 7, ly = lane >> 3;
+  unsigned long long pairs = 0, executed = 0;
+
+  while (true) {
+    const int item = cull_fetch(a.work_counter);
+    if (item >= a.n_tiles) break;
+    const int v = view_of_tile(s_tile_base, a.n_views, item);
+    const CamDev& cam = a.cams[v];
+    const int lt = (int)(item - s_tile_base[v]);
+    const int X0 = (lt % cam.TW) * kTile, Y0 = (lt / cam.TW) * kTile;
+    const float pxb[2] = {(float)(X0 + lx) + 0.5f, (float)(X0 + 8 + lx) + 0.5f};
+    float T[NG], C0[NG], C1[NG], C2[NG];
+    int last[NG], stop_at[NG];
+    unsigned done = 0;
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      const int x = X0 + 8 * (k & 1) + lx, y = Y0 + 4 * (k >> 1) + ly;
+      if (!(x < cam.W && y < cam.H)) done |= 1u << k;
+      T[k] = 1.f;
+      C0[k] = C1[k] = C2[k] = 0.f;
+      last[k] = 0;
+      stop_at[k] = -1;
+    }
+    const uint2 range = a.ranges[item];
+    const ProjRec* projv = a.proj + (size_t)v * a.n;
+    uint32_t exec_groups = 0;
+
+    for (uint32_t b0 = range.x; b0 < range.y; b0 += CBATCH) {
+      unsigned live = 0;
+#pragma unroll
+      for (int k = 0; k < NG; ++k)
+        if (__any_sync(kAll, !((done >> k) & 1u))) live |= 1u << k;
+      if (live == 0) break;
+      const int nb = (int)min((uint32_t)CBATCH, range.y - b0);
+      for (int j = lane; j < nb; j += 32) {
+        const uint32_t id = __ldg(a.ids + b0 + j);
+        const ProjRec* r = projv + id;
+        const float4 ga = __ldg(&r->a), gb = __ldg(&r->b);
+        s_a[j] = ga;
+        s_b[j] = gb;
+        s_c[j] = __ldg(&r->c.x);
+        s_id[j] = id;
+        s_mask[j] = block_mask(ga, gb, log2_amin, (float)X0, (float)Y0);
+      }
+      __syncwarp();
+      const int pos_base = (int)(b0 - range.x) + 1;
+      for (int j = 0; j < nb; ++j) {
+        const unsigned m = s_mask[j] & live;
+        if (m == 0) continue;
+        exec_groups += __popc(m);
+        const float4 ga = s_a[j];
+        const float4 gb = s_b[j];
+        const float cb = s_c[j];
+        const int pos1 = pos_base + j;
+        const float dxb[2] = {__fsub_rn(ga.x, pxb[0]), __fsub_rn(ga.x, pxb[1])};
+        float wsum = 0.f;
+        int bcount = 0;
+#pragma unroll
+        for (int k = 0; k < NG; ++k) {
+          if (!((m >> k) & 1u)) continue;  // warp-uniform
+          const float py = (float)(Y0 + 4 * (k >> 1) + ly) + 0.5f;
+          float dy, b2dy, c2dy2;
+          row_terms(ga.y, py, ga.w, gb.x, dy, b2dy, c2dy2);
+          const float dx = dxb[k & 1];
+          const float p2 = power2_of(dx, ga.z, b2dy, c2dy2);
+          const float G = ex2_approx(p2);
+          const float alpha = alpha_of(gb.y, G, alpha_max);
+          const float Tn = transmit(T[k], alpha);
+          const bool valid = !((done >> k) & 1u) && !(p2 > 0.f) && !(alpha < alpha_min);
+          const bool stop = valid && (Tn < T_min);
+          const bool blend = valid && !stop;
+          const float w = __fmul_rn(alpha, T[k]);
+          if (blend) {
+            C0[k] = __fmaf_rn(gb.z, w, C0[k]);
+            C1[k] = __fmaf_rn(gb.w, w, C1[k]);
+            C2[k] = __fmaf_rn(cb, w, C2[k]);
+            T[k] = Tn;
+            last[k] = pos1;
+          }
+          if (stop) {
+            done |= 1u << k;
+            stop_at[k] = pos1;
+          }
+          if (IMP) {
+            wsum += blend ? w : 0.f;
+            bcount += blend ? 1 : 0;
+          }
+        }
+        if (IMP) {
+          if (__any_sync(kAll, bcount > 0)) {
+            float s = wsum;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kAll, s, o);
+            const int c = __reduce_add_sync(kAll, bcount);
+            if (lane == 0) {
+              atomicAdd(out.imp_w + s_id[j], s);
+              atomicAdd(out.imp_cnt + s_id[j], (uint32_t)c);
+            }
+          }
+        }
+      }
+      __syncwarp();
+    }
+    executed += 32ull * exec_groups;
+    const int64_t HW = (int64_t)cam.W * cam.H;
+    float* rgb = out.rgb + 3 * cam.pix_base;
+    const uint32_t len = range.y - range.x;
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      const int x = X0 + 8 * (k & 1) + lx, y = Y0 + 4 * (k >> 1) + ly;
+      if (x < cam.W && y < cam.H) {
+        // pairs of the definition: list entries up to and including the stop
+        pairs += stop_at[k] > 0 ? (unsigned long long)stop_at[k] : (unsigned long long)len;
+        const int64_t pix = (int64_t)y * cam.W + x;
+        rgb[pix] = __fmaf_rn(T[k], a.rp.bg[0], C0[k]);
+        rgb[HW + pix] = __fmaf_rn(T[k], a.rp.bg[1], C1[k]);
+        rgb[2 * HW + pix] = __fmaf_rn(T[k], a.rp.bg[2], C2[k]);
+        if (out.T) out.T[cam.pix_base + pix] = T[k];
+        out.ncontrib[cam.pix_base + pix] = last[k];
+        if (out.ncontrib_user) out.ncontrib_user[cam.pix_base + pix] = last[k];
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(kAll, pairs, o);
+  if (lane == 0) {
+    if (pairs) {
+      atomicAdd(a.pair_counter, pairs);
+      if (a.pair_total) atomicAdd(a.pair_total, pairs);
+    }
+    if (a.exec_total && executed) atomicAdd(a.exec_total, executed);
+  }
+}
+
+// ------------------------------------------------------------------ 16 -> 4 transpose reduction
+__device__ __forceinline__ void cull_reduce16_to4(float (&v)[16], int lane) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const bool up = lane & 16;
+    const float send = up ? v[k] : v[k + 8];
+    const float keep = up ? v[k + 8] : v[k];
+    v[k] = keep + __shfl_xor_sync(kAll, send, 16);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const bool up = lane & 8;
+    const float send = up ? v[k] : v[k + 4];
+    const float keep = up ? v[k + 4] : v[k];
+    v[k] = keep + __shfl_xor_sync(kAll, send, 8);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const bool up = lane & 4;
+    const float send = up ? v[k] : v[k + 2];
+    const float keep = up ? v[k + 2] : v[k];
+    v[k] = keep + __shfl_xor_sync(kAll, send, 4);
+  }
+  v[0] += __shfl_xor_sync(kAll, v[0], 1);
+  v[1] += __shfl_xor_sync(kAll, v[1], 1);
+  v[0] += __shfl_xor_sync(kAll, v[0], 2);
+  v[1] += __shfl_xor_sync(kAll, v[1], 2);
+  v[2] = __shfl_xor_sync(kAll, v[0], 4);
+  v[3] = __shfl_xor_sync(kAll, v[1], 4);
+}
+
+// ------------------------------------------------------------------ backward
+// Sums per (tile, Gaussian), scaled when flushed (see blend_warp.cu):
+//   0 mx (x ln2), 1 my (x ln2), 2 A (x -1/2), 3 B (x -1), 4 C (x -1/2),
+//   5 opacity, 6-8 colour, 9 blend weight.
+template <bool L1, bool IMP>
+__global__ void __launch_bounds__(32) k_blend_bwd_cull(BlendArgs a, BwdIn in) {
+  __shared__ float4 s_a[CBATCH];
+  __shared__ float4 s_b[CBATCH];
+  __shared__ float s_c[CBATCH];
+  __shared__ uint32_t s_id[CBATCH];
+  __shared__ unsigned s_mask[CBATCH];
+  __shared__ int64_t s_tile_base[AIRGS_MAX_VIEWS_DEV];
+
+  const int lane = threadIdx.x;
+  for (int v = lane; v < a.n_views; v += 32) s_tile_base[v] = a.cams[v].tile_base;
+  __syncwarp();
+  const float alpha_max = a.rp.alpha_max, alpha_min = a.rp.alpha_min;
+  const float log2_amin = log2f(alpha_min);
+  const int lx = lane & 7, ly = lane >> 3;
+  unsigned long long pairs = 0, executed = 0;
+  float loss_acc = 0.f;
+
+  while (true) {
+    const int item = cull_fetch(a.work_counter);
+    if (item >= a.n_tiles) break;
+    const int v = view_of_tile(s_tile_base, a.n_views, item);
+    const CamDev& cam = a.cams[v];
+    const int lt = (int)(item - s_tile_base[v]);
+    const int X0 = (lt % cam.TW) * kTile, Y0 = (lt / cam.TW) * kTile;
+    const float pxb[2] = {(float)(X0 + lx) + 0.5f, (float)(X0 + 8 + lx) + 0.5f};
+    const int64_t HW = (int64_t)cam.W * cam.H;
+    const int64_t base3 = 3 * cam.pix_base;
+
+    float T[NG], gP[NG], gC[NG], g0[NG], g1[NG], g2[NG];
+    int nc[NG], gmax[NG];
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      const int x = X0 + 8 * (k & 1) + lx, y = Y0 + 4 * (k >> 1) + ly;
+      T[k] = 1.f;
+      gP[k] = 0.f;
+      g0[k] = g1[k] = g2[k] = gC[k] = 0.f;
+      nc[k] = 0;
+      if (x < cam.W && y < cam.H) {
+        const int64_t pix = (int64_t)y * cam.W + x;
+        float cf[3], gg[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+          cf[ch] = in.rgb[base3 + ch * HW + pix];
+          if (L1) {
+            const float d = cf[ch] - in.target[base3 + ch * HW + pix];
+            gg[ch] = d > 0.f ? in.inv_norm : (d < 0.f ? -in.inv_norm : 0.f);
+            loss_acc += fabsf(d);
+          } else {
+            gg[ch] = in.dL[base3 + ch * HW + pix];
+          }
+        }
+        g0[k] = gg[0];
+        g1[k] = gg[1];
+        g2[k] = gg[2];
+        gC[k] = gg[0] * cf[0] + gg[1] * cf[1] + gg[2] * cf[2];
+        nc[k] = in.ncontrib[cam.pix_base + pix];
+        pairs += (unsigned long long)nc[k];
+      }
+      gmax[k] = (int)__reduce_max_sync(kAll, (unsigned)nc[k]);  // warp-uniform
+    }
+    int maxnc = 0;
+#pragma unroll
+    for (int k = 0; k < NG; ++k) maxnc = max(maxnc, gmax[k]);
+    const uint2 range = a.ranges[item];
+    const uint32_t end = range.x + (uint32_t)maxnc;
+    const ProjRec* projv = a.proj + (size_t)v * a.n;
+    GradRec* gradv = in.grad + (size_t)v * a.n;
+    uint32_t exec_groups = 0;
+
+    for (uint32_t b0 = range.x; b0 < end; b0 += CBATCH) {
+      const int nb = (int)min((uint32_t)CBATCH, end - b0);
+      for (int j = lane; j < nb; j += 32) {
+        const uint32_t id = __ldg(a.ids + b0 + j);
+        const ProjRec* r = projv + id;
+        const float4 ga = __ldg(&r->a), gb = __ldg(&r->b);
+        s_a[j] = ga;
+        s_b[j] = gb;
+        s_c[j] = __ldg(&r->c.x);
+        s_id[j] = id;
+        s_mask[j] = block_mask(ga, gb, log2_amin, (float)X0, (float)Y0);
+      }
+      __syncwarp();
+      const int pos0 = (int)(b0 - range.x);
+      for (int j = 0; j < nb; ++j) {
+        const int pos = pos0 + j;
+        unsigned live = 0;
+#pragma unroll
+        for (int k = 0; k < NG; ++k) live |= (pos < gmax[k] ? 1u : 0u) << k;
+        const unsigned m = s_mask[j] & live;
+        if (m == 0) continue;
+        exec_groups += __popc(m);
+        const float4 ga = s_a[j];
+        const float4 gb = s_b[j];
+        const float cb = s_c[j];
+        const float dxb[2] = {__fsub_rn(ga.x, pxb[0]), __fsub_rn(ga.x, pxb[1])};
+        const float twoa2 = 2.f * ga.z;
+        float acc[10];
+#pragma unroll
+        for (int q = 0; q < 10; ++q) acc[q] = 0.f;
+        int cnt = 0;
+#pragma unroll
+        for (int k = 0; k < NG; ++k) {
+          if (!((m >> k) & 1u)) continue;  // warp-uniform
+          const float py = (float)(Y0 + 4 * (k >> 1) + ly) + 0.5f;
+          float dy, b2dy, c2dy2;
+          row_terms(ga.y, py, ga.w, gb.x, dy, b2dy, c2dy2);
+          const float dx = dxb[k & 1];
+          const float p2 = power2_of(dx, ga.z, b2dy, c2dy2);
+          const float G = ex2_approx(p2);
+          const float oG = __fmul_rn(gb.y, G);
+          const float alpha = alpha_of(gb.y, G, alpha_max);
+          const bool valid = (pos < nc[k]) && !(p2 > 0.f) && !(alpha < alpha_min);
+          const float ae = valid ? alpha : 0.f;
+          const bool graded = valid && (oG <= alpha_max);
+          const float w = __fmul_rn(ae, T[k]);
+          const float gc = g0[k] * gb.z + g1[k] * gb.w + g2[k] * cb;
+          acc[6] = fmaf(w, g0[k], acc[6]);
+          acc[7] = fmaf(w, g1[k], acc[7]);
+          acc[8] = fmaf(w, g2[k], acc[8]);
+          gP[k] = fmaf(gc, w, gP[k]);
+          const float om = __fsub_rn(1.0f, ae);
+          const float dL_dalpha = T[k] * gc - __fdividef(gC[k] - gP[k], om);
+          T[k] = __fmul_rn(T[k], om);
+          const float dL_dpow = graded ? dL_dalpha * alpha : 0.f;
+          acc[5] = fmaf(dL_dalpha, graded ? G : 0.f, acc[5]);
+          acc[2] = fmaf(dL_dpow, dx * dx, acc[2]);
+          acc[3] = fmaf(dL_dpow, dx * dy, acc[3]);
+          acc[4] = fmaf(dL_dpow, dy * dy, acc[4]);
+          acc[0] = fmaf(dL_dpow, fmaf(twoa2, dx, b2dy), acc[0]);
+          acc[1] = fmaf(dL_dpow, fmaf(ga.w, dx, 2.f * gb.x * dy), acc[1]);
+          if (IMP) acc[9] += w;
+          cnt += valid ? 1 : 0;
+        }
+        if (__any_sync(kAll, cnt > 0)) {
+          float vals[16];
+#pragma unroll
+          for (int q = 0; q < 10; ++q) vals[q] = acc[q];
+#pragma unroll
+          for (int q = 10; q < 16; ++q) vals[q] = 0.f;
+          cull_reduce16_to4(vals, lane);
+          const uint32_t id = s_id[j];
+          float* gr = reinterpret_cast<float*>(gradv + id);
+          if (lane == 0) red_add_v4(gr, vals[0] * kLn2, vals[1] * kLn2, -0.5f * vals[2], -vals[3]);
+          if (lane == 8) red_add_v4(gr + 4, -0.5f * vals[0], vals[1], vals[2], vals[3]);
+          if (lane == 16) {
+            red_add_v4(gr + 8, vals[0], 0.f, 0.f, 0.f);
+            if (IMP && vals[1] != 0.f) atomicAdd(in.imp_w + id, vals[1]);
+          }
+          if (IMP) {
+            const int c = __reduce_add_sync(kAll, cnt);
+            if (lane == 0 && c) atomicAdd(in.imp_cnt + id, (uint32_t)c);
+          }
+        }
+      }
+      __syncwarp();
+    }
+    executed += 32ull * exec_groups;
+  }
+  for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(kAll, pairs, o);
+  if (lane == 0) {
+    if (pairs) {
+      atomicAdd(a.pair_counter, pairs);
+      if (a.pair_total) atomicAdd(a.pair_total, pairs);
+    }
+    if (a.exec_total && executed) atomicAdd(a.exec_total, executed);
+  }
+  if (L1 && in.loss) {
+    for (int o = 16; o > 0; o >>= 1) loss_acc += __shfl_xor_sync(kAll, loss_acc, o);
+    if (lane == 0) atomicAdd(in.loss, loss_acc * in.inv_norm);
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+template <class K>
+static int cull_grid(K kernel, int num_sms, int64_t n_tiles, cudaError_t& e) {
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 32, 0);
+  int64_t g = (int64_t)(occ > 0 ? occ : 1) * num_sms;
+  return (int)(n_tiles < g ? n_tiles : g);
+}
+
+cudaError_t launch_blend_fwd_cull(cudaStream_t st, int num_sms, const BlendArgs& a, const FwdOut& o) {
+  cudaError_t e = cudaSuccess;
+  if (o.imp_w) {
+    int grid = cull_grid(k_blend_fwd_cull<true>, num_sms, a.n_tiles, e);
+    if (e != cudaSuccess) return e;
+    if (grid > 0) k_blend_fwd_cull<true><<<grid, 32, 0, st>>>(a, o);
+  } else {
+    int grid = cull_grid(k_blend_fwd_cull<false>, num_sms, a.n_tiles, e);
+    if (e != cudaSuccess) return e;
+    if (grid > 0) k_blend_fwd_cull<false><<<grid, 32, 0, st>>>(a, o);
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <bool L1, bool IMP>
+static cudaError_t bwd_cull(cudaStream_t st, int num_sms, const BlendArgs& a, const BwdIn& in) {
+  cudaError_t e = cudaSuccess;
+  int grid = cull_grid(k_blend_bwd_cull<L1, IMP>, num_sms, a.n_tiles, e);
+  if (e != cudaSuccess) return e;
+  if (grid > 0) k_blend_bwd_cull<L1, IMP><<<grid, 32, 0, st>>>(a, in);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_blend_bwd_cull(cudaStream_t st, int num_sms, const BlendArgs& a, const BwdIn& in) {
+  const bool l1 = in.target != nullptr, imp = in.imp_w != nullptr;
+  if (l1) return imp ? bwd_cull<true, true>(st, num_sms, a, in) : bwd_cull<true, false>(st, num_sms, a, in);
+  return imp ? bwd_cull<false, true>(st, num_sms, a, in) : bwd_cull<false, false>(st, num_sms, a, in);
+}
+
+}  // namespace airgs

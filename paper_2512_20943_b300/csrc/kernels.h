@@ -51,6 +51,7 @@ struct BlendArgs {
   int* work_counter;
   unsigned long long* pair_counter;
   unsigned long long* pair_total;  // nullable: cumulative counter of the context
+  unsigned long long* exec_total;  // nullable: cumulative lane evaluations actually issued (culling variants)
 };
 
 struct FwdOut {
@@ -78,6 +79,10 @@ int blend_variant_count();
 const char* blend_variant_name(int v);
 cudaError_t launch_blend_fwd(cudaStream_t st, int variant, int num_sms, const BlendArgs& a, const FwdOut& o);
 cudaError_t launch_blend_bwd(cudaStream_t st, int variant, int num_sms, const BlendArgs& a, const BwdIn& in);
+cudaError_t launch_blend_fwd_cull(cudaStream_t st, int num_sms, const BlendArgs& a, const FwdOut& o);
+cudaError_t launch_blend_bwd_cull(cudaStream_t st, int num_sms, const BlendArgs& a, const BwdIn& in);
+cudaError_t launch_blend_fwd_warp(cudaStream_t st, int num_sms, const BlendArgs& a, const FwdOut& o);
+cudaError_t launch_blend_bwd_warp(cudaStream_t st, int num_sms, const BlendArgs& a, const BwdIn& in);
 
 cudaError_t launch_project_bwd(cudaStream_t st, int64_t n, int sh_degree, const float* means,
                                const float* log_scales, const float* quats, const float* opacity_logit,

@@ -355,11 +355,12 @@ class Rasterizer:
         n = _abi.AIRGS_NUM_STAGES
         ms = (ctypes.c_double * n)()
         launches = (ctypes.c_int64 * n)()
-        pairs = (ctypes.c_int64 * 2)()
+        pairs = (ctypes.c_int64 * 4)()
         self._check(self.lib.airgs_stage_times(self.ctx, ms, launches, pairs))
         names = [self.lib.airgs_stage_name(i).decode() for i in range(n)]
         return dict(ms={names[i]: ms[i] for i in range(n)}, launches={names[i]: launches[i] for i in range(n)},
-                    pairs_forward=pairs[0], pairs_backward=pairs[1])
+                    pairs_forward=pairs[0], pairs_backward=pairs[1], issued_forward=pairs[2],
+                    issued_backward=pairs[3])
 
     @staticmethod
     def kernel_launch_count() -> int:

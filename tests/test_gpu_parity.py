@@ -24,6 +24,22 @@ def rast():
     return Rasterizer()
 
 
+_by_variant = {}
+
+
+def rast_variant(v):
+    """A context pinned to blend kernel variant v (0-2: tile per CTA with 1, 2,
+    4 pixels per thread; 3: tile per warp, 8 pixels per lane; 4: tile per warp
+    in 8x4 blocks with exact block culling)."""
+    from paper_2512_20943_b300 import RasterConfig, Rasterizer
+    if v not in _by_variant:
+        _by_variant[v] = Rasterizer(RasterConfig(blend_variant=v))
+    return _by_variant[v]
+
+
+VARIANTS = [0, 1, 2, 3, 4]
+
+
 def render_gpu(rast, g, cams, **kw):
     t = to_cuda(g)
     res = rast.render_gaussians(*params(t), cams, **kw)
@@ -89,8 +105,10 @@ def test_tile_lists_match_fp64_sets(rast, name):
     res.state.release()
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("name", ["plain_2k", "sh3_ragged"])
-def test_forward_matches_oracle(rast, name):
+def test_forward_matches_oracle(name, variant):
+    rast = rast_variant(variant)
     g, cams = scenes()[name]
     t, res = render_gpu(rast, g, cams, T=True, n_contrib=True)
     ref = oracle.render(synthetic.widen(g), cams)
@@ -105,7 +123,9 @@ def test_forward_matches_oracle(rast, name):
     assert max(r.max() for r in ref["rgb"]) > 0.2  # not an empty image
 
 
-def test_importance_matches_oracle(rast):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_importance_matches_oracle(variant):
+    rast = rast_variant(variant)
     g, cams = small_sh3_scene()
     t, res = render_gpu(rast, g, cams, importance=True, save=True)
     ref = oracle.render(synthetic.widen(g), cams)
@@ -140,8 +160,10 @@ def masked_dL(cams, ref, seed):
     return out
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("name", ["plain_2k", "sh3_ragged"])
-def test_backward_matches_oracle(rast, name):
+def test_backward_matches_oracle(name, variant):
+    rast = rast_variant(variant)
     g, cams = scenes()[name]
     ref = oracle.render(synthetic.widen(g), cams)
     dL = masked_dL(cams, ref, 5)
@@ -155,7 +177,9 @@ def test_backward_matches_oracle(rast, name):
     res.state.release()
 
 
-def test_l1_fused_equals_explicit_gradient(rast):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_l1_fused_equals_explicit_gradient(variant):
+    rast = rast_variant(variant)
     g, cams = small_sh3_scene()
     tgt = synthetic.target_images(cams, 1)
     target = torch.from_numpy(np.concatenate([x.reshape(-1) for x in tgt])).cuda()
@@ -222,7 +246,9 @@ def test_radix_sort_stable_bit_exact(rast, n, bits):
     assert np.array_equal(vo.cpu().numpy().view(np.uint32), vals[order])
 
 
-def test_permutation_invariance_gpu(rast):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_permutation_invariance_gpu(variant):
+    rast = rast_variant(variant)
     g, cams = small_sh3_scene()
     perm = np.random.default_rng(4).permutation(g["means"].shape[0])
     gp = dict(g)
@@ -266,3 +292,12 @@ def test_frame_update_map_too_small_is_an_error(rast):
     rast.set_anchor(*params(to_cuda(g)))
     with pytest.raises(AirGSError):
         rast.apply_frame_update(torch.zeros((7, 5, 5), dtype=torch.uint16, device="cuda"), np.zeros(7), np.ones(7))
+
+
+def test_variants_agree_bitwise_forward():
+    """Every variant evaluates the same pairs with the same arithmetic: the
+    images are bit-identical across variants."""
+    g, cams = small_sh3_scene()
+    imgs = [render_gpu(rast_variant(v), g, cams)[1].rgb for v in VARIANTS]
+    for im in imgs[1:]:
+        assert torch.equal(im, imgs[0])
