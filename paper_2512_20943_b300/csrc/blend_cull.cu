@@ -1,7 +1,9 @@
 // Warp-per-tile blend kernels with exact block culling (sm_103a).
 //
-// A warp owns one 16x16 tile, split into eight 8x4 pixel blocks; block k
-// (bx = k & 1, by = k >> 1) gives lane l the pixel (8 bx + (l & 7), 4 by + (l >> 3)).
+// A 16x16 tile is split into eight 8x4 pixel blocks; block k (bx = k & 1,
+// by = k >> 1) gives lane l the pixel (8 bx + (l & 7), 4 by + (l >> 3)).  A warp
+// owns either the whole tile (eight blocks) or one half of it (four blocks,
+// each half an independent work item, so twice the warps fit per SM).
 // Most (pixel, Gaussian) pairs of a tile list cannot contribute: a Gaussian is
 // listed for every tile its 3-sigma square touches, but it blends only where
 // alpha = o G >= alpha_min, i.e. inside the ellipse
@@ -24,7 +26,7 @@
 
 namespace airgs {
 
-constexpr int NG = 8;          // 8x4 blocks per tile
+constexpr int NG_TILE = 8;     // 8x4 blocks per tile
 constexpr int CBATCH = 64;     // records staged per batch (two per lane)
 constexpr unsigned kAll = 0xffffffffu;
 
@@ -40,7 +42,8 @@ __device__ __forceinline__ float lg2_approx(float x) {
   return y;
 }
 
-// Blocks of the tile at (X0, Y0) that the Gaussian's alpha >= alpha_min box meets.
+// Blocks of the tile at (X0, Y0) that the Gaussian's alpha >= alpha_min box
+// meets (bit k: block bx = k & 1, by = k >> 1).
 __device__ __forceinline__ unsigned block_mask(float4 ga, float4 gb, float log2_amin, float X0, float Y0) {
   const float mx = ga.x, my = ga.y;
   const float ap = -ga.z, bp = -ga.w, cp = -gb.x;  // Q = ap dx^2 + bp dx dy + cp dy^2
@@ -66,8 +69,11 @@ __device__ __forceinline__ unsigned block_mask(float4 ga, float4 gb, float log2_
 }
 
 // ------------------------------------------------------------------ forward
-template <bool IMP>
+// NG blocks per warp: 8 = the whole tile, 4 = one half (rows 8h .. 8h+7) of it,
+// so that two warps with half the per-lane state share a tile independently.
+template <int NG, bool IMP>
 __global__ void __launch_bounds__(32) k_blend_fwd_cull(BlendArgs a, FwdOut out) {
+  constexpr int PARTS = NG_TILE / NG;
   __shared__ float4 s_a[CBATCH];
   __shared__ float4 s_b[CBATCH];
   __shared__ float s_c[CBATCH];
@@ -84,12 +90,13 @@ __global__ void __launch_bounds__(32) k_blend_fwd_cull(BlendArgs a, FwdOut out) 
   unsigned long long pairs = 0, executed = 0;
 
   while (true) {
-    const int item = cull_fetch(a.work_counter);
-    if (item >= a.n_tiles) break;
+    const int work = cull_fetch(a.work_counter);
+    if (work >= a.n_tiles * PARTS) break;
+    const int item = work / PARTS, part = work % PARTS;
     const int v = view_of_tile(s_tile_base, a.n_views, item);
     const CamDev& cam = a.cams[v];
     const int lt = (int)(item - s_tile_base[v]);
-    const int X0 = (lt % cam.TW) * kTile, Y0 = (lt / cam.TW) * kTile;
+    const int X0 = (lt % cam.TW) * kTile, Y0 = (lt / cam.TW) * kTile + part * (kTile / PARTS);
     const float pxb[2] = {(float)(X0 + lx) + 0.5f, (float)(X0 + 8 + lx) + 0.5f};
     float T[NG], C0[NG], C1[NG], C2[NG];
     int last[NG], stop_at[NG];
@@ -122,7 +129,7 @@ __global__ void __launch_bounds__(32) k_blend_fwd_cull(BlendArgs a, FwdOut out) 
         s_b[j] = gb;
         s_c[j] = __ldg(&r->c.x);
         s_id[j] = id;
-        s_mask[j] = block_mask(ga, gb, log2_amin, (float)X0, (float)Y0);
+        s_mask[j] = block_mask(ga, gb, log2_amin, (float)X0, (float)Y0) & ((1u << NG) - 1u);
       }
       __syncwarp();
       const int pos_base = (int)(b0 - range.x) + 1;
@@ -248,8 +255,9 @@ __device__ __forceinline__ void cull_reduce16_to4(float (&v)[16], int lane) {
 // Sums per (tile, Gaussian), scaled when flushed (see blend_warp.cu):
 //   0 mx (x ln2), 1 my (x ln2), 2 A (x -1/2), 3 B (x -1), 4 C (x -1/2),
 //   5 opacity, 6-8 colour, 9 blend weight.
-template <bool L1, bool IMP>
+template <int NG, bool L1, bool IMP>
 __global__ void __launch_bounds__(32) k_blend_bwd_cull(BlendArgs a, BwdIn in) {
+  constexpr int PARTS = NG_TILE / NG;
   __shared__ float4 s_a[CBATCH];
   __shared__ float4 s_b[CBATCH];
   __shared__ float s_c[CBATCH];
@@ -267,12 +275,13 @@ __global__ void __launch_bounds__(32) k_blend_bwd_cull(BlendArgs a, BwdIn in) {
   float loss_acc = 0.f;
 
   while (true) {
-    const int item = cull_fetch(a.work_counter);
-    if (item >= a.n_tiles) break;
+    const int work = cull_fetch(a.work_counter);
+    if (work >= a.n_tiles * PARTS) break;
+    const int item = work / PARTS, part = work % PARTS;
     const int v = view_of_tile(s_tile_base, a.n_views, item);
     const CamDev& cam = a.cams[v];
     const int lt = (int)(item - s_tile_base[v]);
-    const int X0 = (lt % cam.TW) * kTile, Y0 = (lt / cam.TW) * kTile;
+    const int X0 = (lt % cam.TW) * kTile, Y0 = (lt / cam.TW) * kTile + part * (kTile / PARTS);
     const float pxb[2] = {(float)(X0 + lx) + 0.5f, (float)(X0 + 8 + lx) + 0.5f};
     const int64_t HW = (int64_t)cam.W * cam.H;
     const int64_t base3 = 3 * cam.pix_base;
@@ -328,7 +337,7 @@ __global__ void __launch_bounds__(32) k_blend_bwd_cull(BlendArgs a, BwdIn in) {
         s_b[j] = gb;
         s_c[j] = __ldg(&r->c.x);
         s_id[j] = id;
-        s_mask[j] = block_mask(ga, gb, log2_amin, (float)X0, (float)Y0);
+        s_mask[j] = block_mask(ga, gb, log2_amin, (float)X0, (float)Y0) & ((1u << NG) - 1u);
       }
       __syncwarp();
       const int pos0 = (int)(b0 - range.x);
@@ -423,42 +432,51 @@ __global__ void __launch_bounds__(32) k_blend_bwd_cull(BlendArgs a, BwdIn in) {
 
 // ------------------------------------------------------------------ launchers
 template <class K>
-static int cull_grid(K kernel, int num_sms, int64_t n_tiles, cudaError_t& e) {
+static int cull_grid(K kernel, int num_sms, int64_t items, cudaError_t& e) {
   int occ = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 32, 0);
   int64_t g = (int64_t)(occ > 0 ? occ : 1) * num_sms;
-  return (int)(n_tiles < g ? n_tiles : g);
+  return (int)(items < g ? items : g);
 }
 
-cudaError_t launch_blend_fwd_cull(cudaStream_t st, int num_sms, const BlendArgs& a, const FwdOut& o) {
+template <int NG, bool IMP>
+static cudaError_t fwd_cull(cudaStream_t st, int num_sms, const BlendArgs& a, const FwdOut& o) {
   cudaError_t e = cudaSuccess;
-  if (o.imp_w) {
-    int grid = cull_grid(k_blend_fwd_cull<true>, num_sms, a.n_tiles, e);
-    if (e != cudaSuccess) return e;
-    if (grid > 0) k_blend_fwd_cull<true><<<grid, 32, 0, st>>>(a, o);
-  } else {
-    int grid = cull_grid(k_blend_fwd_cull<false>, num_sms, a.n_tiles, e);
-    if (e != cudaSuccess) return e;
-    if (grid > 0) k_blend_fwd_cull<false><<<grid, 32, 0, st>>>(a, o);
-  }
+  int grid = cull_grid(k_blend_fwd_cull<NG, IMP>, num_sms, a.n_tiles * (NG_TILE / NG), e);
+  if (e != cudaSuccess) return e;
+  if (grid > 0) k_blend_fwd_cull<NG, IMP><<<grid, 32, 0, st>>>(a, o);
   count_launches(1);
   return cudaGetLastError();
 }
 
-template <bool L1, bool IMP>
+cudaError_t launch_blend_fwd_cull(cudaStream_t st, int num_sms, int blocks_per_warp, const BlendArgs& a,
+                                  const FwdOut& o) {
+  const bool imp = o.imp_w != nullptr;
+  if (blocks_per_warp == 4) return imp ? fwd_cull<4, true>(st, num_sms, a, o) : fwd_cull<4, false>(st, num_sms, a, o);
+  return imp ? fwd_cull<8, true>(st, num_sms, a, o) : fwd_cull<8, false>(st, num_sms, a, o);
+}
+
+template <int NG, bool L1, bool IMP>
 static cudaError_t bwd_cull(cudaStream_t st, int num_sms, const BlendArgs& a, const BwdIn& in) {
   cudaError_t e = cudaSuccess;
-  int grid = cull_grid(k_blend_bwd_cull<L1, IMP>, num_sms, a.n_tiles, e);
+  int grid = cull_grid(k_blend_bwd_cull<NG, L1, IMP>, num_sms, a.n_tiles * (NG_TILE / NG), e);
   if (e != cudaSuccess) return e;
-  if (grid > 0) k_blend_bwd_cull<L1, IMP><<<grid, 32, 0, st>>>(a, in);
+  if (grid > 0) k_blend_bwd_cull<NG, L1, IMP><<<grid, 32, 0, st>>>(a, in);
   count_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_blend_bwd_cull(cudaStream_t st, int num_sms, const BlendArgs& a, const BwdIn& in) {
+template <int NG>
+static cudaError_t bwd_cull_dispatch(cudaStream_t st, int num_sms, const BlendArgs& a, const BwdIn& in) {
   const bool l1 = in.target != nullptr, imp = in.imp_w != nullptr;
-  if (l1) return imp ? bwd_cull<true, true>(st, num_sms, a, in) : bwd_cull<true, false>(st, num_sms, a, in);
-  return imp ? bwd_cull<false, true>(st, num_sms, a, in) : bwd_cull<false, false>(st, num_sms, a, in);
+  if (l1) return imp ? bwd_cull<NG, true, true>(st, num_sms, a, in) : bwd_cull<NG, true, false>(st, num_sms, a, in);
+  return imp ? bwd_cull<NG, false, true>(st, num_sms, a, in) : bwd_cull<NG, false, false>(st, num_sms, a, in);
+}
+
+cudaError_t launch_blend_bwd_cull(cudaStream_t st, int num_sms, int blocks_per_warp, const BlendArgs& a,
+                                  const BwdIn& in) {
+  if (blocks_per_warp == 4) return bwd_cull_dispatch<4>(st, num_sms, a, in);
+  return bwd_cull_dispatch<8>(st, num_sms, a, in);
 }
 
 }  // namespace airgs
