@@ -253,7 +253,7 @@ def run_ours(args):
     n_frames = args.warmup + args.steps
     wl = Workload(n_frames, device)
     stream = torch.cuda.Stream()
-    rast = Rasterizer(RasterConfig(blend_variant=args.variant), stream=stream)
+    rast = Rasterizer(RasterConfig(blend_variant=args.variant, sort_mode=args.sort_mode), stream=stream)
     p = wl.params
     with torch.cuda.stream(stream):
         rast.set_anchor(p["means"], p["log_scales"], p["quats"], p["opacity_logit"], p["sh"])
@@ -444,6 +444,7 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--autotune", action="store_true", help="time every blend variant first and keep the fastest")
     ap.add_argument("--variant", type=int, default=-1, help="blend kernel variant (-1: autotuned choice or default)")
+    ap.add_argument("--sort-mode", type=int, default=-1, help="-1/0: global radix ordering; 1: per-tile ordering when lists fit")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -74,6 +74,8 @@ typedef struct {
   float T_min;     /* 1e-4 */
   float bg[3];     /* background colour, added as T_final * bg (black) */
   int blend_variant;          /* -1: autotuned per workload, else a fixed kernel variant */
+  int sort_mode;              /* -1 or 0: global two-stage radix ordering; 1: per-tile ordering
+                                 (lists sorted in shared memory) when every list fits one CTA */
   const char* autotune_cache; /* nullable path of a text cache of autotune choices */
 } airgs_config;
 

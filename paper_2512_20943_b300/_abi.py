@@ -39,6 +39,7 @@ class airgs_config(ctypes.Structure):
         ("T_min", ctypes.c_float),
         ("bg", ctypes.c_float * 3),
         ("blend_variant", ctypes.c_int),
+        ("sort_mode", ctypes.c_int),
         ("autotune_cache", ctypes.c_char_p),
     ]
 

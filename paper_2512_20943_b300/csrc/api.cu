@@ -240,7 +240,7 @@ int choose_variant(airgs_ctx* ctx, int64_t n, int64_t pixels, int views) {
   if (ctx->cfg.blend_variant >= 0 && ctx->cfg.blend_variant < blend_variant_count()) return ctx->cfg.blend_variant;
   auto it = ctx->tuned.find(tune_key(n, pixels, views));
   if (it != ctx->tuned.end()) return it->second;
-  return 4;  // warp-per-tile with block culling unless tuned otherwise
+  return 5;  // half-tile warps with block culling unless tuned otherwise
 }
 
 // Forward pipeline: project -> depth sort -> emit -> tile sort -> ranges -> blend.
@@ -315,69 +315,121 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
 
   int64_t n_inst = 0;
   if (N > 0) {
-    uint32_t *dkeys, *tiles, *keys_b, *vals_a, *vals_b, *counts_sorted, *rs_scratch;
-    uint64_t* chunk;
+    uint32_t *dkeys, *tiles, *tile_counts = nullptr;
     TALLOC(dkeys, V * N);
     TALLOC(tiles, V * N);
-    TALLOC(keys_b, V * N);
-    TALLOC(vals_a, V * N);
-    TALLOC(vals_b, V * N);
-    TALLOC(counts_sorted, V * N);
-    TALLOC(rs_scratch, radix_scratch_bytes(N, n_views, ctx->num_sms) / sizeof(uint32_t) + 1);
-    int64_t n_chunks = (V * N + 1023) / 1024;
-    TALLOC(chunk, n_chunks + 1);
-    {
-    StageScope sc(ctx, ST_PROJECT);
-    CK(launch_project(st, N, g->sh_degree, g->means, g->log_scales, g->quats, g->opacity_logit, g->sh, s->d_cams,
-                      n_views, rp, s->proj, dkeys, tiles));
+    const bool per_tile = ctx->cfg.sort_mode == 1;
+    if (per_tile) {
+      TALLOC(tile_counts, s->n_tiles);
+      CK(cudaMemsetAsync(tile_counts, 0, s->n_tiles * sizeof(uint32_t), st));
     }
-    bool in_b = false;
     {
-      StageScope sc(ctx, ST_DEPTH_SORT);
-      CK(radix_sort_pairs(st, ctx->num_sms, dkeys, vals_a, keys_b, vals_b, N, n_views, 32, true, rs_scratch, &in_b));
+      StageScope sc(ctx, ST_PROJECT);
+      CK(launch_project(st, N, g->sh_degree, g->means, g->log_scales, g->quats, g->opacity_logit, g->sh, s->d_cams,
+                        n_views, rp, s->proj, dkeys, tiles, tile_counts));
     }
-    const uint32_t* order = in_b ? vals_b : vals_a;
-    int64_t nc2 = 0;
-    {
-      StageScope sc(ctx, ST_EMIT);
-      CK(launch_count_gather(st, V * N, N, order, tiles, counts_sorted, chunk, &nc2));
-      CK(launch_scan_spans(st, chunk, nc2, chunk + n_chunks));
-    }
-    CK(cudaMemcpyAsync(ctx->h_pinned, chunk + n_chunks, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    n_inst = (int64_t)ctx->h_pinned[0];
-    if (n_inst >= (int64_t)0xFFFFFFFFll)
-      return fail(ctx, AIRGS_E_CAPACITY, "%lld tile instances exceed the 32-bit list limit", (long long)n_inst);
-    s->n_inst = n_inst;
-    if (n_inst > 0) {
-      uint32_t *ikeys_a, *ikeys_b, *ivals_b, *ivals_a, *rs2;
-      TALLOC(ikeys_a, n_inst);
-      TALLOC(ikeys_b, n_inst);
-      TALLOC(ivals_b, n_inst);
-      ALLOC(ivals_a, n_inst);  // may end up holding the sorted values
-      TALLOC(rs2, radix_scratch_bytes(n_inst, 1, ctx->num_sms) / sizeof(uint32_t) + 1);
+    bool use_radix = !per_tile;
+    if (per_tile) {
+      // per-tile lists: offsets from the counts, scatter, sort each list in shared memory
+      const int64_t chunks = (int64_t)tile_offsets_chunks(s->n_tiles);
+      uint64_t* csum;
+      uint32_t *cursor, *big_list, *info;
+      TALLOC(csum, chunks + 1);
+      TALLOC(cursor, s->n_tiles);
+      TALLOC(big_list, s->n_tiles);
+      TALLOC(info, 4);
+      CK(cudaMemsetAsync(info, 0, 4 * sizeof(uint32_t), st));
       {
         StageScope sc(ctx, ST_EMIT);
-        CK(launch_emit(st, V * N, N, order, counts_sorted, chunk, s->proj, s->d_cams, ikeys_a, ivals_a));
+        CK(launch_tile_offsets(st, tile_counts, s->n_tiles, csum, s->ranges, cursor, big_list, info));
       }
-      bool in_b2 = false;
+      CK(cudaMemcpyAsync(ctx->h_pinned, csum + chunks, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(ctx->h_pinned + 1, info, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      n_inst = (int64_t)ctx->h_pinned[0];
+      const uint32_t longest = (uint32_t)(ctx->h_pinned[1] & 0xFFFFFFFFu);
+      const int64_t n_big = (int64_t)(ctx->h_pinned[1] >> 32);
+      if (n_inst >= (int64_t)0xFFFFFFFFll)
+        return fail(ctx, AIRGS_E_CAPACITY, "%lld tile instances exceed the 32-bit list limit", (long long)n_inst);
+      s->n_inst = n_inst;
+      if (longest > (uint32_t)kTileSortBig) {
+        use_radix = true;  // a list too long for one CTA: order globally instead
+        CK(cudaMemsetAsync(s->ranges, 0, s->n_tiles * sizeof(uint2), st));
+      } else if (n_inst > 0) {
+        uint2* ipairs;
+        uint32_t* ivals;
+        TALLOC(ipairs, n_inst);
+        ALLOC(ivals, n_inst);
+        {
+          StageScope sc(ctx, ST_EMIT);
+          CK(launch_scatter(st, V * N, N, s->proj, s->d_cams, dkeys, cursor, ipairs));
+        }
+        {
+          StageScope sc(ctx, ST_TILE_SORT);
+          CK(launch_sort_tiles(st, s->n_tiles, s->ranges, big_list, n_big, ipairs, ivals));
+        }
+        s->ids = ivals;
+      }
+    }
+    if (use_radix) {
+      uint32_t *keys_b, *vals_a, *vals_b, *counts_sorted, *rs_scratch;
+      uint64_t* chunk;
+      TALLOC(keys_b, V * N);
+      TALLOC(vals_a, V * N);
+      TALLOC(vals_b, V * N);
+      TALLOC(counts_sorted, V * N);
+      TALLOC(rs_scratch, radix_scratch_bytes(N, n_views, ctx->num_sms) / sizeof(uint32_t) + 1);
+      int64_t n_chunks = (V * N + 1023) / 1024;
+      TALLOC(chunk, n_chunks + 1);
+      bool in_b = false;
       {
-        StageScope sc(ctx, ST_TILE_SORT);
-        CK(radix_sort_pairs(st, ctx->num_sms, ikeys_a, ivals_a, ikeys_b, ivals_b, n_inst, 1, bits_for(s->n_tiles),
-                            false, rs2, &in_b2));
+        StageScope sc(ctx, ST_DEPTH_SORT);
+        CK(radix_sort_pairs(st, ctx->num_sms, dkeys, vals_a, keys_b, vals_b, N, n_views, 32, true, rs_scratch,
+                            &in_b));
       }
-      const uint32_t* skeys = in_b2 ? ikeys_b : ikeys_a;
-      if (in_b2) {
-        // keep the sorted values: move ivals_b into the state, ivals_a to the temporaries
-        s->owned.back() = ivals_b;
-        tmp.erase(std::find(tmp.begin(), tmp.end(), (void*)ivals_b));
-        tmp.push_back(ivals_a);
-        s->ids = ivals_b;
-      } else {
-        s->ids = ivals_a;
+      const uint32_t* order = in_b ? vals_b : vals_a;
+      int64_t nc2 = 0;
+      {
+        StageScope sc(ctx, ST_EMIT);
+        CK(launch_count_gather(st, V * N, N, order, tiles, counts_sorted, chunk, &nc2));
+        CK(launch_scan_spans(st, chunk, nc2, chunk + n_chunks));
       }
-      StageScope sc(ctx, ST_RANGES);
-      CK(launch_tile_ranges(st, n_inst, skeys, s->ranges));
+      CK(cudaMemcpyAsync(ctx->h_pinned, chunk + n_chunks, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      n_inst = (int64_t)ctx->h_pinned[0];
+      if (n_inst >= (int64_t)0xFFFFFFFFll)
+        return fail(ctx, AIRGS_E_CAPACITY, "%lld tile instances exceed the 32-bit list limit", (long long)n_inst);
+      s->n_inst = n_inst;
+      if (n_inst > 0) {
+        uint32_t *ikeys_a, *ikeys_b, *ivals_b, *ivals_a, *rs2;
+        TALLOC(ikeys_a, n_inst);
+        TALLOC(ikeys_b, n_inst);
+        TALLOC(ivals_b, n_inst);
+        ALLOC(ivals_a, n_inst);  // may end up holding the sorted values
+        TALLOC(rs2, radix_scratch_bytes(n_inst, 1, ctx->num_sms) / sizeof(uint32_t) + 1);
+        {
+          StageScope sc(ctx, ST_EMIT);
+          CK(launch_emit(st, V * N, N, order, counts_sorted, chunk, s->proj, s->d_cams, ikeys_a, ivals_a));
+        }
+        bool in_b2 = false;
+        {
+          StageScope sc(ctx, ST_TILE_SORT);
+          CK(radix_sort_pairs(st, ctx->num_sms, ikeys_a, ivals_a, ikeys_b, ivals_b, n_inst, 1,
+                              bits_for(s->n_tiles), false, rs2, &in_b2));
+        }
+        const uint32_t* skeys = in_b2 ? ikeys_b : ikeys_a;
+        if (in_b2) {
+          // keep the sorted values: move ivals_b into the state, ivals_a to the temporaries
+          s->owned.back() = ivals_b;
+          tmp.erase(std::find(tmp.begin(), tmp.end(), (void*)ivals_b));
+          tmp.push_back(ivals_a);
+          s->ids = ivals_b;
+        } else {
+          s->ids = ivals_a;
+        }
+        StageScope sc(ctx, ST_RANGES);
+        CK(launch_tile_ranges(st, n_inst, skeys, s->ranges));
+      }
     }
   }
 
@@ -523,6 +575,7 @@ void airgs_default_config(airgs_config* c) {
   c->T_min = 1e-4f;
   c->bg[0] = c->bg[1] = c->bg[2] = 0.f;
   c->blend_variant = -1;
+  c->sort_mode = -1;
   c->autotune_cache = nullptr;
 }
 

@@ -20,7 +20,18 @@ cudaError_t launch_decode_apply(cudaStream_t st, int64_t n, const uint16_t* map,
 cudaError_t launch_project(cudaStream_t st, int64_t n, int sh_degree, const float* means, const float* log_scales,
                            const float* quats, const float* opacity_logit, const float* sh, const CamDev* cams,
                            int n_views, const RasterParams& rp, ProjRec* proj, uint32_t* depth_keys,
-                           uint32_t* tiles_touched);
+                           uint32_t* tiles_touched, uint32_t* tile_counts);
+
+// Per-tile ordering (order.cu).
+constexpr int kTileSortSmall = 2048;  // entries sorted by one 256-thread CTA
+constexpr int kTileSortBig = 16384;   // entries sorted by one 1024-thread CTA
+cudaError_t launch_tile_offsets(cudaStream_t st, const uint32_t* counts, int64_t n_tiles, uint64_t* chunk_sums,
+                                uint2* ranges, uint32_t* cursor, uint32_t* big_list, uint32_t* info);
+size_t tile_offsets_chunks(int64_t n_tiles);
+cudaError_t launch_scatter(cudaStream_t st, int64_t total, int64_t n, const ProjRec* proj, const CamDev* cams,
+                           const uint32_t* depth_keys, uint32_t* cursor, uint2* pairs);
+cudaError_t launch_sort_tiles(cudaStream_t st, int64_t n_tiles, const uint2* ranges, const uint32_t* big_list,
+                              int64_t n_big, const uint2* pairs, uint32_t* vals);
 
 size_t radix_scratch_bytes(int64_t seg_len, int n_seg, int num_sms);
 cudaError_t radix_sort_pairs(cudaStream_t st, int num_sms, uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b,

@@ -107,7 +107,8 @@ __global__ void __launch_bounds__(128) k_project(int64_t n, const float* __restr
                                                  const float* __restrict__ sh, const CamDev* __restrict__ cams,
                                                  int n_views, RasterParams rp, ProjRec* __restrict__ proj,
                                                  uint32_t* __restrict__ depth_keys,
-                                                 uint32_t* __restrict__ tiles_touched) {
+                                                 uint32_t* __restrict__ tiles_touched,
+                                                 uint32_t* __restrict__ tile_counts) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -194,6 +195,11 @@ __global__ void __launch_bounds__(128) k_project(int64_t n, const float* __restr
         tile_rect(mx, my, radius, cam.TW, cam.TH, x0, y0, x1, y1);
         if (x0 < x1 && y0 < y1) {
           ntiles = (uint32_t)((x1 - x0) * (y1 - y0));
+          if (tile_counts) {  // per-tile list lengths for the per-tile ordering
+            uint32_t* tc = tile_counts + cam.tile_base;
+            for (int ty = y0; ty < y1; ++ty)
+              for (int tx = x0; tx < x1; ++tx) atomicAdd(tc + ty * cam.TW + tx, 1u);
+          }
           dkey = __float_as_uint(tz);
           flags |= kFlagVisible;
           a2 = -0.5f * kLog2e * A;
@@ -231,25 +237,25 @@ cudaError_t launch_decode_apply(cudaStream_t st, int64_t n, const uint16_t* map,
 cudaError_t launch_project(cudaStream_t st, int64_t n, int sh_degree, const float* means, const float* log_scales,
                            const float* quats, const float* opacity_logit, const float* sh, const CamDev* cams,
                            int n_views, const RasterParams& rp, ProjRec* proj, uint32_t* depth_keys,
-                           uint32_t* tiles_touched) {
+                           uint32_t* tiles_touched, uint32_t* tile_counts) {
   if (n == 0) return cudaSuccess;
   int blocks = (int)((n + 127) / 128);
   switch (sh_degree) {
     case 0:
       k_project<0><<<blocks, 128, 0, st>>>(n, means, log_scales, quats, opacity_logit, sh, cams, n_views, rp, proj,
-                                           depth_keys, tiles_touched);
+                                           depth_keys, tiles_touched, tile_counts);
       break;
     case 1:
       k_project<1><<<blocks, 128, 0, st>>>(n, means, log_scales, quats, opacity_logit, sh, cams, n_views, rp, proj,
-                                           depth_keys, tiles_touched);
+                                           depth_keys, tiles_touched, tile_counts);
       break;
     case 2:
       k_project<2><<<blocks, 128, 0, st>>>(n, means, log_scales, quats, opacity_logit, sh, cams, n_views, rp, proj,
-                                           depth_keys, tiles_touched);
+                                           depth_keys, tiles_touched, tile_counts);
       break;
     default:
       k_project<3><<<blocks, 128, 0, st>>>(n, means, log_scales, quats, opacity_logit, sh, cams, n_views, rp, proj,
-                                           depth_keys, tiles_touched);
+                                           depth_keys, tiles_touched, tile_counts);
       break;
   }
   count_launches(1);

@@ -13,7 +13,7 @@
 // The radix sort is reduce-then-scan, 8-bit digits: k_rs_upsweep counts digits
 // per CTA, k_rs_spine scans the counts of each segment (digit-major, so each
 // CTA's run of a digit lands after the previous CTAs' runs: stability), and
-// k_rs_downsweep ranks each 4096-key tile stably in shared memory (warp
+// k_rs_downsweep ranks each 2048-key tile stably in shared memory (warp
 // match/popc per 32-key round) and writes it out digit-contiguously, which
 // keeps the global writes coalesced.
 #include "airgs_internal.cuh"
@@ -23,14 +23,14 @@ namespace airgs {
 
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
-constexpr int RS_ITEMS = 16;  // keys per thread per tile
+constexpr int RS_ITEMS = 8;   // keys per thread per tile
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 constexpr int RS_RADIX = 256;
 
 struct SortGeom {
   int64_t seg_len;    // keys per segment
   int n_seg;          // segments (views), each sorted independently
-  int64_t tiles_seg;  // 4096-key tiles per segment
+  int64_t tiles_seg;  // RS_TILE-key tiles per segment
   int ctas_seg;       // CTAs per segment
   int64_t tiles_cta;  // tiles handled by one CTA (contiguous)
 };
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(const uint32_t* __r
     for (int k = tid; k < RS_WARPS * RS_RADIX; k += RS_THREADS) (&s_warp_cnt[0][0])[k] = 0;
     __syncthreads();
 
-    // warp w ranks tile positions [w*512, w*512 + 512), 32 per round, in order
+    // warp w ranks tile positions [w*256, w*256 + 256), 32 per round, in order
     uint32_t key[RS_ITEMS], val[RS_ITEMS], rank[RS_ITEMS];
 #pragma unroll
     for (int j = 0; j < RS_ITEMS; ++j) {

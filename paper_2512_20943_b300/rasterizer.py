@@ -33,6 +33,7 @@ class RasterConfig:
     T_min: float = 1e-4
     bg: tuple = (0.0, 0.0, 0.0)
     blend_variant: int = -1  # -1: autotuned choice (default variant until tuned)
+    sort_mode: int = -1      # -1/0: global radix ordering; 1: per-tile ordering when lists fit a CTA
     autotune_cache: str | None = None
 
     def to_c(self):
@@ -41,6 +42,7 @@ class RasterConfig:
         for k in range(3):
             c.bg[k] = float(self.bg[k])
         c.blend_variant = int(self.blend_variant)
+        c.sort_mode = int(self.sort_mode)
         c.autotune_cache = self.autotune_cache.encode() if self.autotune_cache else None
         return c
 

@@ -71,10 +71,24 @@ def test_projection_matches_oracle(rast, name):
     res.state.release()
 
 
+_by_sort = {}
+
+
+def rast_sort(mode):
+    """A context pinned to an ordering path: 1 per-tile lists sorted in shared
+    memory, 0 the global two-stage radix ordering (default)."""
+    from paper_2512_20943_b300 import RasterConfig, Rasterizer
+    if mode not in _by_sort:
+        _by_sort[mode] = Rasterizer(RasterConfig(sort_mode=mode))
+    return _by_sort[mode]
+
+
+@pytest.mark.parametrize("sort_mode", [1, 0])
 @pytest.mark.parametrize("name", ["plain_2k", "sh3_ragged"])
-def test_tile_lists_bit_exact(rast, name):
+def test_tile_lists_bit_exact(name, sort_mode):
     """The GPU's binning and stable (tile, depth, index) ordering equal the
     oracle's when the oracle is given the GPU's own centres, radii and depths."""
+    rast = rast_sort(sort_mode)
     g, cams = scenes()[name]
     t, res = render_gpu(rast, g, cams, save=True)
     for v, cam in enumerate(cams):
@@ -301,3 +315,27 @@ def test_variants_agree_bitwise_forward():
     imgs = [render_gpu(rast_variant(v), g, cams)[1].rgb for v in VARIANTS]
     for im in imgs[1:]:
         assert torch.equal(im, imgs[0])
+
+
+@pytest.mark.parametrize("n", [5000, 20000])
+def test_long_tile_lists(n):
+    """Lists longer than one 256-thread CTA sorts (5000 entries: the 1024-thread
+    path) and longer than one CTA can hold (20000: the global radix fallback)
+    are ordered exactly like the oracle's."""
+    rng = np.random.default_rng(n)
+    g = synthetic.gaussians(n, n, mean_mode="uniform", mean_scale=(0.02, 0.02, 1.0), log_scale=(-4.5, 0.3),
+                            sh_degree=0, rgb_dc=True)
+    g["opacity_logit"][:] = -3.0  # faint, so pixels do not stop early
+    cams = [synthetic.camera((0, 0, -4.0), 32, 32, fx=32.0)]
+    rast = rast_sort(1)
+    t, res = render_gpu(rast, g, cams, save=True)
+    m2, d, r = (x.cpu().numpy() for x in rast.state_projection(res.state, 0))
+    ranges, ids = (x.cpu().numpy() for x in rast.state_tile_lists(res.state, 0))
+    ref_ranges, ref_ids = oracle.bin_sort(m2.astype(np.float64), r, d.astype(np.float64), r > 0, 32, 32)
+    assert (ranges[:, 1] - ranges[:, 0]).max() > (4096 if n > 10000 else 2048)
+    assert np.array_equal(ranges, ref_ranges)
+    assert np.array_equal(ids, ref_ids)
+    ref = oracle.render(synthetic.widen(g), cams)
+    ok = ~ref["ambig"][0]
+    assert np.abs(views_np(res.rgb, cams)[0] - ref["rgb"][0])[:, ok].max() < RGB_ATOL
+    res.state.release()
