@@ -109,6 +109,47 @@ __device__ __forceinline__ int view_of_tile(const int64_t* tile_base, int n_view
   return lo;
 }
 
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Axis-aligned half-widths of the region where a Gaussian can blend
+// (o G >= alpha_min):  Q(d) = -log2(e) power(d) = d^T M d <= L = log2(o/alpha_min),
+// half-widths sqrt(L (M^-1)_xx), sqrt(L (M^-1)_yy), widened by a margin far above
+// the single-precision error of the per-pair test.  Returns 0 if the Gaussian
+// can never blend, 1 with (hx, hy) set, 2 if no bound applies (degenerate or NaN).
+__device__ __forceinline__ int alpha_box(float4 ga, float4 gb, float log2_amin, float& hx, float& hy) {
+  const float ap = -ga.z, bp = -ga.w, cp = -gb.x;  // Q = ap dx^2 + bp dx dy + cp dy^2
+  const float L = lg2_approx(gb.y) - log2_amin + 1e-3f;
+  if (L <= 0.f) return 0;
+  if (!(L > 0.f)) return 2;
+  const float det = ap * cp - 0.25f * bp * bp;
+  if (!(det > 0.f)) return 2;
+  hx = sqrtf(L * cp / det) * 1.0001f + 0.01f;
+  hy = sqrtf(L * ap / det) * 1.0001f + 0.01f;
+  return 1;
+}
+
+// Instance keys carry the global tile id in the low bits and, in bits 30-31,
+// whether the Gaussian can blend in the tile's top / bottom 16x8 half; the
+// tile sort orders by the low bits only.
+constexpr uint32_t kKeyTileMask = 0x3FFFFFFFu;
+constexpr int kKeyHalfShift = 30;
+
+// Halves (bit 0 top, bit 1 bottom) of the tile at (X0, Y0) that a Gaussian's
+// alpha >= alpha_min box meets; (kind, hx, hy) come from alpha_box.
+__device__ __forceinline__ uint32_t half_flags_of(float4 ga, int kind, float hx, float hy, float X0, float Y0) {
+  if (kind == 0) return 0u;
+  if (kind == 2) return 3u;
+  if (!(ga.x + hx >= X0 + 0.5f && ga.x - hx <= X0 + 15.5f)) return 0u;
+  uint32_t f = 0;
+  if (ga.y + hy >= Y0 + 0.5f && ga.y - hy <= Y0 + 7.5f) f |= 1u;
+  if (ga.y + hy >= Y0 + 8.5f && ga.y - hy <= Y0 + 15.5f) f |= 2u;
+  return f;
+}
+
 __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
                : "memory");

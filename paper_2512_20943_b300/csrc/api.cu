@@ -74,6 +74,8 @@ struct airgs_state {
   uint32_t* ids = nullptr;     // sorted instance values
   uint2* ranges = nullptr;     // [tiles]
   int32_t* ncontrib = nullptr; // [pixels]
+  uint2* hl = nullptr;         // half-tile lists (variant with half-tile warps), nullable
+  uint2* hranges = nullptr;    // [2][tiles]
   int* work = nullptr;         // [2] work counters (forward, backward)
   unsigned long long* pairs = nullptr;  // [2] pair counters (forward, backward)
   const float* rgb = nullptr;  // caller's forward output
@@ -164,7 +166,7 @@ int build_cams(airgs_ctx* ctx, const airgs_camera* cams, int n_views, std::vecto
     n_tiles += (int64_t)d.TW * d.TH;
     n_pixels += (int64_t)c.width * c.height;
   }
-  if (n_tiles >= (1ll << 31)) return fail(ctx, AIRGS_E_CAPACITY, "too many tiles (%lld)", (long long)n_tiles);
+  if (n_tiles >= (1ll << 30)) return fail(ctx, AIRGS_E_CAPACITY, "too many tiles (%lld)", (long long)n_tiles);
   return AIRGS_OK;
 }
 
@@ -409,7 +411,8 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
         TALLOC(rs2, radix_scratch_bytes(n_inst, 1, ctx->num_sms) / sizeof(uint32_t) + 1);
         {
           StageScope sc(ctx, ST_EMIT);
-          CK(launch_emit(st, V * N, N, order, counts_sorted, chunk, s->proj, s->d_cams, ikeys_a, ivals_a));
+          CK(launch_emit(st, V * N, N, order, counts_sorted, chunk, s->proj, s->d_cams, ctx->cfg.alpha_min, s->n_tiles,
+                         ikeys_a, ivals_a));
         }
         bool in_b2 = false;
         {
@@ -427,8 +430,24 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
         } else {
           s->ids = ivals_a;
         }
-        StageScope sc(ctx, ST_RANGES);
-        CK(launch_tile_ranges(st, n_inst, skeys, s->ranges));
+        {
+          StageScope sc(ctx, ST_RANGES);
+          CK(launch_tile_ranges(st, n_inst, skeys, s->ranges));
+        }
+        if (s->variant == 5) {
+          // compacted half-tile lists for the half-tile culling kernels
+          const int64_t hchunks = (int64_t)half_list_chunks(n_inst);
+          uint8_t* hflags;
+          uint64_t* hsums;
+          TALLOC(hflags, n_inst);
+          TALLOC(hsums, 2 * (hchunks + 1));
+          ALLOC(s->hl, 2 * n_inst);
+          ALLOC(s->hranges, 2 * s->n_tiles);
+          CK(cudaMemsetAsync(s->hranges, 0, 2 * s->n_tiles * sizeof(uint2), st));
+          StageScope sc(ctx, ST_RANGES);
+          CK(launch_half_lists(st, skeys, s->ids, s->ranges, s->d_cams, n_views, s->proj, N, n_inst,
+                               ctx->cfg.alpha_min, s->n_tiles, hflags, hsums, s->hl, s->hranges));
+        }
       }
     }
   }
@@ -446,6 +465,8 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
   a.pair_counter = s->pairs;
   a.pair_total = ctx->profiling ? ctx->d_pair_total : nullptr;
   a.exec_total = ctx->profiling ? ctx->d_pair_total + 2 : nullptr;
+  a.hl = s->hl;
+  a.hranges = s->hranges;
   FwdOut o;
   o.rgb = rgb_out;
   o.T = T_out;
@@ -503,6 +524,8 @@ int backward_impl(airgs_ctx* ctx, airgs_state* s, const float* dL, const float* 
   a.pair_counter = s->pairs + 1;
   a.pair_total = ctx->profiling ? ctx->d_pair_total + 1 : nullptr;
   a.exec_total = ctx->profiling ? ctx->d_pair_total + 3 : nullptr;
+  a.hl = s->hl;
+  a.hranges = s->hranges;
   BwdIn in;
   in.rgb = s->rgb;
   in.dL = dL;

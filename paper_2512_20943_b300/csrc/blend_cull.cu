@@ -36,24 +36,14 @@ __device__ __forceinline__ int cull_fetch(int* counter) {
   return __shfl_sync(kAll, it, 0);
 }
 
-__device__ __forceinline__ float lg2_approx(float x) {
-  float y;
-  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
 // Blocks of the tile at (X0, Y0) that the Gaussian's alpha >= alpha_min box
 // meets (bit k: block bx = k & 1, by = k >> 1).
 __device__ __forceinline__ unsigned block_mask(float4 ga, float4 gb, float log2_amin, float X0, float Y0) {
   const float mx = ga.x, my = ga.y;
-  const float ap = -ga.z, bp = -ga.w, cp = -gb.x;  // Q = ap dx^2 + bp dx dy + cp dy^2
-  const float L = lg2_approx(gb.y) - log2_amin + 1e-3f;
-  if (L <= 0.f) return 0u;        // o below alpha_min: never blends
-  if (!(L > 0.f)) return 0xFFu;   // NaN opacity: leave it to the per-pair test
-  const float det = ap * cp - 0.25f * bp * bp;
-  if (!(det > 0.f)) return 0xFFu; // degenerate conic: no culling
-  const float hx = sqrtf(L * cp / det) * 1.0001f + 0.01f;
-  const float hy = sqrtf(L * ap / det) * 1.0001f + 0.01f;
+  float hx = 0.f, hy = 0.f;
+  const int kind = alpha_box(ga, gb, log2_amin, hx, hy);
+  if (kind == 0) return 0u;     // o below alpha_min: never blends
+  if (kind == 2) return 0xFFu;  // no bound: leave it to the per-pair test
   unsigned xm = 0, m = 0;
 #pragma unroll
   for (int bx = 0; bx < 2; ++bx) {
@@ -78,6 +68,7 @@ __global__ void __launch_bounds__(32) k_blend_fwd_cull(BlendArgs a, FwdOut out) 
   __shared__ float4 s_b[CBATCH];
   __shared__ float s_c[CBATCH];
   __shared__ uint32_t s_id[CBATCH];
+  __shared__ uint32_t s_pos[CBATCH];  // position in the tile's full list
   __shared__ unsigned s_mask[CBATCH];
   __shared__ int64_t s_tile_base[AIRGS_MAX_VIEWS_DEV];
 
@@ -111,28 +102,39 @@ __global__ void __launch_bounds__(32) k_blend_fwd_cull(BlendArgs a, FwdOut out) 
       stop_at[k] = -1;
     }
     const uint2 range = a.ranges[item];
+    const bool use_hl = PARTS > 1 && a.hl != nullptr;  // this half's compacted list
+    uint2 er = range;
+    if (use_hl) er = a.hranges[(int64_t)part * a.n_tiles + item];
     const ProjRec* projv = a.proj + (size_t)v * a.n;
     uint32_t exec_groups = 0;
 
-    for (uint32_t b0 = range.x; b0 < range.y; b0 += CBATCH) {
+    for (uint32_t b0 = er.x; b0 < er.y; b0 += CBATCH) {
       unsigned live = 0;
 #pragma unroll
       for (int k = 0; k < NG; ++k)
         if (__any_sync(kAll, !((done >> k) & 1u))) live |= 1u << k;
       if (live == 0) break;
-      const int nb = (int)min((uint32_t)CBATCH, range.y - b0);
+      const int nb = (int)min((uint32_t)CBATCH, er.y - b0);
       for (int j = lane; j < nb; j += 32) {
-        const uint32_t id = __ldg(a.ids + b0 + j);
+        uint32_t id, pos;
+        if (use_hl) {
+          const uint2 en = __ldg(a.hl + b0 + j);
+          id = en.x;
+          pos = en.y;
+        } else {
+          id = __ldg(a.ids + b0 + j);
+          pos = b0 + j - range.x;
+        }
         const ProjRec* r = projv + id;
         const float4 ga = __ldg(&r->a), gb = __ldg(&r->b);
         s_a[j] = ga;
         s_b[j] = gb;
         s_c[j] = __ldg(&r->c.x);
         s_id[j] = id;
+        s_pos[j] = pos;
         s_mask[j] = block_mask(ga, gb, log2_amin, (float)X0, (float)Y0) & ((1u << NG) - 1u);
       }
       __syncwarp();
-      const int pos_base = (int)(b0 - range.x) + 1;
       for (int j = 0; j < nb; ++j) {
         const unsigned m = s_mask[j] & live;
         if (m == 0) continue;
@@ -140,7 +142,7 @@ __global__ void __launch_bounds__(32) k_blend_fwd_cull(BlendArgs a, FwdOut out) 
         const float4 ga = s_a[j];
         const float4 gb = s_b[j];
         const float cb = s_c[j];
-        const int pos1 = pos_base + j;
+        const int pos1 = (int)s_pos[j] + 1;
         const float dxb[2] = {__fsub_rn(ga.x, pxb[0]), __fsub_rn(ga.x, pxb[1])};
         float wsum = 0.f;
         int bcount = 0;
@@ -262,6 +264,7 @@ __global__ void __launch_bounds__(32) k_blend_bwd_cull(BlendArgs a, BwdIn in) {
   __shared__ float4 s_b[CBATCH];
   __shared__ float s_c[CBATCH];
   __shared__ uint32_t s_id[CBATCH];
+  __shared__ uint32_t s_pos[CBATCH];  // position in the tile's full list
   __shared__ unsigned s_mask[CBATCH];
   __shared__ int64_t s_tile_base[AIRGS_MAX_VIEWS_DEV];
 
@@ -322,27 +325,42 @@ __global__ void __launch_bounds__(32) k_blend_bwd_cull(BlendArgs a, BwdIn in) {
 #pragma unroll
     for (int k = 0; k < NG; ++k) maxnc = max(maxnc, gmax[k]);
     const uint2 range = a.ranges[item];
-    const uint32_t end = range.x + (uint32_t)maxnc;
+    const bool use_hl = PARTS > 1 && a.hl != nullptr;  // this half's compacted list
+    uint2 er = make_uint2(range.x, range.x + (uint32_t)maxnc);
+    if (use_hl) er = a.hranges[(int64_t)part * a.n_tiles + item];
     const ProjRec* projv = a.proj + (size_t)v * a.n;
     GradRec* gradv = in.grad + (size_t)v * a.n;
     uint32_t exec_groups = 0;
+    bool past_end = false;
 
-    for (uint32_t b0 = range.x; b0 < end; b0 += CBATCH) {
-      const int nb = (int)min((uint32_t)CBATCH, end - b0);
+    for (uint32_t b0 = er.x; b0 < er.y && !past_end; b0 += CBATCH) {
+      const int nb = (int)min((uint32_t)CBATCH, er.y - b0);
       for (int j = lane; j < nb; j += 32) {
-        const uint32_t id = __ldg(a.ids + b0 + j);
+        uint32_t id, pos;
+        if (use_hl) {
+          const uint2 en = __ldg(a.hl + b0 + j);
+          id = en.x;
+          pos = en.y;
+        } else {
+          id = __ldg(a.ids + b0 + j);
+          pos = b0 + j - range.x;
+        }
         const ProjRec* r = projv + id;
         const float4 ga = __ldg(&r->a), gb = __ldg(&r->b);
         s_a[j] = ga;
         s_b[j] = gb;
         s_c[j] = __ldg(&r->c.x);
         s_id[j] = id;
+        s_pos[j] = pos;
         s_mask[j] = block_mask(ga, gb, log2_amin, (float)X0, (float)Y0) & ((1u << NG) - 1u);
       }
       __syncwarp();
-      const int pos0 = (int)(b0 - range.x);
       for (int j = 0; j < nb; ++j) {
-        const int pos = pos0 + j;
+        const int pos = (int)s_pos[j];
+        if (pos >= maxnc) {  // positions increase along the list
+          past_end = true;
+          break;
+        }
         unsigned live = 0;
 #pragma unroll
         for (int k = 0; k < NG; ++k) live |= (pos < gmax[k] ? 1u : 0u) << k;

@@ -1,0 +1,152 @@
+// Half-tile blend lists (sm_103a).
+//
+// When an instance is emitted it is tested once against the two 16x8 halves of
+// its tile: the Gaussian's alpha >= alpha_min box (the same conservative box the
+// blend kernels use per 8x4 block) either meets a half or cannot blend anywhere
+// in it; the two flags ride in the key's top bits through the tile sort.  Each half gets its own compacted list of
+// (Gaussian id, position in the tile's full list) in the full list's order, so
+// the half-tile blend kernels stage only entries that can matter while still
+// reporting and replaying positions of the definition's list.
+#include "airgs_internal.cuh"
+#include "kernels.h"
+
+namespace airgs {
+
+constexpr int HL_THREADS = 1024;
+constexpr int HL_ITEMS = 4;
+constexpr int HL_CHUNK = HL_THREADS * HL_ITEMS;
+
+size_t half_list_chunks(int64_t n_inst) { return (size_t)((n_inst + HL_CHUNK - 1) / HL_CHUNK); }
+
+// bit 0: the entry can blend in the top half (rows 0-7), bit 1: bottom half;
+// k_emit stored them in the key's top bits.
+__device__ __forceinline__ unsigned half_flags(int64_t p, const uint32_t* __restrict__ keys) {
+  return keys[p] >> kKeyHalfShift;
+}
+
+struct HalfArgs {
+  const uint32_t* keys;  // sorted tile ids
+  const uint32_t* ids;   // sorted Gaussian ids
+  const uint2* ranges;   // full tile ranges
+  const CamDev* cams;
+  int n_views;
+  const ProjRec* proj;
+  int64_t n;
+  int64_t n_inst;
+  float log2_amin;
+};
+
+__global__ void __launch_bounds__(HL_THREADS) k_half_sums(HalfArgs h, uint8_t* __restrict__ flags,
+                                                          uint64_t* __restrict__ sums_top,
+                                                          uint64_t* __restrict__ sums_bot) {
+  __shared__ uint32_t s_t[HL_THREADS / 32], s_b[HL_THREADS / 32];
+  const int64_t c0 = (int64_t)blockIdx.x * HL_CHUNK;
+  uint32_t nt = 0, nb = 0;
+#pragma unroll
+  for (int k = 0; k < HL_ITEMS; ++k) {
+    const int64_t p = c0 + k * HL_THREADS + threadIdx.x;
+    if (p < h.n_inst) {
+      const unsigned f = half_flags(p, h.keys);
+      flags[p] = (uint8_t)f;
+      nt += f & 1u;
+      nb += f >> 1;
+    }
+  }
+  nt = __reduce_add_sync(0xffffffffu, nt);
+  nb = __reduce_add_sync(0xffffffffu, nb);
+  if ((threadIdx.x & 31) == 0) {
+    s_t[threadIdx.x >> 5] = nt;
+    s_b[threadIdx.x >> 5] = nb;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t a = 0, b = 0;
+    for (int w = 0; w < HL_THREADS / 32; ++w) {
+      a += s_t[w];
+      b += s_b[w];
+    }
+    sums_top[blockIdx.x] = a;
+    sums_bot[blockIdx.x] = b;
+  }
+}
+
+// Exclusive block scan of two counters (blocked: thread t owns HL_ITEMS consecutive entries).
+__global__ void __launch_bounds__(HL_THREADS) k_half_compact(HalfArgs h, const uint8_t* __restrict__ flags,
+                                                             const uint64_t* __restrict__ off_top,
+                                                             const uint64_t* __restrict__ off_bot,
+                                                             uint64_t bot_base, uint2* __restrict__ hl,
+                                                             uint2* __restrict__ hranges, int64_t n_tiles) {
+  __shared__ uint32_t s_t[HL_THREADS / 32], s_b[HL_THREADS / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t p0 = (int64_t)blockIdx.x * HL_CHUNK + (int64_t)tid * HL_ITEMS;
+  unsigned f[HL_ITEMS];
+  uint32_t lt = 0, lb = 0;
+#pragma unroll
+  for (int k = 0; k < HL_ITEMS; ++k) {
+    f[k] = (p0 + k < h.n_inst) ? flags[p0 + k] : 0u;
+    lt += f[k] & 1u;
+    lb += f[k] >> 1;
+  }
+  uint32_t xt = lt, xb = lb;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t yt = __shfl_up_sync(0xffffffffu, xt, o), yb = __shfl_up_sync(0xffffffffu, xb, o);
+    if (lane >= o) {
+      xt += yt;
+      xb += yb;
+    }
+  }
+  if (lane == 31) {
+    s_t[warp] = xt;
+    s_b[warp] = xb;
+  }
+  __syncthreads();
+  uint32_t wt = 0, wb = 0;
+  for (int w = 0; w < warp; ++w) {
+    wt += s_t[w];
+    wb += s_b[w];
+  }
+  uint64_t ot = off_top[blockIdx.x] + wt + xt - lt;
+  uint64_t ob = bot_base + off_bot[blockIdx.x] + wb + xb - lb;
+#pragma unroll
+  for (int k = 0; k < HL_ITEMS; ++k) {
+    const int64_t p = p0 + k;
+    if (p >= h.n_inst) break;
+    const uint32_t tile = h.keys[p] & kKeyTileMask;
+    const uint32_t start = h.ranges[tile].x;
+    const uint32_t pos = (uint32_t)(p - start);
+    const bool first = p == start, last = p + 1 == h.ranges[tile].y;
+    const uint32_t gid = h.ids[p];
+    if (first) {
+      hranges[tile].x = (uint32_t)ot;
+      hranges[n_tiles + tile].x = (uint32_t)ob;
+    }
+    if (f[k] & 1u) hl[ot++] = make_uint2(gid, pos);
+    if (f[k] & 2u) hl[ob++] = make_uint2(gid, pos);
+    if (last) {
+      hranges[tile].y = (uint32_t)ot;
+      hranges[n_tiles + tile].y = (uint32_t)ob;
+    }
+  }
+}
+
+cudaError_t launch_half_lists(cudaStream_t st, const uint32_t* keys, const uint32_t* ids, const uint2* ranges,
+                              const CamDev* cams, int n_views, const ProjRec* proj, int64_t n, int64_t n_inst,
+                              float alpha_min, int64_t n_tiles, uint8_t* flags, uint64_t* sums, uint2* hl,
+                              uint2* hranges) {
+  if (n_inst == 0) return cudaSuccess;
+  const int64_t chunks = (int64_t)half_list_chunks(n_inst);
+  HalfArgs h{keys, ids, ranges, cams, n_views, proj, n, n_inst, log2f(alpha_min)};
+  uint64_t* st_ = sums;               // [chunks + 1] top
+  uint64_t* sb_ = sums + chunks + 1;  // [chunks + 1] bottom
+  k_half_sums<<<(unsigned)chunks, HL_THREADS, 0, st>>>(h, flags, st_, sb_);
+  cudaError_t e = launch_scan_spans(st, st_, chunks, st_ + chunks);
+  if (e == cudaSuccess) e = launch_scan_spans(st, sb_, chunks, sb_ + chunks);
+  if (e != cudaSuccess) return e;
+  k_half_compact<<<(unsigned)chunks, HL_THREADS, 0, st>>>(h, flags, st_, sb_, (uint64_t)n_inst, hl, hranges,
+                                                          n_tiles);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+}  // namespace airgs

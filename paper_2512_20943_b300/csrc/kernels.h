@@ -47,8 +47,15 @@ cudaError_t launch_count_gather(cudaStream_t st, int64_t total, int64_t n, const
 cudaError_t launch_scan_spans(cudaStream_t st, uint64_t* sums, int64_t n_chunks, uint64_t* total_out);
 cudaError_t launch_emit(cudaStream_t st, int64_t total, int64_t n, const uint32_t* order,
                         const uint32_t* counts_sorted, const uint64_t* chunk_offsets, const ProjRec* proj,
-                        const CamDev* cams, uint32_t* keys, uint32_t* vals);
+                        const CamDev* cams, float alpha_min, int64_t n_tiles, uint32_t* keys, uint32_t* vals);
 cudaError_t launch_tile_ranges(cudaStream_t st, int64_t n_inst, const uint32_t* keys, uint2* ranges);
+
+// Half-tile blend lists (cull_lists.cu).
+size_t half_list_chunks(int64_t n_inst);
+cudaError_t launch_half_lists(cudaStream_t st, const uint32_t* keys, const uint32_t* ids, const uint2* ranges,
+                              const CamDev* cams, int n_views, const ProjRec* proj, int64_t n, int64_t n_inst,
+                              float alpha_min, int64_t n_tiles, uint8_t* flags, uint64_t* sums, uint2* hl,
+                              uint2* hranges);
 
 struct BlendArgs {
   const ProjRec* proj;  // [V][N]
@@ -63,6 +70,8 @@ struct BlendArgs {
   unsigned long long* pair_counter;
   unsigned long long* pair_total;  // nullable: cumulative counter of the context
   unsigned long long* exec_total;  // nullable: cumulative lane evaluations actually issued (culling variants)
+  const uint2* hl;                 // nullable: half-tile lists of (Gaussian id, full-list position)
+  const uint2* hranges;            // [2][tiles] ranges into hl (top halves, then bottom halves)
 };
 
 struct FwdOut {

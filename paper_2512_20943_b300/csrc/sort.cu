@@ -291,7 +291,8 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(int64_t total, int64_t n, c
                                                     const uint32_t* __restrict__ counts_sorted,
                                                     const uint64_t* __restrict__ chunk_offsets,
                                                     const ProjRec* __restrict__ proj, const CamDev* __restrict__ cams,
-                                                    uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+                                                    float log2_amin, bool with_halves, uint32_t* __restrict__ keys,
+                                                    uint32_t* __restrict__ vals) {
   __shared__ uint64_t s_w[EM_THREADS / 32];
   int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int64_t c0 = (int64_t)blockIdx.x * EM_CHUNK;
@@ -327,9 +328,13 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(int64_t total, int64_t n, c
       int x0, y0, x1, y1;
       tile_rect(rec.a.x, rec.a.y, radius, cam.TW, cam.TH, x0, y0, x1, y1);
       uint32_t tb = (uint32_t)cam.tile_base;
+      float hx = 0.f, hy = 0.f;
+      const int kind = with_halves ? alpha_box(rec.a, rec.b, log2_amin, hx, hy) : 2;
       for (int ty = y0; ty < y1; ++ty)
         for (int tx = x0; tx < x1; ++tx) {
-          keys[off] = tb + (uint32_t)(ty * cam.TW + tx);
+          // with more than 2^24 tiles the sort reaches the top bits: keep them uniform
+          const uint32_t halves = half_flags_of(rec.a, kind, hx, hy, (float)(tx * kTile), (float)(ty * kTile));
+          keys[off] = (tb + (uint32_t)(ty * cam.TW + tx)) | (halves << kKeyHalfShift);
           vals[off] = gid;
           ++off;
         }
@@ -340,9 +345,9 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(int64_t total, int64_t n, c
 __global__ void k_tile_ranges(int64_t n_inst, const uint32_t* __restrict__ keys, uint2* __restrict__ ranges) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n_inst) return;
-  uint32_t k = keys[p];
-  if (p == 0 || keys[p - 1] != k) ranges[k].x = (uint32_t)p;
-  if (p == n_inst - 1 || keys[p + 1] != k) ranges[k].y = (uint32_t)(p + 1);
+  uint32_t k = keys[p] & kKeyTileMask;
+  if (p == 0 || (keys[p - 1] & kKeyTileMask) != k) ranges[k].x = (uint32_t)p;
+  if (p == n_inst - 1 || (keys[p + 1] & kKeyTileMask) != k) ranges[k].y = (uint32_t)(p + 1);
 }
 
 // ------------------------------------------------------------------ host side
@@ -430,11 +435,11 @@ cudaError_t launch_scan_spans(cudaStream_t st, uint64_t* sums, int64_t n_chunks,
 
 cudaError_t launch_emit(cudaStream_t st, int64_t total, int64_t n, const uint32_t* order,
                         const uint32_t* counts_sorted, const uint64_t* chunk_offsets, const ProjRec* proj,
-                        const CamDev* cams, uint32_t* keys, uint32_t* vals) {
+                        const CamDev* cams, float alpha_min, int64_t n_tiles, uint32_t* keys, uint32_t* vals) {
   if (total == 0) return cudaSuccess;
   int64_t n_chunks = (total + EM_CHUNK - 1) / EM_CHUNK;
-  k_emit<<<(unsigned)n_chunks, EM_THREADS, 0, st>>>(total, n, order, counts_sorted, chunk_offsets, proj, cams, keys,
-                                                     vals);
+  k_emit<<<(unsigned)n_chunks, EM_THREADS, 0, st>>>(total, n, order, counts_sorted, chunk_offsets, proj, cams,
+                                                     log2f(alpha_min), n_tiles <= (1ll << 24), keys, vals);
   count_launches(1);
   return cudaGetLastError();
 }
