@@ -388,6 +388,8 @@ def run_ours(args):
     }
     if e2e is not None:
         line["e2e"] = e2e
+    if not args.no_serving and world == 1:
+        line["serving"] = run_serving(args, device)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_line()
     if rank == 0:
@@ -395,6 +397,41 @@ def run_ours(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def run_serving(args, device):
+    """Served-view latency of the continuous-batching engine vs the plain
+    one-view-per-launch loop on the serving workload: 500k-Gaussian SH3 anchor
+    with 30 fps frame updates resident on the device, 64 viewers issuing
+    Poisson requests (30/s each) at 640x480 / 1280x720 / 1920x1080 from poses on
+    a 3 m sphere, admission by a memory budget that binds at peak."""
+    import torch
+    from paper_2512_20943_b300.serving import FrameStream, ServingEngine, make_requests, run_plain_loop, view_bytes
+    n = 500_000
+    g = synthetic.serving_scene(n)
+    anchor = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in g.items() if k != "sh_degree"}
+    maps = []
+    for t in range(30):
+        m, lo, hi = synthetic.update_map(n, 2000 + t, size=MAP_SIZE)
+        maps.append(torch.from_numpy(m.view(np.int16)).to(device).view(torch.uint16))
+    frames = FrameStream(maps, lo, hi, period_s=1.0 / 30.0)
+    stream = synthetic.serving_requests(n_viewers=64, rate_hz=30.0, duration_s=args.serve_seconds, seed=4)
+    budget = 24 * view_bytes(n, dict(width=1920, height=1080))
+    # warm-up: a few batches so that pools and kernels are ready
+    warm = make_requests([(0.0, 0, c) for _, _, c in stream[:16]])
+    ServingEngine(anchor, frames, budget, max_batch_views=64).run(warm, realtime=False)
+    eng = ServingEngine(anchor, frames, budget, max_batch_views=64)
+    st_eng = eng.run(make_requests(stream), realtime=True)
+    st_plain = run_plain_loop(anchor, frames, make_requests(stream), realtime=True)
+    keep = ("n_requests", "completed", "rejected", "p50_ms", "p99_ms", "mean_ms", "views_per_s", "mpix_per_s",
+            "batches", "mean_batch", "peak_bytes", "makespan_s")
+    return {
+        "workload": f"500k Gaussians SH3, 64 viewers x Poisson 30/s for {args.serve_seconds:g} s, sizes 640x480/"
+                    "1280x720/1920x1080, 30 fps frame updates on device, memory budget "
+                    f"{budget / 2**30:.2f} GiB",
+        "continuous_batching": {k: getattr(st_eng, k) for k in keep},
+        "plain_loop": {k: getattr(st_plain, k) for k in keep},
+    }
 
 
 def run_e2e(rast, wl, args, device, stream, imp, world):
@@ -442,6 +479,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=3.0, help="length of the served request stream")
     ap.add_argument("--autotune", action="store_true", help="time every blend variant first and keep the fastest")
     ap.add_argument("--variant", type=int, default=-1, help="blend kernel variant (-1: autotuned choice or default)")
     ap.add_argument("--sort-mode", type=int, default=-1, help="-1/0: global radix ordering; 1: per-tile ordering when lists fit")
