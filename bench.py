@@ -120,6 +120,12 @@ def dist_setup():
     return world, rank, local
 
 
+def whole_job_value(world, px_per_step, steps, max_ms):
+    """Mpix/s of the whole job: the pixels every rank rendered (each rank runs
+    the same per-GPU workload) over the slowest rank's time."""
+    return world * px_per_step * steps / (max_ms / 1e3) / 1e6
+
+
 def barrier_max(world, value, device=None):
     if world == 1:
         return value
@@ -299,7 +305,7 @@ def run_ours(args):
     total_ms = sum(step_ms)
     total_ms = barrier_max(world, total_ms, device)
     px_step = VIEWS_PER_STEP * WIDTH * HEIGHT
-    value = world * px_step * args.steps / (total_ms / 1e3) / 1e6
+    value = whole_job_value(world, px_step, args.steps, total_ms)
 
     # one untimed render to read the variant and list sizes the timed steps used
     with torch.cuda.stream(stream):

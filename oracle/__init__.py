@@ -38,6 +38,7 @@ DEFAULT_SETTINGS = dict(
     tol_px=1e-3,
     tol_rel=1e-5,
     tol_stop=1e-3,
+    tol_depth=1e-6,
 )
 
 QUAT_COMPOSE = 0
@@ -64,8 +65,8 @@ def _load():
         lib.orc_project.argtypes = [ctypes.c_int64, ctypes.c_int] + [P] * 7 + [P] * 10
         lib.orc_bin_sort.argtypes = [ctypes.c_int64, P, P, P, P, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int64]
         lib.orc_bin_sort.restype = ctypes.c_int64
-        lib.orc_render.argtypes = [ctypes.c_int64, ctypes.c_int] + [P] * 5 + [ctypes.c_int, P, P] + [P] * 8
-        lib.orc_render_backward.argtypes = [ctypes.c_int64, ctypes.c_int] + [P] * 5 + [ctypes.c_int, P, P] + [P] * 6
+        lib.orc_render.argtypes = [ctypes.c_int64, ctypes.c_int] + [P] * 5 + [ctypes.c_int, P, P] + [P] * 9
+        lib.orc_render_backward.argtypes = [ctypes.c_int64, ctypes.c_int] + [P] * 5 + [ctypes.c_int, P, P] + [P] * 7
         _lib = lib
     return _lib
 
@@ -82,7 +83,8 @@ def settings_array(**kw) -> np.ndarray:
     s = dict(DEFAULT_SETTINGS)
     s.update(kw)
     return np.array(
-        [s["dilation"], s["alpha_max"], s["alpha_min"], s["T_min"], *s["bg"], s["tol_px"], s["tol_rel"], s["tol_stop"]],
+        [s["dilation"], s["alpha_max"], s["alpha_min"], s["T_min"], *s["bg"], s["tol_px"], s["tol_rel"], s["tol_stop"],
+         s["tol_depth"]],
         dtype=np.float64,
     )
 
@@ -169,10 +171,18 @@ def _cams(cams):
     return np.ascontiguousarray(np.stack([camera_array(c) for c in cams]), dtype=np.float64)
 
 
-def render(g: dict, cams, **settings):
+def _windows(windows, n):
+    if windows is None:
+        return None
+    w = np.ascontiguousarray(np.asarray(windows, np.int32).reshape(n, 4))
+    return w
+
+
+def render(g: dict, cams, windows=None, **settings):
     """Forward over several views.  Returns a dict with per-view lists of
     rgb [3,H,W], T [H,W], n_contrib [H,W], ambig [H,W], and the per-Gaussian
-    importance weight/count and ambiguity flags, and the evaluated pair count."""
+    importance weight/count and ambiguity flags, and the evaluated pair count.
+    windows (optional, per view (x0, y0, x1, y1)): blend only those pixels."""
     lib = _load()
     means, ls, qs, ol, sh = _params(g)
     N = means.shape[0]
@@ -188,7 +198,7 @@ def render(g: dict, cams, **settings):
     pairs = np.zeros(1, np.int64)
     rc = lib.orc_render(N, int(g["sh_degree"]), _p(means), _p(ls), _p(qs), _p(ol), _p(sh), len(cams), _p(_cams(cams)),
                         _p(settings_array(**settings)), _p(rgb), _p(T), _p(nc), _p(w), _p(cnt), _p(amb), _p(gamb),
-                        _p(pairs))
+                        _p(pairs), _p(_windows(windows, len(cams))))
     if rc != 0:
         raise ValueError("bad sh degree")
     out = dict(rgb=[], T=[], n_contrib=[], ambig=[], importance_w=w, importance_cnt=cnt, gauss_ambig=gamb,
@@ -204,9 +214,10 @@ def render(g: dict, cams, **settings):
     return out
 
 
-def render_backward(g: dict, cams, dL_drgb, **settings):
+def render_backward(g: dict, cams, dL_drgb, windows=None, **settings):
     """Analytic gradients of sum(dL_drgb * rgb) w.r.t. the raw parameters.
-    dL_drgb is a list of [3,H,W] arrays, one per view."""
+    dL_drgb is a list of [3,H,W] arrays, one per view; with windows, dL_drgb
+    must be zero outside them (only window pixels are replayed)."""
     lib = _load()
     means, ls, qs, ol, sh = _params(g)
     N = means.shape[0]
@@ -215,7 +226,7 @@ def render_backward(g: dict, cams, dL_drgb, **settings):
     gm, gl, gq, go, gs = np.zeros((N, 3)), np.zeros((N, 3)), np.zeros((N, 4)), np.zeros(N), np.zeros((N, K, 3))
     rc = lib.orc_render_backward(N, int(g["sh_degree"]), _p(means), _p(ls), _p(qs), _p(ol), _p(sh), len(cams),
                                  _p(_cams(cams)), _p(settings_array(**settings)), _p(flat), _p(gm), _p(gl), _p(gq),
-                                 _p(go), _p(gs))
+                                 _p(go), _p(gs), _p(_windows(windows, len(cams))))
     if rc != 0:
         raise ValueError("bad sh degree")
     return dict(means=gm, log_scales=gl, quats=gq, opacity_logit=go, sh=gs)

@@ -71,16 +71,18 @@ Camera read_camera(const double* c) {
   return cam;
 }
 
-// Flat layout of the rasterizer settings (10 doubles):
+// Flat layout of the rasterizer settings (11 doubles):
 //   [0] dilation added to the 2D covariance diagonal
 //   [1] alpha_max (0.99)   [2] alpha_min (1/255)   [3] T_min (1e-4)
 //   [4..6] background colour
 //   [7] ambiguity tolerance in pixels for tile-rectangle edges
 //   [8] relative ambiguity tolerance for alpha / radius / depth-tie tests
 //   [9] relative ambiguity tolerance for the termination test
+//   [10] relative gap below which two blended depths count as a possible tie
+//        (single-precision camera-space z carries about 1.5e-7 relative error)
 struct Settings {
   double dilation, alpha_max, alpha_min, T_min, bg[3];
-  double tol_px, tol_rel, tol_stop;
+  double tol_px, tol_rel, tol_stop, tol_depth;
 };
 
 Settings read_settings(const double* s) {
@@ -95,6 +97,7 @@ Settings read_settings(const double* s) {
   o.tol_px = s[7];
   o.tol_rel = s[8];
   o.tol_stop = s[9];
+  o.tol_depth = s[10];
   return o;
 }
 
@@ -490,7 +493,7 @@ PixelResult blend_pixel(const BlendView& bv, const TileLists& tl, int u, int v, 
     if (test < st.T_min) break;
     // two blended Gaussians whose depths a single-precision projection could
     // order differently
-    if (prev_id >= 0 && std::fabs(bv.depth[i] - prev_depth) <= st.tol_rel * std::fabs(bv.depth[i])) pr.ambig = true;
+    if (prev_id >= 0 && std::fabs(bv.depth[i] - prev_depth) <= st.tol_depth * std::fabs(bv.depth[i])) pr.ambig = true;
     prev_depth = bv.depth[i];
     prev_id = i;
     for (int ch = 0; ch < 3; ++ch) pr.C[ch] += bv.rgb[3 * i + ch] * alpha * pr.T;
@@ -789,10 +792,12 @@ int64_t orc_bin_sort(int64_t N, const double* mean2d, const int32_t* radius, con
 // and views; gauss_ambig (nullable) marks Gaussians that were ambiguous in a
 // projection or took part in an ambiguous pixel.  pairs (nullable) receives
 // the number of evaluated (pixel, list entry) pairs.
+// windows (nullable): per view x0, y0, x1, y1; only pixels inside are blended
+// (the others keep zero outputs), e.g. to check sampled windows of large views.
 int orc_render(int64_t N, int degree, const double* means, const double* log_scales, const double* quats,
                const double* opacity_logit, const double* sh, int n_views, const double* cams,
                const double* settings, double* rgb_out, double* T_out, int32_t* ncontrib_out, double* imp_w,
-               int64_t* imp_cnt, uint8_t* pix_ambig, uint8_t* gauss_ambig, int64_t* pairs) {
+               int64_t* imp_cnt, uint8_t* pix_ambig, uint8_t* gauss_ambig, int64_t* pairs, const int32_t* windows) {
   if (degree < 0 || degree > 3) return -1;
   Settings st = read_settings(settings);
   if (imp_w)
@@ -812,8 +817,15 @@ int orc_render(int64_t N, int degree, const double* means, const double* log_sca
     BlendView bv = blend_view_of(vf);
     int W = vf.cam.W, H = vf.cam.H;
     int64_t HW = (int64_t)W * H;
-    for (int v = 0; v < H; ++v)
-      for (int u = 0; u < W; ++u) {
+    int wx0 = 0, wy0 = 0, wx1 = W, wy1 = H;
+    if (windows) {
+      wx0 = windows[4 * vi];
+      wy0 = windows[4 * vi + 1];
+      wx1 = windows[4 * vi + 2];
+      wy1 = windows[4 * vi + 3];
+    }
+    for (int v = wy0; v < wy1; ++v)
+      for (int u = wx0; u < wx1; ++u) {
         PixelResult pr = blend_pixel(bv, vf.tl, u, v, st, [&](int, int32_t i, double alpha, double T, double) {
           if (imp_w) imp_w[i] += alpha * T;
           if (imp_cnt) imp_cnt[i] += 1;
@@ -840,7 +852,7 @@ int orc_render(int64_t N, int degree, const double* means, const double* log_sca
 int orc_render_backward(int64_t N, int degree, const double* means, const double* log_scales, const double* quats,
                         const double* opacity_logit, const double* sh, int n_views, const double* cams,
                         const double* settings, const double* dL_drgb, double* g_means, double* g_log_scales,
-                        double* g_quats, double* g_opacity_logit, double* g_sh) {
+                        double* g_quats, double* g_opacity_logit, double* g_sh, const int32_t* windows) {
   if (degree < 0 || degree > 3) return -1;
   int K = (degree + 1) * (degree + 1);
   Settings st = read_settings(settings);
@@ -858,8 +870,15 @@ int orc_render_backward(int64_t N, int degree, const double* means, const double
     int64_t HW = (int64_t)W * H;
     // per-Gaussian gradients of this view's projected quantities
     std::vector<double> g_m2(2 * N, 0), g_con(3 * N, 0), g_op(N, 0), g_rgb(3 * N, 0);
-    for (int v = 0; v < H; ++v)
-      for (int u = 0; u < W; ++u) {
+    int wx0 = 0, wy0 = 0, wx1 = W, wy1 = H;  // pixels outside a window must have zero dL/d(rgb)
+    if (windows) {
+      wx0 = windows[4 * vi];
+      wy0 = windows[4 * vi + 1];
+      wx1 = windows[4 * vi + 2];
+      wy1 = windows[4 * vi + 3];
+    }
+    for (int v = wy0; v < wy1; ++v)
+      for (int u = wx0; u < wx1; ++u) {
         int64_t pix = (int64_t)v * W + u;
         // the forward result of this pixel
         PixelResult fin = blend_pixel(bv, vf.tl, u, v, st, [](int, int32_t, double, double, double) {});
