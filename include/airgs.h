@@ -184,12 +184,81 @@ int airgs_render_backward_l1(airgs_ctx* ctx, airgs_state* saved, const float* ta
                              float* g_means, float* g_log_scales, float* g_quats, float* g_opacity_logit,
                              float* g_sh, float* importance_w, uint32_t* importance_cnt);
 
+/* Optional outputs of the adjoint, for render_backward_ex. */
+typedef struct {
+  const float* dL_drgb;     /* dL/d(rgb) laid out like rgb_out (ignored when target is set) */
+  const float* target;      /* nullable: L1 of Eq. 1 against this image, fused (as render_backward_l1) */
+  float* loss_out;          /* nullable device float: the L1 loss when target is set */
+  float* g_means;           /* device gradients, overwritten (required) */
+  float* g_log_scales;
+  float* g_quats;
+  float* g_opacity_logit;
+  float* g_sh;
+  float* importance_w;      /* nullable, += blend weight (with importance_cnt) */
+  uint32_t* importance_cnt;
+  float* densify_grad;      /* nullable, += sum over views of |dL/d mean2d| in pixels (with densify_views) */
+  uint32_t* densify_views;  /* nullable, += number of views in which the Gaussian is visible */
+} airgs_backward_args;
+
+/* render_backward_ex: the adjoint with every optional output; densify_grad and
+ * densify_views are the statistics of the densification step of keyframe
+ * reconstruction (Sec. III-B: Gaussians with large screen-space gradients are
+ * cloned or split). */
+int airgs_render_backward_ex(airgs_ctx* ctx, airgs_state* saved, const airgs_backward_args* args);
+
+/* mask_out[i] = 1 where densify_views[i] > 0 and the mean screen-space gradient
+ * densify_grad[i] / densify_views[i] exceeds threshold (the paper leaves the
+ * threshold open), else 0.  All device arrays of length n. */
+int airgs_densify_select(airgs_ctx* ctx, const float* densify_grad, const uint32_t* densify_views, int64_t n,
+                         float threshold, uint8_t* mask_out);
+
 /* gaussian_importance: the per-Gaussian blend weight and blended-pair count of
  * the current frame over n_views cameras, without colour output (the usage
  * frequency of Sec. III-C).  w_out [n] float and cnt_out [n] uint32 are
  * overwritten (device). */
 int airgs_gaussian_importance(airgs_ctx* ctx, const airgs_camera* cams, int n_views, float* w_out,
                               uint32_t* cnt_out);
+
+/* Usage-frequency pruning p(.) of Sec. III-C.  keep_out[i] = 0 for the
+ * n_prune Gaussians with the smallest blend weight importance[i] (the usage
+ * frequency airgs_gaussian_importance or the render calls accumulate), 1 for
+ * the others; equal weights prune the lower index first, negative or NaN
+ * weights rank lowest.  importance: device float [n]; keep_out: device uint8
+ * [n].  0 <= n_prune <= n. */
+int airgs_prune_mask(airgs_ctx* ctx, const float* importance, int64_t n, int64_t n_prune, uint8_t* keep_out);
+
+/* Pruned differential delta of Sec. III-C, d'_t = p(D_t - D'_{t-1}): for every
+ * Gaussian i and channel c of channel-major device float arrays [channels][n],
+ *   d_out = keep[i] ? D_t - D_sent : 0,   then   D_sent += d_out,
+ * so D_sent goes from the record D'_{t-1} of what was transmitted to D'_t.
+ * Channels are treated additively (the paper's GS_{t+1} = GS_t + d_{t+1}).
+ * nonzero_out (device uint64, nullable) receives the number of Gaussians whose
+ * transmitted delta has a non-zero channel (the delta's size in Gaussians). */
+int airgs_prune_delta(airgs_ctx* ctx, int64_t n, int channels, const float* D_t, float* D_sent, const uint8_t* keep,
+                      float* d_out, uint64_t* nonzero_out);
+
+/* apply_frame_delta: as airgs_apply_frame_update with an already decoded
+ * float delta (device, channel-major [7][n]: dx, dy, dz, qw, qx, qy, qz). */
+int airgs_apply_frame_delta(airgs_ctx* ctx, const float* delta, int mode, int64_t frame_id);
+
+/* Per-view sum of squared differences of two images laid out like rgb_out
+ * (device float), written to sse_out[n_views] (device double, overwritten);
+ * the PSNR of a pruning level is 10 log10(3 H W / sse) for images in [0, 1]. */
+int airgs_image_sse(airgs_ctx* ctx, const airgs_camera* cams, int n_views, const float* a, const float* b,
+                    double* sse_out);
+
+/* The 3DGS training loss of Eq. 1, L = (1 - lambda) L1 + lambda (1 - SSIM)
+ * (lambda = 0.2 in Sec. IV-A), over all views, and its gradient with respect
+ * to the rendered image, to feed airgs_render_backward.  SSIM per (view,
+ * channel) with an 11x11 Gaussian window (sigma 1.5, normalised, zero padding,
+ * output the size of the image), C1 = 0.01^2, C2 = 0.03^2, averaged over
+ * views, pixels and channels; L1 is the mean absolute difference.
+ *   rgb, target   device float laid out like rgb_out
+ *   loss_out      device double[3] (nullable): L, L1, SSIM
+ *   dL_drgb_out   device float laid out like rgb_out (overwritten)
+ * Synchronises on the stream (its host-side plane table must outlive the copy). */
+int airgs_l3dgs_loss(airgs_ctx* ctx, const airgs_camera* cams, int n_views, const float* rgb, const float* target,
+                     float lambda, double* loss_out, float* dL_drgb_out);
 
 /* Release a state returned by a render call (its device memory is returned to
  * the context's pool once the stream passes this point). */

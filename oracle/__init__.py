@@ -66,7 +66,7 @@ def _load():
         lib.orc_bin_sort.argtypes = [ctypes.c_int64, P, P, P, P, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int64]
         lib.orc_bin_sort.restype = ctypes.c_int64
         lib.orc_render.argtypes = [ctypes.c_int64, ctypes.c_int] + [P] * 5 + [ctypes.c_int, P, P] + [P] * 9
-        lib.orc_render_backward.argtypes = [ctypes.c_int64, ctypes.c_int] + [P] * 5 + [ctypes.c_int, P, P] + [P] * 7
+        lib.orc_render_backward.argtypes = [ctypes.c_int64, ctypes.c_int] + [P] * 5 + [ctypes.c_int, P, P] + [P] * 9
         _lib = lib
     return _lib
 
@@ -214,7 +214,7 @@ def render(g: dict, cams, windows=None, **settings):
     return out
 
 
-def render_backward(g: dict, cams, dL_drgb, windows=None, **settings):
+def render_backward(g: dict, cams, dL_drgb, windows=None, densify=False, **settings):
     """Analytic gradients of sum(dL_drgb * rgb) w.r.t. the raw parameters.
     dL_drgb is a list of [3,H,W] arrays, one per view; with windows, dL_drgb
     must be zero outside them (only window pixels are replayed)."""
@@ -224,12 +224,103 @@ def render_backward(g: dict, cams, dL_drgb, windows=None, **settings):
     K = sh.shape[1]
     flat = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float64).reshape(-1) for x in dL_drgb]))
     gm, gl, gq, go, gs = np.zeros((N, 3)), np.zeros((N, 3)), np.zeros((N, 4)), np.zeros(N), np.zeros((N, K, 3))
+    dg, dv = (np.zeros(N), np.zeros(N, np.int64)) if densify else (None, None)
     rc = lib.orc_render_backward(N, int(g["sh_degree"]), _p(means), _p(ls), _p(qs), _p(ol), _p(sh), len(cams),
                                  _p(_cams(cams)), _p(settings_array(**settings)), _p(flat), _p(gm), _p(gl), _p(gq),
-                                 _p(go), _p(gs), _p(_windows(windows, len(cams))))
+                                 _p(go), _p(gs), _p(_windows(windows, len(cams))), _p(dg), _p(dv))
     if rc != 0:
         raise ValueError("bad sh degree")
-    return dict(means=gm, log_scales=gl, quats=gq, opacity_logit=go, sh=gs)
+    out = dict(means=gm, log_scales=gl, quats=gq, opacity_logit=go, sh=gs)
+    if densify:
+        out["densify_grad"], out["densify_views"] = dg, dv
+    return out
+
+
+def prune_mask(importance, n_prune):
+    """Usage-frequency pruning p(.) (Sec. III-C): keep = 0 for the n_prune
+    Gaussians of smallest blend weight, equal weights pruning the lower index
+    first (a stable ascending sort); negative and NaN weights count as 0."""
+    w = np.asarray(importance, np.float64).copy()
+    w[~(w > 0)] = 0.0
+    order = np.argsort(w, kind="stable")
+    keep = np.ones(w.shape[0], np.uint8)
+    keep[order[:n_prune]] = 0
+    return keep
+
+
+def prune_delta(D_t, D_sent, keep):
+    """d'_t = p(D_t - D'_{t-1}) and D'_t = D'_{t-1} + d'_t (Sec. III-C), channel-major [C, n]."""
+    D_t = np.asarray(D_t, np.float64)
+    D_sent = np.asarray(D_sent, np.float64)
+    d = np.where(np.asarray(keep)[None, :] != 0, D_t - D_sent, 0.0)
+    return d, D_sent + d
+
+
+def apply_delta(base_means, base_quats, delta, quat_add=False):
+    """Frame state from a decoded float delta [7, n]: means + (dx, dy, dz) and
+    q = normalize(dq (x) q) (Hamilton product) or q + dq."""
+    bm = np.asarray(base_means, np.float64)
+    bq = np.asarray(base_quats, np.float64)
+    d = np.asarray(delta, np.float64)
+    means = bm + d[0:3].T
+    if quat_add:
+        return means, bq + d[3:7].T
+    w1, x1, y1, z1 = d[3], d[4], d[5], d[6]
+    w2, x2, y2, z2 = bq[:, 0], bq[:, 1], bq[:, 2], bq[:, 3]
+    q = np.stack([w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2,
+                  w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+                  w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2,
+                  w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2], axis=1)
+    return means, q / np.linalg.norm(q, axis=1, keepdims=True)
+
+
+def ssim_window(radius=5, sigma=1.5):
+    """Normalised 1D Gaussian weights; the 2D window is their outer product."""
+    j = np.arange(-radius, radius + 1, dtype=np.float64)
+    w = np.exp(-j * j / (2.0 * sigma * sigma))
+    return w / w.sum()
+
+
+def _blur(img, w):
+    """2D zero-padded 'same' convolution of one plane with the window w w^T
+    (scipy.signal.convolve2d; the window is symmetric)."""
+    from scipy.signal import convolve2d
+    return convolve2d(img, np.outer(w, w), mode="same", boundary="fill", fillvalue=0.0)
+
+
+def l3dgs_loss_grad(rgb_views, target_views, lam=0.2, C1=0.01 ** 2, C2=0.03 ** 2):
+    """L_3DGS of Eq. 1: L = (1 - lam) L1 + lam (1 - SSIM), SSIM with an 11x11
+    Gaussian window (sigma 1.5), zero padding, averaged over views, channels and
+    pixels; returns (L, L1, SSIM, [dL/d rgb per view]).  The gradient is the
+    window correlation of the SSIM map's partials with respect to the local
+    moments mu_x, E[x^2], E[xy]."""
+    w = ssim_window()
+    total = sum(np.asarray(r).size for r in rgb_views)
+    s_sum, l1_sum, grads = 0.0, 0.0, []
+    for rv, tv in zip(rgb_views, target_views):
+        rv = np.asarray(rv, np.float64)
+        tv = np.asarray(tv, np.float64)
+        g = np.zeros_like(rv)
+        for c in range(rv.shape[0]):
+            x, y = rv[c], tv[c]
+            mx, my = _blur(x, w), _blur(y, w)
+            mxx, myy, mxy = _blur(x * x, w), _blur(y * y, w), _blur(x * y, w)
+            A = 2 * mx * my + C1
+            B = 2 * (mxy - mx * my) + C2
+            Cc = mx * mx + my * my + C1
+            D = (mxx - mx * mx) + (myy - my * my) + C2
+            S = A * B / (Cc * D)
+            s_sum += S.sum()
+            P1 = 2 * my * (B - A) / (Cc * D) - 2 * mx * S / Cc + 2 * mx * S / D
+            P2 = -S / D
+            P3 = 2 * A / (Cc * D)
+            dS = _blur(P1, w) + 2 * x * _blur(P2, w) + y * _blur(P3, w)
+            d = x - y
+            l1_sum += np.abs(d).sum()
+            g[c] = -lam * dS / total + (1 - lam) * np.sign(d) / total
+        grads.append(g)
+    ssim, l1 = s_sum / total, l1_sum / total
+    return (1 - lam) * l1 + lam * (1 - ssim), l1, ssim, grads
 
 
 def l1_loss_grad(rgb_views, target_views):

@@ -849,10 +849,13 @@ int orc_render(int64_t N, int degree, const double* means, const double* log_sca
 
 // Analytic adjoint of orc_render: given dL/d(rgb) laid out like rgb_out,
 // write dL/d(means, log_scales, quats, opacity_logit, sh) (overwritten).
+// dens_grad / dens_views (nullable, accumulated) receive, per Gaussian, the sum
+// over views of |dL/d mean2d| and the number of views in which it is visible.
 int orc_render_backward(int64_t N, int degree, const double* means, const double* log_scales, const double* quats,
                         const double* opacity_logit, const double* sh, int n_views, const double* cams,
                         const double* settings, const double* dL_drgb, double* g_means, double* g_log_scales,
-                        double* g_quats, double* g_opacity_logit, double* g_sh, const int32_t* windows) {
+                        double* g_quats, double* g_opacity_logit, double* g_sh, const int32_t* windows,
+                        double* dens_grad, int64_t* dens_views) {
   if (degree < 0 || degree > 3) return -1;
   int K = (degree + 1) * (degree + 1);
   Settings st = read_settings(settings);
@@ -914,6 +917,9 @@ int orc_render_backward(int64_t N, int degree, const double* means, const double
       }
     for (int64_t i = 0; i < N; ++i) {
       if (!vf.visible[i]) continue;
+      // densification statistic: |dL/d mean2d| of this view, and the view count
+      if (dens_grad) dens_grad[i] += std::sqrt(g_m2[2 * i] * g_m2[2 * i] + g_m2[2 * i + 1] * g_m2[2 * i + 1]);
+      if (dens_views) dens_views[i] += 1;
       Gaussian g = read_gaussian(i, K, means, log_scales, quats, opacity_logit, sh);
       project_backward_one(g, K, degree, vf.cam, vf.proj[i], &g_m2[2 * i], &g_con[3 * i], g_op[i], &g_rgb[3 * i],
                            g_means + 3 * i, g_log_scales + 3 * i, g_quats + 4 * i, g_opacity_logit + i,

@@ -69,6 +69,23 @@ class airgs_gaussians(ctypes.Structure):
     ]
 
 
+class airgs_backward_args(ctypes.Structure):
+    _fields_ = [
+        ("dL_drgb", ctypes.c_void_p),
+        ("target", ctypes.c_void_p),
+        ("loss_out", ctypes.c_void_p),
+        ("g_means", ctypes.c_void_p),
+        ("g_log_scales", ctypes.c_void_p),
+        ("g_quats", ctypes.c_void_p),
+        ("g_opacity_logit", ctypes.c_void_p),
+        ("g_sh", ctypes.c_void_p),
+        ("importance_w", ctypes.c_void_p),
+        ("importance_cnt", ctypes.c_void_p),
+        ("densify_grad", ctypes.c_void_p),
+        ("densify_views", ctypes.c_void_p),
+    ]
+
+
 class airgs_stats(ctypes.Structure):
     _fields_ = [
         ("n_instances", ctypes.c_int64),
@@ -103,7 +120,14 @@ SIGNATURES = {
                                    P, P, ctypes.POINTER(STATE)]),
     "airgs_render_backward": (I, [CTX, STATE, P, P, P, P, P, P, P, P]),
     "airgs_render_backward_l1": (I, [CTX, STATE, P, P, P, P, P, P, P, P, P]),
+    "airgs_render_backward_ex": (I, [CTX, STATE, ctypes.POINTER(airgs_backward_args)]),
+    "airgs_densify_select": (I, [CTX, P, P, I64, ctypes.c_float, P]),
     "airgs_gaussian_importance": (I, [CTX, ctypes.POINTER(airgs_camera), I, P, P]),
+    "airgs_prune_mask": (I, [CTX, P, I64, I64, P]),
+    "airgs_prune_delta": (I, [CTX, I64, I, P, P, P, P, P]),
+    "airgs_apply_frame_delta": (I, [CTX, P, I, I64]),
+    "airgs_image_sse": (I, [CTX, ctypes.POINTER(airgs_camera), I, P, P, P]),
+    "airgs_l3dgs_loss": (I, [CTX, ctypes.POINTER(airgs_camera), I, P, P, ctypes.c_float, P, P]),
     "airgs_release_state": (I, [CTX, STATE]),
     "airgs_state_stats": (I, [CTX, STATE, ctypes.POINTER(airgs_stats)]),
     "airgs_state_view_info": (I, [CTX, STATE, I, ctypes.POINTER(I64), ctypes.POINTER(I64)]),

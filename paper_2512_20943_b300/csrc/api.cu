@@ -489,7 +489,7 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
 
 int backward_impl(airgs_ctx* ctx, airgs_state* s, const float* dL, const float* target, float* loss_out,
                   float* g_means, float* g_log_scales, float* g_quats, float* g_opacity, float* g_sh, float* imp_w,
-                  uint32_t* imp_cnt) {
+                  uint32_t* imp_cnt, float* dens_grad = nullptr, uint32_t* dens_views = nullptr) {
   if (!s) return fail(ctx, AIRGS_E_STATE, "null state");
   if (!dL && !target) return fail(ctx, AIRGS_E_ARG, "dL_drgb or target required");
   if (s->n > 0 && (!g_means || !g_log_scales || !g_quats || !g_opacity || !g_sh))
@@ -497,6 +497,8 @@ int backward_impl(airgs_ctx* ctx, airgs_state* s, const float* dL, const float* 
   if (s->n > 0 && !aligned16(g_quats)) return fail(ctx, AIRGS_E_ARG, "g_quats must be 16-byte aligned");
   if ((imp_w == nullptr) != (imp_cnt == nullptr))
     return fail(ctx, AIRGS_E_ARG, "importance_w and importance_cnt go together");
+  if ((dens_grad == nullptr) != (dens_views == nullptr))
+    return fail(ctx, AIRGS_E_ARG, "densify_grad and densify_views go together");
   cudaStream_t st = ctx->stream;
   if (loss_out) CK(cudaMemsetAsync(loss_out, 0, sizeof(float), st));
   if (s->n == 0) return AIRGS_OK;
@@ -542,7 +544,8 @@ int backward_impl(airgs_ctx* ctx, airgs_state* s, const float* dL, const float* 
   }
   StageScope sc(ctx, ST_PROJECT_BWD);
   CK(launch_project_bwd(st, s->n, s->sh_degree, s->means, s->log_scales, s->quats, s->opacity, s->sh, s->d_cams,
-                        s->n_views, s->proj, grad, g_means, g_log_scales, g_quats, g_opacity, g_sh));
+                        s->n_views, s->proj, grad, g_means, g_log_scales, g_quats, g_opacity, g_sh, dens_grad,
+                        dens_views));
   return AIRGS_OK;
 }
 
@@ -764,6 +767,24 @@ int airgs_render_backward_l1(airgs_ctx* ctx, airgs_state* saved, const float* ta
                        importance_w, importance_cnt);
 }
 
+int airgs_render_backward_ex(airgs_ctx* ctx, airgs_state* saved, const airgs_backward_args* a) {
+  if (!ctx) return AIRGS_E_ARG;
+  if (!a) return fail(ctx, AIRGS_E_ARG, "null arguments");
+  if (!a->dL_drgb && !a->target) return fail(ctx, AIRGS_E_ARG, "dL_drgb or target required");
+  return backward_impl(ctx, saved, a->target ? nullptr : a->dL_drgb, a->target, a->loss_out, a->g_means,
+                       a->g_log_scales, a->g_quats, a->g_opacity_logit, a->g_sh, a->importance_w, a->importance_cnt,
+                       a->densify_grad, a->densify_views);
+}
+
+int airgs_densify_select(airgs_ctx* ctx, const float* densify_grad, const uint32_t* densify_views, int64_t n,
+                         float threshold, uint8_t* mask_out) {
+  if (!ctx) return AIRGS_E_ARG;
+  if (n < 0 || (n > 0 && (!densify_grad || !densify_views || !mask_out)))
+    return fail(ctx, AIRGS_E_ARG, "bad densify_select arguments");
+  CK(launch_densify_select(ctx->stream, n, densify_grad, densify_views, threshold, mask_out));
+  return AIRGS_OK;
+}
+
 int airgs_gaussian_importance(airgs_ctx* ctx, const airgs_camera* cams, int n_views, float* w_out,
                               uint32_t* cnt_out) {
   if (!ctx) return AIRGS_E_ARG;
@@ -937,6 +958,111 @@ int airgs_autotune(airgs_ctx* ctx, const airgs_camera* cams, int n_views, int* v
   ctx->tuned[tune_key(ctx->n, np, n_views)] = best;
   save_tune_cache(ctx);
   if (variant) *variant = best;
+  return AIRGS_OK;
+}
+
+int airgs_prune_mask(airgs_ctx* ctx, const float* importance, int64_t n, int64_t n_prune, uint8_t* keep_out) {
+  if (!ctx) return AIRGS_E_ARG;
+  if (n < 0 || n >= (1ll << 32) || n_prune < 0 || n_prune > n || (n > 0 && (!importance || !keep_out)))
+    return fail(ctx, AIRGS_E_ARG, "bad prune_mask arguments");
+  if (n == 0) return AIRGS_OK;
+  uint32_t *ka, *va, *kb, *vb, *scr;
+  int rc;
+  if ((rc = dalloc(ctx, &ka, n)) || (rc = dalloc(ctx, &va, n)) || (rc = dalloc(ctx, &kb, n)) ||
+      (rc = dalloc(ctx, &vb, n)) ||
+      (rc = dalloc(ctx, &scr, radix_scratch_bytes(n, 1, ctx->num_sms) / sizeof(uint32_t) + 1)))
+    return rc;
+  cudaError_t e = launch_prune_mask(ctx->stream, ctx->num_sms, n, n_prune, importance, ka, va, kb, vb, scr, keep_out);
+  for (void* p : {(void*)ka, (void*)va, (void*)kb, (void*)vb, (void*)scr}) dfree(ctx, p);
+  if (e != cudaSuccess) return fail(ctx, AIRGS_E_CUDA, "prune_mask: %s", cudaGetErrorString(e));
+  return AIRGS_OK;
+}
+
+int airgs_prune_delta(airgs_ctx* ctx, int64_t n, int channels, const float* D_t, float* D_sent, const uint8_t* keep,
+                      float* d_out, uint64_t* nonzero_out) {
+  if (!ctx) return AIRGS_E_ARG;
+  if (n < 0 || channels < 1 || channels > 64 || (n > 0 && (!D_t || !D_sent || !keep || !d_out)))
+    return fail(ctx, AIRGS_E_ARG, "bad prune_delta arguments");
+  if (nonzero_out) CK(cudaMemsetAsync(nonzero_out, 0, sizeof(uint64_t), ctx->stream));
+  CK(launch_prune_delta(ctx->stream, n, channels, D_t, D_sent, keep, d_out, (unsigned long long*)nonzero_out));
+  return AIRGS_OK;
+}
+
+int airgs_apply_frame_delta(airgs_ctx* ctx, const float* delta, int mode, int64_t frame_id) {
+  if (!ctx) return AIRGS_E_ARG;
+  if (ctx->sh_degree < 0) return fail(ctx, AIRGS_E_STATE, "set_anchor first");
+  if (!delta && ctx->n > 0) return fail(ctx, AIRGS_E_ARG, "null delta");
+  if (mode & ~3) return fail(ctx, AIRGS_E_ARG, "unknown mode bits");
+  const int base = mode & 1, quat_add = (mode & AIRGS_QUAT_ADD) ? 1 : 0;
+  const float* bm = base == AIRGS_DELTA_ANCHOR ? ctx->a_means : ctx->c_means;
+  const float* bq = base == AIRGS_DELTA_ANCHOR ? ctx->a_quats : ctx->c_quats;
+  StageScope sc(ctx, ST_DECODE);
+  CK(launch_apply_delta(ctx->stream, ctx->n, delta, quat_add, bm, bq, ctx->c_means, ctx->c_quats));
+  ctx->frame_id = frame_id;
+  return AIRGS_OK;
+}
+
+int airgs_image_sse(airgs_ctx* ctx, const airgs_camera* cams, int n_views, const float* a, const float* b,
+                    double* sse_out) {
+  if (!ctx) return AIRGS_E_ARG;
+  std::vector<CamDev> tmp;
+  int64_t nt = 0, np = 0;
+  int rc = build_cams(ctx, cams, n_views, tmp, nt, np);
+  if (rc) return rc;
+  if (!a || !b || !sse_out) return fail(ctx, AIRGS_E_ARG, "null image pointer");
+  std::vector<int64_t> off(n_views + 1, 0);
+  for (int v = 0; v < n_views; ++v) off[v + 1] = off[v] + 3 * (int64_t)tmp[v].W * tmp[v].H;
+  int64_t* d_off = nullptr;
+  if ((rc = dalloc(ctx, &d_off, n_views + 1))) return rc;
+  cudaError_t e = cudaMemcpyAsync(d_off, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sse_out, 0, n_views * sizeof(double), ctx->stream);
+  if (e == cudaSuccess) e = launch_sq_err(ctx->stream, a, b, d_off, n_views, sse_out);
+  // the offsets are read by the kernel before the stream-ordered free
+  dfree(ctx, d_off);
+  if (e != cudaSuccess) return fail(ctx, AIRGS_E_CUDA, "image_sse: %s", cudaGetErrorString(e));
+  return AIRGS_OK;
+}
+
+int airgs_l3dgs_loss(airgs_ctx* ctx, const airgs_camera* cams, int n_views, const float* rgb, const float* target,
+                     float lambda, double* loss_out, float* dL_drgb_out) {
+  if (!ctx) return AIRGS_E_ARG;
+  std::vector<CamDev> tmp;
+  int64_t nt = 0, np = 0;
+  int rc = build_cams(ctx, cams, n_views, tmp, nt, np);
+  if (rc) return rc;
+  if (!rgb || !target || !dL_drgb_out) return fail(ctx, AIRGS_E_ARG, "null image pointer");
+  if (!(lambda >= 0.f && lambda <= 1.f)) return fail(ctx, AIRGS_E_ARG, "lambda must be in [0, 1]");
+  const int n_planes = 3 * n_views;
+  std::vector<int64_t> off(n_planes + 1, 0);
+  std::vector<int> w(n_planes), h(n_planes);
+  for (int v = 0; v < n_views; ++v)
+    for (int c = 0; c < 3; ++c) {
+      const int p = 3 * v + c;
+      w[p] = tmp[v].W;
+      h[p] = tmp[v].H;
+      off[p + 1] = off[p] + (int64_t)tmp[v].W * tmp[v].H;
+    }
+  const int64_t total = off[n_planes];
+  int64_t* d_off;
+  int *d_w, *d_h;
+  float* scratch;
+  double* sums;
+  if ((rc = dalloc(ctx, &d_off, n_planes + 1)) || (rc = dalloc(ctx, &d_w, n_planes)) ||
+      (rc = dalloc(ctx, &d_h, n_planes)) || (rc = dalloc(ctx, &scratch, 8 * total)) || (rc = dalloc(ctx, &sums, 5)))
+    return rc;
+  cudaStream_t st = ctx->stream;
+  cudaError_t e = cudaMemcpyAsync(d_off, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_w, w.data(), w.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_h, h.data(), h.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sums, 0, 5 * sizeof(double), st);
+  if (e == cudaSuccess)
+    e = launch_ssim_loss(st, d_off, d_w, d_h, n_planes, total, rgb, target, lambda, scratch, sums, dL_drgb_out);
+  if (e == cudaSuccess && loss_out)
+    e = cudaMemcpyAsync(loss_out, sums + 2, 3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  // host arrays were copied (stream-ordered); device temporaries return to the pool
+  CK(cudaStreamSynchronize(st));
+  for (void* p : {(void*)d_off, (void*)d_w, (void*)d_h, (void*)scratch, (void*)sums}) dfree(ctx, p);
+  if (e != cudaSuccess) return fail(ctx, AIRGS_E_CUDA, "l3dgs_loss: %s", cudaGetErrorString(e));
   return AIRGS_OK;
 }
 

@@ -50,6 +50,25 @@ cudaError_t launch_emit(cudaStream_t st, int64_t total, int64_t n, const uint32_
                         const CamDev* cams, float alpha_min, int64_t n_tiles, uint32_t* keys, uint32_t* vals);
 cudaError_t launch_tile_ranges(cudaStream_t st, int64_t n_inst, const uint32_t* keys, uint2* ranges);
 
+// Usage-frequency pruning (prune.cu).
+cudaError_t launch_prune_mask(cudaStream_t st, int num_sms, int64_t n, int64_t n_prune, const float* w,
+                              uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b,
+                              uint32_t* scratch, uint8_t* keep);
+cudaError_t launch_prune_delta(cudaStream_t st, int64_t n, int channels, const float* D_t, float* D_sent,
+                               const uint8_t* keep, float* d_out, unsigned long long* nonzero);
+cudaError_t launch_apply_delta(cudaStream_t st, int64_t n, const float* delta, int quat_add, const float* base_means,
+                               const float* base_quats, float* out_means, float* out_quats);
+cudaError_t launch_densify_select(cudaStream_t st, int64_t n, const float* g, const uint32_t* views, float threshold,
+                                  uint8_t* mask);
+cudaError_t launch_sq_err(cudaStream_t st, const float* a, const float* b, const int64_t* view_off, int n_views,
+                          double* out);
+
+// L_3DGS = (1 - lambda) L1 + lambda (1 - SSIM) and its image gradient (ssim.cu).
+// scratch: 8 x total floats; sums: 5 doubles (zeroed; [2..4] receive L, L1, SSIM).
+cudaError_t launch_ssim_loss(cudaStream_t st, const int64_t* d_off, const int* d_w, const int* d_h, int n_planes,
+                             int64_t total, const float* x, const float* y, float lambda, float* scratch,
+                             double* sums, float* grad);
+
 // Half-tile blend lists (cull_lists.cu).
 size_t half_list_chunks(int64_t n_inst);
 cudaError_t launch_half_lists(cudaStream_t st, const uint32_t* keys, const uint32_t* ids, const uint2* ranges,
@@ -110,6 +129,6 @@ cudaError_t launch_project_bwd(cudaStream_t st, int64_t n, int sh_degree, const 
                                const float* log_scales, const float* quats, const float* opacity_logit,
                                const float* sh, const CamDev* cams, int n_views, const ProjRec* proj,
                                const GradRec* grad, float* g_means, float* g_log_scales, float* g_quats,
-                               float* g_opacity, float* g_sh);
+                               float* g_opacity, float* g_sh, float* dens_grad, uint32_t* dens_views);
 
 }  // namespace airgs

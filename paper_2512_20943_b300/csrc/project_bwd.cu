@@ -75,7 +75,8 @@ __global__ void __launch_bounds__(128) k_project_bwd(int64_t n, const float* __r
                                                      int n_views, const ProjRec* __restrict__ proj,
                                                      const GradRec* __restrict__ grad, float* __restrict__ g_means,
                                                      float* __restrict__ g_log_scales, float* __restrict__ g_quats,
-                                                     float* __restrict__ g_opacity, float* __restrict__ g_sh) {
+                                                     float* __restrict__ g_opacity, float* __restrict__ g_sh,
+                                                     float* __restrict__ dens_grad, uint32_t* __restrict__ dens_views) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -98,6 +99,8 @@ __global__ void __launch_bounds__(128) k_project_bwd(int64_t n, const float* __r
 #pragma unroll
   for (int k = 0; k < 9; ++k) gR[k] = 0.f;
   float gop = 0.f;
+  float dgrad = 0.f;   // sum over views of |dL/d mean2d| (densification statistic)
+  uint32_t dviews = 0; // views in which the Gaussian is visible
   float gsh[K * 3];
 #pragma unroll
   for (int k = 0; k < K * 3; ++k) gsh[k] = 0.f;
@@ -109,6 +112,8 @@ __global__ void __launch_bounds__(128) k_project_bwd(int64_t n, const float* __r
     if (!(flags & kFlagVisible)) continue;
     const GradRec gr = grad[o];
     const float gmx = gr.a.x, gmy = gr.a.y, gA = gr.a.z, gB = gr.a.w, gC = gr.b.x, go = gr.b.y;
+    ++dviews;
+    dgrad += sqrtf(gmx * gmx + gmy * gmy);
     const float grgb[3] = {gr.b.z, gr.b.w, gr.c.x};
     if (gmx == 0.f && gmy == 0.f && gA == 0.f && gB == 0.f && gC == 0.f && go == 0.f && grgb[0] == 0.f &&
         grgb[1] == 0.f && grgb[2] == 0.f)
@@ -247,18 +252,22 @@ __global__ void __launch_bounds__(128) k_project_bwd(int64_t n, const float* __r
   float* gshi = g_sh + (size_t)i * K * 3;
 #pragma unroll
   for (int k = 0; k < K * 3; ++k) gshi[k] = gsh[k];
+  if (dens_grad) {
+    dens_grad[i] += dgrad;
+    dens_views[i] += dviews;
+  }
 }
 
 cudaError_t launch_project_bwd(cudaStream_t st, int64_t n, int sh_degree, const float* means,
                                const float* log_scales, const float* quats, const float* opacity_logit,
                                const float* sh, const CamDev* cams, int n_views, const ProjRec* proj,
                                const GradRec* grad, float* g_means, float* g_log_scales, float* g_quats,
-                               float* g_opacity, float* g_sh) {
+                               float* g_opacity, float* g_sh, float* dens_grad, uint32_t* dens_views) {
   if (n == 0) return cudaSuccess;
   int blocks = (int)((n + 127) / 128);
 #define AIRGS_PB(D)                                                                                              \
   k_project_bwd<D><<<blocks, 128, 0, st>>>(n, means, log_scales, quats, opacity_logit, sh, cams, n_views, proj, \
-                                           grad, g_means, g_log_scales, g_quats, g_opacity, g_sh)
+                                           grad, g_means, g_log_scales, g_quats, g_opacity, g_sh, dens_grad, dens_views)
   switch (sh_degree) {
     case 0: AIRGS_PB(0); break;
     case 1: AIRGS_PB(1); break;

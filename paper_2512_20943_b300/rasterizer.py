@@ -14,8 +14,8 @@ import numpy as np
 import torch
 
 from . import _abi
-from ._abi import (AIRGS_DELTA_ANCHOR, AIRGS_DELTA_PREV, AIRGS_QUAT_ADD, airgs_camera, airgs_config, airgs_gaussians,
-                   airgs_stats, load_library)
+from ._abi import (AIRGS_DELTA_ANCHOR, AIRGS_DELTA_PREV, AIRGS_QUAT_ADD, airgs_backward_args, airgs_camera,
+                   airgs_config, airgs_gaussians, airgs_stats, load_library)
 
 
 class AirGSError(RuntimeError):
@@ -296,11 +296,90 @@ class Rasterizer:
                                                       _ptr(gr["opacity_logit"]), _ptr(gr["sh"]), _ptr(iw), _ptr(ic)))
         return loss, gr
 
+    def render_backward_ex(self, state: RenderState, dL_drgb=None, target=None, importance=None, densify=None):
+        """The adjoint with every optional output: dL_drgb or an L1 target,
+        importance (w, cnt) and densification statistics (grad_norm_sum,
+        views) accumulators.  Returns (gradients, loss or None)."""
+        a = airgs_backward_args()
+        ref = state.keep[0]
+        if target is not None:
+            _check_cuda(target, "target", torch.float32, ref.shape)
+            a.target = target.data_ptr()
+            loss = self._new((1,), torch.float32)
+            a.loss_out = loss.data_ptr()
+        else:
+            _check_cuda(dL_drgb, "dL_drgb", torch.float32, ref.shape)
+            a.dL_drgb = dL_drgb.data_ptr()
+            loss = None
+        gr = self._grad_buffers(state)
+        a.g_means, a.g_log_scales, a.g_quats = gr["means"].data_ptr(), gr["log_scales"].data_ptr(), gr["quats"].data_ptr()
+        a.g_opacity_logit, a.g_sh = gr["opacity_logit"].data_ptr(), gr["sh"].data_ptr()
+        if importance is not None:
+            a.importance_w, a.importance_cnt = importance[0].data_ptr(), importance[1].data_ptr()
+        if densify is not None:
+            a.densify_grad, a.densify_views = densify[0].data_ptr(), densify[1].data_ptr()
+        self._check(self.lib.airgs_render_backward_ex(self.ctx, state.handle, ctypes.byref(a)))
+        return gr, loss
+
+    def densify_select(self, grad_sum: torch.Tensor, views: torch.Tensor, threshold: float) -> torch.Tensor:
+        """uint8 mask of Gaussians whose mean screen-space gradient exceeds threshold."""
+        _check_cuda(grad_sum, "grad_sum", torch.float32)
+        mask = self._new((grad_sum.numel(),), torch.uint8)
+        self._check(self.lib.airgs_densify_select(self.ctx, _ptr(grad_sum), _ptr(views), grad_sum.numel(),
+                                                  float(threshold), _ptr(mask)))
+        return mask
+
     def gaussian_importance(self, cams):
         w = self._new((self.n,), torch.float32)
         c = self._new((self.n,), torch.int32)
         self._check(self.lib.airgs_gaussian_importance(self.ctx, camera_array(cams), len(cams), _ptr(w), _ptr(c)))
         return w, c
+
+    # ------------------------------------------------------------ pruning (Sec. III-C)
+    def prune_mask(self, importance: torch.Tensor, n_prune: int) -> torch.Tensor:
+        """uint8 keep mask: 0 for the n_prune Gaussians of lowest usage frequency."""
+        _check_cuda(importance, "importance", torch.float32)
+        keep = self._new((importance.numel(),), torch.uint8)
+        self._check(self.lib.airgs_prune_mask(self.ctx, _ptr(importance), importance.numel(), int(n_prune),
+                                              _ptr(keep)))
+        return keep
+
+    def prune_delta(self, D_t: torch.Tensor, D_sent: torch.Tensor, keep: torch.Tensor):
+        """d'_t = p(D_t - D'_{t-1}) for channel-major [C, n] deltas; updates D_sent
+        in place.  Returns (d'_t, number of Gaussians with a non-zero delta)."""
+        _check_cuda(D_t, "D_t", torch.float32)
+        _check_cuda(D_sent, "D_sent", torch.float32, D_t.shape)
+        _check_cuda(keep, "keep", torch.uint8, (D_t.shape[1],))
+        d = self._new(tuple(D_t.shape), torch.float32)
+        nz = self._new((1,), torch.int64)
+        self._check(self.lib.airgs_prune_delta(self.ctx, D_t.shape[1], D_t.shape[0], _ptr(D_t), _ptr(D_sent),
+                                               _ptr(keep), _ptr(d), _ptr(nz)))
+        return d, nz
+
+    def apply_frame_delta(self, delta: torch.Tensor, mode=AIRGS_DELTA_PREV, quat_add=False, frame_id=0):
+        """Apply a decoded float delta [7, n] to the previous frame or the anchor."""
+        _check_cuda(delta, "delta", torch.float32, (7, self.n))
+        m = int(mode) | (AIRGS_QUAT_ADD if quat_add else 0)
+        self._check(self.lib.airgs_apply_frame_delta(self.ctx, _ptr(delta), m, int(frame_id)))
+
+    def image_sse(self, cams, a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
+        """Per-view sum of squared differences (device float64 [n_views])."""
+        _check_cuda(a, "a", torch.float32)
+        _check_cuda(b, "b", torch.float32, a.shape)
+        out = self._new((len(cams),), torch.float64)
+        self._check(self.lib.airgs_image_sse(self.ctx, camera_array(cams), len(cams), _ptr(a), _ptr(b), _ptr(out)))
+        return out
+
+    def l3dgs_loss(self, cams, rgb: torch.Tensor, target: torch.Tensor, lam: float = 0.2):
+        """L = (1 - lam) L1 + lam (1 - SSIM) of Eq. 1 and dL/d(rgb).  Returns
+        (float64 tensor [L, L1, SSIM], gradient laid out like rgb)."""
+        _check_cuda(rgb, "rgb", torch.float32)
+        _check_cuda(target, "target", torch.float32, rgb.shape)
+        loss = self._new((3,), torch.float64)
+        grad = self._new(tuple(rgb.shape), torch.float32)
+        self._check(self.lib.airgs_l3dgs_loss(self.ctx, camera_array(cams), len(cams), _ptr(rgb), _ptr(target),
+                                              float(lam), _ptr(loss), _ptr(grad)))
+        return loss, grad
 
     def _release(self, state: RenderState):
         if not state.released and self.ctx is not None:

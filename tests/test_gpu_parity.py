@@ -339,3 +339,31 @@ def test_long_tile_lists(n):
     ok = ~ref["ambig"][0]
     assert np.abs(views_np(res.rgb, cams)[0] - ref["rgb"][0])[:, ok].max() < RGB_ATOL
     res.state.release()
+
+
+def test_densify_statistics_match_oracle():
+    """Sum over views of |dL/d mean2d| and the visible-view count per Gaussian
+    (densification statistics of keyframe reconstruction), and the selection."""
+    from paper_2512_20943_b300 import Rasterizer
+    rast = Rasterizer()
+    g, cams = small_sh3_scene()
+    ref = oracle.render(synthetic.widen(g), cams)
+    dL = masked_dL(cams, ref, 8)
+    t, res = render_gpu(rast, g, cams, save=True)
+    n = g["means"].shape[0]
+    dg = torch.zeros(n, dtype=torch.float32, device="cuda")
+    dv = torch.zeros(n, dtype=torch.int32, device="cuda")
+    flat = torch.from_numpy(np.concatenate([d.reshape(-1) for d in dL]).astype(np.float32)).cuda()
+    rast.render_backward_ex(res.state, dL_drgb=flat, densify=(dg, dv))
+    torch.cuda.synchronize()
+    ref_g = oracle.render_backward(synthetic.widen(g), cams, dL, densify=True)
+    ok = ref["gauss_ambig"] == 0
+    assert np.array_equal(dv.cpu().numpy()[ok], ref_g["densify_views"][ok])
+    assert_grad_close(dg.cpu().numpy()[ok], ref_g["densify_grad"][ok], "densify_grad")
+    thr = float(np.median(ref_g["densify_grad"][ref_g["densify_views"] > 0] /
+                          ref_g["densify_views"][ref_g["densify_views"] > 0]))
+    mask = rast.densify_select(dg, dv, thr).cpu().numpy()
+    d, v = dg.cpu().numpy(), dv.cpu().numpy()
+    assert np.array_equal(mask, ((v > 0) & (d > thr * v)).astype(np.uint8))
+    assert 0 < mask.sum() < n
+    res.state.release()
