@@ -242,7 +242,7 @@ int choose_variant(airgs_ctx* ctx, int64_t n, int64_t pixels, int views) {
   if (ctx->cfg.blend_variant >= 0 && ctx->cfg.blend_variant < blend_variant_count()) return ctx->cfg.blend_variant;
   auto it = ctx->tuned.find(tune_key(n, pixels, views));
   if (it != ctx->tuned.end()) return it->second;
-  return 5;  // half-tile warps with block culling unless tuned otherwise
+  return 6;  // half-tile warps with block culling and compacted staging unless tuned otherwise
 }
 
 // Forward pipeline: project -> depth sort -> emit -> tile sort -> ranges -> blend.
@@ -434,7 +434,7 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
           StageScope sc(ctx, ST_RANGES);
           CK(launch_tile_ranges(st, n_inst, skeys, s->ranges));
         }
-        if (s->variant == 5) {
+        if (s->variant == 5 || s->variant == 6) {
           // compacted half-tile lists for the half-tile culling kernels
           const int64_t hchunks = (int64_t)half_list_chunks(n_inst);
           uint8_t* hflags;

@@ -412,10 +412,11 @@ __global__ void __launch_bounds__(kTilePixels / PX) k_blend_bwd(BlendArgs a, Bwd
 // Variants 0-2: a 16x16 tile per CTA with 1, 2 or 4 pixels per thread;
 // variant 3: a tile per warp with 8 pixels per lane (blend_warp.cu);
 // variant 4: a tile per warp in eight 8x4 blocks with exact block culling;
-// variant 5: the same with a half tile (four blocks) per warp (blend_cull.cu).
+// variant 5: the same with a half tile (four blocks) per warp (blend_cull.cu);
+// variant 6: variant 5 with compacted staging and deferred backward reductions.
 static const char* kVariantName[] = {"px1_256t", "px2_128t", "px4_64t", "warp_px8", "warp_cull8x4",
-                                     "halfwarp_cull8x4"};
-constexpr int kNumVariants = 6;
+                                     "halfwarp_cull8x4", "halfwarp_cull8x4_compact"};
+constexpr int kNumVariants = 7;
 
 int blend_variant_count() { return kNumVariants; }
 const char* blend_variant_name(int v) { return (v >= 0 && v < kNumVariants) ? kVariantName[v] : ""; }
@@ -440,9 +441,11 @@ cudaError_t launch_blend_fwd(cudaStream_t st, int variant, int num_sms, const Bl
     case 3:
       return launch_blend_fwd_warp(st, num_sms, a, o);
     case 4:
-      return launch_blend_fwd_cull(st, num_sms, 8, a, o);
+      return launch_blend_fwd_cull(st, num_sms, 8, false, a, o);
     case 5:
-      return launch_blend_fwd_cull(st, num_sms, 4, a, o);
+      return launch_blend_fwd_cull(st, num_sms, 4, false, a, o);
+    case 6:
+      return launch_blend_fwd_cull(st, num_sms, 4, true, a, o);
     case 1:
       return imp ? fwd_launch<2, true>(st, 0, num_sms, a, o) : fwd_launch<2, false>(st, 0, num_sms, a, o);
     case 2:
@@ -477,9 +480,11 @@ cudaError_t launch_blend_bwd(cudaStream_t st, int variant, int num_sms, const Bl
     case 3:
       return launch_blend_bwd_warp(st, num_sms, a, in);
     case 4:
-      return launch_blend_bwd_cull(st, num_sms, 8, a, in);
+      return launch_blend_bwd_cull(st, num_sms, 8, false, a, in);
     case 5:
-      return launch_blend_bwd_cull(st, num_sms, 4, a, in);
+      return launch_blend_bwd_cull(st, num_sms, 4, false, a, in);
+    case 6:
+      return launch_blend_bwd_cull(st, num_sms, 4, true, a, in);
     case 1:
       return bwd_dispatch<2>(st, num_sms, a, in);
     case 2:

@@ -21,6 +21,14 @@
 // Per-pixel arithmetic uses the exact-replay helpers of airgs_internal.cuh; the
 // backward reduces each Gaussian's ten sums once per tile with the 20-shuffle
 // transpose butterfly and three red.global.add.v4.f32.
+//
+// COMPACT (variant 6): staging keeps only the list entries whose block mask is
+// non-zero (ballot + prefix count), so the serial walk over a batch touches
+// useful entries only; the backward also folds the live-block test into the
+// staging, and defers each Gaussian's ten sums (plus its blended-pair count)
+// into a per-warp shared-memory table of three Gaussians, reduced by one
+// column sum per lane (a transpose through shared memory) and flushed with one
+// scalar red.global.add per sum.
 #include "airgs_internal.cuh"
 #include "kernels.h"
 
@@ -58,11 +66,88 @@ __device__ __forceinline__ unsigned block_mask(float4 ga, float4 gb, float log2_
   return m;
 }
 
+
+// Tile bases of the views as 32-bit values (global tile ids stay below 2^30).
+__device__ __forceinline__ int view_of_tile32(const int* tile_base, int n_views, int tile) {
+  int lo = 0, hi = n_views - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tile_base[mid] <= tile) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Stages the list entries [b0, b0 + nb) of a tile (or half-tile) item into
+// shared memory, keeping only those whose block mask is non-zero, in list
+// order; returns how many were kept.  With LIVE the mask is also restricted to
+// the blocks whose largest n_contrib (gmax) lies beyond the entry's position,
+// and `past` is set when an entry lies at or beyond maxnc (positions increase
+// along the list, so no later batch can contribute).
+template <int NG, bool LIVE>
+__device__ __forceinline__ int stage_compact(const BlendArgs& a, bool use_hl, uint32_t b0, int nb, uint32_t list0,
+                                             const ProjRec* projv, float log2_amin, float X0, float Y0,
+                                             const int (&gmax)[NG], int maxnc, float4* s_a, float4* s_b, float* s_c,
+                                             uint32_t* s_id, uint32_t* s_pos, unsigned* s_mask, bool& past) {
+  const int lane = threadIdx.x & 31;
+  int kept = 0;
+  bool beyond = false;
+  for (int j0 = 0; j0 < nb; j0 += 32) {
+    const int j = j0 + lane;
+    unsigned msk = 0u;
+    float4 ga = make_float4(0.f, 0.f, 0.f, 0.f), gb = ga;
+    float gc = 0.f;
+    uint32_t id = 0u, pos = 0u;
+    if (j < nb) {
+      if (use_hl) {
+        const uint2 en = __ldg(a.hl + b0 + j);
+        id = en.x;
+        pos = en.y;
+      } else {
+        id = __ldg(a.ids + b0 + j);
+        pos = b0 + j - list0;
+      }
+      if (LIVE && (int)pos >= maxnc) {
+        beyond = true;
+      } else {
+        const ProjRec* r = projv + id;
+        ga = __ldg(&r->a);
+        gb = __ldg(&r->b);
+        gc = __ldg(&r->c.x);
+        msk = block_mask(ga, gb, log2_amin, X0, Y0) & ((1u << NG) - 1u);
+        if (LIVE) {
+          unsigned live = 0u;
+#pragma unroll
+          for (int k = 0; k < NG; ++k) live |= ((int)pos < gmax[k] ? 1u : 0u) << k;
+          msk &= live;
+        }
+      }
+    }
+    const unsigned bal = __ballot_sync(kAll, msk != 0u);
+    if (msk) {
+      const int d = kept + __popc(bal & ((1u << lane) - 1u));
+      s_a[d] = ga;
+      s_b[d] = gb;
+      s_c[d] = gc;
+      s_id[d] = id;
+      s_pos[d] = pos;
+      s_mask[d] = msk;
+    }
+    kept += __popc(bal);
+  }
+  if (LIVE && __any_sync(kAll, beyond)) past = true;
+  __syncwarp();
+  return kept;
+}
+
 // ------------------------------------------------------------------ forward
 // NG blocks per warp: 8 = the whole tile, 4 = one half (rows 8h .. 8h+7) of it,
 // so that two warps with half the per-lane state share a tile independently.
-template <int NG, bool IMP>
-__global__ void __launch_bounds__(32) k_blend_fwd_cull(BlendArgs a, FwdOut out) {
+#ifndef AIRGS_CULL_FWD_MINB
+#define AIRGS_CULL_FWD_MINB 32  // 64 registers: the 32-block limit of 32-thread CTAs
+#endif
+template <int NG, bool IMP, bool COMPACT>
+__global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_FWD_MINB : 1) k_blend_fwd_cull(BlendArgs a, FwdOut out) {
   constexpr int PARTS = NG_TILE / NG;
   __shared__ float4 s_a[CBATCH];
   __shared__ float4 s_b[CBATCH];
@@ -70,10 +155,10 @@ __global__ void __launch_bounds__(32) k_blend_fwd_cull(BlendArgs a, FwdOut out) 
   __shared__ uint32_t s_id[CBATCH];
   __shared__ uint32_t s_pos[CBATCH];  // position in the tile's full list
   __shared__ unsigned s_mask[CBATCH];
-  __shared__ int64_t s_tile_base[AIRGS_MAX_VIEWS_DEV];
+  __shared__ int s_tile_base[AIRGS_MAX_VIEWS_DEV];
 
   const int lane = threadIdx.x;
-  for (int v = lane; v < a.n_views; v += 32) s_tile_base[v] = a.cams[v].tile_base;
+  for (int v = lane; v < a.n_views; v += 32) s_tile_base[v] = (int)a.cams[v].tile_base;
   __syncwarp();
   const float alpha_max = a.rp.alpha_max, alpha_min = a.rp.alpha_min, T_min = a.rp.T_min;
   const float log2_amin = log2f(alpha_min);
@@ -84,9 +169,9 @@ __global__ void __launch_bounds__(32) k_blend_fwd_cull(BlendArgs a, FwdOut out) 
     const int work = cull_fetch(a.work_counter);
     if (work >= a.n_tiles * PARTS) break;
     const int item = work / PARTS, part = work % PARTS;
-    const int v = view_of_tile(s_tile_base, a.n_views, item);
+    const int v = view_of_tile32(s_tile_base, a.n_views, item);
     const CamDev& cam = a.cams[v];
-    const int lt = (int)(item - s_tile_base[v]);
+    const int lt = item - s_tile_base[v];
     const int X0 = (lt % cam.TW) * kTile, Y0 = (lt / cam.TW) * kTile + part * (kTile / PARTS);
     const float pxb[2] = {(float)(X0 + lx) + 0.5f, (float)(X0 + 8 + lx) + 0.5f};
     float T[NG], C0[NG], C1[NG], C2[NG];
@@ -114,7 +199,13 @@ __global__ void __launch_bounds__(32) k_blend_fwd_cull(BlendArgs a, FwdOut out) 
       for (int k = 0; k < NG; ++k)
         if (__any_sync(kAll, !((done >> k) & 1u))) live |= 1u << k;
       if (live == 0) break;
-      const int nb = (int)min((uint32_t)CBATCH, er.y - b0);
+      int nb = (int)min((uint32_t)CBATCH, er.y - b0);
+      if (COMPACT) {
+        const int none[NG] = {};
+        bool unused = false;
+        nb = stage_compact<NG, false>(a, use_hl, b0, nb, range.x, projv, log2_amin, (float)X0, (float)Y0, none, 0,
+                                      s_a, s_b, s_c, s_id, s_pos, s_mask, unused);
+      } else
       for (int j = lane; j < nb; j += 32) {
         uint32_t id, pos;
         if (use_hl) {
@@ -253,23 +344,87 @@ __device__ __forceinline__ void cull_reduce16_to4(float (&v)[16], int lane) {
   v[3] = __shfl_xor_sync(kAll, v[1], 4);
 }
 
+
+// Deferred per-Gaussian reduction of the backward (COMPACT): rows 10 f + q of
+// the table hold, per lane (column), sum q of the f-th deferred Gaussian,
+//   0 S_x = sum t dx, 1 S_y = sum t dy, 2 sum t dx^2, 3 sum t dx dy, 4 sum t dy^2,
+//   5 sum t, 6-8 colour, 9 blend weight,   t = dL/dalpha G on unclamped pairs,
+// so that with power2 = a2 dx^2 + b2 dx dy + c2 dy^2 and dL/dpower = o t the
+// mean gradient is o (2 a2 S_x + b2 S_y, b2 S_x + 2 c2 S_y) (times ln 2); row
+// 30 holds the lanes' blended-pair counts of the three Gaussians packed in 8-bit
+// fields (at most 4 pixels per lane and 128 per half tile, so the packed sums
+// are integers below 2^24 and exact in single precision).  Lane s sums row s
+// (the rows are padded to 33 floats, so the 32 lanes read 32 different banks)
+// and sends it with one scalar reduction.
+constexpr int kDeferG = 3;
+
+template <bool IMP>
+__device__ __forceinline__ void flush_deferred(float (*s_red)[33], const uint32_t* s_fid, const float4* s_fcon, int nf,
+                                               uint32_t cpack, GradRec* gradv, const BwdIn& in, int lane) {
+  if (IMP) s_red[30][lane] = (float)cpack;
+  __syncwarp();
+  const int row = lane < 31 ? lane : 30;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+  for (int i = 0; i < 32; i += 4) {
+    s0 += s_red[row][i];
+    s1 += s_red[row][i + 1];
+    s2 += s_red[row][i + 2];
+    s3 += s_red[row][i + 3];
+  }
+  const float sum = (s0 + s1) + (s2 + s3);
+  const float other = __shfl_xor_sync(kAll, sum, 1);  // S_y for the S_x lane and vice versa
+  if (lane < 10 * nf) {
+    const int f = lane / 10, q = lane - 10 * f;
+    const uint32_t id = s_fid[f];
+    if (q < 9) {
+      // GradRec floats 0-8: mean2d, conic A (x -1/2), B (x -1), C (x -1/2), opacity, colour
+      const float4 cf = s_fcon[f];
+      float val;
+      if (q == 0) val = kLn2 * cf.w * (2.f * cf.x * sum + cf.y * other);
+      else if (q == 1) val = kLn2 * cf.w * (cf.y * other + 2.f * cf.z * sum);
+      else if (q < 5) val = (q == 3 ? -1.f : -0.5f) * cf.w * sum;
+      else val = sum;
+      float* dst = reinterpret_cast<float*>(gradv + id) + q;
+      asm volatile("red.global.add.f32 [%0], %1;" ::"l"(dst), "f"(val) : "memory");
+    } else if (IMP && sum != 0.f) {
+      atomicAdd(in.imp_w + id, sum);
+    }
+  }
+  if (IMP) {
+    const uint32_t packed = (uint32_t)__shfl_sync(kAll, sum, 30);
+    if (lane < nf) {
+      const uint32_t c = (packed >> (8 * lane)) & 0xFFu;
+      if (c) atomicAdd(in.imp_cnt + s_fid[lane], c);
+    }
+  }
+  __syncwarp();  // the table is refilled after this
+}
+
 // ------------------------------------------------------------------ backward
 // Sums per (tile, Gaussian), scaled when flushed (see blend_warp.cu):
 //   0 mx (x ln2), 1 my (x ln2), 2 A (x -1/2), 3 B (x -1), 4 C (x -1/2),
 //   5 opacity, 6-8 colour, 9 blend weight.
-template <int NG, bool L1, bool IMP>
-__global__ void __launch_bounds__(32) k_blend_bwd_cull(BlendArgs a, BwdIn in) {
+#ifndef AIRGS_CULL_BWD_MINB
+#define AIRGS_CULL_BWD_MINB 24  // 80 registers: 24 warps per SM (measured best of 1, 20-32)
+#endif
+template <int NG, bool L1, bool IMP, bool COMPACT>
+__global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_BWD_MINB : 1) k_blend_bwd_cull(BlendArgs a, BwdIn in) {
   constexpr int PARTS = NG_TILE / NG;
+  static_assert(!COMPACT || NG * 32 < 256, "packed 8-bit pair counts");
+  __shared__ float s_red[COMPACT ? 31 : 1][33];
+  __shared__ uint32_t s_fid[kDeferG];
+  __shared__ float4 s_fcon[kDeferG];  // (a2, b2, c2, o) of the deferred Gaussians
   __shared__ float4 s_a[CBATCH];
   __shared__ float4 s_b[CBATCH];
   __shared__ float s_c[CBATCH];
   __shared__ uint32_t s_id[CBATCH];
   __shared__ uint32_t s_pos[CBATCH];  // position in the tile's full list
   __shared__ unsigned s_mask[CBATCH];
-  __shared__ int64_t s_tile_base[AIRGS_MAX_VIEWS_DEV];
+  __shared__ int s_tile_base[AIRGS_MAX_VIEWS_DEV];
 
   const int lane = threadIdx.x;
-  for (int v = lane; v < a.n_views; v += 32) s_tile_base[v] = a.cams[v].tile_base;
+  for (int v = lane; v < a.n_views; v += 32) s_tile_base[v] = (int)a.cams[v].tile_base;
   __syncwarp();
   const float alpha_max = a.rp.alpha_max, alpha_min = a.rp.alpha_min;
   const float log2_amin = log2f(alpha_min);
@@ -281,9 +436,9 @@ __global__ void __launch_bounds__(32) k_blend_bwd_cull(BlendArgs a, BwdIn in) {
     const int work = cull_fetch(a.work_counter);
     if (work >= a.n_tiles * PARTS) break;
     const int item = work / PARTS, part = work % PARTS;
-    const int v = view_of_tile(s_tile_base, a.n_views, item);
+    const int v = view_of_tile32(s_tile_base, a.n_views, item);
     const CamDev& cam = a.cams[v];
-    const int lt = (int)(item - s_tile_base[v]);
+    const int lt = item - s_tile_base[v];
     const int X0 = (lt % cam.TW) * kTile, Y0 = (lt / cam.TW) * kTile + part * (kTile / PARTS);
     const float pxb[2] = {(float)(X0 + lx) + 0.5f, (float)(X0 + 8 + lx) + 0.5f};
     const int64_t HW = (int64_t)cam.W * cam.H;
@@ -332,9 +487,15 @@ __global__ void __launch_bounds__(32) k_blend_bwd_cull(BlendArgs a, BwdIn in) {
     GradRec* gradv = in.grad + (size_t)v * a.n;
     uint32_t exec_groups = 0;
     bool past_end = false;
+    int ns = 0;          // deferred Gaussians in the table (COMPACT)
+    uint32_t cpack = 0;  // this lane's packed pair counts of those
 
     for (uint32_t b0 = er.x; b0 < er.y && !past_end; b0 += CBATCH) {
-      const int nb = (int)min((uint32_t)CBATCH, er.y - b0);
+      int nb = (int)min((uint32_t)CBATCH, er.y - b0);
+      if (COMPACT) {
+        nb = stage_compact<NG, true>(a, use_hl, b0, nb, range.x, projv, log2_amin, (float)X0, (float)Y0, gmax, maxnc,
+                                     s_a, s_b, s_c, s_id, s_pos, s_mask, past_end);
+      } else
       for (int j = lane; j < nb; j += 32) {
         uint32_t id, pos;
         if (use_hl) {
@@ -357,15 +518,18 @@ __global__ void __launch_bounds__(32) k_blend_bwd_cull(BlendArgs a, BwdIn in) {
       __syncwarp();
       for (int j = 0; j < nb; ++j) {
         const int pos = (int)s_pos[j];
-        if (pos >= maxnc) {  // positions increase along the list
-          past_end = true;
-          break;
-        }
-        unsigned live = 0;
+        unsigned m = s_mask[j];
+        if (!COMPACT) {
+          if (pos >= maxnc) {  // positions increase along the list
+            past_end = true;
+            break;
+          }
+          unsigned live = 0;
 #pragma unroll
-        for (int k = 0; k < NG; ++k) live |= (pos < gmax[k] ? 1u : 0u) << k;
-        const unsigned m = s_mask[j] & live;
-        if (m == 0) continue;
+          for (int k = 0; k < NG; ++k) live |= (pos < gmax[k] ? 1u : 0u) << k;
+          m &= live;
+          if (m == 0) continue;
+        }
         exec_groups += __popc(m);
         const float4 ga = s_a[j];
         const float4 gb = s_b[j];
@@ -376,6 +540,7 @@ __global__ void __launch_bounds__(32) k_blend_bwd_cull(BlendArgs a, BwdIn in) {
 #pragma unroll
         for (int q = 0; q < 10; ++q) acc[q] = 0.f;
         int cnt = 0;
+        if (!COMPACT) {
 #pragma unroll
         for (int k = 0; k < NG; ++k) {
           if (!((m >> k) & 1u)) continue;  // warp-uniform
@@ -409,7 +574,60 @@ __global__ void __launch_bounds__(32) k_blend_bwd_cull(BlendArgs a, BwdIn in) {
           if (IMP) acc[9] += w;
           cnt += valid ? 1 : 0;
         }
-        if (__any_sync(kAll, cnt > 0)) {
+        } else {
+#pragma unroll
+        for (int k = 0; k < NG; ++k) {
+          if (!((m >> k) & 1u)) continue;  // warp-uniform
+          const float py = (float)(Y0 + 4 * (k >> 1) + ly) + 0.5f;
+          float dy, b2dy, c2dy2;
+          row_terms(ga.y, py, ga.w, gb.x, dy, b2dy, c2dy2);
+          const float dx = dxb[k & 1];
+          const float p2 = power2_of(dx, ga.z, b2dy, c2dy2);
+          const float G = ex2_approx(p2);
+          const float oG = __fmul_rn(gb.y, G);
+          const float alpha = alpha_of(gb.y, G, alpha_max);
+          const bool valid = (pos < nc[k]) && !(p2 > 0.f) && !(alpha < alpha_min);
+          const float ae = valid ? alpha : 0.f;
+          const bool graded = valid && (oG <= alpha_max);
+          const float w = __fmul_rn(ae, T[k]);
+          const float gc = g0[k] * gb.z + g1[k] * gb.w + g2[k] * cb;
+          acc[6] = fmaf(w, g0[k], acc[6]);
+          acc[7] = fmaf(w, g1[k], acc[7]);
+          acc[8] = fmaf(w, g2[k], acc[8]);
+          // gC[k] holds the colour still ahead of the replay, R = gC - gP
+          gC[k] = fmaf(-gc, w, gC[k]);
+          const float om = __fsub_rn(1.0f, ae);
+          const float dL_dalpha = T[k] * gc - __fdividef(gC[k], om);
+          T[k] = __fmul_rn(T[k], om);
+          // t = dL/dalpha G on unclamped pairs; dL/dpower = o t, o applied at the flush
+          const float tt = dL_dalpha * (graded ? G : 0.f);
+          acc[5] += tt;
+          const float tdx = tt * dx, tdy = tt * dy;
+          acc[0] += tdx;
+          acc[1] += tdy;
+          acc[2] = fmaf(tdx, dx, acc[2]);
+          acc[3] = fmaf(tdx, dy, acc[3]);
+          acc[4] = fmaf(tdy, dy, acc[4]);
+          if (IMP) acc[9] += w;
+          cnt += valid ? 1 : 0;
+        }
+        }
+        if (COMPACT) {
+          if (__any_sync(kAll, cnt > 0)) {
+#pragma unroll
+            for (int q = 0; q < 10; ++q) s_red[ns * 10 + q][lane] = acc[q];
+            if (IMP) cpack += (uint32_t)cnt << (8 * ns);
+            if (lane == 0) {
+              s_fid[ns] = s_id[j];
+              s_fcon[ns] = make_float4(ga.z, ga.w, gb.x, gb.y);
+            }
+            if (++ns == kDeferG) {
+              flush_deferred<IMP>(s_red, s_fid, s_fcon, ns, cpack, gradv, in, lane);
+              ns = 0;
+              cpack = 0;
+            }
+          }
+        } else if (__any_sync(kAll, cnt > 0)) {
           float vals[16];
 #pragma unroll
           for (int q = 0; q < 10; ++q) vals[q] = acc[q];
@@ -432,6 +650,7 @@ __global__ void __launch_bounds__(32) k_blend_bwd_cull(BlendArgs a, BwdIn in) {
       }
       __syncwarp();
     }
+    if (COMPACT && ns > 0) flush_deferred<IMP>(s_red, s_fid, s_fcon, ns, cpack, gradv, in, lane);
     executed += 32ull * exec_groups;
   }
   for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(kAll, pairs, o);
@@ -457,44 +676,63 @@ static int cull_grid(K kernel, int num_sms, int64_t items, cudaError_t& e) {
   return (int)(items < g ? items : g);
 }
 
-template <int NG, bool IMP>
+// Shared memory is carved out to the maximum once per kernel, so that the
+// occupancy the register count allows is not cut by the per-warp tables.
+template <class K>
+static cudaError_t prefer_shared(K kernel) {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  done = true;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+}
+
+template <int NG, bool IMP, bool COMPACT>
 static cudaError_t fwd_cull(cudaStream_t st, int num_sms, const BlendArgs& a, const FwdOut& o) {
-  cudaError_t e = cudaSuccess;
-  int grid = cull_grid(k_blend_fwd_cull<NG, IMP>, num_sms, a.n_tiles * (NG_TILE / NG), e);
+  cudaError_t e = prefer_shared(k_blend_fwd_cull<NG, IMP, COMPACT>);
   if (e != cudaSuccess) return e;
-  if (grid > 0) k_blend_fwd_cull<NG, IMP><<<grid, 32, 0, st>>>(a, o);
+  int grid = cull_grid(k_blend_fwd_cull<NG, IMP, COMPACT>, num_sms, a.n_tiles * (NG_TILE / NG), e);
+  if (e != cudaSuccess) return e;
+  if (grid > 0) k_blend_fwd_cull<NG, IMP, COMPACT><<<grid, 32, 0, st>>>(a, o);
   count_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_blend_fwd_cull(cudaStream_t st, int num_sms, int blocks_per_warp, const BlendArgs& a,
+cudaError_t launch_blend_fwd_cull(cudaStream_t st, int num_sms, int blocks_per_warp, bool compact, const BlendArgs& a,
                                   const FwdOut& o) {
   const bool imp = o.imp_w != nullptr;
-  if (blocks_per_warp == 4) return imp ? fwd_cull<4, true>(st, num_sms, a, o) : fwd_cull<4, false>(st, num_sms, a, o);
-  return imp ? fwd_cull<8, true>(st, num_sms, a, o) : fwd_cull<8, false>(st, num_sms, a, o);
+  if (compact)
+    return imp ? fwd_cull<4, true, true>(st, num_sms, a, o) : fwd_cull<4, false, true>(st, num_sms, a, o);
+  if (blocks_per_warp == 4)
+    return imp ? fwd_cull<4, true, false>(st, num_sms, a, o) : fwd_cull<4, false, false>(st, num_sms, a, o);
+  return imp ? fwd_cull<8, true, false>(st, num_sms, a, o) : fwd_cull<8, false, false>(st, num_sms, a, o);
 }
 
-template <int NG, bool L1, bool IMP>
+template <int NG, bool L1, bool IMP, bool COMPACT>
 static cudaError_t bwd_cull(cudaStream_t st, int num_sms, const BlendArgs& a, const BwdIn& in) {
-  cudaError_t e = cudaSuccess;
-  int grid = cull_grid(k_blend_bwd_cull<NG, L1, IMP>, num_sms, a.n_tiles * (NG_TILE / NG), e);
+  cudaError_t e = prefer_shared(k_blend_bwd_cull<NG, L1, IMP, COMPACT>);
   if (e != cudaSuccess) return e;
-  if (grid > 0) k_blend_bwd_cull<NG, L1, IMP><<<grid, 32, 0, st>>>(a, in);
+  int grid = cull_grid(k_blend_bwd_cull<NG, L1, IMP, COMPACT>, num_sms, a.n_tiles * (NG_TILE / NG), e);
+  if (e != cudaSuccess) return e;
+  if (grid > 0) k_blend_bwd_cull<NG, L1, IMP, COMPACT><<<grid, 32, 0, st>>>(a, in);
   count_launches(1);
   return cudaGetLastError();
 }
 
-template <int NG>
+template <int NG, bool COMPACT>
 static cudaError_t bwd_cull_dispatch(cudaStream_t st, int num_sms, const BlendArgs& a, const BwdIn& in) {
   const bool l1 = in.target != nullptr, imp = in.imp_w != nullptr;
-  if (l1) return imp ? bwd_cull<NG, true, true>(st, num_sms, a, in) : bwd_cull<NG, true, false>(st, num_sms, a, in);
-  return imp ? bwd_cull<NG, false, true>(st, num_sms, a, in) : bwd_cull<NG, false, false>(st, num_sms, a, in);
+  if (l1)
+    return imp ? bwd_cull<NG, true, true, COMPACT>(st, num_sms, a, in)
+               : bwd_cull<NG, true, false, COMPACT>(st, num_sms, a, in);
+  return imp ? bwd_cull<NG, false, true, COMPACT>(st, num_sms, a, in)
+             : bwd_cull<NG, false, false, COMPACT>(st, num_sms, a, in);
 }
 
-cudaError_t launch_blend_bwd_cull(cudaStream_t st, int num_sms, int blocks_per_warp, const BlendArgs& a,
+cudaError_t launch_blend_bwd_cull(cudaStream_t st, int num_sms, int blocks_per_warp, bool compact, const BlendArgs& a,
                                   const BwdIn& in) {
-  if (blocks_per_warp == 4) return bwd_cull_dispatch<4>(st, num_sms, a, in);
-  return bwd_cull_dispatch<8>(st, num_sms, a, in);
+  if (compact) return bwd_cull_dispatch<4, true>(st, num_sms, a, in);
+  if (blocks_per_warp == 4) return bwd_cull_dispatch<4, false>(st, num_sms, a, in);
+  return bwd_cull_dispatch<8, false>(st, num_sms, a, in);
 }
 
 }  // namespace airgs

@@ -118,9 +118,9 @@ int blend_variant_count();
 const char* blend_variant_name(int v);
 cudaError_t launch_blend_fwd(cudaStream_t st, int variant, int num_sms, const BlendArgs& a, const FwdOut& o);
 cudaError_t launch_blend_bwd(cudaStream_t st, int variant, int num_sms, const BlendArgs& a, const BwdIn& in);
-cudaError_t launch_blend_fwd_cull(cudaStream_t st, int num_sms, int blocks_per_warp, const BlendArgs& a,
+cudaError_t launch_blend_fwd_cull(cudaStream_t st, int num_sms, int blocks_per_warp, bool compact, const BlendArgs& a,
                                   const FwdOut& o);
-cudaError_t launch_blend_bwd_cull(cudaStream_t st, int num_sms, int blocks_per_warp, const BlendArgs& a,
+cudaError_t launch_blend_bwd_cull(cudaStream_t st, int num_sms, int blocks_per_warp, bool compact, const BlendArgs& a,
                                   const BwdIn& in);
 cudaError_t launch_blend_fwd_warp(cudaStream_t st, int num_sms, const BlendArgs& a, const FwdOut& o);
 cudaError_t launch_blend_bwd_warp(cudaStream_t st, int num_sms, const BlendArgs& a, const BwdIn& in);

@@ -30,14 +30,15 @@ _by_variant = {}
 def rast_variant(v):
     """A context pinned to blend kernel variant v (0-2: tile per CTA with 1, 2,
     4 pixels per thread; 3: tile per warp, 8 pixels per lane; 4: tile per warp
-    in 8x4 blocks with exact block culling; 5: the same per half tile)."""
+    in 8x4 blocks with exact block culling; 5: the same per half tile; 6: 5
+    with compacted staging and deferred backward reductions)."""
     from paper_2512_20943_b300 import RasterConfig, Rasterizer
     if v not in _by_variant:
         _by_variant[v] = Rasterizer(RasterConfig(blend_variant=v))
     return _by_variant[v]
 
 
-VARIANTS = [0, 1, 2, 3, 4, 5]
+VARIANTS = [0, 1, 2, 3, 4, 5, 6]
 
 
 def render_gpu(rast, g, cams, **kw):
