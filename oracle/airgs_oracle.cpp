@@ -487,6 +487,8 @@ PixelResult blend_pixel(const BlendView& bv, const TileLists& tl, int u, int v, 
     double G = std::exp(power);
     double alpha = std::min(st.alpha_max, bv.opacity[i] * G);
     if (std::fabs(alpha - st.alpha_min) <= st.tol_rel * st.alpha_min) pr.ambig = true;
+    // the alpha_max clamp decides whether o and G receive gradient
+    if (std::fabs(bv.opacity[i] * G - st.alpha_max) <= st.tol_rel * st.alpha_max) pr.ambig = true;
     if (alpha < st.alpha_min) continue;
     double test = pr.T * (1 - alpha);
     if (std::fabs(test - st.T_min) <= st.tol_stop * st.T_min) pr.ambig = true;

@@ -67,6 +67,61 @@ __device__ __forceinline__ unsigned block_mask(float4 ga, float4 gb, float log2_
 }
 
 
+// Largest value over the rectangle [xlo, xhi] x [ylo, yhi] of offsets d = p - m
+// of the concave quadratic P(d) = a2 dx^2 + b2 dx dy + c2 dy^2 (negative
+// definite), with kx = -b2 / (2 a2), ky = -b2 / (2 c2) the maximisers along a
+// row and a column; S receives the sum of the terms' magnitudes there (the
+// scale of its rounding error).  When the centre is outside, the maximum lies
+// on a face whose outer side holds the centre (the gradient there must point
+// out of the rectangle), so only the nearer vertical and horizontal faces are
+// searched, each at its clamped 1-D maximiser.
+__device__ __forceinline__ float rect_max_power2(float a2, float b2, float c2, float kx, float ky, float xlo,
+                                                 float xhi, float ylo, float yhi, float& S) {
+  const bool in_x = xlo <= 0.f && xhi >= 0.f, in_y = ylo <= 0.f && yhi >= 0.f;
+  S = 0.f;
+  if (in_x && in_y) return 0.f;
+  float best = -INFINITY;
+  if (!in_x) {
+    const float DX = xlo > 0.f ? xlo : xhi;
+    const float dy = fminf(fmaxf(ky * DX, ylo), yhi);
+    best = fmaf(a2 * DX, DX, fmaf(b2 * DX, dy, c2 * dy * dy));
+    S = fabsf(a2) * DX * DX + fabsf(b2 * DX * dy) + fabsf(c2) * dy * dy;
+  }
+  if (!in_y) {
+    const float DY = ylo > 0.f ? ylo : yhi;
+    const float dx = fminf(fmaxf(kx * DY, xlo), xhi);
+    const float p = fmaf(a2 * dx, dx, fmaf(b2 * dx, DY, c2 * DY * DY));
+    S = fmaxf(S, fabsf(a2) * dx * dx + fabsf(b2 * dx * DY) + fabsf(c2) * DY * DY);
+    best = fmaxf(best, p);
+  }
+  return best;
+}
+
+// block_mask refined by the exact test of each block's pixel-centre rectangle
+// against the ellipse alpha >= alpha_min, i.e. P >= -L with
+// L = log2(o / alpha_min): a block is dropped only when the largest P over its
+// rectangle lies below -L by a margin far above the single-precision error of
+// both this test and the per-pair test.  Pairs in dropped blocks have
+// alpha < alpha_min, so results are bit-identical to the unrefined mask.
+__device__ __forceinline__ unsigned block_mask_exact(float4 ga, float4 gb, float log2_amin, float X0, float Y0,
+                                                     unsigned keep_bits) {
+  unsigned m = block_mask(ga, gb, log2_amin, X0, Y0) & keep_bits;
+  const float a2 = ga.z, b2 = ga.w, c2 = gb.x;
+  if (m == 0u || !(a2 < 0.f && c2 < 0.f && 4.f * a2 * c2 > 1.0001f * b2 * b2)) return m;
+  const float L = lg2_approx(gb.y) - log2_amin + 1e-3f;
+  const float kx = __fdividef(-b2, 2.f * a2), ky = __fdividef(-b2, 2.f * c2);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (!((m >> k) & 1u)) continue;
+    const float xlo = (X0 + 8.f * (k & 1) + 0.5f) - ga.x, xhi = xlo + 7.f;
+    const float ylo = (Y0 + 4.f * (k >> 1) + 0.5f) - ga.y, yhi = ylo + 3.f;
+    float S;
+    const float pm = rect_max_power2(a2, b2, c2, kx, ky, xlo, xhi, ylo, yhi, S);
+    if (pm < -L - (0.01f + 1e-5f * S)) m &= ~(1u << k);
+  }
+  return m;
+}
+
 // Tile bases of the views as 32-bit values (global tile ids stay below 2^30).
 __device__ __forceinline__ int view_of_tile32(const int* tile_base, int n_views, int tile) {
   int lo = 0, hi = n_views - 1;
@@ -114,7 +169,7 @@ __device__ __forceinline__ int stage_compact(const BlendArgs& a, bool use_hl, ui
         ga = __ldg(&r->a);
         gb = __ldg(&r->b);
         gc = __ldg(&r->c.x);
-        msk = block_mask(ga, gb, log2_amin, X0, Y0) & ((1u << NG) - 1u);
+        msk = block_mask_exact(ga, gb, log2_amin, X0, Y0, (1u << NG) - 1u);
         if (LIVE) {
           unsigned live = 0u;
 #pragma unroll
