@@ -10,6 +10,7 @@ constexpr int kTile = 16;            // 16x16 pixel tiles
 constexpr int kTilePixels = kTile * kTile;
 constexpr float kLog2e = 1.4426950408889634f;  // 1 / ln 2
 constexpr float kLn2 = 0.6931471805599453f;
+constexpr int kMaxDevicesAttr = 64;  // devices for which per-device kernel attributes are remembered
 
 // One camera as the kernels see it.
 struct CamDev {
@@ -147,6 +148,60 @@ __device__ __forceinline__ uint32_t half_flags_of(float4 ga, int kind, float hx,
   uint32_t f = 0;
   if (ga.y + hy >= Y0 + 0.5f && ga.y - hy <= Y0 + 7.5f) f |= 1u;
   if (ga.y + hy >= Y0 + 8.5f && ga.y - hy <= Y0 + 15.5f) f |= 2u;
+  return f;
+}
+
+// Largest value over the rectangle [xlo, xhi] x [ylo, yhi] of offsets d = p - m
+// of the concave quadratic P(d) = a2 dx^2 + b2 dx dy + c2 dy^2 (negative
+// definite), with kx = -b2 / (2 a2), ky = -b2 / (2 c2) the maximisers along a
+// row and a column; S receives the sum of the terms' magnitudes there (the
+// scale of its rounding error).  When the centre is outside, the maximum lies
+// on a face whose outer side holds the centre (the gradient there must point
+// out of the rectangle), so only the nearer vertical and horizontal faces are
+// searched, each at its clamped 1-D maximiser.
+__device__ __forceinline__ float rect_max_power2(float a2, float b2, float c2, float kx, float ky, float xlo,
+                                                 float xhi, float ylo, float yhi, float& S) {
+  const bool in_x = xlo <= 0.f && xhi >= 0.f, in_y = ylo <= 0.f && yhi >= 0.f;
+  S = 0.f;
+  if (in_x && in_y) return 0.f;
+  float best = -INFINITY;
+  if (!in_x) {
+    const float DX = xlo > 0.f ? xlo : xhi;
+    const float dy = fminf(fmaxf(ky * DX, ylo), yhi);
+    best = fmaf(a2 * DX, DX, fmaf(b2 * DX, dy, c2 * dy * dy));
+    S = fabsf(a2) * DX * DX + fabsf(b2 * DX * dy) + fabsf(c2) * dy * dy;
+  }
+  if (!in_y) {
+    const float DY = ylo > 0.f ? ylo : yhi;
+    const float dx = fminf(fmaxf(kx * DY, xlo), xhi);
+    const float p = fmaf(a2 * dx, dx, fmaf(b2 * dx, DY, c2 * DY * DY));
+    S = fmaxf(S, fabsf(a2) * dx * dx + fabsf(b2 * dx * DY) + fabsf(c2) * DY * DY);
+    best = fmaxf(best, p);
+  }
+  return best;
+}
+
+// Halves of the tile at (X0, Y0) in which the Gaussian can reach alpha_min:
+// the bounding-box flags of half_flags_of refined by the exact test of each
+// half's pixel-centre rectangle against the ellipse P >= -L (see
+// rect_max_power2), with the same margin the blend kernels' block test uses.
+__device__ __forceinline__ uint32_t half_flags_exact(float4 ra, float4 rb, float log2_amin, float X0, float Y0) {
+  float hx = 0.f, hy = 0.f;
+  const int kind = alpha_box(ra, rb, log2_amin, hx, hy);
+  uint32_t f = half_flags_of(ra, kind, hx, hy, X0, Y0);
+  const float a2 = ra.z, b2 = ra.w, c2 = rb.x;
+  if (f == 0u || kind != 1 || !(a2 < 0.f && c2 < 0.f && 4.f * a2 * c2 > 1.0001f * b2 * b2)) return f;
+  const float L = lg2_approx(rb.y) - log2_amin + 1e-3f;
+  const float kx = __fdividef(-b2, 2.f * a2), ky = __fdividef(-b2, 2.f * c2);
+  const float xlo = (X0 + 0.5f) - ra.x, xhi = xlo + 15.f;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    if (!((f >> h) & 1u)) continue;
+    const float ylo = (Y0 + 8.f * h + 0.5f) - ra.y, yhi = ylo + 7.f;
+    float S;
+    const float pm = rect_max_power2(a2, b2, c2, kx, ky, xlo, xhi, ylo, yhi, S);
+    if (pm < -L - (0.01f + 1e-5f * S)) f &= ~(1u << h);
+  }
   return f;
 }
 

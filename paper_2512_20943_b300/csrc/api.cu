@@ -381,7 +381,7 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
       TALLOC(vals_b, V * N);
       TALLOC(counts_sorted, V * N);
       TALLOC(rs_scratch, radix_scratch_bytes(N, n_views, ctx->num_sms) / sizeof(uint32_t) + 1);
-      int64_t n_chunks = (V * N + 1023) / 1024;
+      int64_t n_chunks = emit_chunks(V * N);
       TALLOC(chunk, n_chunks + 1);
       bool in_b = false;
       {
@@ -399,11 +399,11 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
       CK(cudaMemcpyAsync(ctx->h_pinned, chunk + n_chunks, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       n_inst = (int64_t)ctx->h_pinned[0];
-      if (n_inst >= (int64_t)0xFFFFFFFFll)
+      if (n_inst >= (int64_t)0xFFFF0000ll)
         return fail(ctx, AIRGS_E_CAPACITY, "%lld tile instances exceed the 32-bit list limit", (long long)n_inst);
       s->n_inst = n_inst;
       if (n_inst > 0) {
-        uint32_t *ikeys_a, *ikeys_b, *ivals_b, *ivals_a, *rs2;
+        uint32_t *ikeys_a, *ikeys_b, *ivals_b, *ivals_a, *rs2, *pieces;
         TALLOC(ikeys_a, n_inst);
         TALLOC(ikeys_b, n_inst);
         TALLOC(ivals_b, n_inst);
@@ -411,8 +411,9 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
         TALLOC(rs2, radix_scratch_bytes(n_inst, 1, ctx->num_sms) / sizeof(uint32_t) + 1);
         {
           StageScope sc(ctx, ST_EMIT);
-          CK(launch_emit(st, V * N, N, order, counts_sorted, chunk, s->proj, s->d_cams, ctx->cfg.alpha_min, s->n_tiles,
-                         ikeys_a, ivals_a));
+          TALLOC(pieces, emit_piece_words(V * N, n_inst));
+          CK(launch_emit(st, V * N, N, order, counts_sorted, chunk, n_inst, pieces, s->proj, s->d_cams,
+                         ctx->cfg.alpha_min, s->n_tiles, ikeys_a, ivals_a));
         }
         bool in_b2 = false;
         {

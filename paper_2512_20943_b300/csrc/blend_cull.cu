@@ -67,36 +67,6 @@ __device__ __forceinline__ unsigned block_mask(float4 ga, float4 gb, float log2_
 }
 
 
-// Largest value over the rectangle [xlo, xhi] x [ylo, yhi] of offsets d = p - m
-// of the concave quadratic P(d) = a2 dx^2 + b2 dx dy + c2 dy^2 (negative
-// definite), with kx = -b2 / (2 a2), ky = -b2 / (2 c2) the maximisers along a
-// row and a column; S receives the sum of the terms' magnitudes there (the
-// scale of its rounding error).  When the centre is outside, the maximum lies
-// on a face whose outer side holds the centre (the gradient there must point
-// out of the rectangle), so only the nearer vertical and horizontal faces are
-// searched, each at its clamped 1-D maximiser.
-__device__ __forceinline__ float rect_max_power2(float a2, float b2, float c2, float kx, float ky, float xlo,
-                                                 float xhi, float ylo, float yhi, float& S) {
-  const bool in_x = xlo <= 0.f && xhi >= 0.f, in_y = ylo <= 0.f && yhi >= 0.f;
-  S = 0.f;
-  if (in_x && in_y) return 0.f;
-  float best = -INFINITY;
-  if (!in_x) {
-    const float DX = xlo > 0.f ? xlo : xhi;
-    const float dy = fminf(fmaxf(ky * DX, ylo), yhi);
-    best = fmaf(a2 * DX, DX, fmaf(b2 * DX, dy, c2 * dy * dy));
-    S = fabsf(a2) * DX * DX + fabsf(b2 * DX * dy) + fabsf(c2) * dy * dy;
-  }
-  if (!in_y) {
-    const float DY = ylo > 0.f ? ylo : yhi;
-    const float dx = fminf(fmaxf(kx * DY, xlo), xhi);
-    const float p = fmaf(a2 * dx, dx, fmaf(b2 * dx, DY, c2 * DY * DY));
-    S = fmaxf(S, fabsf(a2) * dx * dx + fabsf(b2 * dx * DY) + fabsf(c2) * DY * DY);
-    best = fmaxf(best, p);
-  }
-  return best;
-}
-
 // block_mask refined by the exact test of each block's pixel-centre rectangle
 // against the ellipse alpha >= alpha_min, i.e. P >= -L with
 // L = log2(o / alpha_min): a block is dropped only when the largest P over its
@@ -735,9 +705,12 @@ static int cull_grid(K kernel, int num_sms, int64_t items, cudaError_t& e) {
 // occupancy the register count allows is not cut by the per-warp tables.
 template <class K>
 static cudaError_t prefer_shared(K kernel) {
-  static bool done = false;
-  if (done) return cudaSuccess;
-  done = true;
+  static bool done[kMaxDevicesAttr] = {};  // per device
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < kMaxDevicesAttr && done[dev]) return cudaSuccess;
+  if (dev < kMaxDevicesAttr) done[dev] = true;
   return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
 }
 

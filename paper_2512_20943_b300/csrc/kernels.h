@@ -45,9 +45,12 @@ cudaError_t launch_count_gather(cudaStream_t st, int64_t total, int64_t n, const
                                 const uint32_t* tiles_touched, uint32_t* counts_sorted, uint64_t* chunk_sums,
                                 int64_t* n_chunks);
 cudaError_t launch_scan_spans(cudaStream_t st, uint64_t* sums, int64_t n_chunks, uint64_t* total_out);
+size_t emit_piece_words(int64_t total, int64_t n_inst);
+int64_t emit_chunks(int64_t total);  // depth-order chunks of the count/scan/emit kernels
 cudaError_t launch_emit(cudaStream_t st, int64_t total, int64_t n, const uint32_t* order,
-                        const uint32_t* counts_sorted, const uint64_t* chunk_offsets, const ProjRec* proj,
-                        const CamDev* cams, float alpha_min, int64_t n_tiles, uint32_t* keys, uint32_t* vals);
+                        const uint32_t* counts_sorted, const uint64_t* chunk_offsets, int64_t n_inst,
+                        uint32_t* piece_off, const ProjRec* proj, const CamDev* cams, float alpha_min,
+                        int64_t n_tiles, uint32_t* keys, uint32_t* vals);
 cudaError_t launch_tile_ranges(cudaStream_t st, int64_t n_inst, const uint32_t* keys, uint2* ranges);
 
 // Usage-frequency pruning (prune.cu).

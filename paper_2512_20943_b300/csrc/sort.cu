@@ -11,11 +11,13 @@
 // Then k_tile_ranges marks each tile's [start, end).
 //
 // The radix sort is reduce-then-scan, 8-bit digits: k_rs_upsweep counts digits
-// per CTA, k_rs_spine scans the counts of each segment (digit-major, so each
-// CTA's run of a digit lands after the previous CTAs' runs: stability), and
-// k_rs_downsweep ranks each 2048-key tile stably in shared memory (warp
-// match/popc per 32-key round) and writes it out digit-contiguously, which
-// keeps the global writes coalesced.
+// per CTA, k_rs_spine scans each (segment, digit) row of per-CTA counts with
+// one warp per row (digit-major, so each CTA's run of a digit lands after the
+// previous CTAs' runs: stability) and leaves the row totals, whose scan over
+// digits every k_rs_downsweep CTA redoes in shared memory; k_rs_downsweep ranks
+// each 2048-key tile stably in shared memory (warp match/popc per 32-key
+// round) and writes it out digit-contiguously, which keeps the global writes
+// coalesced.  About RS_CTAS_PER_SM CTAs per SM keep loads in flight.
 #include "airgs_internal.cuh"
 #include "kernels.h"
 
@@ -26,6 +28,7 @@ constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_ITEMS = 8;   // keys per thread per tile
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 constexpr int RS_RADIX = 256;
+constexpr int RS_CTAS_PER_SM = 8;
 
 struct SortGeom {
   int64_t seg_len;    // keys per segment
@@ -67,42 +70,26 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_upsweep(const uint32_t* __res
   }
 }
 
-// Exclusive scan of one segment's RS_RADIX * ctas_seg counts (in place).
-__global__ void __launch_bounds__(1024) k_rs_spine(uint32_t* counts, int ctas_seg) {
-  __shared__ uint32_t warp_sums[32];
-  __shared__ uint32_t carry;
-  int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  uint32_t* c = counts + (size_t)blockIdx.x * RS_RADIX * ctas_seg;
-  int64_t total = (int64_t)RS_RADIX * ctas_seg;
-  if (tid == 0) carry = 0;
-  __syncthreads();
-  for (int64_t base = 0; base < total; base += 1024) {
-    int64_t idx = base + tid;
-    uint32_t v = idx < total ? c[idx] : 0;
+// One warp per (segment, digit) row: exclusive scan of the row's per-CTA counts
+// in place, row total -> totals[segment * RS_RADIX + digit].
+__global__ void __launch_bounds__(256) k_rs_spine(uint32_t* counts, uint32_t* totals, int ctas_seg, int rows) {
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  uint32_t* c = counts + (size_t)row * ctas_seg;
+  uint32_t carry = 0;
+  for (int base = 0; base < ctas_seg; base += 32) {
+    const int idx = base + lane;
+    const uint32_t v = idx < ctas_seg ? c[idx] : 0u;
     uint32_t x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
     }
-    if (lane == 31) warp_sums[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-      uint32_t ws = warp_sums[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, ws, o);
-        if (lane >= o) ws += y;
-      }
-      warp_sums[lane] = ws;  // inclusive
-    }
-    __syncthreads();
-    uint32_t excl = carry + (warp ? warp_sums[warp - 1] : 0) + x - v;
-    if (idx < total) c[idx] = excl;
-    __syncthreads();
-    if (tid == 1023) carry = excl + v;
-    __syncthreads();
+    if (idx < ctas_seg) c[idx] = carry + x - v;
+    carry += __shfl_sync(0xffffffffu, x, 31);
   }
+  if (lane == 0) totals[row] = carry;
 }
 
 // vals_in == nullptr: the value of a key is its index within its segment.
@@ -110,7 +97,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(const uint32_t* __r
                                                             const uint32_t* __restrict__ vals_in,
                                                             uint32_t* __restrict__ keys_out,
                                                             uint32_t* __restrict__ vals_out, SortGeom g, int shift,
-                                                            const uint32_t* __restrict__ counts) {
+                                                            const uint32_t* __restrict__ counts,
+                                                            const uint32_t* __restrict__ totals) {
   __shared__ uint32_t s_keys[RS_TILE];
   __shared__ uint32_t s_vals[RS_TILE];
   __shared__ uint32_t s_warp_cnt[RS_WARPS][RS_RADIX];  // per-warp digit counts, then per-warp offsets
@@ -124,7 +112,22 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(const uint32_t* __r
   cta_range(g, blockIdx.x, seg, t0, t1);
   int64_t base = (int64_t)seg * g.seg_len;
   int c = blockIdx.x % g.ctas_seg;
-  for (int d = tid; d < RS_RADIX; d += RS_THREADS) s_offset[d] = counts[((size_t)seg * RS_RADIX + d) * g.ctas_seg + c];
+  {
+    // digit bases of this segment: exclusive scan of the row totals (RS_THREADS == RS_RADIX)
+    const uint32_t tot = totals[(size_t)seg * RS_RADIX + tid];
+    uint32_t x = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_scan[warp] = x;
+    __syncthreads();
+    uint32_t wb = 0;
+    for (int w = 0; w < warp; ++w) wb += s_scan[w];
+    s_offset[tid] = wb + x - tot + counts[((size_t)seg * RS_RADIX + tid) * g.ctas_seg + c];
+    __syncthreads();
+  }
   const uint32_t lanemask_lt = (1u << lane) - 1u;
 
   for (int64_t t = t0; t < t1; ++t) {
@@ -214,8 +217,10 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(const uint32_t* __r
 
 // ------------------------------------------------------------------ instance emission
 constexpr int EM_THREADS = 256;
-constexpr int EM_ITEMS = 4;
+constexpr int EM_ITEMS = 2;
 constexpr int EM_CHUNK = EM_THREADS * EM_ITEMS;
+
+int64_t emit_chunks(int64_t total) { return (total + EM_CHUNK - 1) / EM_CHUNK; }
 
 // counts_sorted[p] = tiles_touched of the Gaussian at depth-order position p;
 // chunk_sums[b] = sum over chunk b.
@@ -285,60 +290,227 @@ __global__ void __launch_bounds__(1024) k_scan_spans(uint64_t* sums, int64_t n_c
   if (tid == 0) *total_out = carry;
 }
 
-// Emit every instance of every Gaussian in depth order: key = global tile id,
-// value = Gaussian index.  Tiles of one Gaussian go out row-major.
+// Pieces of at most EM_PIECE instances per chunk: piece_off[c] = exclusive
+// scan over chunks of ceil(instances of chunk c / EM_PIECE) (one CTA), total
+// pieces in piece_off[n_chunks].  chunk_offsets holds the chunks' exclusive
+// instance offsets with the total in chunk_offsets[n_chunks].
+constexpr int EM_RUN = 8;                                     // instances per thread and piece
+constexpr uint32_t EM_PIECE = (uint32_t)EM_THREADS * EM_RUN;  // instances per CTA
+constexpr int EM_STAGE = EM_THREADS * (EM_RUN + 1);            // padded staging rows (no bank conflicts)
+constexpr size_t EM_SMEM = 3 * EM_CHUNK * sizeof(float4) + EM_CHUNK * sizeof(float2) +
+                           (EM_CHUNK + 4) * sizeof(uint32_t) + 2 * EM_STAGE * sizeof(uint32_t);
+
+__global__ void __launch_bounds__(1024) k_emit_pieces(const uint64_t* __restrict__ chunk_offsets, int64_t n_chunks,
+                                                     uint32_t* __restrict__ piece_off) {
+  __shared__ uint32_t warp_sums[32];
+  __shared__ uint32_t carry;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < n_chunks; base += 1024) {
+    const int64_t c = base + tid;
+    const uint32_t v =
+        c < n_chunks ? (uint32_t)((chunk_offsets[c + 1] - chunk_offsets[c] + EM_PIECE - 1) / EM_PIECE) : 0u;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    uint32_t wb = 0;
+    for (int w = 0; w < warp; ++w) wb += warp_sums[w];
+    const uint32_t excl = carry + wb + x - v;
+    if (c < n_chunks) piece_off[c] = excl;
+    __syncthreads();
+    if (tid == 1023) carry = excl + v;
+    __syncthreads();
+  }
+  if (tid == 0) piece_off[n_chunks] = carry;
+}
+
+// piece_chunk[b] = the chunk that owns piece b (one thread per chunk).
+__global__ void k_emit_piece_map(const uint32_t* __restrict__ piece_off, int64_t n_chunks,
+                                 uint32_t* __restrict__ piece_chunk) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_chunks) return;
+  for (uint32_t b = piece_off[c]; b < piece_off[c + 1]; ++b) piece_chunk[b] = (uint32_t)c;
+}
+
+// Emit every instance of every Gaussian in depth order: key = global tile id
+// (plus the half flags in bits 30-31), value = Gaussian index; the tiles of one
+// Gaussian go out row-major.  A CTA takes one piece (at most EM_PIECE
+// instances) of a chunk of EM_CHUNK consecutive depth-order positions, so that
+// no CTA carries much more work than another however uneven the counts are
+// (nearby Gaussians, which come first in depth order, cover many tiles).  The
+// CTA scans the chunk's counts into list offsets and describes the Gaussians
+// that own the piece's instances in shared memory (one per thread: first key,
+// rectangle, alpha box and terms of the exact half test).  Thread t then
+// produces the piece's instances t*EM_RUN .. +EM_RUN: one binary search for
+// the owner of the first, then tile by tile (row-major stepping, no division
+// past the first), moving to the next Gaussian when the offsets say so; the
+// run goes to shared memory (rows padded to EM_RUN + 1 words) and the CTA
+// writes the piece out coalesced.
 __global__ void __launch_bounds__(EM_THREADS) k_emit(int64_t total, int64_t n, const uint32_t* __restrict__ order,
                                                     const uint32_t* __restrict__ counts_sorted,
                                                     const uint64_t* __restrict__ chunk_offsets,
+                                                    const uint32_t* __restrict__ piece_off,
+                                                    const uint32_t* __restrict__ piece_chunk, int64_t n_chunks,
                                                     const ProjRec* __restrict__ proj, const CamDev* __restrict__ cams,
                                                     float log2_amin, bool with_halves, uint32_t* __restrict__ keys,
                                                     uint32_t* __restrict__ vals) {
-  __shared__ uint64_t s_w[EM_THREADS / 32];
-  int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  int64_t c0 = (int64_t)blockIdx.x * EM_CHUNK;
-  // blocked arrangement: thread t owns positions c0 + t*EM_ITEMS .. +EM_ITEMS
+  // dynamic shared memory (EM_SMEM bytes):
+  extern __shared__ float4 em_smem[];
+  float4* s_box = em_smem;                   // centre, alpha-box half-widths (-inf: never, +inf: unbounded)
+  float4* s_quad = s_box + EM_CHUNK;         // a2, b2, c2 (a2 = 0: no exact test), L = log2(o / alpha_min)
+  uint4* s_rect = reinterpret_cast<uint4*>(s_quad + EM_CHUNK);  // first key, width | tile columns << 16,
+                                                                // x0 | y0 << 16, Gaussian id
+  float2* s_kxy = reinterpret_cast<float2*>(s_rect + EM_CHUNK);     // maximisers along a row / column
+  uint32_t* s_off = reinterpret_cast<uint32_t*>(s_kxy + EM_CHUNK);  // [EM_CHUNK + 1] chunk-local first instances
+  uint32_t* s_key = s_off + EM_CHUNK + 4;                             // [EM_STAGE] staged keys
+  uint32_t* s_val = s_key + EM_STAGE;                                 // [EM_STAGE] staged values
+  __shared__ uint32_t s_w[EM_THREADS / 32];
+  __shared__ int s_g0, s_g1;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t b = blockIdx.x;
+  if (b >= piece_off[n_chunks]) return;  // the grid is an upper bound on the pieces
+  const int64_t chunk = piece_chunk[b];
+  const uint32_t piece = b - piece_off[chunk];
+  const int64_t c0 = chunk * EM_CHUNK;
+  // chunk offsets: blocked, thread t scans chunk positions t*EM_ITEMS .. +EM_ITEMS
   uint32_t cnt[EM_ITEMS];
-  uint64_t local = 0;
+  uint32_t local = 0;
 #pragma unroll
   for (int j = 0; j < EM_ITEMS; ++j) {
-    int64_t p = c0 + (int64_t)tid * EM_ITEMS + j;
+    const int64_t p = c0 + (int64_t)tid * EM_ITEMS + j;
     cnt[j] = p < total ? __ldg(counts_sorted + p) : 0u;
-    local += cnt[j];
+    local += cnt[j];  // chunk totals stay below 2^32: the instance count was checked
   }
-  uint64_t x = local;
+  uint32_t x = local;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
     if (lane >= o) x += y;
   }
   if (lane == 31) s_w[warp] = x;
   __syncthreads();
-  uint64_t woff = 0;
-  for (int w = 0; w < warp; ++w) woff += s_w[w];
-  uint64_t off = chunk_offsets[blockIdx.x] + woff + x - local;
+  uint32_t off = x - local;
+  for (int w = 0; w < warp; ++w) off += s_w[w];
 #pragma unroll
   for (int j = 0; j < EM_ITEMS; ++j) {
-    int64_t p = c0 + (int64_t)tid * EM_ITEMS + j;
-    if (cnt[j]) {
-      int v = (int)(p / n);
-      uint32_t gid = __ldg(order + p);
-      const CamDev& cam = cams[v];
-      ProjRec rec = proj[(size_t)v * n + gid];
-      int radius = __float_as_int(rec.c.z);
-      int x0, y0, x1, y1;
-      tile_rect(rec.a.x, rec.a.y, radius, cam.TW, cam.TH, x0, y0, x1, y1);
-      uint32_t tb = (uint32_t)cam.tile_base;
-      float hx = 0.f, hy = 0.f;
-      const int kind = with_halves ? alpha_box(rec.a, rec.b, log2_amin, hx, hy) : 2;
-      for (int ty = y0; ty < y1; ++ty)
-        for (int tx = x0; tx < x1; ++tx) {
-          // with more than 2^24 tiles the sort reaches the top bits: keep them uniform
-          const uint32_t halves = half_flags_of(rec.a, kind, hx, hy, (float)(tx * kTile), (float)(ty * kTile));
-          keys[off] = (tb + (uint32_t)(ty * cam.TW + tx)) | (halves << kKeyHalfShift);
-          vals[off] = gid;
-          ++off;
-        }
+    s_off[tid * EM_ITEMS + j] = off;
+    off += cnt[j];
+  }
+  if (tid == EM_THREADS - 1) s_off[EM_CHUNK] = off;
+  __syncthreads();
+
+  const uint32_t p0 = piece * EM_PIECE;
+  const uint32_t p1 = (uint32_t)min((uint64_t)s_off[EM_CHUNK], (uint64_t)p0 + EM_PIECE);
+  // the last Gaussian whose first instance is <= i owns instance i
+  auto owner = [&](uint32_t i, int lo, int hi) {
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_off[mid] <= i) lo = mid;
+      else hi = mid - 1;
     }
+    return lo;
+  };
+  if (tid == 0) {
+    s_g0 = owner(p0, 0, EM_CHUNK - 1);
+    s_g1 = owner(p1 - 1, 0, EM_CHUNK - 1);
+  }
+  __syncthreads();
+  const int g0 = s_g0, g1 = s_g1;
+  for (int g = g0 + tid; g <= g1; g += EM_THREADS) {
+    if (s_off[g + 1] == s_off[g]) continue;  // no instances
+    const int64_t p = c0 + g;
+    const int v = (total < (int64_t)0xFFFFFFFFll) ? (int)((uint32_t)p / (uint32_t)n) : (int)(p / n);
+    const uint32_t gid = __ldg(order + p);
+    const CamDev& cam = cams[v];
+    const ProjRec* rec = proj + (size_t)v * n + gid;
+    const float4 ra = __ldg(&rec->a), rb = __ldg(&rec->b);
+    const int radius = __float_as_int(__ldg(&rec->c.z));
+    int x0, y0, x1, y1;
+    tile_rect(ra.x, ra.y, radius, cam.TW, cam.TH, x0, y0, x1, y1);
+    s_rect[g] = make_uint4((uint32_t)cam.tile_base + (uint32_t)(y0 * cam.TW + x0),
+                           (uint32_t)(x1 - x0) | ((uint32_t)cam.TW << 16), (uint32_t)x0 | ((uint32_t)y0 << 16), gid);
+    if (with_halves) {
+      float hx = 0.f, hy = 0.f;
+      const int kind = alpha_box(ra, rb, log2_amin, hx, hy);
+      if (kind == 0) hx = hy = -INFINITY;
+      if (kind == 2) hx = hy = INFINITY;
+      const bool exact = kind == 1 && ra.z < 0.f && rb.x < 0.f && 4.f * ra.z * rb.x > 1.0001f * ra.w * ra.w;
+      s_box[g] = make_float4(ra.x, ra.y, hx, hy);
+      s_quad[g] = make_float4(exact ? ra.z : 0.f, ra.w, rb.x, lg2_approx(rb.y) - log2_amin + 1e-3f);
+      s_kxy[g] = exact ? make_float2(__fdividef(-ra.w, 2.f * ra.z), __fdividef(-ra.w, 2.f * rb.x)) : make_float2(0.f, 0.f);
+    }
+  }
+  __syncthreads();
+  const uint32_t i0 = p0 + (uint32_t)tid * EM_RUN;
+  const uint32_t i1 = min(i0 + (uint32_t)EM_RUN, p1);
+  if (i0 < i1) {
+    int g = owner(i0, g0, g1);
+    uint4 r = s_rect[g];
+    float4 bx = s_box[g], qd = s_quad[g];
+    float2 kxy = s_kxy[g];
+    uint32_t w = r.y & 0xFFFFu, tw = r.y >> 16;
+    uint32_t qy, rx;
+    {
+      const uint32_t li = i0 - s_off[g];
+      qy = li / w;
+      rx = li - qy * w;
+    }
+    for (uint32_t i = i0; i < i1; ++i) {
+      if (i >= s_off[g + 1]) {  // first instance of the next Gaussian with instances
+        do {
+          ++g;
+        } while (i >= s_off[g + 1]);
+        r = s_rect[g];
+        bx = s_box[g];
+        qd = s_quad[g];
+        kxy = s_kxy[g];
+        w = r.y & 0xFFFFu;
+        tw = r.y >> 16;
+        qy = rx = 0;
+      }
+      // with more than 2^24 tiles the sort reaches the top bits: keep them uniform
+      uint32_t halves = 3u;
+      if (with_halves) {
+        const float X0 = (float)(((r.z & 0xFFFFu) + rx) * kTile), Y0 = (float)(((r.z >> 16) + qy) * kTile);
+        halves = 0u;
+        if (bx.x + bx.z >= X0 + 0.5f && bx.x - bx.z <= X0 + 15.5f) {
+          if (bx.y + bx.w >= Y0 + 0.5f && bx.y - bx.w <= Y0 + 7.5f) halves |= 1u;
+          if (bx.y + bx.w >= Y0 + 8.5f && bx.y - bx.w <= Y0 + 15.5f) halves |= 2u;
+        }
+        if (halves != 0u && qd.x < 0.f) {  // refine by the exact rectangle test (half_flags_exact)
+          const float xlo = (X0 + 0.5f) - bx.x, xhi = xlo + 15.f;
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            if (!((halves >> k) & 1u)) continue;
+            const float ylo = (Y0 + 8.f * k + 0.5f) - bx.y, yhi = ylo + 7.f;
+            float S;
+            const float pm = rect_max_power2(qd.x, qd.y, qd.z, kxy.x, kxy.y, xlo, xhi, ylo, yhi, S);
+            if (pm < -qd.w - (0.01f + 1e-5f * S)) halves &= ~(1u << k);
+          }
+        }
+      }
+      const int slot = tid * (EM_RUN + 1) + (int)(i - i0);
+      s_key[slot] = (r.x + qy * tw + rx) | (halves << kKeyHalfShift);
+      s_val[slot] = r.w;
+      if (++rx == w) {
+        rx = 0;
+        ++qy;
+      }
+    }
+  }
+  __syncthreads();
+  const uint64_t base = chunk_offsets[chunk] + p0;
+  const uint32_t np = p1 - p0;
+  for (uint32_t k = tid; k < np; k += EM_THREADS) {
+    const uint32_t slot = (k / EM_RUN) * (EM_RUN + 1) + (k % EM_RUN);
+    keys[base + k] = s_key[slot];
+    vals[base + k] = s_val[slot];
   }
 }
 
@@ -357,15 +529,16 @@ static SortGeom make_geom(int64_t seg_len, int n_seg, int num_sms) {
   g.n_seg = n_seg;
   g.tiles_seg = (seg_len + RS_TILE - 1) / RS_TILE;
   if (g.tiles_seg == 0) g.tiles_seg = 1;
-  int target = max(1, (2 * num_sms + n_seg - 1) / n_seg);  // about two CTAs per SM overall
+  int target = max(1, (RS_CTAS_PER_SM * num_sms + n_seg - 1) / n_seg);
   g.tiles_cta = (g.tiles_seg + target - 1) / target;
   g.ctas_seg = (int)((g.tiles_seg + g.tiles_cta - 1) / g.tiles_cta);
   return g;
 }
 
+// counts [n_seg][RS_RADIX][ctas_seg], then totals [n_seg][RS_RADIX]
 size_t radix_scratch_bytes(int64_t seg_len, int n_seg, int num_sms) {
   SortGeom g = make_geom(seg_len, n_seg, num_sms);
-  return (size_t)n_seg * RS_RADIX * g.ctas_seg * sizeof(uint32_t);
+  return (size_t)n_seg * RS_RADIX * (g.ctas_seg + 1) * sizeof(uint32_t);
 }
 
 // Sorts each of n_seg segments of seg_len keys by bits [0, key_bits), ping-
@@ -384,10 +557,11 @@ cudaError_t radix_sort_pairs(cudaStream_t st, int num_sms, uint32_t* keys_a, uin
   uint32_t *ki = keys_a, *vi = vals_a, *ko = keys_b, *vo = vals_b;
   for (int pass = 0; pass < passes; ++pass) {
     int shift = 8 * pass;
+    uint32_t* totals = scratch + (size_t)n_seg * RS_RADIX * g.ctas_seg;
     k_rs_upsweep<<<grid, RS_THREADS, 0, st>>>(ki, g, shift, scratch);
-    k_rs_spine<<<n_seg, 1024, 0, st>>>(scratch, g.ctas_seg);
+    k_rs_spine<<<(n_seg * RS_RADIX + 7) / 8, 256, 0, st>>>(scratch, totals, g.ctas_seg, n_seg * RS_RADIX);
     k_rs_downsweep<<<grid, RS_THREADS, 0, st>>>(ki, (pass == 0 && identity_vals) ? nullptr : vi, ko, vo, g, shift,
-                                                 scratch);
+                                                 scratch, totals);
     count_launches(3);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -409,9 +583,10 @@ cudaError_t radix_sort_pass(cudaStream_t st, int num_sms, const uint32_t* keys_i
                             uint32_t* keys_out, uint32_t* vals_out, int64_t n, int shift, uint32_t* counts) {
   if (n == 0) return cudaSuccess;
   SortGeom g = make_geom(n, 1, num_sms);
+  uint32_t* totals = counts + (size_t)RS_RADIX * g.ctas_seg;
   k_rs_upsweep<<<g.ctas_seg, RS_THREADS, 0, st>>>(keys_in, g, shift, counts);
-  k_rs_spine<<<1, 1024, 0, st>>>(counts, g.ctas_seg);
-  k_rs_downsweep<<<g.ctas_seg, RS_THREADS, 0, st>>>(keys_in, vals_in, keys_out, vals_out, g, shift, counts);
+  k_rs_spine<<<(RS_RADIX + 7) / 8, 256, 0, st>>>(counts, totals, g.ctas_seg, RS_RADIX);
+  k_rs_downsweep<<<g.ctas_seg, RS_THREADS, 0, st>>>(keys_in, vals_in, keys_out, vals_out, g, shift, counts, totals);
   count_launches(3);
   return cudaGetLastError();
 }
@@ -433,14 +608,39 @@ cudaError_t launch_scan_spans(cudaStream_t st, uint64_t* sums, int64_t n_chunks,
   return cudaGetLastError();
 }
 
+// piece offsets [n_chunks + 1], then the piece -> chunk map [n_inst / EM_PIECE + n_chunks + 1]
+size_t emit_piece_words(int64_t total, int64_t n_inst) {
+  const int64_t n_chunks = (total + EM_CHUNK - 1) / EM_CHUNK;
+  return (size_t)(2 * n_chunks + n_inst / EM_PIECE + 2);
+}
+
 cudaError_t launch_emit(cudaStream_t st, int64_t total, int64_t n, const uint32_t* order,
-                        const uint32_t* counts_sorted, const uint64_t* chunk_offsets, const ProjRec* proj,
-                        const CamDev* cams, float alpha_min, int64_t n_tiles, uint32_t* keys, uint32_t* vals) {
-  if (total == 0) return cudaSuccess;
-  int64_t n_chunks = (total + EM_CHUNK - 1) / EM_CHUNK;
-  k_emit<<<(unsigned)n_chunks, EM_THREADS, 0, st>>>(total, n, order, counts_sorted, chunk_offsets, proj, cams,
-                                                     log2f(alpha_min), n_tiles <= (1ll << 24), keys, vals);
-  count_launches(1);
+                        const uint32_t* counts_sorted, const uint64_t* chunk_offsets, int64_t n_inst,
+                        uint32_t* piece_off, const ProjRec* proj, const CamDev* cams, float alpha_min,
+                        int64_t n_tiles, uint32_t* keys, uint32_t* vals) {
+  if (total == 0 || n_inst == 0) return cudaSuccess;
+  const int64_t n_chunks = (total + EM_CHUNK - 1) / EM_CHUNK;
+  // sum over chunks of ceil(count / EM_PIECE) <= n_inst / EM_PIECE + n_chunks; surplus CTAs return at once
+  const int64_t grid = n_chunks + n_inst / EM_PIECE + 1;
+  uint32_t* piece_chunk = piece_off + n_chunks + 1;
+  k_emit_pieces<<<1, 1024, 0, st>>>(chunk_offsets, n_chunks, piece_off);
+  k_emit_piece_map<<<(unsigned)((n_chunks + 255) / 256), 256, 0, st>>>(piece_off, n_chunks, piece_chunk);
+  // the attribute is per device: set it once for each device this process uses
+  static bool smem_set[kMaxDevicesAttr] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= kMaxDevicesAttr || !smem_set[dev]) {
+    e = cudaFuncSetAttribute(k_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EM_SMEM);
+    if (e == cudaSuccess)  // several CTAs per SM rather than the largest L1
+      e = cudaFuncSetAttribute(k_emit, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    if (dev < kMaxDevicesAttr) smem_set[dev] = true;
+  }
+  k_emit<<<(unsigned)grid, EM_THREADS, EM_SMEM, st>>>(total, n, order, counts_sorted, chunk_offsets, piece_off,
+                                                       piece_chunk, n_chunks,
+                                                proj, cams, log2f(alpha_min), n_tiles <= (1ll << 24), keys, vals);
+  count_launches(3);
   return cudaGetLastError();
 }
 

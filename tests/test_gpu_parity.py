@@ -344,7 +344,7 @@ def test_variants_agree_bitwise_forward(scene):
 @pytest.mark.parametrize("variant", [5, 6])
 def test_needles_backward_matches_oracle(variant):
     rast = rast_variant(variant)
-    g, cams = needle_scene(thin=-4.5, long=-2.5)
+    g, cams = needle_scene(thin=-3.5, long=-2.0)
     ref = oracle.render(synthetic.widen(g), cams)
     dL = masked_dL(cams, ref, 9)
     t, res = render_gpu(rast, g, cams, save=True)
