@@ -288,6 +288,17 @@ def _blur(img, w):
     return convolve2d(img, np.outer(w, w), mode="same", boundary="fill", fillvalue=0.0)
 
 
+def ssim_map(x, y, C1=0.01 ** 2, C2=0.03 ** 2):
+    """Per-pixel SSIM of two planes (the map l3dgs_loss_grad averages)."""
+    w = ssim_window()
+    x = np.asarray(x, np.float64)
+    y = np.asarray(y, np.float64)
+    mx, my = _blur(x, w), _blur(y, w)
+    mxx, myy, mxy = _blur(x * x, w), _blur(y * y, w), _blur(x * y, w)
+    return ((2 * mx * my + C1) * (2 * (mxy - mx * my) + C2) /
+            ((mx * mx + my * my + C1) * ((mxx - mx * mx) + (myy - my * my) + C2)))
+
+
 def l3dgs_loss_grad(rgb_views, target_views, lam=0.2, C1=0.01 ** 2, C2=0.03 ** 2):
     """L_3DGS of Eq. 1: L = (1 - lam) L1 + lam (1 - SSIM), SSIM with an 11x11
     Gaussian window (sigma 1.5), zero padding, averaged over views, channels and

@@ -40,6 +40,35 @@ def test_ssim_identity_symmetry_and_direct_windows():
     assert oracle.ssim_window().sum() == pytest.approx(1.0, abs=1e-15)
 
 
+def test_ssim_closed_forms_away_from_the_border():
+    """Where the 11x11 window lies inside the image: constant planes a and b
+    give the luminance term (2ab + C1) / (a^2 + b^2 + C1) alone (no variance);
+    y = x + c (same variance, covariance = variance) gives the same luminance
+    term of the local means; y = s x gives the contrast-structure term
+    (2 s v + C2) / ((1 + s^2) v + C2) (v the local variance) times the
+    luminance term of the local means."""
+    C1, C2 = 1e-4, 9e-4
+    a, b = 0.3, 0.7
+    S = oracle.ssim_map(np.full((20, 24), a), np.full((20, 24), b))
+    assert np.allclose(S[5:-5, 5:-5], (2 * a * b + C1) / (a * a + b * b + C1), rtol=0, atol=1e-14)
+    rng = np.random.default_rng(3)
+    x = rng.random((30, 31))
+    w = oracle.ssim_window()
+    W2 = np.outer(w, w)
+    for r, c in ((12, 9), (5, 5), (24, 25)):
+        win = x[r - 5:r + 6, c - 5:c + 6]
+        mu, var = (W2 * win).sum(), (W2 * win * win).sum() - (W2 * win).sum() ** 2
+        cshift = 0.2
+        S_shift = oracle.ssim_map(x, x + cshift)[r, c]
+        lum = (2 * mu * (mu + cshift) + C1) / (mu ** 2 + (mu + cshift) ** 2 + C1)
+        assert abs(S_shift - lum) < 1e-12
+        s = 0.6
+        S_scale = oracle.ssim_map(x, s * x)[r, c]
+        lum_s = (2 * mu * s * mu + C1) / (mu ** 2 + (s * mu) ** 2 + C1)
+        cs = (2 * s * var + C2) / ((1 + s * s) * var + C2)
+        assert abs(S_scale - lum_s * cs) < 1e-12
+
+
 def test_l3dgs_gradient_central_differences():
     rng = np.random.default_rng(1)
     x = rng.random((3, 9, 12))
