@@ -46,9 +46,40 @@ MAP_SIZE = 768
 # Algorithmic work per unit (see the design notes): flops per evaluated
 # (pixel, Gaussian) pair of the blend forward and of the backward replay, and
 # bytes per Gaussian of the projection.
-FLOPS_PER_PAIR_FWD = 20
-FLOPS_PER_PAIR_BWD = 65
+# Algorithmic FP32 flops of the blending definition (exp counted apart):
+# every pair of a pixel's list up to its termination is evaluated (offsets 2,
+# quadratic form 9, o*G 1, clamp 1, T(1 - alpha) 2 with the skip and stop tests
+# = 14 + 1 exp); a blended pair adds alpha*T and three colour FMAs (7) in the
+# forward, and in the replay the colour adjoint, running prefix, dL/dalpha,
+# transmittance, opacity, mean and conic chains and the blend weight (43).
+FLOPS_TEST = 14
+FLOPS_BLEND_FWD = 7
+FLOPS_BLEND_BWD = 43
+FLOPS_ISSUED_FWD = FLOPS_TEST + FLOPS_BLEND_FWD   # per lane evaluation the kernel issues
+FLOPS_ISSUED_BWD = FLOPS_TEST + FLOPS_BLEND_BWD
 FP32_LANES_PER_SM = 128
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# dominant kernels from one ncu capture of this workload (the summary and the
+# command are under profiles/), keyed to the SHA-256 of the sources the kernel
+# was built from: once those change the counters no longer describe it (null).
+NCU_TRAFFIC = {}
+
+
+def _sources_sha256(paths):
+    import hashlib
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def dominant_traffic(stage):
+    rec = NCU_TRAFFIC.get(stage)
+    if not rec or _sources_sha256(rec["sources"]) != rec["sha256"]:
+        return None
+    return rec["bytes_per_launch"]
 
 
 def measured_peaks():
@@ -276,6 +307,7 @@ def run_ours(args):
     stream.synchronize()
 
     # timed region: per-step CUDA events on the library's stream
+    blended0 = int(imp_c.sum(dtype=torch.int64))
     rast.set_profiling(True)
     rast.stage_times()  # clear
     sampler = ClockSampler(device.index)
@@ -301,6 +333,7 @@ def run_ours(args):
     launches = Rasterizer.kernel_launch_count() - launches0
     stages = rast.stage_times()
     rast.set_profiling(False)
+    blended = (int(imp_c.sum(dtype=torch.int64)) - blended0) / args.steps  # blended pairs per step
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     total_ms = barrier_max(world, total_ms, device)
@@ -333,36 +366,39 @@ def run_ours(args):
             continue
         stage_lines[name] = {"ms_per_launch": ms[name] / nl[name], "launches": nl[name],
                              "share": ms[name] / max(1e-9, sum(ms.values()))}
-    # Blend work: the definition's pairs (list entries up to termination) and the
-    # lane evaluations the kernel actually issued (the culling variants decide
-    # most definition pairs per 8x4 block without per-pair arithmetic).  The
-    # roofline uses the issued evaluations when the variant counts them.
-    def tflops(n, flops, name):
-        return n * flops / (ms[name] / 1e3) / 1e12 if ms[name] else 0.0
-    fwd_units = stages["issued_forward"] or stages["pairs_forward"]
-    bwd_units = stages["issued_backward"] or stages["pairs_backward"]
-    fwd_tflops = tflops(fwd_units, FLOPS_PER_PAIR_FWD, "blend_fwd")
-    bwd_tflops = tflops(bwd_units, FLOPS_PER_PAIR_BWD, "blend_bwd")
-    for name, units, defn, flops in (("blend_fwd", fwd_units, stages["pairs_forward"], FLOPS_PER_PAIR_FWD),
-                                     ("blend_bwd", bwd_units, stages["pairs_backward"], FLOPS_PER_PAIR_BWD)):
+    # Blend work (algorithmic): the definition's pairs (list entries up to each
+    # pixel's termination, counted by the kernels) times the test flops, plus the
+    # blended pairs (the importance counts) times the blend flops.  The culling
+    # variants decide most definition pairs per 8x4 block without per-pair
+    # arithmetic; the lane evaluations they do issue are reported beside.
+    def rate(flops, name):
+        return flops / (ms[name] / 1e3) / 1e12 if ms[name] else 0.0
+    alg = {"blend_fwd": stages["pairs_forward"] * FLOPS_TEST + blended * args.steps * FLOPS_BLEND_FWD,
+           "blend_bwd": stages["pairs_backward"] * FLOPS_TEST + blended * args.steps * FLOPS_BLEND_BWD}
+    issued = {"blend_fwd": stages["issued_forward"] * FLOPS_ISSUED_FWD,
+              "blend_bwd": stages["issued_backward"] * FLOPS_ISSUED_BWD}
+    for name, key in (("blend_fwd", "forward"), ("blend_bwd", "backward")):
         if name in stage_lines:
-            stage_lines[name]["tflops_issued"] = tflops(units, flops, name)
-            stage_lines[name]["tflops_definition_pairs"] = tflops(defn, flops, name)
-            stage_lines[name]["issued_evals_per_launch"] = units / max(1, nl[name])
-            stage_lines[name]["definition_pairs_per_launch"] = defn / max(1, nl[name])
+            n_l = max(1, nl[name])
+            stage_lines[name]["tflops_algorithmic"] = rate(alg[name], name)
+            stage_lines[name]["tflops_issued_lanes"] = rate(issued[name], name)
+            stage_lines[name]["definition_pairs_per_launch"] = stages["pairs_" + key] / n_l
+            stage_lines[name]["issued_evals_per_launch"] = stages["issued_" + key] / n_l
+            stage_lines[name]["blended_pairs_per_launch"] = blended * args.steps / n_l
     proj_bytes = N_GAUSS * (236 + VIEWS_PER_STEP * 56)
     if ms["project_sh"]:
         stage_lines["project_sh"]["gbs"] = proj_bytes / (ms["project_sh"] / nl["project_sh"] / 1e3) / 1e9
-    if dom == "blend_bwd":
-        roof = {"bound": "alu", "achieved": bwd_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": bwd_tflops / fp32_peak, "traffic": None, "kernel": "k_blend_bwd",
+    if dom in ("blend_bwd", "blend_fwd"):
+        fl = FLOPS_BLEND_BWD if dom == "blend_bwd" else FLOPS_BLEND_FWD
+        a_t = rate(alg[dom], dom)
+        i_t = rate(issued[dom], dom)
+        roof = {"bound": "alu", "achieved": a_t, "peak": fp32_peak, "unit": "TFLOP/s", "frac": a_t / fp32_peak,
+                "traffic": dominant_traffic(dom), "kernel": "k_blend_bwd_cull" if dom == "blend_bwd" else
+                "k_blend_fwd_cull",
                 "peak_source": f"derived: {n_sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz ({peak_kind} max clock)",
-                "work": f"{FLOPS_PER_PAIR_BWD} flops per issued (pixel, Gaussian) evaluation of the replay"}
-    elif dom == "blend_fwd":
-        roof = {"bound": "alu", "achieved": fwd_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": fwd_tflops / fp32_peak, "traffic": None, "kernel": "k_blend_fwd",
-                "peak_source": f"derived: {n_sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz ({peak_kind} max clock)",
-                "work": f"{FLOPS_PER_PAIR_FWD} flops per issued (pixel, Gaussian) evaluation"}
+                "work": f"{FLOPS_TEST} flops per definition pair (list entries up to termination) + {fl} per "
+                        f"blended pair",
+                "achieved_issued_lanes": i_t, "frac_issued_lanes": i_t / fp32_peak}
     else:
         gbs = stage_lines.get(dom, {}).get("gbs")
         roof = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -387,7 +423,7 @@ def run_ours(args):
         "stages": stage_lines,
         "blend_variant": probe["variant"],
         "instances_per_step": probe["n_instances"],
-        "pairs_per_step": {"forward": stages["pairs_forward"] / args.steps,
+        "pairs_per_step": {"blended": blended, "forward": stages["pairs_forward"] / args.steps,
                            "backward": stages["pairs_backward"] / args.steps,
                            "issued_forward": stages["issued_forward"] / args.steps,
                            "issued_backward": stages["issued_backward"] / args.steps},

@@ -103,6 +103,17 @@ __device__ __forceinline__ int view_of_tile32(const int* tile_base, int n_views,
   return lo;
 }
 
+// The same search over the cameras' own tile bases (read through the cache).
+__device__ __forceinline__ int view_of_tile_cams(const CamDev* cams, int n_views, int tile) {
+  int lo = 0, hi = n_views - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((int)__ldg(&cams[mid].tile_base) <= tile) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 // Stages the list entries [b0, b0 + nb) of a tile (or half-tile) item into
 // shared memory, keeping only those whose block mask is non-zero, in list
 // order; returns how many were kept.  With LIVE the mask is also restricted to
@@ -180,10 +191,11 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_FWD_MINB : 1) k_blend
   __shared__ uint32_t s_id[CBATCH];
   __shared__ uint32_t s_pos[CBATCH];  // position in the tile's full list
   __shared__ unsigned s_mask[CBATCH];
-  __shared__ int s_tile_base[AIRGS_MAX_VIEWS_DEV];
+  __shared__ int s_tile_base[COMPACT ? 1 : AIRGS_MAX_VIEWS_DEV];  // COMPACT reads the bases from the cameras
 
   const int lane = threadIdx.x;
-  for (int v = lane; v < a.n_views; v += 32) s_tile_base[v] = (int)a.cams[v].tile_base;
+  if (!COMPACT)
+    for (int v = lane; v < a.n_views; v += 32) s_tile_base[v] = (int)a.cams[v].tile_base;
   __syncwarp();
   const float alpha_max = a.rp.alpha_max, alpha_min = a.rp.alpha_min, T_min = a.rp.T_min;
   const float log2_amin = log2f(alpha_min);
@@ -194,11 +206,14 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_FWD_MINB : 1) k_blend
     const int work = cull_fetch(a.work_counter);
     if (work >= a.n_tiles * PARTS) break;
     const int item = work / PARTS, part = work % PARTS;
-    const int v = view_of_tile32(s_tile_base, a.n_views, item);
+    const int v = COMPACT ? view_of_tile_cams(a.cams, a.n_views, item) : view_of_tile32(s_tile_base, a.n_views, item);
     const CamDev& cam = a.cams[v];
-    const int lt = item - s_tile_base[v];
+    const int lt = item - (COMPACT ? (int)__ldg(&a.cams[v].tile_base) : s_tile_base[v]);
     const int X0 = (lt % cam.TW) * kTile, Y0 = (lt / cam.TW) * kTile + part * (kTile / PARTS);
     const float pxb[2] = {(float)(X0 + lx) + 0.5f, (float)(X0 + 8 + lx) + 0.5f};
+    float pyb[NG / 2];  // pixel-centre rows of the item's block rows
+#pragma unroll
+    for (int by = 0; by < NG / 2; ++by) pyb[by] = (float)(Y0 + 4 * by + ly) + 0.5f;
     float T[NG], C0[NG], C1[NG], C2[NG];
     int last[NG], stop_at[NG];
     unsigned done = 0;
@@ -263,12 +278,15 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_FWD_MINB : 1) k_blend
         float wsum = 0.f;
         int bcount = 0;
 #pragma unroll
-        for (int k = 0; k < NG; ++k) {
+        for (int by = 0; by < NG / 2; ++by) {
+          if (!((m >> (2 * by)) & 3u)) continue;  // warp-uniform
+          float dy, b2dy, c2dy2;  // shared by the row's two blocks
+          row_terms(ga.y, pyb[by], ga.w, gb.x, dy, b2dy, c2dy2);
+#pragma unroll
+        for (int bx = 0; bx < 2; ++bx) {
+          const int k = 2 * by + bx;
           if (!((m >> k) & 1u)) continue;  // warp-uniform
-          const float py = (float)(Y0 + 4 * (k >> 1) + ly) + 0.5f;
-          float dy, b2dy, c2dy2;
-          row_terms(ga.y, py, ga.w, gb.x, dy, b2dy, c2dy2);
-          const float dx = dxb[k & 1];
+          const float dx = dxb[bx];
           const float p2 = power2_of(dx, ga.z, b2dy, c2dy2);
           const float G = ex2_approx(p2);
           const float alpha = alpha_of(gb.y, G, alpha_max);
@@ -292,6 +310,7 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_FWD_MINB : 1) k_blend
             wsum += blend ? w : 0.f;
             bcount += blend ? 1 : 0;
           }
+        }
         }
         if (IMP) {
           if (__any_sync(kAll, bcount > 0)) {
@@ -379,25 +398,30 @@ __device__ __forceinline__ void cull_reduce16_to4(float (&v)[16], int lane) {
 // 30 holds the lanes' blended-pair counts of the three Gaussians packed in 8-bit
 // fields (at most 4 pixels per lane and 128 per half tile, so the packed sums
 // are integers below 2^24 and exact in single precision).  Lane s sums row s
-// (the rows are padded to 33 floats, so the 32 lanes read 32 different banks)
-// and sends it with one scalar reduction.
+// with eight 16-byte loads (rows padded to 36 floats: each 8-lane phase of a
+// 16-byte load touches 32 different banks) and sends it with one scalar
+// reduction.
 constexpr int kDeferG = 3;
+constexpr int kRedStride = 36;  // row stride (floats): 16-byte rows, conflict-free 8-lane phases of LDS.128
 
 template <bool IMP>
-__device__ __forceinline__ void flush_deferred(float (*s_red)[33], const uint32_t* s_fid, const float4* s_fcon, int nf,
+__device__ __forceinline__ void flush_deferred(float (*s_red)[kRedStride], const uint32_t* s_fid, const float4* s_fcon,
+                                               int nf,
                                                uint32_t cpack, GradRec* gradv, const BwdIn& in, int lane) {
   if (IMP) s_red[30][lane] = (float)cpack;
   __syncwarp();
   const int row = lane < 31 ? lane : 30;
-  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  const float4* rp = reinterpret_cast<const float4*>(&s_red[row][0]);
+  float4 s = rp[0];
 #pragma unroll
-  for (int i = 0; i < 32; i += 4) {
-    s0 += s_red[row][i];
-    s1 += s_red[row][i + 1];
-    s2 += s_red[row][i + 2];
-    s3 += s_red[row][i + 3];
+  for (int i = 1; i < 8; ++i) {
+    const float4 u = rp[i];
+    s.x += u.x;
+    s.y += u.y;
+    s.z += u.z;
+    s.w += u.w;
   }
-  const float sum = (s0 + s1) + (s2 + s3);
+  const float sum = (s.x + s.y) + (s.z + s.w);
   const float other = __shfl_xor_sync(kAll, sum, 1);  // S_y for the S_x lane and vice versa
   if (lane < 10 * nf) {
     const int f = lane / 10, q = lane - 10 * f;
@@ -437,7 +461,7 @@ template <int NG, bool L1, bool IMP, bool COMPACT>
 __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_BWD_MINB : 1) k_blend_bwd_cull(BlendArgs a, BwdIn in) {
   constexpr int PARTS = NG_TILE / NG;
   static_assert(!COMPACT || NG * 32 < 256, "packed 8-bit pair counts");
-  __shared__ float s_red[COMPACT ? 31 : 1][33];
+  __shared__ __align__(16) float s_red[COMPACT ? 31 : 1][kRedStride];
   __shared__ uint32_t s_fid[kDeferG];
   __shared__ float4 s_fcon[kDeferG];  // (a2, b2, c2, o) of the deferred Gaussians
   __shared__ float4 s_a[CBATCH];
@@ -446,10 +470,11 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_BWD_MINB : 1) k_blend
   __shared__ uint32_t s_id[CBATCH];
   __shared__ uint32_t s_pos[CBATCH];  // position in the tile's full list
   __shared__ unsigned s_mask[CBATCH];
-  __shared__ int s_tile_base[AIRGS_MAX_VIEWS_DEV];
+  __shared__ int s_tile_base[COMPACT ? 1 : AIRGS_MAX_VIEWS_DEV];  // COMPACT reads the bases from the cameras
 
   const int lane = threadIdx.x;
-  for (int v = lane; v < a.n_views; v += 32) s_tile_base[v] = (int)a.cams[v].tile_base;
+  if (!COMPACT)
+    for (int v = lane; v < a.n_views; v += 32) s_tile_base[v] = (int)a.cams[v].tile_base;
   __syncwarp();
   const float alpha_max = a.rp.alpha_max, alpha_min = a.rp.alpha_min;
   const float log2_amin = log2f(alpha_min);
@@ -461,11 +486,14 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_BWD_MINB : 1) k_blend
     const int work = cull_fetch(a.work_counter);
     if (work >= a.n_tiles * PARTS) break;
     const int item = work / PARTS, part = work % PARTS;
-    const int v = view_of_tile32(s_tile_base, a.n_views, item);
+    const int v = COMPACT ? view_of_tile_cams(a.cams, a.n_views, item) : view_of_tile32(s_tile_base, a.n_views, item);
     const CamDev& cam = a.cams[v];
-    const int lt = item - s_tile_base[v];
+    const int lt = item - (COMPACT ? (int)__ldg(&a.cams[v].tile_base) : s_tile_base[v]);
     const int X0 = (lt % cam.TW) * kTile, Y0 = (lt / cam.TW) * kTile + part * (kTile / PARTS);
     const float pxb[2] = {(float)(X0 + lx) + 0.5f, (float)(X0 + 8 + lx) + 0.5f};
+    float pyb[NG / 2];  // pixel-centre rows of the item's block rows
+#pragma unroll
+    for (int by = 0; by < NG / 2; ++by) pyb[by] = (float)(Y0 + 4 * by + ly) + 0.5f;
     const int64_t HW = (int64_t)cam.W * cam.H;
     const int64_t base3 = 3 * cam.pix_base;
 
@@ -601,12 +629,15 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_BWD_MINB : 1) k_blend
         }
         } else {
 #pragma unroll
-        for (int k = 0; k < NG; ++k) {
+        for (int by = 0; by < NG / 2; ++by) {
+          if (!((m >> (2 * by)) & 3u)) continue;  // warp-uniform
+          float dy, b2dy, c2dy2;  // shared by the row's two blocks
+          row_terms(ga.y, pyb[by], ga.w, gb.x, dy, b2dy, c2dy2);
+#pragma unroll
+        for (int bx = 0; bx < 2; ++bx) {
+          const int k = 2 * by + bx;
           if (!((m >> k) & 1u)) continue;  // warp-uniform
-          const float py = (float)(Y0 + 4 * (k >> 1) + ly) + 0.5f;
-          float dy, b2dy, c2dy2;
-          row_terms(ga.y, py, ga.w, gb.x, dy, b2dy, c2dy2);
-          const float dx = dxb[k & 1];
+          const float dx = dxb[bx];
           const float p2 = power2_of(dx, ga.z, b2dy, c2dy2);
           const float G = ex2_approx(p2);
           const float oG = __fmul_rn(gb.y, G);
@@ -635,6 +666,7 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_BWD_MINB : 1) k_blend
           acc[4] = fmaf(tdy, dy, acc[4]);
           if (IMP) acc[9] += w;
           cnt += valid ? 1 : 0;
+        }
         }
         }
         if (COMPACT) {
