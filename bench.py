@@ -48,13 +48,14 @@ MAP_SIZE = 768
 # bytes per Gaussian of the projection.
 # Algorithmic FP32 flops of the blending definition (exp counted apart):
 # every pair of a pixel's list up to its termination is evaluated (offsets 2,
-# quadratic form 9, o*G 1, clamp 1, T(1 - alpha) 2 with the skip and stop tests
-# = 14 + 1 exp); a blended pair adds alpha*T and three colour FMAs (7) in the
-# forward, and in the replay the colour adjoint, running prefix, dL/dalpha,
-# transmittance, opacity, mean and conic chains and the blend weight (43).
-FLOPS_TEST = 14
+# quadratic form -(a dx^2 + c dy^2)/2 - b dx dy 9, o*G 1, clamp 1, T(1 - alpha) 2,
+# with the skip and stop tests: 15 + 1 exp); a blended pair adds alpha*T and
+# three colour FMAs (7) in the forward; in the replay alpha*T 1, the colour
+# adjoint 5, colour gradients 6, the colour still ahead 2, dL/dalpha 3,
+# dL/dpower 1, opacity 2, mean 10, conic 9, blend weight and count 2 (41).
+FLOPS_TEST = 15
 FLOPS_BLEND_FWD = 7
-FLOPS_BLEND_BWD = 43
+FLOPS_BLEND_BWD = 41
 FLOPS_ISSUED_FWD = FLOPS_TEST + FLOPS_BLEND_FWD   # per lane evaluation the kernel issues
 FLOPS_ISSUED_BWD = FLOPS_TEST + FLOPS_BLEND_BWD
 FP32_LANES_PER_SM = 128
@@ -63,7 +64,14 @@ FP32_LANES_PER_SM = 128
 # dominant kernels from one ncu capture of this workload (the summary and the
 # command are under profiles/), keyed to the SHA-256 of the sources the kernel
 # was built from: once those change the counters no longer describe it (null).
-NCU_TRAFFIC = {}
+_BLEND_SOURCES = ("paper_2512_20943_b300/csrc/blend_cull.cu", "paper_2512_20943_b300/csrc/airgs_internal.cuh",
+                  "paper_2512_20943_b300/csrc/kernels.h")
+NCU_TRAFFIC = {
+    "blend_bwd": {"bytes_per_launch": (639.598336 + 83.516416) * 1e6, "sources": _BLEND_SOURCES,
+                  "sha256": "21a13d87b638f773e370179945dfd77e7ce52160a371a1295c9fd058ca444831"},
+    "blend_fwd": {"bytes_per_launch": (227.444736 + 150.167040) * 1e6, "sources": _BLEND_SOURCES,
+                  "sha256": "21a13d87b638f773e370179945dfd77e7ce52160a371a1295c9fd058ca444831"},
+}
 
 
 def _sources_sha256(paths):
