@@ -628,6 +628,7 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_BWD_MINB : 1) k_blend
           cnt += valid ? 1 : 0;
         }
         } else {
+        float2 a01 = make_float2(0.f, 0.f), a24 = a01, a67 = a01;
 #pragma unroll
         for (int by = 0; by < NG / 2; ++by) {
           if (!((m >> (2 * by)) & 3u)) continue;  // warp-uniform
@@ -647,8 +648,8 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_BWD_MINB : 1) k_blend
           const bool graded = valid && (oG <= alpha_max);
           const float w = __fmul_rn(ae, T[k]);
           const float gc = g0[k] * gb.z + g1[k] * gb.w + g2[k] * cb;
-          acc[6] = fmaf(w, g0[k], acc[6]);
-          acc[7] = fmaf(w, g1[k], acc[7]);
+          // independent sums in pairs: one packed FP32x2 operation each
+          a67 = __ffma2_rn(make_float2(w, w), make_float2(g0[k], g1[k]), a67);
           acc[8] = fmaf(w, g2[k], acc[8]);
           // gC[k] holds the colour still ahead of the replay, R = gC - gP
           gC[k] = fmaf(-gc, w, gC[k]);
@@ -658,16 +659,21 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_BWD_MINB : 1) k_blend
           // t = dL/dalpha G on unclamped pairs; dL/dpower = o t, o applied at the flush
           const float tt = dL_dalpha * (graded ? G : 0.f);
           acc[5] += tt;
-          const float tdx = tt * dx, tdy = tt * dy;
-          acc[0] += tdx;
-          acc[1] += tdy;
-          acc[2] = fmaf(tdx, dx, acc[2]);
-          acc[3] = fmaf(tdx, dy, acc[3]);
-          acc[4] = fmaf(tdy, dy, acc[4]);
+          const float2 d2 = make_float2(dx, dy);
+          const float2 td = __fmul2_rn(make_float2(tt, tt), d2);  // (t dx, t dy)
+          a01 = __fadd2_rn(a01, td);
+          a24 = __ffma2_rn(td, d2, a24);                           // (t dx^2, t dy^2)
+          acc[3] = fmaf(td.x, dy, acc[3]);
           if (IMP) acc[9] += w;
           cnt += valid ? 1 : 0;
         }
         }
+        acc[0] = a01.x;
+        acc[1] = a01.y;
+        acc[2] = a24.x;
+        acc[4] = a24.y;
+        acc[6] = a67.x;
+        acc[7] = a67.y;
         }
         if (COMPACT) {
           if (__any_sync(kAll, cnt > 0)) {
