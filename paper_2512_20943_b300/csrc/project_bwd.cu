@@ -67,7 +67,10 @@ __device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float* 
 }
 
 template <int DEG>
-__global__ void __launch_bounds__(128) k_project_bwd(int64_t n, const float* __restrict__ means,
+#ifndef AIRGS_PROJ_BWD_MINB
+#define AIRGS_PROJ_BWD_MINB 4  // 128 registers, 16 warps per SM (measured best of 1, 4, 5, 6)
+#endif
+__global__ void __launch_bounds__(128, AIRGS_PROJ_BWD_MINB) k_project_bwd(int64_t n, const float* __restrict__ means,
                                                      const float* __restrict__ log_scales,
                                                      const float* __restrict__ quats,
                                                      const float* __restrict__ opacity_logit,
