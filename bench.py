@@ -283,6 +283,37 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- ours
+def bits_for_tiles(n_tiles):
+    return max(1, math.ceil(math.log2(max(2, n_tiles))))
+
+
+def add_stage_bandwidths(stage_lines, ms, nl, n, views, n_inst, tile_bits, sh_floats=48):
+    """Achieved GB/s of the HBM-bound stages from their algorithmic bytes per
+    launch: decode/apply 70 B per Gaussian; projection the parameters once
+    (59 + 3 + 3 + 4 + 1 floats with SH3) plus a 48 B record and 8 B of keys/counts
+    per (view, Gaussian); each radix pass 4 B read (count) + 8 B read + 8 B
+    written (scatter) per key (4 passes over view x Gaussian depth keys,
+    ceil(tile bits / 8) over the instances); emission 8 B written per instance
+    plus 52 B read per (view, Gaussian) (order, counts, record); the projection
+    adjoint the parameters read and their gradients written once plus a 48 B
+    record and a 48 B gradient record per (view, Gaussian)."""
+    params = 4 * (3 + 3 + 4 + 1 + sh_floats)
+    vn = views * n
+    model = {
+        "decode_apply": 70 * n,
+        "project_sh": params * n + 56 * vn,
+        "depth_sort": 4 * 20 * vn,
+        "tile_sort": ((tile_bits + 7) // 8) * 20 * n_inst,
+        "scan_emit": 8 * n_inst + 52 * vn,
+        "project_bwd": 2 * params * n + 96 * vn,
+    }
+    for name, nbytes in model.items():
+        if name in stage_lines and ms.get(name):
+            per_launch = ms[name] / max(1, nl[name]) / 1e3
+            launches_per_step = max(1, nl[name]) / max(1, nl.get("blend_fwd", 1))
+            stage_lines[name]["gbs"] = nbytes / (per_launch * launches_per_step) / 1e9
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_setup()
@@ -393,9 +424,8 @@ def run_ours(args):
             stage_lines[name]["definition_pairs_per_launch"] = stages["pairs_" + key] / n_l
             stage_lines[name]["issued_evals_per_launch"] = stages["issued_" + key] / n_l
             stage_lines[name]["blended_pairs_per_launch"] = blended * args.steps / n_l
-    proj_bytes = N_GAUSS * (236 + VIEWS_PER_STEP * 56)
-    if ms["project_sh"]:
-        stage_lines["project_sh"]["gbs"] = proj_bytes / (ms["project_sh"] / nl["project_sh"] / 1e3) / 1e9
+    add_stage_bandwidths(stage_lines, ms, nl, N_GAUSS, VIEWS_PER_STEP, probe["n_instances"],
+                         bits_for_tiles(VIEWS_PER_STEP * math.ceil(WIDTH / 16) * math.ceil(HEIGHT / 16)))
     if dom in ("blend_bwd", "blend_fwd"):
         fl = FLOPS_BLEND_BWD if dom == "blend_bwd" else FLOPS_BLEND_FWD
         a_t = rate(alg[dom], dom)
@@ -442,6 +472,128 @@ def run_ours(args):
         line["serving"] = run_serving(args, device)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_line()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+WORKLOADS = {
+    "plain": "plain forward render: 2,000 Gaussians SH0, one 128x128 view (forward only)",
+    "per_frame": "per-frame training step: 200k Gaussians SH3, 20 views at 1352x1014 in one launch, fused L1 backward",
+    "large": "large scene: 2M Gaussians SH3, 16 views at 3840x2160 in one launch, fused L1 backward with "
+             "importance accumulation, blend variant autotuned",
+}
+
+
+def run_config(args):
+    """The other workload shapes with the same timing, stage profiling and
+    roofline (one GPU; replicas under torchrun like the streaming step).  A step
+    is one batched render (plain) or render + fused L1 backward (per-frame,
+    large) of all the workload's views."""
+    import torch
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    device = torch.device("cuda", torch.cuda.current_device())
+    from paper_2512_20943_b300 import RasterConfig, Rasterizer
+    kind = args.workload
+    if kind == "plain":
+        g, cams = synthetic.plain_forward_scene()
+    elif kind == "per_frame":
+        g, cams = synthetic.per_frame_training_scene()
+    else:
+        g, cams = synthetic.large_scene()
+    backward = kind != "plain"
+    n = g["means"].shape[0]
+    p = [torch.from_numpy(np.ascontiguousarray(g[k])).to(device)
+         for k in ("means", "log_scales", "quats", "opacity_logit", "sh")]
+    stream = torch.cuda.Stream()
+    rast = Rasterizer(RasterConfig(blend_variant=args.variant, sort_mode=args.sort_mode), stream=stream)
+    target = None
+    if backward:
+        target = torch.from_numpy(np.concatenate([x.reshape(-1) for x in synthetic.target_images(cams, 1)])).to(device)
+    imp = None
+    if kind == "large":
+        imp = (torch.zeros(n, dtype=torch.float32, device=device), torch.zeros(n, dtype=torch.int32, device=device))
+    with torch.cuda.stream(stream):
+        if kind == "large" or args.autotune:
+            rast.set_anchor(*p)
+            rast.autotune(cams)
+
+    def step():
+        res = rast.render_gaussians(*p, cams, save=backward)
+        if backward:
+            rast.render_backward_l1(res.state, target, importance=imp)
+            res.state.release()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    stream.synchronize()
+    blended0 = int(imp[1].sum(dtype=torch.int64)) if imp is not None else 0
+    rast.set_profiling(True)
+    rast.stage_times()
+    sampler = ClockSampler(device.index)
+    launches0 = Rasterizer.kernel_launch_count()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = Rasterizer.kernel_launch_count() - launches0
+    stages = rast.stage_times()
+    rast.set_profiling(False)
+    total_ms = barrier_max(world, sum(a.elapsed_time(b) for a, b in ev), device)
+    px = sum(int(c["width"]) * int(c["height"]) for c in cams)
+    value = whole_job_value(world, px, args.steps, total_ms)
+    ms, nl = stages["ms"], stages["launches"]
+    stage_lines = {name: {"ms_per_launch": ms[name] / nl[name], "launches": nl[name],
+                          "share": ms[name] / max(1e-9, sum(ms.values()))} for name in ms if nl[name]}
+    with torch.cuda.stream(stream):
+        res = rast.render_gaussians(*p, cams, save=True)
+        st = rast.stats(res.state)
+        res.state.release()
+    n_tiles = sum(math.ceil(int(c["width"]) / 16) * math.ceil(int(c["height"]) / 16) for c in cams)
+    add_stage_bandwidths(stage_lines, ms, nl, n, len(cams), st["n_instances"], bits_for_tiles(n_tiles),
+                         sh_floats=3 * (int(g["sh_degree"]) + 1) ** 2)
+    peaks, peak_kind = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    n_sms = torch.cuda.get_device_properties(device).multi_processor_count
+    fp32_peak = n_sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    line = {
+        "metric": ("fwd+bwd" if backward else "fwd") + " Mpix/s", "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS[kind], "global_batch": len(cams) * world, "seq_len": px // len(cams),
+                   "parallelism": f"replicas x{world}" if world > 1 else "none"},
+        "gpu_launches": launches, "clocks": clocks, "stages": stage_lines,
+        "blend_variant": Rasterizer.variant_names()[st["blend_variant"]], "instances_per_step": st["n_instances"],
+    }
+    blended = (int(imp[1].sum(dtype=torch.int64)) - blended0) / args.steps if imp is not None else None
+    for name, key, fl in (("blend_fwd", "forward", FLOPS_BLEND_FWD), ("blend_bwd", "backward", FLOPS_BLEND_BWD)):
+        if name in stage_lines and blended is not None:
+            flops = stages["pairs_" + key] * FLOPS_TEST + blended * args.steps * fl
+            t_s = ms[name] / 1e3
+            stage_lines[name]["tflops_algorithmic"] = flops / t_s / 1e12
+            stage_lines[name]["frac_fp32_peak"] = flops / t_s / 1e12 / fp32_peak
+        if name in stage_lines:
+            stage_lines[name]["definition_pairs_per_launch"] = stages["pairs_" + key] / max(1, nl[name])
+            stage_lines[name]["issued_evals_per_launch"] = stages["issued_" + key] / max(1, nl[name])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -534,11 +686,15 @@ def main(argv=None):
     ap.add_argument("--autotune", action="store_true", help="time every blend variant first and keep the fastest")
     ap.add_argument("--variant", type=int, default=-1, help="blend kernel variant (-1: autotuned choice or default)")
     ap.add_argument("--sort-mode", type=int, default=-1, help="-1/0: global radix ordering; 1: per-tile ordering when lists fit")
+    ap.add_argument("--workload", choices=["streaming"] + sorted(WORKLOADS), default="streaming",
+                    help="streaming (the default line) or another workload shape, reported the same way")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "streaming":
+        return run_config(args)
     return run_ours(args)
 
 
