@@ -103,6 +103,15 @@ __device__ __forceinline__ int view_of_tile32(const int* tile_base, int n_views,
   return lo;
 }
 
+// Per staged list entry, read back with one 16-byte load: position in the
+// tile's full list, block mask, third colour channel, Gaussian id.
+struct __align__(16) StageMeta {
+  uint32_t pos;
+  unsigned mask;
+  float c;
+  uint32_t id;
+};
+
 // The same search over the cameras' own tile bases (read through the cache).
 __device__ __forceinline__ int view_of_tile_cams(const CamDev* cams, int n_views, int tile) {
   int lo = 0, hi = n_views - 1;
@@ -123,8 +132,8 @@ __device__ __forceinline__ int view_of_tile_cams(const CamDev* cams, int n_views
 template <int NG, bool LIVE>
 __device__ __forceinline__ int stage_compact(const BlendArgs& a, bool use_hl, uint32_t b0, int nb, uint32_t list0,
                                              const ProjRec* projv, float log2_amin, float X0, float Y0,
-                                             const int (&gmax)[NG], int maxnc, float4* s_a, float4* s_b, float* s_c,
-                                             uint32_t* s_id, uint32_t* s_pos, unsigned* s_mask, bool& past) {
+                                             const int (&gmax)[NG], int maxnc, float4* s_a, float4* s_b,
+                                             StageMeta* s_meta, bool& past) {
   const int lane = threadIdx.x & 31;
   int kept = 0;
   bool beyond = false;
@@ -164,10 +173,7 @@ __device__ __forceinline__ int stage_compact(const BlendArgs& a, bool use_hl, ui
       const int d = kept + __popc(bal & ((1u << lane) - 1u));
       s_a[d] = ga;
       s_b[d] = gb;
-      s_c[d] = gc;
-      s_id[d] = id;
-      s_pos[d] = pos;
-      s_mask[d] = msk;
+      s_meta[d] = StageMeta{pos, msk, gc, id};
     }
     kept += __popc(bal);
   }
@@ -187,10 +193,7 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_FWD_MINB : 1) k_blend
   constexpr int PARTS = NG_TILE / NG;
   __shared__ float4 s_a[CBATCH];
   __shared__ float4 s_b[CBATCH];
-  __shared__ float s_c[CBATCH];
-  __shared__ uint32_t s_id[CBATCH];
-  __shared__ uint32_t s_pos[CBATCH];  // position in the tile's full list
-  __shared__ unsigned s_mask[CBATCH];
+  __shared__ StageMeta s_meta[CBATCH];
   __shared__ int s_tile_base[COMPACT ? 1 : AIRGS_MAX_VIEWS_DEV];  // COMPACT reads the bases from the cameras
 
   const int lane = threadIdx.x;
@@ -244,7 +247,7 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_FWD_MINB : 1) k_blend
         const int none[NG] = {};
         bool unused = false;
         nb = stage_compact<NG, false>(a, use_hl, b0, nb, range.x, projv, log2_amin, (float)X0, (float)Y0, none, 0,
-                                      s_a, s_b, s_c, s_id, s_pos, s_mask, unused);
+                                      s_a, s_b, s_meta, unused);
       } else
       for (int j = lane; j < nb; j += 32) {
         uint32_t id, pos;
@@ -260,20 +263,19 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_FWD_MINB : 1) k_blend
         const float4 ga = __ldg(&r->a), gb = __ldg(&r->b);
         s_a[j] = ga;
         s_b[j] = gb;
-        s_c[j] = __ldg(&r->c.x);
-        s_id[j] = id;
-        s_pos[j] = pos;
-        s_mask[j] = block_mask(ga, gb, log2_amin, (float)X0, (float)Y0) & ((1u << NG) - 1u);
+        s_meta[j] = StageMeta{pos, block_mask(ga, gb, log2_amin, (float)X0, (float)Y0) & ((1u << NG) - 1u),
+                              __ldg(&r->c.x), id};
       }
       __syncwarp();
       for (int j = 0; j < nb; ++j) {
-        const unsigned m = s_mask[j] & live;
+        const StageMeta me = s_meta[j];
+        const unsigned m = me.mask & live;
         if (m == 0) continue;
         exec_groups += __popc(m);
         const float4 ga = s_a[j];
         const float4 gb = s_b[j];
-        const float cb = s_c[j];
-        const int pos1 = (int)s_pos[j] + 1;
+        const float cb = me.c;
+        const int pos1 = (int)me.pos + 1;
         const float dxb[2] = {__fsub_rn(ga.x, pxb[0]), __fsub_rn(ga.x, pxb[1])};
         float wsum = 0.f;
         int bcount = 0;
@@ -319,8 +321,8 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_FWD_MINB : 1) k_blend
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kAll, s, o);
             const int c = __reduce_add_sync(kAll, bcount);
             if (lane == 0) {
-              atomicAdd(out.imp_w + s_id[j], s);
-              atomicAdd(out.imp_cnt + s_id[j], (uint32_t)c);
+              atomicAdd(out.imp_w + me.id, s);
+              atomicAdd(out.imp_cnt + me.id, (uint32_t)c);
             }
           }
         }
@@ -413,15 +415,15 @@ __device__ __forceinline__ void flush_deferred(float (*s_red)[kRedStride], const
   const int row = lane < 31 ? lane : 30;
   const float4* rp = reinterpret_cast<const float4*>(&s_red[row][0]);
   float4 s = rp[0];
+  float2 s01 = make_float2(s.x, s.y), s23 = make_float2(s.z, s.w);
 #pragma unroll
-  for (int i = 1; i < 8; ++i) {
+  for (int i = 1; i < 8; ++i) {  // column sums as packed FP32x2 additions
     const float4 u = rp[i];
-    s.x += u.x;
-    s.y += u.y;
-    s.z += u.z;
-    s.w += u.w;
+    s01 = __fadd2_rn(s01, make_float2(u.x, u.y));
+    s23 = __fadd2_rn(s23, make_float2(u.z, u.w));
   }
-  const float sum = (s.x + s.y) + (s.z + s.w);
+  const float2 s4 = __fadd2_rn(s01, s23);
+  const float sum = s4.x + s4.y;
   const float other = __shfl_xor_sync(kAll, sum, 1);  // S_y for the S_x lane and vice versa
   if (lane < 10 * nf) {
     const int f = lane / 10, q = lane - 10 * f;
@@ -466,10 +468,7 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_BWD_MINB : 1) k_blend
   __shared__ float4 s_fcon[kDeferG];  // (a2, b2, c2, o) of the deferred Gaussians
   __shared__ float4 s_a[CBATCH];
   __shared__ float4 s_b[CBATCH];
-  __shared__ float s_c[CBATCH];
-  __shared__ uint32_t s_id[CBATCH];
-  __shared__ uint32_t s_pos[CBATCH];  // position in the tile's full list
-  __shared__ unsigned s_mask[CBATCH];
+  __shared__ StageMeta s_meta[CBATCH];
   __shared__ int s_tile_base[COMPACT ? 1 : AIRGS_MAX_VIEWS_DEV];  // COMPACT reads the bases from the cameras
 
   const int lane = threadIdx.x;
@@ -547,7 +546,7 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_BWD_MINB : 1) k_blend
       int nb = (int)min((uint32_t)CBATCH, er.y - b0);
       if (COMPACT) {
         nb = stage_compact<NG, true>(a, use_hl, b0, nb, range.x, projv, log2_amin, (float)X0, (float)Y0, gmax, maxnc,
-                                     s_a, s_b, s_c, s_id, s_pos, s_mask, past_end);
+                                     s_a, s_b, s_meta, past_end);
       } else
       for (int j = lane; j < nb; j += 32) {
         uint32_t id, pos;
@@ -563,15 +562,14 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_BWD_MINB : 1) k_blend
         const float4 ga = __ldg(&r->a), gb = __ldg(&r->b);
         s_a[j] = ga;
         s_b[j] = gb;
-        s_c[j] = __ldg(&r->c.x);
-        s_id[j] = id;
-        s_pos[j] = pos;
-        s_mask[j] = block_mask(ga, gb, log2_amin, (float)X0, (float)Y0) & ((1u << NG) - 1u);
+        s_meta[j] = StageMeta{pos, block_mask(ga, gb, log2_amin, (float)X0, (float)Y0) & ((1u << NG) - 1u),
+                              __ldg(&r->c.x), id};
       }
       __syncwarp();
       for (int j = 0; j < nb; ++j) {
-        const int pos = (int)s_pos[j];
-        unsigned m = s_mask[j];
+        const StageMeta me = s_meta[j];
+        const int pos = (int)me.pos;
+        unsigned m = me.mask;
         if (!COMPACT) {
           if (pos >= maxnc) {  // positions increase along the list
             past_end = true;
@@ -586,7 +584,7 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_BWD_MINB : 1) k_blend
         exec_groups += __popc(m);
         const float4 ga = s_a[j];
         const float4 gb = s_b[j];
-        const float cb = s_c[j];
+        const float cb = me.c;
         const float dxb[2] = {__fsub_rn(ga.x, pxb[0]), __fsub_rn(ga.x, pxb[1])};
         const float twoa2 = 2.f * ga.z;
         float acc[10];
@@ -681,7 +679,7 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_BWD_MINB : 1) k_blend
             for (int q = 0; q < 10; ++q) s_red[ns * 10 + q][lane] = acc[q];
             if (IMP) cpack += (uint32_t)cnt << (8 * ns);
             if (lane == 0) {
-              s_fid[ns] = s_id[j];
+              s_fid[ns] = me.id;
               s_fcon[ns] = make_float4(ga.z, ga.w, gb.x, gb.y);
             }
             if (++ns == kDeferG) {
@@ -697,7 +695,7 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_BWD_MINB : 1) k_blend
 #pragma unroll
           for (int q = 10; q < 16; ++q) vals[q] = 0.f;
           cull_reduce16_to4(vals, lane);
-          const uint32_t id = s_id[j];
+          const uint32_t id = me.id;
           float* gr = reinterpret_cast<float*>(gradv + id);
           if (lane == 0) red_add_v4(gr, vals[0] * kLn2, vals[1] * kLn2, -0.5f * vals[2], -vals[3]);
           if (lane == 8) red_add_v4(gr + 4, -0.5f * vals[0], vals[1], vals[2], vals[3]);
