@@ -205,6 +205,60 @@ __device__ __forceinline__ uint32_t half_flags_exact(float4 ra, float4 rb, float
   return f;
 }
 
+// Blocks of the tile at (X0, Y0) that the Gaussian's alpha >= alpha_min box
+// meets (bit k: block bx = k & 1, by = k >> 1).
+__device__ __forceinline__ unsigned block_mask(float4 ga, float4 gb, float log2_amin, float X0, float Y0) {
+  const float mx = ga.x, my = ga.y;
+  float hx = 0.f, hy = 0.f;
+  const int kind = alpha_box(ga, gb, log2_amin, hx, hy);
+  if (kind == 0) return 0u;     // o below alpha_min: never blends
+  if (kind == 2) return 0xFFu;  // no bound: leave it to the per-pair test
+  unsigned xm = 0, m = 0;
+#pragma unroll
+  for (int bx = 0; bx < 2; ++bx) {
+    const float lo = X0 + 8.f * bx + 0.5f, hi = lo + 7.f;
+    if (mx + hx >= lo && mx - hx <= hi) xm |= 1u << bx;
+  }
+#pragma unroll
+  for (int by = 0; by < 4; ++by) {
+    const float lo = Y0 + 4.f * by + 0.5f, hi = lo + 3.f;
+    if (my + hy >= lo && my - hy <= hi) m |= xm << (2 * by);
+  }
+  return m;
+}
+
+
+// block_mask refined by the exact test of each block's pixel-centre rectangle
+// against the ellipse alpha >= alpha_min, i.e. P >= -L with
+// L = log2(o / alpha_min): a block is dropped only when the largest P over its
+// rectangle lies below -L by a margin far above the single-precision error of
+// both this test and the per-pair test.  Pairs in dropped blocks have
+// alpha < alpha_min, so results are bit-identical to the unrefined mask.
+__device__ __forceinline__ unsigned block_mask_exact(float4 ga, float4 gb, float log2_amin, float X0, float Y0,
+                                                     unsigned keep_bits) {
+  unsigned m = block_mask(ga, gb, log2_amin, X0, Y0) & keep_bits;
+  const float a2 = ga.z, b2 = ga.w, c2 = gb.x;
+  if (m == 0u || !(a2 < 0.f && c2 < 0.f && 4.f * a2 * c2 > 1.0001f * b2 * b2)) return m;
+  const float L = lg2_approx(gb.y) - log2_amin + 1e-3f;
+  const float kx = __fdividef(-b2, 2.f * a2), ky = __fdividef(-b2, 2.f * c2);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (!((m >> k) & 1u)) continue;
+    const float xlo = (X0 + 8.f * (k & 1) + 0.5f) - ga.x, xhi = xlo + 7.f;
+    const float ylo = (Y0 + 4.f * (k >> 1) + 0.5f) - ga.y, yhi = ylo + 3.f;
+    float S;
+    const float pm = rect_max_power2(a2, b2, c2, kx, ky, xlo, xhi, ylo, yhi, S);
+    if (pm < -L - (0.01f + 1e-5f * S)) m &= ~(1u << k);
+  }
+  return m;
+}
+
+// Half-tile list entries: (Gaussian id, position in the tile's full list in
+// bits 0-27 | the half's 8x4 blocks the Gaussian can reach alpha_min in, bits
+// 28-31, as block_mask_exact gives them).
+constexpr uint32_t kHlPosMask = 0x0FFFFFFFu;
+constexpr int kHlMaskShift = 28;
+
 __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
                : "memory");

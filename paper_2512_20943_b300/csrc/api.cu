@@ -435,8 +435,9 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
           StageScope sc(ctx, ST_RANGES);
           CK(launch_tile_ranges(st, n_inst, skeys, s->ranges));
         }
-        if (s->variant == 5 || s->variant == 6) {
-          // compacted half-tile lists for the half-tile culling kernels
+        if ((s->variant == 5 || s->variant == 6) && n_inst < (1ll << 28)) {
+          // compacted half-tile lists for the half-tile culling kernels (list positions fit 28 bits;
+          // otherwise the kernels walk the full lists and test the blocks themselves)
           const int64_t hchunks = (int64_t)half_list_chunks(n_inst);
           uint8_t* hflags;
           uint64_t* hsums;
@@ -467,6 +468,7 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
   a.pair_total = ctx->profiling ? ctx->d_pair_total : nullptr;
   a.exec_total = ctx->profiling ? ctx->d_pair_total + 2 : nullptr;
   a.hl = s->hl;
+  a.hl_mut = s->hl;
   a.hranges = s->hranges;
   FwdOut o;
   o.rgb = rgb_out;
@@ -528,6 +530,7 @@ int backward_impl(airgs_ctx* ctx, airgs_state* s, const float* dL, const float* 
   a.pair_total = ctx->profiling ? ctx->d_pair_total + 1 : nullptr;
   a.exec_total = ctx->profiling ? ctx->d_pair_total + 3 : nullptr;
   a.hl = s->hl;
+  a.hl_mut = s->hl;
   a.hranges = s->hranges;
   BwdIn in;
   in.rgb = s->rgb;

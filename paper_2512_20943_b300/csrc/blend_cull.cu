@@ -44,53 +44,6 @@ __device__ __forceinline__ int cull_fetch(int* counter) {
   return __shfl_sync(kAll, it, 0);
 }
 
-// Blocks of the tile at (X0, Y0) that the Gaussian's alpha >= alpha_min box
-// meets (bit k: block bx = k & 1, by = k >> 1).
-__device__ __forceinline__ unsigned block_mask(float4 ga, float4 gb, float log2_amin, float X0, float Y0) {
-  const float mx = ga.x, my = ga.y;
-  float hx = 0.f, hy = 0.f;
-  const int kind = alpha_box(ga, gb, log2_amin, hx, hy);
-  if (kind == 0) return 0u;     // o below alpha_min: never blends
-  if (kind == 2) return 0xFFu;  // no bound: leave it to the per-pair test
-  unsigned xm = 0, m = 0;
-#pragma unroll
-  for (int bx = 0; bx < 2; ++bx) {
-    const float lo = X0 + 8.f * bx + 0.5f, hi = lo + 7.f;
-    if (mx + hx >= lo && mx - hx <= hi) xm |= 1u << bx;
-  }
-#pragma unroll
-  for (int by = 0; by < 4; ++by) {
-    const float lo = Y0 + 4.f * by + 0.5f, hi = lo + 3.f;
-    if (my + hy >= lo && my - hy <= hi) m |= xm << (2 * by);
-  }
-  return m;
-}
-
-
-// block_mask refined by the exact test of each block's pixel-centre rectangle
-// against the ellipse alpha >= alpha_min, i.e. P >= -L with
-// L = log2(o / alpha_min): a block is dropped only when the largest P over its
-// rectangle lies below -L by a margin far above the single-precision error of
-// both this test and the per-pair test.  Pairs in dropped blocks have
-// alpha < alpha_min, so results are bit-identical to the unrefined mask.
-__device__ __forceinline__ unsigned block_mask_exact(float4 ga, float4 gb, float log2_amin, float X0, float Y0,
-                                                     unsigned keep_bits) {
-  unsigned m = block_mask(ga, gb, log2_amin, X0, Y0) & keep_bits;
-  const float a2 = ga.z, b2 = ga.w, c2 = gb.x;
-  if (m == 0u || !(a2 < 0.f && c2 < 0.f && 4.f * a2 * c2 > 1.0001f * b2 * b2)) return m;
-  const float L = lg2_approx(gb.y) - log2_amin + 1e-3f;
-  const float kx = __fdividef(-b2, 2.f * a2), ky = __fdividef(-b2, 2.f * c2);
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    if (!((m >> k) & 1u)) continue;
-    const float xlo = (X0 + 8.f * (k & 1) + 0.5f) - ga.x, xhi = xlo + 7.f;
-    const float ylo = (Y0 + 4.f * (k >> 1) + 0.5f) - ga.y, yhi = ylo + 3.f;
-    float S;
-    const float pm = rect_max_power2(a2, b2, c2, kx, ky, xlo, xhi, ylo, yhi, S);
-    if (pm < -L - (0.01f + 1e-5f * S)) m &= ~(1u << k);
-  }
-  return m;
-}
 
 // Tile bases of the views as 32-bit values (global tile ids stay below 2^30).
 __device__ __forceinline__ int view_of_tile32(const int* tile_base, int n_views, int tile) {
@@ -125,10 +78,13 @@ __device__ __forceinline__ int view_of_tile_cams(const CamDev* cams, int n_views
 
 // Stages the list entries [b0, b0 + nb) of a tile (or half-tile) item into
 // shared memory, keeping only those whose block mask is non-zero, in list
-// order; returns how many were kept.  With LIVE the mask is also restricted to
-// the blocks whose largest n_contrib (gmax) lies beyond the entry's position,
-// and `past` is set when an entry lies at or beyond maxnc (positions increase
-// along the list, so no later batch can contribute).
+// order; returns how many were kept.  With LIVE (the backward) the mask is also
+// restricted to the blocks whose largest n_contrib (gmax) lies beyond the
+// entry's position, and `past` is set when an entry lies at or beyond maxnc
+// (positions increase along the list, so no later batch can contribute).
+// Half-list entries: the forward computes each staged entry's exact block mask
+// and stores it in the entry's top bits; the backward reads it from there (every
+// entry before maxnc was staged by the forward of the same state).
 template <int NG, bool LIVE>
 __device__ __forceinline__ int stage_compact(const BlendArgs& a, bool use_hl, uint32_t b0, int nb, uint32_t list0,
                                              const ProjRec* projv, float log2_amin, float X0, float Y0,
@@ -144,28 +100,37 @@ __device__ __forceinline__ int stage_compact(const BlendArgs& a, bool use_hl, ui
     float gc = 0.f;
     uint32_t id = 0u, pos = 0u;
     if (j < nb) {
+      bool have_mask = false;
       if (use_hl) {
-        const uint2 en = __ldg(a.hl + b0 + j);
+        const uint2 en = a.hl[b0 + j];  // not through the read-only cache: the forward writes the masks
         id = en.x;
-        pos = en.y;
+        pos = en.y & kHlPosMask;
+        msk = en.y >> kHlMaskShift;
+        have_mask = LIVE;  // the backward reads the forward's masks
       } else {
         id = __ldg(a.ids + b0 + j);
         pos = b0 + j - list0;
       }
       if (LIVE && (int)pos >= maxnc) {
         beyond = true;
+        msk = 0u;
       } else {
-        const ProjRec* r = projv + id;
-        ga = __ldg(&r->a);
-        gb = __ldg(&r->b);
-        gc = __ldg(&r->c.x);
-        msk = block_mask_exact(ga, gb, log2_amin, X0, Y0, (1u << NG) - 1u);
         if (LIVE) {
           unsigned live = 0u;
 #pragma unroll
           for (int k = 0; k < NG; ++k) live |= ((int)pos < gmax[k] ? 1u : 0u) << k;
-          msk &= live;
+          msk = have_mask ? (msk & live) : live;
+        } else if (!have_mask) {
+          msk = (1u << NG) - 1u;
         }
+        if (msk) {
+          const ProjRec* r = projv + id;
+          ga = __ldg(&r->a);
+          gb = __ldg(&r->b);
+          gc = __ldg(&r->c.x);
+          if (!have_mask) msk &= block_mask_exact(ga, gb, log2_amin, X0, Y0, (1u << NG) - 1u);
+        }
+        if (!LIVE && use_hl) a.hl_mut[b0 + j].y = pos | (msk << kHlMaskShift);
       }
     }
     const unsigned bal = __ballot_sync(kAll, msk != 0u);
@@ -254,7 +219,7 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_FWD_MINB : 1) k_blend
         if (use_hl) {
           const uint2 en = __ldg(a.hl + b0 + j);
           id = en.x;
-          pos = en.y;
+          pos = en.y & kHlPosMask;
         } else {
           id = __ldg(a.ids + b0 + j);
           pos = b0 + j - range.x;
@@ -553,7 +518,7 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_BWD_MINB : 1) k_blend
         if (use_hl) {
           const uint2 en = __ldg(a.hl + b0 + j);
           id = en.x;
-          pos = en.y;
+          pos = en.y & kHlPosMask;
         } else {
           id = __ldg(a.ids + b0 + j);
           pos = b0 + j - range.x;

@@ -92,7 +92,8 @@ struct BlendArgs {
   unsigned long long* pair_counter;
   unsigned long long* pair_total;  // nullable: cumulative counter of the context
   unsigned long long* exec_total;  // nullable: cumulative lane evaluations actually issued (culling variants)
-  const uint2* hl;                 // nullable: half-tile lists of (Gaussian id, full-list position)
+  const uint2* hl;                 // nullable: half-tile lists of (Gaussian id, full-list position | block mask)
+  uint2* hl_mut;                   // the same lists, written by the compacting forward (block masks)
   const uint2* hranges;            // [2][tiles] ranges into hl (top halves, then bottom halves)
 };
 
