@@ -437,6 +437,10 @@ def run_ours(args):
                 "work": f"{FLOPS_TEST} flops per definition pair (list entries up to termination) + {fl} per "
                         f"blended pair",
                 "achieved_issued_lanes": i_t, "frac_issued_lanes": i_t / fp32_peak}
+        with torch.cuda.stream(stream):
+            measured = rast.measure_fp32_peak()  # an FMA probe on this GPU, after the timed region
+        roof["peak_measured_fma_probe"] = measured
+        roof["frac_of_measured_peak"] = a_t / measured
     else:
         gbs = stage_lines.get(dom, {}).get("gbs")
         roof = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",

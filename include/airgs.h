@@ -330,6 +330,14 @@ int airgs_set_profiling(airgs_ctx* ctx, int enabled);
 int airgs_stage_times(airgs_ctx* ctx, double* ms, int64_t* launches, int64_t* pairs);
 const char* airgs_stage_name(int stage);
 
+/* Measured FP32 throughput of the context's GPU (an FMA probe, 16 independent
+ * chains per thread, 8 CTAs of 256 threads per SM, fastest of three timed
+ * runs) in TFLOP/s -> *tflops.  Synchronises the context's stream.  The
+ * measurement aid for the blend kernels' roofline; the paper has no
+ * counterpart.  Returns AIRGS_E_ARG for a null pointer, AIRGS_E_OOM or
+ * AIRGS_E_CUDA on failure. */
+int airgs_measure_fp32_peak(airgs_ctx* ctx, double* tflops);
+
 /* Process-wide number of kernel launches the library has issued. */
 int64_t airgs_kernel_launch_count(void);
 

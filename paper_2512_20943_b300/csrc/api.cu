@@ -1112,6 +1112,17 @@ int airgs_stage_times(airgs_ctx* ctx, double* ms, int64_t* launches, int64_t* pa
 
 const char* airgs_stage_name(int stage) { return (stage >= 0 && stage < ST_COUNT) ? kStageNames[stage] : ""; }
 
+int airgs_measure_fp32_peak(airgs_ctx* ctx, double* tflops) {
+  if (!ctx || !tflops) return AIRGS_E_ARG;
+  float* scratch = nullptr;
+  int rc = dalloc(ctx, &scratch, fp32_probe_words(ctx->num_sms));
+  if (rc) return rc;
+  const cudaError_t e = measure_fp32_peak(ctx->stream, ctx->num_sms, scratch, tflops);
+  dfree(ctx, scratch);
+  if (e != cudaSuccess) return fail(ctx, AIRGS_E_CUDA, "fp32 probe: %s", cudaGetErrorString(e));
+  return AIRGS_OK;
+}
+
 int64_t airgs_kernel_launch_count(void) { return g_launches.load(); }
 
 int airgs_blend_variant_count(void) { return blend_variant_count(); }

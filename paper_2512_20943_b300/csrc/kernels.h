@@ -135,4 +135,7 @@ cudaError_t launch_project_bwd(cudaStream_t st, int64_t n, int sh_degree, const 
                                const GradRec* grad, float* g_means, float* g_log_scales, float* g_quats,
                                float* g_opacity, float* g_sh, float* dens_grad, uint32_t* dens_views);
 
+cudaError_t measure_fp32_peak(cudaStream_t st, int num_sms, float* scratch, double* tflops);
+size_t fp32_probe_words(int num_sms);
+
 }  // namespace airgs

@@ -25,7 +25,10 @@ namespace airgs {
 
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
-constexpr int RS_ITEMS = 8;   // keys per thread per tile
+#ifndef AIRGS_RS_ITEMS
+#define AIRGS_RS_ITEMS 8
+#endif
+constexpr int RS_ITEMS = AIRGS_RS_ITEMS;  // keys per thread per tile
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 constexpr int RS_RADIX = 256;
 constexpr int RS_CTAS_PER_SM = 8;

@@ -447,6 +447,12 @@ class Rasterizer:
     def kernel_launch_count() -> int:
         return int(load_library().airgs_kernel_launch_count())
 
+    def measure_fp32_peak(self) -> float:
+        """Measured FP32 throughput of this context's GPU, TFLOP/s."""
+        v = ctypes.c_double(0.0)
+        self._check(self.lib.airgs_measure_fp32_peak(self.ctx, ctypes.byref(v)))
+        return v.value
+
     @staticmethod
     def variant_names():
         lib = load_library()

@@ -408,3 +408,9 @@ def test_densify_statistics_match_oracle():
     assert np.array_equal(mask, ((v > 0) & (d > thr * v)).astype(np.uint8))
     assert 0 < mask.sum() < n
     res.state.release()
+
+
+def test_fp32_probe_reports_a_plausible_peak(rast):
+    """The FMA probe the benchmark reports beside the derived FP32 peak."""
+    v = rast.measure_fp32_peak()
+    assert 10.0 < v < 200.0, v
