@@ -182,7 +182,8 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_FWD_MINB : 1) k_blend
     float pyb[NG / 2];  // pixel-centre rows of the item's block rows
 #pragma unroll
     for (int by = 0; by < NG / 2; ++by) pyb[by] = (float)(Y0 + 4 * by + ly) + 0.5f;
-    float T[NG], C0[NG], C1[NG], C2[NG];
+    float T[NG], C2[NG];
+    float2 C01[NG];  // the first two colour channels, updated as one packed FMA
     int last[NG], stop_at[NG];
     unsigned done = 0;
 #pragma unroll
@@ -190,7 +191,8 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_FWD_MINB : 1) k_blend
       const int x = X0 + 8 * (k & 1) + lx, y = Y0 + 4 * (k >> 1) + ly;
       if (!(x < cam.W && y < cam.H)) done |= 1u << k;
       T[k] = 1.f;
-      C0[k] = C1[k] = C2[k] = 0.f;
+      C01[k] = make_float2(0.f, 0.f);
+      C2[k] = 0.f;
       last[k] = 0;
       stop_at[k] = -1;
     }
@@ -263,8 +265,7 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_FWD_MINB : 1) k_blend
           const bool blend = valid && !stop;
           const float w = __fmul_rn(alpha, T[k]);
           if (blend) {
-            C0[k] = __fmaf_rn(gb.z, w, C0[k]);
-            C1[k] = __fmaf_rn(gb.w, w, C1[k]);
+            C01[k] = __ffma2_rn(make_float2(gb.z, gb.w), make_float2(w, w), C01[k]);
             C2[k] = __fmaf_rn(cb, w, C2[k]);
             T[k] = Tn;
             last[k] = pos1;
@@ -305,8 +306,8 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_FWD_MINB : 1) k_blend
         // pairs of the definition: list entries up to and including the stop
         pairs += stop_at[k] > 0 ? (unsigned long long)stop_at[k] : (unsigned long long)len;
         const int64_t pix = (int64_t)y * cam.W + x;
-        rgb[pix] = __fmaf_rn(T[k], a.rp.bg[0], C0[k]);
-        rgb[HW + pix] = __fmaf_rn(T[k], a.rp.bg[1], C1[k]);
+        rgb[pix] = __fmaf_rn(T[k], a.rp.bg[0], C01[k].x);
+        rgb[HW + pix] = __fmaf_rn(T[k], a.rp.bg[1], C01[k].y);
         rgb[2 * HW + pix] = __fmaf_rn(T[k], a.rp.bg[2], C2[k]);
         if (out.T) out.T[cam.pix_base + pix] = T[k];
         out.ncontrib[cam.pix_base + pix] = last[k];
@@ -639,7 +640,7 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_BWD_MINB : 1) k_blend
         acc[7] = a67.y;
         }
         if (COMPACT) {
-          if (__any_sync(kAll, cnt > 0)) {
+          {  // every compacted entry has a live block: defer without a vote
 #pragma unroll
             for (int q = 0; q < 10; ++q) s_red[ns * 10 + q][lane] = acc[q];
             if (IMP) cpack += (uint32_t)cnt << (8 * ns);
