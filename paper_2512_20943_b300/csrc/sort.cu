@@ -139,15 +139,22 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(const uint32_t* __r
     for (int k = tid; k < RS_WARPS * RS_RADIX; k += RS_THREADS) (&s_warp_cnt[0][0])[k] = 0;
     __syncthreads();
 
-    // warp w ranks tile positions [w*256, w*256 + 256), 32 per round, in order
+    // warp w ranks tile positions [w*256, w*256 + 256), 32 per round, in order;
+    // all of the thread's keys and values are loaded before the ranking, so the
+    // loads overlap instead of each waiting behind the previous round's sync
     uint32_t key[RS_ITEMS], val[RS_ITEMS], rank[RS_ITEMS];
 #pragma unroll
     for (int j = 0; j < RS_ITEMS; ++j) {
-      int p = warp * (RS_ITEMS * 32) + j * 32 + lane;
-      bool valid = p < tile_n;
-      uint32_t k = valid ? __ldg(keys_in + base + e0 + p) : 0xFFFFFFFFu;
+      const int p = warp * (RS_ITEMS * 32) + j * 32 + lane;
+      const bool valid = p < tile_n;
+      key[j] = valid ? __ldg(keys_in + base + e0 + p) : 0xFFFFFFFFu;
       val[j] = valid ? (vals_in ? __ldg(vals_in + base + e0 + p) : (uint32_t)(e0 + p)) : 0u;
-      key[j] = k;
+    }
+#pragma unroll
+    for (int j = 0; j < RS_ITEMS; ++j) {
+      const int p = warp * (RS_ITEMS * 32) + j * 32 + lane;
+      const bool valid = p < tile_n;
+      const uint32_t k = key[j];
       uint32_t d = valid ? ((k >> shift) & 0xFF) : RS_RADIX;  // invalid keys form their own class
       uint32_t peers = __match_any_sync(0xffffffffu, d);
       uint32_t before = 0;
