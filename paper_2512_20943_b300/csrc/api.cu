@@ -431,11 +431,12 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
         } else {
           s->ids = ivals_a;
         }
-        {
+        const bool half_lists = (s->variant == 5 || s->variant == 6) && n_inst < (1ll << 28);
+        if (!half_lists) {  // (the half-list pass writes the ranges itself)
           StageScope sc(ctx, ST_RANGES);
           CK(launch_tile_ranges(st, n_inst, skeys, s->ranges));
         }
-        if ((s->variant == 5 || s->variant == 6) && n_inst < (1ll << 28)) {
+        if (half_lists) {
           // compacted half-tile lists for the half-tile culling kernels (list positions fit 28 bits;
           // otherwise the kernels walk the full lists and test the blocks themselves)
           const int64_t hchunks = (int64_t)half_list_chunks(n_inst);

@@ -18,16 +18,11 @@ constexpr int HL_CHUNK = HL_THREADS * HL_ITEMS;
 
 size_t half_list_chunks(int64_t n_inst) { return (size_t)((n_inst + HL_CHUNK - 1) / HL_CHUNK); }
 
-// bit 0: the entry can blend in the top half (rows 0-7), bit 1: bottom half;
-// k_emit stored them in the key's top bits.
-__device__ __forceinline__ unsigned half_flags(int64_t p, const uint32_t* __restrict__ keys) {
-  return keys[p] >> kKeyHalfShift;
-}
-
 struct HalfArgs {
   const uint32_t* keys;  // sorted tile ids
   const uint32_t* ids;   // sorted Gaussian ids
-  const uint2* ranges;   // full tile ranges
+  const uint2* ranges;   // full tile ranges (k_half_sums writes them, k_half_compact reads them)
+  uint2* ranges_out;
   const CamDev* cams;
   int n_views;
   const ProjRec* proj;
@@ -36,17 +31,33 @@ struct HalfArgs {
   float log2_amin;
 };
 
+// Also writes each tile's [start, end) in the sorted list (the tile-ranges
+// pass): consecutive threads hold consecutive entries, so the neighbouring keys
+// come by shuffle (the warp's end lanes load theirs).
 __global__ void __launch_bounds__(HL_THREADS) k_half_sums(HalfArgs h, uint8_t* __restrict__ flags,
                                                           uint64_t* __restrict__ sums_top,
                                                           uint64_t* __restrict__ sums_bot) {
   __shared__ uint32_t s_t[HL_THREADS / 32], s_b[HL_THREADS / 32];
   const int64_t c0 = (int64_t)blockIdx.x * HL_CHUNK;
+  const int lane = threadIdx.x & 31;
   uint32_t nt = 0, nb = 0;
+  uint32_t key[HL_ITEMS];
 #pragma unroll
   for (int k = 0; k < HL_ITEMS; ++k) {
     const int64_t p = c0 + k * HL_THREADS + threadIdx.x;
+    key[k] = p < h.n_inst ? h.keys[p] : 0u;
+  }
+#pragma unroll
+  for (int k = 0; k < HL_ITEMS; ++k) {
+    const int64_t p = c0 + k * HL_THREADS + threadIdx.x;
+    const uint32_t tile = key[k] & kKeyTileMask;
+    uint32_t prev = __shfl_up_sync(0xffffffffu, tile, 1), next = __shfl_down_sync(0xffffffffu, tile, 1);
     if (p < h.n_inst) {
-      const unsigned f = half_flags(p, h.keys);
+      if (lane == 0 && p > 0) prev = h.keys[p - 1] & kKeyTileMask;
+      if (lane == 31 && p + 1 < h.n_inst) next = h.keys[p + 1] & kKeyTileMask;
+      if (p == 0 || prev != tile) h.ranges_out[tile].x = (uint32_t)p;
+      if (p + 1 == h.n_inst || next != tile) h.ranges_out[tile].y = (uint32_t)(p + 1);
+      const unsigned f = key[k] >> kKeyHalfShift;
       flags[p] = (uint8_t)f;
       nt += f & 1u;
       nb += f >> 1;
@@ -108,15 +119,25 @@ __global__ void __launch_bounds__(HL_THREADS) k_half_compact(HalfArgs h, const u
   }
   uint64_t ot = off_top[blockIdx.x] + wt + xt - lt;
   uint64_t ob = bot_base + off_bot[blockIdx.x] + wb + xb - lb;
+  uint32_t tiles[HL_ITEMS], gids[HL_ITEMS];
+  uint2 rgs[HL_ITEMS];
+#pragma unroll
+  for (int k = 0; k < HL_ITEMS; ++k) {  // all loads first, so that they overlap
+    const int64_t p = p0 + k;
+    tiles[k] = p < h.n_inst ? h.keys[p] & kKeyTileMask : 0u;
+    gids[k] = p < h.n_inst ? h.ids[p] : 0u;
+  }
+#pragma unroll
+  for (int k = 0; k < HL_ITEMS; ++k) rgs[k] = p0 + k < h.n_inst ? h.ranges[tiles[k]] : make_uint2(0u, 0u);
 #pragma unroll
   for (int k = 0; k < HL_ITEMS; ++k) {
     const int64_t p = p0 + k;
     if (p >= h.n_inst) break;
-    const uint32_t tile = h.keys[p] & kKeyTileMask;
-    const uint32_t start = h.ranges[tile].x;
+    const uint32_t tile = tiles[k];
+    const uint32_t start = rgs[k].x;
     const uint32_t pos = (uint32_t)(p - start);
-    const bool first = p == start, last = p + 1 == h.ranges[tile].y;
-    const uint32_t gid = h.ids[p];
+    const bool first = p == start, last = p + 1 == rgs[k].y;
+    const uint32_t gid = gids[k];
     if (first) {
       hranges[tile].x = (uint32_t)ot;
       hranges[n_tiles + tile].x = (uint32_t)ob;
@@ -130,13 +151,13 @@ __global__ void __launch_bounds__(HL_THREADS) k_half_compact(HalfArgs h, const u
   }
 }
 
-cudaError_t launch_half_lists(cudaStream_t st, const uint32_t* keys, const uint32_t* ids, const uint2* ranges,
+cudaError_t launch_half_lists(cudaStream_t st, const uint32_t* keys, const uint32_t* ids, uint2* ranges,
                               const CamDev* cams, int n_views, const ProjRec* proj, int64_t n, int64_t n_inst,
                               float alpha_min, int64_t n_tiles, uint8_t* flags, uint64_t* sums, uint2* hl,
                               uint2* hranges) {
   if (n_inst == 0) return cudaSuccess;
   const int64_t chunks = (int64_t)half_list_chunks(n_inst);
-  HalfArgs h{keys, ids, ranges, cams, n_views, proj, n, n_inst, log2f(alpha_min)};
+  HalfArgs h{keys, ids, ranges, ranges, cams, n_views, proj, n, n_inst, log2f(alpha_min)};
   uint64_t* st_ = sums;               // [chunks + 1] top
   uint64_t* sb_ = sums + chunks + 1;  // [chunks + 1] bottom
   k_half_sums<<<(unsigned)chunks, HL_THREADS, 0, st>>>(h, flags, st_, sb_);

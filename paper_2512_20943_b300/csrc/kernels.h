@@ -74,7 +74,7 @@ cudaError_t launch_ssim_loss(cudaStream_t st, const int64_t* d_off, const int* d
 
 // Half-tile blend lists (cull_lists.cu).
 size_t half_list_chunks(int64_t n_inst);
-cudaError_t launch_half_lists(cudaStream_t st, const uint32_t* keys, const uint32_t* ids, const uint2* ranges,
+cudaError_t launch_half_lists(cudaStream_t st, const uint32_t* keys, const uint32_t* ids, uint2* ranges,
                               const CamDev* cams, int n_views, const ProjRec* proj, int64_t n, int64_t n_inst,
                               float alpha_min, int64_t n_tiles, uint8_t* flags, uint64_t* sums, uint2* hl,
                               uint2* hranges);
