@@ -77,6 +77,10 @@ typedef struct {
   int sort_mode;              /* -1 or 0: global two-stage radix ordering; 1: per-tile ordering
                                  (lists sorted in shared memory) when every list fits one CTA */
   const char* autotune_cache; /* nullable path of a text cache of autotune choices */
+  int cull_lists;             /* 1 (default): a render that neither saves its state nor returns n_contrib
+                                 (whose tile lists nothing can observe) lists a Gaussian only in the
+                                 tiles of its rectangle in which it can reach alpha_min; images, T and
+                                 importance are identical.  0: always the full rectangle lists */
 } airgs_config;
 
 typedef struct {

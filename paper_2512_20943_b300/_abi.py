@@ -41,6 +41,7 @@ class airgs_config(ctypes.Structure):
         ("blend_variant", ctypes.c_int),
         ("sort_mode", ctypes.c_int),
         ("autotune_cache", ctypes.c_char_p),
+        ("cull_lists", ctypes.c_int),
     ]
 
 

@@ -253,6 +253,113 @@ __device__ __forceinline__ unsigned block_mask_exact(float4 ga, float4 gb, float
   return m;
 }
 
+// ------------------------------------------------------------------ culled lists (inference)
+// Row-band extents of the region where a Gaussian can blend.  With
+// P(d) = a2 dx^2 + b2 dx dy + c2 dy^2 (negative definite, d = pixel - centre) a
+// pixel can blend only if P >= -L, L = log2(o / alpha_min).  For fixed dy that
+// is an x-interval centred at kx dy (kx = -b2 / (2 a2)) of half-width
+// w(dy) = sqrt((L + c' dy^2) / (-a2)), c' = det / a2 (det = a2 c2 - b2^2 / 4),
+// nonempty for |dy| <= hy.  Over a band of rows the region's x-extent runs from
+// the smallest left end to the largest right end: the right end is concave in
+// dy, largest (hx) at the rightmost point dy = -b2 hx / (2 c2) and otherwise at
+// the band end nearer to it; the left end mirrors it.  The region is convex, so
+// a tile half of the band meets it exactly when its pixel-centre x-range meets
+// that extent.  L is widened by 0.01 + 1e-5 S (S bounds the terms' magnitudes
+// over the region, the scale of the per-pair test's rounding error) and the
+// extent by a small absolute amount, so no dropped tile holds a pair the
+// per-pair test would blend.  Every operation has an explicit rounding mode:
+// the projection (which counts the live tiles) and the emission (which lists
+// them) compute bit-identical extents.
+struct EllipseBands {
+  float mx, my, kx, cpr, inv_na2, L, hx, hy, dyr, eps;
+  int kind;  // 0: never blends, 1: bounded, 2: no bound (every tile of the rectangle is kept)
+};
+
+__device__ __forceinline__ EllipseBands ellipse_bands(float mx, float my, float a2, float b2, float c2, float o,
+                                                      float log2_amin) {
+  EllipseBands e;
+  e.mx = mx;
+  e.my = my;
+  const float L0 = __fadd_rn(__fadd_rn(lg2_approx(o), -log2_amin), 1e-3f);
+  const bool definite = a2 < 0.f && c2 < 0.f && __fmul_rn(4.f, __fmul_rn(a2, c2)) > __fmul_rn(1.0001f, __fmul_rn(b2, b2));
+  e.kind = L0 <= 0.f ? 0 : ((L0 > 0.f && definite) ? 1 : 2);
+  if (e.kind != 1) return e;
+  const float det = __fmaf_rn(a2, c2, __fmul_rn(-0.25f, __fmul_rn(b2, b2)));
+  const float hx0 = __fsqrt_rn(__fdiv_rn(__fmul_rn(L0, -c2), det));
+  const float hy0 = __fsqrt_rn(__fdiv_rn(__fmul_rn(L0, -a2), det));
+  const float S = __fadd_rn(__fadd_rn(__fmul_rn(-a2, __fmul_rn(hx0, hx0)), __fmul_rn(fabsf(b2), __fmul_rn(hx0, hy0))),
+                            __fmul_rn(-c2, __fmul_rn(hy0, hy0)));
+  e.L = __fadd_rn(__fadd_rn(L0, 0.01f), __fmul_rn(1e-5f, S));
+  e.hx = __fsqrt_rn(__fdiv_rn(__fmul_rn(e.L, -c2), det));
+  e.hy = __fsqrt_rn(__fdiv_rn(__fmul_rn(e.L, -a2), det));
+  e.kx = __fdiv_rn(__fmul_rn(-0.5f, b2), a2);
+  e.cpr = __fdiv_rn(det, a2);
+  e.inv_na2 = __fdiv_rn(-1.f, a2);
+  e.dyr = __fdiv_rn(__fmul_rn(__fmul_rn(-0.5f, b2), e.hx), c2);
+  e.eps = __fadd_rn(0.01f, __fmul_rn(1e-5f, __fadd_rn(__fadd_rn(e.hx, __fmul_rn(fabsf(e.kx), e.hy)), fabsf(mx))));
+  return e;
+}
+
+// x-extent [xmin, xmax] (pixel coordinates) of the region over the rows whose
+// centres lie in [y0, y1] (pixel coordinates); false when the band misses it.
+__device__ __forceinline__ bool band_extent(const EllipseBands& e, float y0, float y1, float& xmin, float& xmax) {
+  const float lo = fmaxf(__fadd_rn(y0, -e.my), -e.hy), hi = fminf(__fadd_rn(y1, -e.my), e.hy);
+  if (lo > hi) return false;
+  const float tr = e.dyr < lo ? lo : (e.dyr > hi ? hi : e.dyr);
+  const float tl = -e.dyr < lo ? lo : (-e.dyr > hi ? hi : -e.dyr);
+  const float wr = __fsqrt_rn(fmaxf(0.f, __fmul_rn(__fmaf_rn(__fmul_rn(e.cpr, tr), tr, e.L), e.inv_na2)));
+  const float wl = __fsqrt_rn(fmaxf(0.f, __fmul_rn(__fmaf_rn(__fmul_rn(e.cpr, tl), tl, e.L), e.inv_na2)));
+  const float rmax = tr == e.dyr ? e.hx : __fmaf_rn(e.kx, tr, wr);
+  const float lmin = tl == -e.dyr ? -e.hx : __fmaf_rn(e.kx, tl, -wl);
+  xmax = __fadd_rn(__fadd_rn(e.mx, rmax), e.eps);
+  xmin = __fadd_rn(__fadd_rn(e.mx, lmin), -e.eps);
+  return true;
+}
+
+// Live tiles of tile row ty within the rectangle's columns [x0, x1): the tiles
+// [lo, hi) that either half-row band of the row meets, and the two bands'
+// extents for the half flags (ok_* false: the band misses the region).
+struct LiveRow {
+  int lo, hi;
+  bool ok_top, ok_bot;
+  float tmin, tmax, bmin, bmax;
+};
+
+__device__ __forceinline__ LiveRow live_row(const EllipseBands& e, int ty, int x0, int x1) {
+  LiveRow r;
+  r.lo = x0;
+  r.hi = x1;
+  r.ok_top = r.ok_bot = true;
+  r.tmin = r.bmin = -INFINITY;
+  r.tmax = r.bmax = INFINITY;
+  if (e.kind == 2) return r;
+  r.lo = r.hi = x0;
+  r.ok_top = r.ok_bot = false;
+  if (e.kind == 0) return r;
+  const float Y0 = (float)(ty * kTile);
+  r.ok_top = band_extent(e, Y0 + 0.5f, Y0 + 7.5f, r.tmin, r.tmax);
+  r.ok_bot = band_extent(e, Y0 + 8.5f, Y0 + 15.5f, r.bmin, r.bmax);
+  if (!r.ok_top && !r.ok_bot) return r;
+  const float xmin = fminf(r.ok_top ? r.tmin : INFINITY, r.ok_bot ? r.bmin : INFINITY);
+  const float xmax = fmaxf(r.ok_top ? r.tmax : -INFINITY, r.ok_bot ? r.bmax : -INFINITY);
+  // tile tx meets [xmin, xmax] iff 16 tx + 0.5 <= xmax and 16 tx + 15.5 >= xmin
+  const float lim = 1048576.0f;
+  const int first = (int)ceilf(__fdiv_rn(fminf(fmaxf(__fadd_rn(xmin, -15.5f), -lim), lim), 16.f));
+  const int last = (int)floorf(__fdiv_rn(fminf(fmaxf(__fadd_rn(xmax, -0.5f), -lim), lim), 16.f));
+  r.lo = max(x0, first);
+  r.hi = max(r.lo, min(x1, last + 1));
+  return r;
+}
+
+// Half flags (bit 0 top, bit 1 bottom) of live tile tx of a row.
+__device__ __forceinline__ uint32_t live_row_halves(const LiveRow& r, int tx) {
+  const float X0 = (float)(tx * kTile);
+  uint32_t f = 0u;
+  if (r.ok_top && r.tmax >= X0 + 0.5f && r.tmin <= X0 + 15.5f) f |= 1u;
+  if (r.ok_bot && r.bmax >= X0 + 0.5f && r.bmin <= X0 + 15.5f) f |= 2u;
+  return f;
+}
+
 // Half-tile list entries: (Gaussian id, position in the tile's full list in
 // bits 0-27 | the half's 8x4 blocks the Gaussian can reach alpha_min in, bits
 // 28-31, as block_mask_exact gives them).

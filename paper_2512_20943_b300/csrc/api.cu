@@ -321,6 +321,8 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
     TALLOC(dkeys, V * N);
     TALLOC(tiles, V * N);
     const bool per_tile = ctx->cfg.sort_mode == 1;
+    // lists nothing can observe (no saved state, no n_contrib output) hold only the live tiles
+    const bool cull = ctx->cfg.cull_lists != 0 && !saved && !nc_out && !per_tile;
     if (per_tile) {
       TALLOC(tile_counts, s->n_tiles);
       CK(cudaMemsetAsync(tile_counts, 0, s->n_tiles * sizeof(uint32_t), st));
@@ -328,7 +330,7 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
     {
       StageScope sc(ctx, ST_PROJECT);
       CK(launch_project(st, N, g->sh_degree, g->means, g->log_scales, g->quats, g->opacity_logit, g->sh, s->d_cams,
-                        n_views, rp, s->proj, dkeys, tiles, tile_counts));
+                        n_views, rp, s->proj, dkeys, tiles, tile_counts, cull));
     }
     bool use_radix = !per_tile;
     if (per_tile) {
@@ -413,7 +415,7 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
           StageScope sc(ctx, ST_EMIT);
           TALLOC(pieces, emit_piece_words(V * N, n_inst));
           CK(launch_emit(st, V * N, N, order, counts_sorted, chunk, n_inst, pieces, s->proj, s->d_cams,
-                         ctx->cfg.alpha_min, s->n_tiles, ikeys_a, ivals_a));
+                         ctx->cfg.alpha_min, s->n_tiles, cull, ikeys_a, ivals_a));
         }
         bool in_b2 = false;
         {
@@ -608,6 +610,7 @@ void airgs_default_config(airgs_config* c) {
   c->blend_variant = -1;
   c->sort_mode = -1;
   c->autotune_cache = nullptr;
+  c->cull_lists = 1;
 }
 
 int airgs_create(airgs_ctx** out, const airgs_config* cfg, void* stream) {

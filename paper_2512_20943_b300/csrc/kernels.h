@@ -20,7 +20,7 @@ cudaError_t launch_decode_apply(cudaStream_t st, int64_t n, const uint16_t* map,
 cudaError_t launch_project(cudaStream_t st, int64_t n, int sh_degree, const float* means, const float* log_scales,
                            const float* quats, const float* opacity_logit, const float* sh, const CamDev* cams,
                            int n_views, const RasterParams& rp, ProjRec* proj, uint32_t* depth_keys,
-                           uint32_t* tiles_touched, uint32_t* tile_counts);
+                           uint32_t* tiles_touched, uint32_t* tile_counts, bool cull);
 
 // Per-tile ordering (order.cu).
 constexpr int kTileSortSmall = 2048;  // entries sorted by one 256-thread CTA
@@ -50,7 +50,7 @@ int64_t emit_chunks(int64_t total);  // depth-order chunks of the count/scan/emi
 cudaError_t launch_emit(cudaStream_t st, int64_t total, int64_t n, const uint32_t* order,
                         const uint32_t* counts_sorted, const uint64_t* chunk_offsets, int64_t n_inst,
                         uint32_t* piece_off, const ProjRec* proj, const CamDev* cams, float alpha_min,
-                        int64_t n_tiles, uint32_t* keys, uint32_t* vals);
+                        int64_t n_tiles, bool cull, uint32_t* keys, uint32_t* vals);
 cudaError_t launch_tile_ranges(cudaStream_t st, int64_t n_inst, const uint32_t* keys, uint2* ranges);
 
 // Usage-frequency pruning (prune.cu).

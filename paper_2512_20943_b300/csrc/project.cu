@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(128) k_project(int64_t n, const float* __restr
                                                  int n_views, RasterParams rp, ProjRec* __restrict__ proj,
                                                  uint32_t* __restrict__ depth_keys,
                                                  uint32_t* __restrict__ tiles_touched,
-                                                 uint32_t* __restrict__ tile_counts) {
+                                                 uint32_t* __restrict__ tile_counts, int cull, float log2_amin) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -195,6 +195,7 @@ __global__ void __launch_bounds__(128) k_project(int64_t n, const float* __restr
         tile_rect(mx, my, radius, cam.TW, cam.TH, x0, y0, x1, y1);
         if (x0 < x1 && y0 < y1) {
           ntiles = (uint32_t)((x1 - x0) * (y1 - y0));
+
           if (tile_counts) {  // per-tile list lengths for the per-tile ordering
             uint32_t* tc = tile_counts + cam.tile_base;
             for (int ty = y0; ty < y1; ++ty)
@@ -205,6 +206,16 @@ __global__ void __launch_bounds__(128) k_project(int64_t n, const float* __restr
           a2 = -0.5f * kLog2e * A;
           b2 = -kLog2e * B;
           c2 = -0.5f * kLog2e * C;
+          if (cull) {  // only the tiles in which the Gaussian can reach alpha_min (culled lists), from
+                       // the values the record stores, as the emission will read them
+            const EllipseBands e = ellipse_bands(mx, my, a2, b2, c2, opacity, log2_amin);
+            uint32_t live = 0;
+            for (int ty = y0; ty < y1; ++ty) {
+              const LiveRow r = live_row(e, ty, x0, x1);
+              live += (uint32_t)(r.hi - r.lo);
+            }
+            ntiles = live;
+          }
         }
       }
     }
@@ -237,25 +248,25 @@ cudaError_t launch_decode_apply(cudaStream_t st, int64_t n, const uint16_t* map,
 cudaError_t launch_project(cudaStream_t st, int64_t n, int sh_degree, const float* means, const float* log_scales,
                            const float* quats, const float* opacity_logit, const float* sh, const CamDev* cams,
                            int n_views, const RasterParams& rp, ProjRec* proj, uint32_t* depth_keys,
-                           uint32_t* tiles_touched, uint32_t* tile_counts) {
+                           uint32_t* tiles_touched, uint32_t* tile_counts, bool cull) {
   if (n == 0) return cudaSuccess;
   int blocks = (int)((n + 127) / 128);
   switch (sh_degree) {
     case 0:
       k_project<0><<<blocks, 128, 0, st>>>(n, means, log_scales, quats, opacity_logit, sh, cams, n_views, rp, proj,
-                                           depth_keys, tiles_touched, tile_counts);
+                                           depth_keys, tiles_touched, tile_counts, cull ? 1 : 0, log2f(rp.alpha_min));
       break;
     case 1:
       k_project<1><<<blocks, 128, 0, st>>>(n, means, log_scales, quats, opacity_logit, sh, cams, n_views, rp, proj,
-                                           depth_keys, tiles_touched, tile_counts);
+                                           depth_keys, tiles_touched, tile_counts, cull ? 1 : 0, log2f(rp.alpha_min));
       break;
     case 2:
       k_project<2><<<blocks, 128, 0, st>>>(n, means, log_scales, quats, opacity_logit, sh, cams, n_views, rp, proj,
-                                           depth_keys, tiles_touched, tile_counts);
+                                           depth_keys, tiles_touched, tile_counts, cull ? 1 : 0, log2f(rp.alpha_min));
       break;
     default:
       k_project<3><<<blocks, 128, 0, st>>>(n, means, log_scales, quats, opacity_logit, sh, cams, n_views, rp, proj,
-                                           depth_keys, tiles_touched, tile_counts);
+                                           depth_keys, tiles_touched, tile_counts, cull ? 1 : 0, log2f(rp.alpha_min));
       break;
   }
   count_launches(1);

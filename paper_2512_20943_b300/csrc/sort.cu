@@ -308,7 +308,7 @@ constexpr int EM_RUN = 8;                                     // instances per t
 constexpr uint32_t EM_PIECE = (uint32_t)EM_THREADS * EM_RUN;  // instances per CTA
 constexpr int EM_STAGE = EM_THREADS * (EM_RUN + 1);            // padded staging rows (no bank conflicts)
 constexpr size_t EM_SMEM = 3 * EM_CHUNK * sizeof(float4) + EM_CHUNK * sizeof(float2) +
-                           (EM_CHUNK + 4) * sizeof(uint32_t) + 2 * EM_STAGE * sizeof(uint32_t);
+                           (2 * EM_CHUNK + 4) * sizeof(uint32_t) + 2 * EM_STAGE * sizeof(uint32_t);
 
 __global__ void __launch_bounds__(1024) k_emit_pieces(const uint64_t* __restrict__ chunk_offsets, int64_t n_chunks,
                                                      uint32_t* __restrict__ piece_off) {
@@ -368,8 +368,8 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(int64_t total, int64_t n, c
                                                     const uint32_t* __restrict__ piece_off,
                                                     const uint32_t* __restrict__ piece_chunk, int64_t n_chunks,
                                                     const ProjRec* __restrict__ proj, const CamDev* __restrict__ cams,
-                                                    float log2_amin, bool with_halves, uint32_t* __restrict__ keys,
-                                                    uint32_t* __restrict__ vals) {
+                                                    float log2_amin, bool with_halves, int cull,
+                                                    uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
   // dynamic shared memory (EM_SMEM bytes):
   extern __shared__ float4 em_smem[];
   float4* s_box = em_smem;                   // centre, alpha-box half-widths (-inf: never, +inf: unbounded)
@@ -378,7 +378,8 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(int64_t total, int64_t n, c
                                                                 // x0 | y0 << 16, Gaussian id
   float2* s_kxy = reinterpret_cast<float2*>(s_rect + EM_CHUNK);     // maximisers along a row / column
   uint32_t* s_off = reinterpret_cast<uint32_t*>(s_kxy + EM_CHUNK);  // [EM_CHUNK + 1] chunk-local first instances
-  uint32_t* s_key = s_off + EM_CHUNK + 4;                             // [EM_STAGE] staged keys
+  uint32_t* s_ext = s_off + EM_CHUNK + 4;                             // culled lists: tile columns | rows << 16
+  uint32_t* s_key = s_ext + EM_CHUNK;                                 // [EM_STAGE] staged keys
   uint32_t* s_val = s_key + EM_STAGE;                                 // [EM_STAGE] staged values
   __shared__ uint32_t s_w[EM_THREADS / 32];
   __shared__ int s_g0, s_g1;
@@ -445,7 +446,14 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(int64_t total, int64_t n, c
     tile_rect(ra.x, ra.y, radius, cam.TW, cam.TH, x0, y0, x1, y1);
     s_rect[g] = make_uint4((uint32_t)cam.tile_base + (uint32_t)(y0 * cam.TW + x0),
                            (uint32_t)(x1 - x0) | ((uint32_t)cam.TW << 16), (uint32_t)x0 | ((uint32_t)y0 << 16), gid);
-    if (with_halves) {
+    if (cull) {  // culled lists: the row-band terms the projection counted with, from the same record values
+      const EllipseBands e = ellipse_bands(ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, log2_amin);
+      s_rect[g].x = (uint32_t)cam.tile_base;
+      s_ext[g] = (uint32_t)cam.TW | ((uint32_t)(y1 - y0) << 16);
+      s_box[g] = make_float4(e.mx, e.my, e.hx, e.hy);
+      s_quad[g] = make_float4(e.kx, e.cpr, e.inv_na2, e.L);
+      s_kxy[g] = make_float2(e.dyr, e.kind == 2 ? -1.f : e.eps);  // (no instances when kind is 0)
+    } else if (with_halves) {
       float hx = 0.f, hy = 0.f;
       const int kind = alpha_box(ra, rb, log2_amin, hx, hy);
       if (kind == 0) hx = hy = -INFINITY;
@@ -459,7 +467,66 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(int64_t total, int64_t n, c
   __syncthreads();
   const uint32_t i0 = p0 + (uint32_t)tid * EM_RUN;
   const uint32_t i1 = min(i0 + (uint32_t)EM_RUN, p1);
-  if (i0 < i1) {
+  if (cull && i0 < i1) {
+    // culled lists: walk the live tiles row by row exactly as the projection counted them
+    auto bands_of = [&](int gg) {
+      EllipseBands e;
+      const float4 b4 = s_box[gg], q4 = s_quad[gg];
+      const float2 k2 = s_kxy[gg];
+      e.mx = b4.x;
+      e.my = b4.y;
+      e.hx = b4.z;
+      e.hy = b4.w;
+      e.kx = q4.x;
+      e.cpr = q4.y;
+      e.inv_na2 = q4.z;
+      e.L = q4.w;
+      e.dyr = k2.x;
+      e.eps = k2.y;
+      e.kind = k2.y < 0.f ? 2 : 1;
+      return e;
+    };
+    int g = owner(i0, g0, g1);
+    EllipseBands e = bands_of(g);
+    uint4 r = s_rect[g];
+    int x0 = (int)(r.z & 0xFFFFu), y0 = (int)(r.z >> 16), x1 = x0 + (int)(r.y & 0xFFFFu);
+    int y1 = y0 + (int)(s_ext[g] >> 16), tw = (int)(s_ext[g] & 0xFFFFu);
+    int ty = y0;
+    LiveRow row = live_row(e, ty, x0, x1);
+    uint32_t li = i0 - s_off[g];
+    while (li >= (uint32_t)(row.hi - row.lo) && ty + 1 < y1) {
+      li -= (uint32_t)(row.hi - row.lo);
+      row = live_row(e, ++ty, x0, x1);
+    }
+    int tx = row.lo + (int)li;
+    for (uint32_t i = i0; i < i1; ++i) {
+      if (i >= s_off[g + 1]) {  // first instance of the next Gaussian with instances
+        do {
+          ++g;
+        } while (i >= s_off[g + 1]);
+        e = bands_of(g);
+        r = s_rect[g];
+        x0 = (int)(r.z & 0xFFFFu);
+        y0 = (int)(r.z >> 16);
+        x1 = x0 + (int)(r.y & 0xFFFFu);
+        y1 = y0 + (int)(s_ext[g] >> 16);
+        tw = (int)(s_ext[g] & 0xFFFFu);
+        ty = y0;
+        row = live_row(e, ty, x0, x1);
+        while (row.hi == row.lo && ty + 1 < y1) row = live_row(e, ++ty, x0, x1);
+        tx = row.lo;
+      } else if (i != i0 && ++tx >= row.hi) {  // next live row
+        do {
+          row = live_row(e, ++ty, x0, x1);
+        } while (row.hi == row.lo && ty + 1 < y1);
+        tx = row.lo;
+      }
+      const uint32_t halves = with_halves ? live_row_halves(row, tx) : 3u;
+      const int slot = tid * (EM_RUN + 1) + (int)(i - i0);
+      s_key[slot] = (r.x + (uint32_t)(ty * tw + tx)) | (halves << kKeyHalfShift);
+      s_val[slot] = r.w;
+    }
+  } else if (i0 < i1) {
     int g = owner(i0, g0, g1);
     uint4 r = s_rect[g];
     float4 bx = s_box[g], qd = s_quad[g];
@@ -627,7 +694,7 @@ size_t emit_piece_words(int64_t total, int64_t n_inst) {
 cudaError_t launch_emit(cudaStream_t st, int64_t total, int64_t n, const uint32_t* order,
                         const uint32_t* counts_sorted, const uint64_t* chunk_offsets, int64_t n_inst,
                         uint32_t* piece_off, const ProjRec* proj, const CamDev* cams, float alpha_min,
-                        int64_t n_tiles, uint32_t* keys, uint32_t* vals) {
+                        int64_t n_tiles, bool cull, uint32_t* keys, uint32_t* vals) {
   if (total == 0 || n_inst == 0) return cudaSuccess;
   const int64_t n_chunks = (total + EM_CHUNK - 1) / EM_CHUNK;
   // sum over chunks of ceil(count / EM_PIECE) <= n_inst / EM_PIECE + n_chunks; surplus CTAs return at once
@@ -649,7 +716,8 @@ cudaError_t launch_emit(cudaStream_t st, int64_t total, int64_t n, const uint32_
   }
   k_emit<<<(unsigned)grid, EM_THREADS, EM_SMEM, st>>>(total, n, order, counts_sorted, chunk_offsets, piece_off,
                                                        piece_chunk, n_chunks,
-                                                proj, cams, log2f(alpha_min), n_tiles <= (1ll << 24), keys, vals);
+                                                proj, cams, log2f(alpha_min), n_tiles <= (1ll << 24), cull ? 1 : 0, keys,
+                                                vals);
   count_launches(3);
   return cudaGetLastError();
 }

@@ -35,6 +35,7 @@ class RasterConfig:
     blend_variant: int = -1  # -1: autotuned choice (default variant until tuned)
     sort_mode: int = -1      # -1/0: global radix ordering; 1: per-tile ordering when lists fit a CTA
     autotune_cache: str | None = None
+    cull_lists: bool = True  # unobservable lists (no saved state, no n_contrib) hold only live tiles
 
     def to_c(self):
         c = airgs_config()
@@ -44,6 +45,7 @@ class RasterConfig:
         c.blend_variant = int(self.blend_variant)
         c.sort_mode = int(self.sort_mode)
         c.autotune_cache = self.autotune_cache.encode() if self.autotune_cache else None
+        c.cull_lists = 1 if self.cull_lists else 0
         return c
 
 
