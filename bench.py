@@ -67,10 +67,10 @@ FP32_LANES_PER_SM = 128
 _BLEND_SOURCES = ("paper_2512_20943_b300/csrc/blend_cull.cu", "paper_2512_20943_b300/csrc/airgs_internal.cuh",
                   "paper_2512_20943_b300/csrc/kernels.h")
 NCU_TRAFFIC = {
-    "blend_bwd": {"bytes_per_launch": (638.128384 + 83.611904) * 1e6, "sources": _BLEND_SOURCES,
-                  "sha256": "20d8875366db0ca2be73b2b2484529814ddb72d0d5ee2157d201aeebe1f12aaf"},
-    "blend_fwd": {"bytes_per_launch": (224.660480 + 238.281216) * 1e6, "sources": _BLEND_SOURCES,
-                  "sha256": "20d8875366db0ca2be73b2b2484529814ddb72d0d5ee2157d201aeebe1f12aaf"},
+    "blend_bwd": {"bytes_per_launch": (639.909632 + 85.719040) * 1e6, "sources": _BLEND_SOURCES,
+                  "sha256": "5e068a7a06a49894e5ba9ba49f1aab1bb5302dc10ac718afc799c4a5995194bc"},
+    "blend_fwd": {"bytes_per_launch": (223.263232 + 238.197760) * 1e6, "sources": _BLEND_SOURCES,
+                  "sha256": "5e068a7a06a49894e5ba9ba49f1aab1bb5302dc10ac718afc799c4a5995194bc"},
 }
 
 
