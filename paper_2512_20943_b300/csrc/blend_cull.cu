@@ -57,9 +57,9 @@ __device__ __forceinline__ int view_of_tile32(const int* tile_base, int n_views,
 }
 
 // Per staged list entry, read back with one 16-byte load: position in the
-// tile's full list, block mask, third colour channel, Gaussian id.
+// tile's full list plus one, block mask, third colour channel, Gaussian id.
 struct __align__(16) StageMeta {
-  uint32_t pos;
+  uint32_t pos1;
   unsigned mask;
   float c;
   uint32_t id;
@@ -84,12 +84,14 @@ __device__ __forceinline__ int view_of_tile_cams(const CamDev* cams, int n_views
 // (positions increase along the list, so no later batch can contribute).
 // Half-list entries: the forward computes each staged entry's exact block mask
 // and stores it in the entry's top bits; the backward reads it from there (every
-// entry before maxnc was staged by the forward of the same state).
+// entry before maxnc was staged by the forward of the same state).  Each lane
+// adds to `groups` the blocks its kept entries will evaluate (mask & alive, the
+// blocks not yet terminated at the batch's start), the issued-work statistic.
 template <int NG, bool LIVE>
 __device__ __forceinline__ int stage_compact(const BlendArgs& a, bool use_hl, uint32_t b0, int nb, uint32_t list0,
                                              const ProjRec* projv, float log2_amin, float X0, float Y0,
-                                             const int (&gmax)[NG], int maxnc, float4* s_a, float4* s_b,
-                                             StageMeta* s_meta, bool& past) {
+                                             const int (&gmax)[NG], int maxnc, unsigned alive, float4* s_a,
+                                             float4* s_b, StageMeta* s_meta, bool& past, uint32_t& groups) {
   const int lane = threadIdx.x & 31;
   int kept = 0;
   bool beyond = false;
@@ -138,7 +140,8 @@ __device__ __forceinline__ int stage_compact(const BlendArgs& a, bool use_hl, ui
       const int d = kept + __popc(bal & ((1u << lane) - 1u));
       s_a[d] = ga;
       s_b[d] = gb;
-      s_meta[d] = StageMeta{pos, msk, gc, id};
+      s_meta[d] = StageMeta{pos + 1u, msk, gc, id};
+      groups += __popc(msk & alive);
     }
     kept += __popc(bal);
   }
@@ -184,37 +187,38 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_FWD_MINB : 1) k_blend
     for (int by = 0; by < NG / 2; ++by) pyb[by] = (float)(Y0 + 4 * by + ly) + 0.5f;
     float T[NG], C2[NG];
     float2 C01[NG];  // the first two colour channels, updated as one packed FMA
+    // last: position + 1 of the last blended entry; stop_at: -1 while the pixel
+    // is blending, else position + 1 of the entry that stopped it (0 for a pixel
+    // outside the image)
     int last[NG], stop_at[NG];
-    unsigned done = 0;
 #pragma unroll
     for (int k = 0; k < NG; ++k) {
       const int x = X0 + 8 * (k & 1) + lx, y = Y0 + 4 * (k >> 1) + ly;
-      if (!(x < cam.W && y < cam.H)) done |= 1u << k;
       T[k] = 1.f;
       C01[k] = make_float2(0.f, 0.f);
       C2[k] = 0.f;
       last[k] = 0;
-      stop_at[k] = -1;
+      stop_at[k] = (x < cam.W && y < cam.H) ? -1 : 0;
     }
     const uint2 range = a.ranges[item];
     const bool use_hl = PARTS > 1 && a.hl != nullptr;  // this half's compacted list
     uint2 er = range;
     if (use_hl) er = a.hranges[(int64_t)part * a.n_tiles + item];
     const ProjRec* projv = a.proj + (size_t)v * a.n;
-    uint32_t exec_groups = 0;
+    uint32_t exec_groups = 0;  // warp-uniform (per-entry count) or per lane (COMPACT: counted while staging)
 
     for (uint32_t b0 = er.x; b0 < er.y; b0 += CBATCH) {
       unsigned live = 0;
 #pragma unroll
       for (int k = 0; k < NG; ++k)
-        if (__any_sync(kAll, !((done >> k) & 1u))) live |= 1u << k;
+        if (__any_sync(kAll, stop_at[k] < 0)) live |= 1u << k;
       if (live == 0) break;
       int nb = (int)min((uint32_t)CBATCH, er.y - b0);
       if (COMPACT) {
         const int none[NG] = {};
         bool unused = false;
         nb = stage_compact<NG, false>(a, use_hl, b0, nb, range.x, projv, log2_amin, (float)X0, (float)Y0, none, 0,
-                                      s_a, s_b, s_meta, unused);
+                                      live, s_a, s_b, s_meta, unused, exec_groups);
       } else
       for (int j = lane; j < nb; j += 32) {
         uint32_t id, pos;
@@ -230,7 +234,7 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_FWD_MINB : 1) k_blend
         const float4 ga = __ldg(&r->a), gb = __ldg(&r->b);
         s_a[j] = ga;
         s_b[j] = gb;
-        s_meta[j] = StageMeta{pos, block_mask(ga, gb, log2_amin, (float)X0, (float)Y0) & ((1u << NG) - 1u),
+        s_meta[j] = StageMeta{pos + 1u, block_mask(ga, gb, log2_amin, (float)X0, (float)Y0) & ((1u << NG) - 1u),
                               __ldg(&r->c.x), id};
       }
       __syncwarp();
@@ -238,11 +242,11 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_FWD_MINB : 1) k_blend
         const StageMeta me = s_meta[j];
         const unsigned m = me.mask & live;
         if (m == 0) continue;
-        exec_groups += __popc(m);
+        if (!COMPACT) exec_groups += __popc(m);
         const float4 ga = s_a[j];
         const float4 gb = s_b[j];
         const float cb = me.c;
-        const int pos1 = (int)me.pos + 1;
+        const int pos1 = (int)me.pos1;
         const float dxb[2] = {__fsub_rn(ga.x, pxb[0]), __fsub_rn(ga.x, pxb[1])};
         float wsum = 0.f;
         int bcount = 0;
@@ -260,7 +264,7 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_FWD_MINB : 1) k_blend
           const float G = ex2_approx(p2);
           const float alpha = alpha_of(gb.y, G, alpha_max);
           const float Tn = transmit(T[k], alpha);
-          const bool valid = !((done >> k) & 1u) && !(p2 > 0.f) && !(alpha < alpha_min);
+          const bool valid = (stop_at[k] < 0) && !(p2 > 0.f) && !(alpha < alpha_min);
           const bool stop = valid && (Tn < T_min);
           const bool blend = valid && !stop;
           const float w = __fmul_rn(alpha, T[k]);
@@ -270,10 +274,7 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_FWD_MINB : 1) k_blend
             T[k] = Tn;
             last[k] = pos1;
           }
-          if (stop) {
-            done |= 1u << k;
-            stop_at[k] = pos1;
-          }
+          if (stop) stop_at[k] = pos1;
           if (IMP) {
             wsum += blend ? w : 0.f;
             bcount += blend ? 1 : 0;
@@ -295,7 +296,7 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_FWD_MINB : 1) k_blend
       }
       __syncwarp();
     }
-    executed += 32ull * exec_groups;
+    executed += (COMPACT ? 1ull : 32ull) * exec_groups;
     const int64_t HW = (int64_t)cam.W * cam.H;
     float* rgb = out.rgb + 3 * cam.pix_base;
     const uint32_t len = range.y - range.x;
@@ -316,6 +317,10 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_FWD_MINB : 1) k_blend
     }
   }
   for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(kAll, pairs, o);
+  if (COMPACT) {  // per-lane block counts: 32 lane evaluations per block
+    for (int o = 16; o > 0; o >>= 1) executed += __shfl_xor_sync(kAll, executed, o);
+    executed *= 32ull;
+  }
   if (lane == 0) {
     if (pairs) {
       atomicAdd(a.pair_counter, pairs);
@@ -512,7 +517,7 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_BWD_MINB : 1) k_blend
       int nb = (int)min((uint32_t)CBATCH, er.y - b0);
       if (COMPACT) {
         nb = stage_compact<NG, true>(a, use_hl, b0, nb, range.x, projv, log2_amin, (float)X0, (float)Y0, gmax, maxnc,
-                                     s_a, s_b, s_meta, past_end);
+                                     (1u << NG) - 1u, s_a, s_b, s_meta, past_end, exec_groups);
       } else
       for (int j = lane; j < nb; j += 32) {
         uint32_t id, pos;
@@ -528,26 +533,26 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_BWD_MINB : 1) k_blend
         const float4 ga = __ldg(&r->a), gb = __ldg(&r->b);
         s_a[j] = ga;
         s_b[j] = gb;
-        s_meta[j] = StageMeta{pos, block_mask(ga, gb, log2_amin, (float)X0, (float)Y0) & ((1u << NG) - 1u),
+        s_meta[j] = StageMeta{pos + 1u, block_mask(ga, gb, log2_amin, (float)X0, (float)Y0) & ((1u << NG) - 1u),
                               __ldg(&r->c.x), id};
       }
       __syncwarp();
       for (int j = 0; j < nb; ++j) {
         const StageMeta me = s_meta[j];
-        const int pos = (int)me.pos;
+        const int pos1 = (int)me.pos1;  // pair (pixel, entry) replayed iff pos1 <= n_contrib
         unsigned m = me.mask;
         if (!COMPACT) {
-          if (pos >= maxnc) {  // positions increase along the list
+          if (pos1 > maxnc) {  // positions increase along the list
             past_end = true;
             break;
           }
           unsigned live = 0;
 #pragma unroll
-          for (int k = 0; k < NG; ++k) live |= (pos < gmax[k] ? 1u : 0u) << k;
+          for (int k = 0; k < NG; ++k) live |= (pos1 <= gmax[k] ? 1u : 0u) << k;
           m &= live;
           if (m == 0) continue;
+          exec_groups += __popc(m);
         }
-        exec_groups += __popc(m);
         const float4 ga = s_a[j];
         const float4 gb = s_b[j];
         const float cb = me.c;
@@ -569,7 +574,7 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_BWD_MINB : 1) k_blend
           const float G = ex2_approx(p2);
           const float oG = __fmul_rn(gb.y, G);
           const float alpha = alpha_of(gb.y, G, alpha_max);
-          const bool valid = (pos < nc[k]) && !(p2 > 0.f) && !(alpha < alpha_min);
+          const bool valid = (pos1 <= nc[k]) && !(p2 > 0.f) && !(alpha < alpha_min);
           const float ae = valid ? alpha : 0.f;
           const bool graded = valid && (oG <= alpha_max);
           const float w = __fmul_rn(ae, T[k]);
@@ -607,7 +612,7 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_BWD_MINB : 1) k_blend
           const float G = ex2_approx(p2);
           const float oG = __fmul_rn(gb.y, G);
           const float alpha = alpha_of(gb.y, G, alpha_max);
-          const bool valid = (pos < nc[k]) && !(p2 > 0.f) && !(alpha < alpha_min);
+          const bool valid = (pos1 <= nc[k]) && !(p2 > 0.f) && !(alpha < alpha_min);
           const float ae = valid ? alpha : 0.f;
           const bool graded = valid && (oG <= alpha_max);
           const float w = __fmul_rn(ae, T[k]);
@@ -678,9 +683,13 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_BWD_MINB : 1) k_blend
       __syncwarp();
     }
     if (COMPACT && ns > 0) flush_deferred<IMP>(s_red, s_fid, s_fcon, ns, cpack, gradv, in, lane);
-    executed += 32ull * exec_groups;
+    executed += (COMPACT ? 1ull : 32ull) * exec_groups;
   }
   for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(kAll, pairs, o);
+  if (COMPACT) {  // per-lane block counts: 32 lane evaluations per block
+    for (int o = 16; o > 0; o >>= 1) executed += __shfl_xor_sync(kAll, executed, o);
+    executed *= 32ull;
+  }
   if (lane == 0) {
     if (pairs) {
       atomicAdd(a.pair_counter, pairs);
