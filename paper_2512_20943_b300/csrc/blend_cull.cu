@@ -396,22 +396,19 @@ __device__ __forceinline__ void flush_deferred(float (*s_red)[kRedStride], const
   const float2 s4 = __fadd2_rn(s01, s23);
   const float sum = s4.x + s4.y;
   const float other = __shfl_xor_sync(kAll, sum, 1);  // S_y for the S_x lane and vice versa
-  if (lane < 10 * nf) {
-    const int f = lane / 10, q = lane - 10 * f;
+  const int f = lane / 10, q = lane - 10 * f;
+  if (lane < 10 * nf && (IMP || q < 9)) {
+    // GradRec floats 0-8: mean2d, conic A (x -1/2), B (x -1), C (x -1/2), opacity,
+    // colour; sum 9 (the blend weight) goes to the importance weights.  One
+    // branch-free coefficient pair per lane: value = ca sum + cb other.
     const uint32_t id = s_fid[f];
-    if (q < 9) {
-      // GradRec floats 0-8: mean2d, conic A (x -1/2), B (x -1), C (x -1/2), opacity, colour
-      const float4 cf = s_fcon[f];
-      float val;
-      if (q == 0) val = kLn2 * cf.w * (2.f * cf.x * sum + cf.y * other);
-      else if (q == 1) val = kLn2 * cf.w * (cf.y * other + 2.f * cf.z * sum);
-      else if (q < 5) val = (q == 3 ? -1.f : -0.5f) * cf.w * sum;
-      else val = sum;
-      float* dst = reinterpret_cast<float*>(gradv + id) + q;
-      asm volatile("red.global.add.f32 [%0], %1;" ::"l"(dst), "f"(val) : "memory");
-    } else if (IMP && sum != 0.f) {
-      atomicAdd(in.imp_w + id, sum);
-    }
+    const float4 cf = s_fcon[f];  // (a2, b2, c2, o)
+    const float o = cf.w, lo = kLn2 * cf.w;
+    const float ca = q == 0 ? 2.f * lo * cf.x : q == 1 ? 2.f * lo * cf.z : q == 3 ? -o : q < 5 ? -0.5f * o : 1.f;
+    const float cb = q < 2 ? lo * cf.y : 0.f;
+    const float val = fmaf(ca, sum, cb * other);
+    float* dst = q < 9 ? reinterpret_cast<float*>(gradv + id) + q : in.imp_w + id;
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(dst), "f"(val) : "memory");
   }
   if (IMP) {
     const uint32_t packed = (uint32_t)__shfl_sync(kAll, sum, 30);
