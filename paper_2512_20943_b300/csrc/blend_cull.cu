@@ -414,7 +414,7 @@ __device__ __forceinline__ void flush_deferred(float (*s_red)[kRedStride], const
     const uint32_t packed = (uint32_t)__shfl_sync(kAll, sum, 30);
     if (lane < nf) {
       const uint32_t c = (packed >> (8 * lane)) & 0xFFu;
-      if (c) atomicAdd(in.imp_cnt + s_fid[lane], c);
+      asm volatile("red.global.add.u32 [%0], %1;" ::"l"(in.imp_cnt + s_fid[lane]), "r"(c) : "memory");
     }
   }
   __syncwarp();  // the table is refilled after this
@@ -646,10 +646,9 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_BWD_MINB : 1) k_blend
 #pragma unroll
             for (int q = 0; q < 10; ++q) s_red[ns * 10 + q][lane] = acc[q];
             if (IMP) cpack += (uint32_t)cnt << (8 * ns);
-            if (lane == 0) {
-              s_fid[ns] = me.id;
-              s_fcon[ns] = make_float4(ga.z, ga.w, gb.x, gb.y);
-            }
+            // every lane stores the same values (one shared-memory word each, no branch)
+            s_fid[ns] = me.id;
+            s_fcon[ns] = make_float4(ga.z, ga.w, gb.x, gb.y);
             if (++ns == kDeferG) {
               flush_deferred<IMP>(s_red, s_fid, s_fcon, ns, cpack, gradv, in, lane);
               ns = 0;
