@@ -158,27 +158,24 @@ __device__ __forceinline__ uint32_t half_flags_of(float4 ga, int kind, float hx,
 // scale of its rounding error).  When the centre is outside, the maximum lies
 // on a face whose outer side holds the centre (the gradient there must point
 // out of the rectangle), so only the nearer vertical and horizontal faces are
-// searched, each at its clamped 1-D maximiser.
+// searched, each at its clamped 1-D maximiser.  Both faces are evaluated and
+// the results selected, so that lanes testing different rectangles do not
+// diverge.
 __device__ __forceinline__ float rect_max_power2(float a2, float b2, float c2, float kx, float ky, float xlo,
                                                  float xhi, float ylo, float yhi, float& S) {
   const bool in_x = xlo <= 0.f && xhi >= 0.f, in_y = ylo <= 0.f && yhi >= 0.f;
-  S = 0.f;
-  if (in_x && in_y) return 0.f;
-  float best = -INFINITY;
-  if (!in_x) {
-    const float DX = xlo > 0.f ? xlo : xhi;
-    const float dy = fminf(fmaxf(ky * DX, ylo), yhi);
-    best = fmaf(a2 * DX, DX, fmaf(b2 * DX, dy, c2 * dy * dy));
-    S = fabsf(a2) * DX * DX + fabsf(b2 * DX * dy) + fabsf(c2) * dy * dy;
-  }
-  if (!in_y) {
-    const float DY = ylo > 0.f ? ylo : yhi;
-    const float dx = fminf(fmaxf(kx * DY, xlo), xhi);
-    const float p = fmaf(a2 * dx, dx, fmaf(b2 * dx, DY, c2 * DY * DY));
-    S = fmaxf(S, fabsf(a2) * dx * dx + fabsf(b2 * dx * DY) + fabsf(c2) * DY * DY);
-    best = fmaxf(best, p);
-  }
-  return best;
+  const float DX = xlo > 0.f ? xlo : xhi;
+  const float dy = fminf(fmaxf(ky * DX, ylo), yhi);
+  const float pv = fmaf(a2 * DX, DX, fmaf(b2 * DX, dy, c2 * dy * dy));
+  const float sv = fabsf(a2) * DX * DX + fabsf(b2 * DX * dy) + fabsf(c2) * dy * dy;
+  const float DY = ylo > 0.f ? ylo : yhi;
+  const float dx = fminf(fmaxf(kx * DY, xlo), xhi);
+  const float ph = fmaf(a2 * dx, dx, fmaf(b2 * dx, DY, c2 * DY * DY));
+  const float sh = fabsf(a2) * dx * dx + fabsf(b2 * dx * DY) + fabsf(c2) * DY * DY;
+  S = fmaxf(in_x ? 0.f : sv, in_y ? 0.f : sh);
+  const float best = fmaxf(in_x ? -INFINITY : pv, in_y ? -INFINITY : ph);
+  if (in_x && in_y) S = 0.f;
+  return in_x && in_y ? 0.f : best;
 }
 
 // Halves of the tile at (X0, Y0) in which the Gaussian can reach alpha_min:
@@ -195,8 +192,7 @@ __device__ __forceinline__ uint32_t half_flags_exact(float4 ra, float4 rb, float
   const float kx = __fdividef(-b2, 2.f * a2), ky = __fdividef(-b2, 2.f * c2);
   const float xlo = (X0 + 0.5f) - ra.x, xhi = xlo + 15.f;
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    if (!((f >> h) & 1u)) continue;
+  for (int h = 0; h < 2; ++h) {  // both halves tested, the result masked (no divergence)
     const float ylo = (Y0 + 8.f * h + 0.5f) - ra.y, yhi = ylo + 7.f;
     float S;
     const float pm = rect_max_power2(a2, b2, c2, kx, ky, xlo, xhi, ylo, yhi, S);

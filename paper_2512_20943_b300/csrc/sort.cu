@@ -563,8 +563,7 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(int64_t total, int64_t n, c
         if (halves != 0u && qd.x < 0.f) {  // refine by the exact rectangle test (half_flags_exact)
           const float xlo = (X0 + 0.5f) - bx.x, xhi = xlo + 15.f;
 #pragma unroll
-          for (int k = 0; k < 2; ++k) {
-            if (!((halves >> k) & 1u)) continue;
+          for (int k = 0; k < 2; ++k) {  // both halves tested, the result masked (no divergence)
             const float ylo = (Y0 + 8.f * k + 0.5f) - bx.y, yhi = ylo + 7.f;
             float S;
             const float pm = rect_max_power2(qd.x, qd.y, qd.z, kxy.x, kxy.y, xlo, xhi, ylo, yhi, S);
