@@ -12,7 +12,10 @@
 
 namespace airgs {
 
-constexpr int HL_THREADS = 1024;
+#ifndef AIRGS_HL_THREADS
+#define AIRGS_HL_THREADS 256  // measured best of 256, 512, 1024
+#endif
+constexpr int HL_THREADS = AIRGS_HL_THREADS;
 constexpr int HL_ITEMS = 4;
 constexpr int HL_CHUNK = HL_THREADS * HL_ITEMS;
 
