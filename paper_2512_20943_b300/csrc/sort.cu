@@ -96,7 +96,10 @@ __global__ void __launch_bounds__(256) k_rs_spine(uint32_t* counts, uint32_t* to
 }
 
 // vals_in == nullptr: the value of a key is its index within its segment.
-__global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(const uint32_t* __restrict__ keys_in,
+#ifndef AIRGS_RS_MINB
+#define AIRGS_RS_MINB 5  // 48 registers, 5 CTAs per SM (measured best of 4 (unbounded), 5, 6, 8)
+#endif
+__global__ void __launch_bounds__(RS_THREADS, AIRGS_RS_MINB) k_rs_downsweep(const uint32_t* __restrict__ keys_in,
                                                             const uint32_t* __restrict__ vals_in,
                                                             uint32_t* __restrict__ keys_out,
                                                             uint32_t* __restrict__ vals_out, SortGeom g, int shift,
