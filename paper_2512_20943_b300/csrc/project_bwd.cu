@@ -14,6 +14,7 @@
 // Every gradient buffer is written once (overwrite), coalesced.
 #include "airgs_internal.cuh"
 #include "kernels.h"
+#include "sh_tile.cuh"
 
 namespace airgs {
 
@@ -72,14 +73,6 @@ __device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float* 
 #endif
 constexpr int PB_THREADS = 128;
 
-// Row stride (floats) of the block's SH tile in shared memory: the 3K
-// coefficients of a Gaussian padded to an odd count, so that the 32 lanes of a
-// warp, each reading its own row, hit 32 different banks.
-template <int DEG>
-__host__ __device__ constexpr int sh_tile_stride() {
-  return (3 * (DEG + 1) * (DEG + 1)) % 2 ? 3 * (DEG + 1) * (DEG + 1) : 3 * (DEG + 1) * (DEG + 1) + 1;
-}
-
 // The block's SH coefficients (one contiguous run of 128 x 3K floats) move
 // between global and shared memory with coalesced accesses; each thread then
 // reads and writes its own Gaussian's row of the tile.
@@ -95,14 +88,11 @@ __global__ void __launch_bounds__(PB_THREADS, AIRGS_PROJ_BWD_MINB) k_project_bwd
                                                      float* __restrict__ g_opacity, float* __restrict__ g_sh,
                                                      float* __restrict__ dens_grad, uint32_t* __restrict__ dens_views) {
   constexpr int K = (DEG + 1) * (DEG + 1);
-  constexpr int W = 3 * K, S = sh_tile_stride<DEG>();
+  constexpr int S = sh_tile_stride<DEG>();
   __shared__ float s_sh[PB_THREADS * S];
   const int64_t g0 = (int64_t)blockIdx.x * PB_THREADS;
   const int nloc = (int)min((int64_t)PB_THREADS, n - g0);
-  {
-    const float* src = sh + g0 * W;
-    for (int e = threadIdx.x; e < nloc * W; e += PB_THREADS) s_sh[(e / W) * S + e % W] = __ldg(src + e);
-  }
+  sh_tile_load<DEG, PB_THREADS>(s_sh, sh, g0, nloc);
   __syncthreads();
   const int t = threadIdx.x;
   const int64_t i = g0 + t;
@@ -286,8 +276,7 @@ __global__ void __launch_bounds__(PB_THREADS, AIRGS_PROJ_BWD_MINB) k_project_bwd
     for (int k = 0; k < K * 3; ++k) s_sh[t * S + k] = gsh[k];
   }
   __syncthreads();
-  float* dst = g_sh + g0 * W;
-  for (int e = threadIdx.x; e < nloc * W; e += PB_THREADS) dst[e] = s_sh[(e / W) * S + e % W];
+  sh_tile_store<DEG, PB_THREADS>(s_sh, g_sh, g0, nloc);
 }
 
 cudaError_t launch_project_bwd(cudaStream_t st, int64_t n, int sh_degree, const float* means,
