@@ -35,7 +35,14 @@
 namespace airgs {
 
 constexpr int NG_TILE = 8;     // 8x4 blocks per tile
-constexpr int CBATCH = 64;     // records staged per batch (two per lane)
+#ifndef AIRGS_CULL_FWD_BATCH
+#define AIRGS_CULL_FWD_BATCH 32  // measured best of 16, 24, 32, 64, 96, 128
+#endif
+#ifndef AIRGS_CULL_BWD_BATCH
+#define AIRGS_CULL_BWD_BATCH 32  // measured best of 32, 64, 96
+#endif
+constexpr int CBATCH = AIRGS_CULL_BWD_BATCH;  // records the backward stages per batch
+constexpr int FBATCH = AIRGS_CULL_FWD_BATCH;  // the forward's batch (its live blocks are refreshed per batch)
 constexpr unsigned kAll = 0xffffffffu;
 
 __device__ __forceinline__ int cull_fetch(int* counter) {
@@ -159,9 +166,9 @@ __device__ __forceinline__ int stage_compact(const BlendArgs& a, bool use_hl, ui
 template <int NG, bool IMP, bool COMPACT>
 __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_FWD_MINB : 1) k_blend_fwd_cull(BlendArgs a, FwdOut out) {
   constexpr int PARTS = NG_TILE / NG;
-  __shared__ float4 s_a[CBATCH];
-  __shared__ float4 s_b[CBATCH];
-  __shared__ StageMeta s_meta[CBATCH];
+  __shared__ float4 s_a[FBATCH];
+  __shared__ float4 s_b[FBATCH];
+  __shared__ StageMeta s_meta[FBATCH];
   __shared__ int s_tile_base[COMPACT ? 1 : AIRGS_MAX_VIEWS_DEV];  // COMPACT reads the bases from the cameras
 
   const int lane = threadIdx.x;
@@ -207,13 +214,13 @@ __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_FWD_MINB : 1) k_blend
     const ProjRec* projv = a.proj + (size_t)v * a.n;
     uint32_t exec_groups = 0;  // warp-uniform (per-entry count) or per lane (COMPACT: counted while staging)
 
-    for (uint32_t b0 = er.x; b0 < er.y; b0 += CBATCH) {
+    for (uint32_t b0 = er.x; b0 < er.y; b0 += FBATCH) {
       unsigned live = 0;
 #pragma unroll
       for (int k = 0; k < NG; ++k)
         if (__any_sync(kAll, stop_at[k] < 0)) live |= 1u << k;
       if (live == 0) break;
-      int nb = (int)min((uint32_t)CBATCH, er.y - b0);
+      int nb = (int)min((uint32_t)FBATCH, er.y - b0);
       if (COMPACT) {
         const int none[NG] = {};
         bool unused = false;
