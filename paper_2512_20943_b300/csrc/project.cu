@@ -99,8 +99,11 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, float* Y) {
 }
 
 // ------------------------------------------------------------------ projection
+#ifndef AIRGS_PROJ_MINB
+#define AIRGS_PROJ_MINB 1  // unbounded (117 registers); 5 and 6 measured no faster
+#endif
 template <int DEG>
-__global__ void __launch_bounds__(128) k_project(int64_t n, const float* __restrict__ means,
+__global__ void __launch_bounds__(128, AIRGS_PROJ_MINB) k_project(int64_t n, const float* __restrict__ means,
                                                  const float* __restrict__ log_scales,
                                                  const float* __restrict__ quats,
                                                  const float* __restrict__ opacity_logit,
@@ -124,8 +127,19 @@ __global__ void __launch_bounds__(128) k_project(int64_t n, const float* __restr
   float opacity = 1.f / (1.f + expf(-opacity_logit[i]));
   float coef[K * 3];
   const float* shi = sh + (size_t)i * K * 3;
+  if ((K * 3) % 4 == 0 && (reinterpret_cast<uintptr_t>(sh) & 15u) == 0) {  // 16-byte loads when aligned
 #pragma unroll
-  for (int k = 0; k < K * 3; ++k) coef[k] = __ldg(shi + k);
+    for (int q = 0; q < (K * 3) / 4; ++q) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(shi) + q);
+      coef[4 * q] = v.x;
+      coef[4 * q + 1] = v.y;
+      coef[4 * q + 2] = v.z;
+      coef[4 * q + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < K * 3; ++k) coef[k] = __ldg(shi + k);
+  }
 
   for (int v = 0; v < n_views; ++v) {
     const CamDev& cam = cams[v];
