@@ -67,10 +67,10 @@ FP32_LANES_PER_SM = 128
 _BLEND_SOURCES = ("paper_2512_20943_b300/csrc/blend_cull.cu", "paper_2512_20943_b300/csrc/airgs_internal.cuh",
                   "paper_2512_20943_b300/csrc/kernels.h")
 NCU_TRAFFIC = {
-    "blend_bwd": {"bytes_per_launch": (640.320768 + 87.026944) * 1e6, "sources": _BLEND_SOURCES,
-                  "sha256": "433206f79d631b2df0ff717806e24a5ced9dfc34800441908542b283ec0b55c5"},
-    "blend_fwd": {"bytes_per_launch": (225.184768 + 234.346752) * 1e6, "sources": _BLEND_SOURCES,
-                  "sha256": "433206f79d631b2df0ff717806e24a5ced9dfc34800441908542b283ec0b55c5"},
+    "blend_bwd": {"bytes_per_launch": (641.003776 + 87.287552) * 1e6, "sources": _BLEND_SOURCES,
+                  "sha256": "195791f80dda507320979f80f650bd8a48b6d2d224c0727177e147d2dff87458"},
+    "blend_fwd": {"bytes_per_launch": (224.844288 + 233.991168) * 1e6, "sources": _BLEND_SOURCES,
+                  "sha256": "195791f80dda507320979f80f650bd8a48b6d2d224c0727177e147d2dff87458"},
 }
 
 

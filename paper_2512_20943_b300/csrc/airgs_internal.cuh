@@ -139,18 +139,6 @@ __device__ __forceinline__ int alpha_box(float4 ga, float4 gb, float log2_amin, 
 constexpr uint32_t kKeyTileMask = 0x3FFFFFFFu;
 constexpr int kKeyHalfShift = 30;
 
-// Halves (bit 0 top, bit 1 bottom) of the tile at (X0, Y0) that a Gaussian's
-// alpha >= alpha_min box meets; (kind, hx, hy) come from alpha_box.
-__device__ __forceinline__ uint32_t half_flags_of(float4 ga, int kind, float hx, float hy, float X0, float Y0) {
-  if (kind == 0) return 0u;
-  if (kind == 2) return 3u;
-  if (!(ga.x + hx >= X0 + 0.5f && ga.x - hx <= X0 + 15.5f)) return 0u;
-  uint32_t f = 0;
-  if (ga.y + hy >= Y0 + 0.5f && ga.y - hy <= Y0 + 7.5f) f |= 1u;
-  if (ga.y + hy >= Y0 + 8.5f && ga.y - hy <= Y0 + 15.5f) f |= 2u;
-  return f;
-}
-
 // Largest value over the rectangle [xlo, xhi] x [ylo, yhi] of offsets d = p - m
 // of the concave quadratic P(d) = a2 dx^2 + b2 dx dy + c2 dy^2 (negative
 // definite), with kx = -b2 / (2 a2), ky = -b2 / (2 c2) the maximisers along a
@@ -176,29 +164,6 @@ __device__ __forceinline__ float rect_max_power2(float a2, float b2, float c2, f
   const float best = fmaxf(in_x ? -INFINITY : pv, in_y ? -INFINITY : ph);
   if (in_x && in_y) S = 0.f;
   return in_x && in_y ? 0.f : best;
-}
-
-// Halves of the tile at (X0, Y0) in which the Gaussian can reach alpha_min:
-// the bounding-box flags of half_flags_of refined by the exact test of each
-// half's pixel-centre rectangle against the ellipse P >= -L (see
-// rect_max_power2), with the same margin the blend kernels' block test uses.
-__device__ __forceinline__ uint32_t half_flags_exact(float4 ra, float4 rb, float log2_amin, float X0, float Y0) {
-  float hx = 0.f, hy = 0.f;
-  const int kind = alpha_box(ra, rb, log2_amin, hx, hy);
-  uint32_t f = half_flags_of(ra, kind, hx, hy, X0, Y0);
-  const float a2 = ra.z, b2 = ra.w, c2 = rb.x;
-  if (f == 0u || kind != 1 || !(a2 < 0.f && c2 < 0.f && 4.f * a2 * c2 > 1.0001f * b2 * b2)) return f;
-  const float L = lg2_approx(rb.y) - log2_amin + 1e-3f;
-  const float kx = __fdividef(-b2, 2.f * a2), ky = __fdividef(-b2, 2.f * c2);
-  const float xlo = (X0 + 0.5f) - ra.x, xhi = xlo + 15.f;
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {  // both halves tested, the result masked (no divergence)
-    const float ylo = (Y0 + 8.f * h + 0.5f) - ra.y, yhi = ylo + 7.f;
-    float S;
-    const float pm = rect_max_power2(a2, b2, c2, kx, ky, xlo, xhi, ylo, yhi, S);
-    if (pm < -L - (0.01f + 1e-5f * S)) f &= ~(1u << h);
-  }
-  return f;
 }
 
 // Blocks of the tile at (X0, Y0) that the Gaussian's alpha >= alpha_min box

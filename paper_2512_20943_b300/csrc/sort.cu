@@ -563,7 +563,7 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(int64_t total, int64_t n, c
           if (bx.y + bx.w >= Y0 + 0.5f && bx.y - bx.w <= Y0 + 7.5f) halves |= 1u;
           if (bx.y + bx.w >= Y0 + 8.5f && bx.y - bx.w <= Y0 + 15.5f) halves |= 2u;
         }
-        if (halves != 0u && qd.x < 0.f) {  // refine by the exact rectangle test (half_flags_exact)
+        if (halves != 0u && qd.x < 0.f) {  // refine by the exact test of each half's rectangle (rect_max_power2)
           const float xlo = (X0 + 0.5f) - bx.x, xhi = xlo + 15.f;
 #pragma unroll
           for (int k = 0; k < 2; ++k) {  // both halves tested, the result masked (no divergence)

@@ -462,8 +462,9 @@ def test_unaligned_sh_buffer_renders_identically(rast):
     dL = torch.ones_like(a.rgb)
     ga = {k: v.clone() for k, v in rast.render_backward(a.state, dL).items()}
     gb = rast.render_backward(b.state, dL)
-    # gradients are accumulated with atomics: equal up to the order of the additions
+    # gradients are accumulated with atomics, so they agree up to the order of the
+    # additions; held to the parity bars of the gradient tests
     for k in ga:
-        torch.testing.assert_close(ga[k], gb[k], rtol=1e-5, atol=1e-6)
+        assert_grad_close(gb[k].cpu().numpy(), ga[k].cpu().numpy(), k)
     a.state.release()
     b.state.release()
