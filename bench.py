@@ -67,10 +67,12 @@ FP32_LANES_PER_SM = 128
 _BLEND_SOURCES = ("paper_2512_20943_b300/csrc/blend_cull.cu", "paper_2512_20943_b300/csrc/airgs_internal.cuh",
                   "paper_2512_20943_b300/csrc/kernels.h")
 NCU_TRAFFIC = {
-    "blend_bwd": {"bytes_per_launch": (641.003776 + 87.287552) * 1e6, "sources": _BLEND_SOURCES,
-                  "sha256": "195791f80dda507320979f80f650bd8a48b6d2d224c0727177e147d2dff87458"},
-    "blend_fwd": {"bytes_per_launch": (224.844288 + 233.991168) * 1e6, "sources": _BLEND_SOURCES,
-                  "sha256": "195791f80dda507320979f80f650bd8a48b6d2d224c0727177e147d2dff87458"},
+    "blend_bwd": {"bytes_per_launch": (640.500736 + 86.741504) * 1e6, "smem_bytes_per_launch": 419024757 * 128,
+                  "sources": _BLEND_SOURCES,
+                  "sha256": "157d5c483f84e4b55ad21bae33d37041bb6757cc84ae473774d915b948b5c380"},
+    "blend_fwd": {"bytes_per_launch": (225.171456 + 234.556416) * 1e6, "smem_bytes_per_launch": 82653512 * 128,
+                  "sources": _BLEND_SOURCES,
+                  "sha256": "157d5c483f84e4b55ad21bae33d37041bb6757cc84ae473774d915b948b5c380"},
 }
 
 
@@ -81,6 +83,15 @@ def _sources_sha256(paths):
         with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), p), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
+
+
+def dominant_smem_bytes(stage):
+    """Shared-memory bytes per launch (ncu wavefronts x 128 B) of the same capture
+    as the traffic, reported under the same source-hash rule."""
+    rec = NCU_TRAFFIC.get(stage)
+    if not rec or "smem_bytes_per_launch" not in rec or _sources_sha256(rec["sources"]) != rec["sha256"]:
+        return None
+    return rec["smem_bytes_per_launch"]
 
 
 def dominant_traffic(stage):
@@ -439,8 +450,20 @@ def run_ours(args):
                 "achieved_issued_lanes": i_t, "frac_issued_lanes": i_t / fp32_peak}
         with torch.cuda.stream(stream):
             measured = rast.measure_fp32_peak()  # an FMA probe on this GPU, after the timed region
+            smem_measured = rast.measure_smem_peak()  # and a shared-memory load probe
         roof["peak_measured_fma_probe"] = measured
         roof["frac_of_measured_peak"] = a_t / measured
+        # the second bound of the blend kernels: shared-memory bytes per launch from the
+        # ncu capture (wavefronts x 128 B) over the live CUDA-event time of a launch
+        smem_bytes = dominant_smem_bytes(dom)
+        smem_peak = n_sms * 128 * sm_max * 1e6 / 1e12
+        smem_tbs = smem_bytes / (ms[dom] / max(1, nl[dom]) / 1e3) / 1e12 if smem_bytes else None
+        roof["smem"] = {"achieved": smem_tbs, "unit": "TB/s", "peak": smem_peak,
+                        "peak_source": f"derived: {n_sms} SMs x 128 B/clock x {sm_max:.0f} MHz",
+                        "frac": smem_tbs / smem_peak if smem_tbs else None,
+                        "peak_measured_lds_probe": smem_measured,
+                        "frac_of_measured_peak": smem_tbs / smem_measured if smem_tbs else None,
+                        "bytes_per_launch": smem_bytes}
     else:
         gbs = stage_lines.get(dom, {}).get("gbs")
         roof = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",

@@ -342,6 +342,14 @@ const char* airgs_stage_name(int stage);
  * AIRGS_E_CUDA on failure. */
 int airgs_measure_fp32_peak(airgs_ctx* ctx, double* tflops);
 
+/* Measured shared-memory load throughput of the context's GPU, in TB/s, into
+ * *tbs (host pointer): conflict-free 16-byte shared loads from every SM, timed
+ * with CUDA events on the context's stream (synchronous).  A measurement aid
+ * for the blend kernels' shared-memory roofline; the paper has no counterpart.
+ * Returns AIRGS_E_ARG for a null pointer, AIRGS_E_OOM or AIRGS_E_CUDA on
+ * failure. */
+int airgs_measure_smem_peak(airgs_ctx* ctx, double* tbs);
+
 /* Process-wide number of kernel launches the library has issued. */
 int64_t airgs_kernel_launch_count(void);
 

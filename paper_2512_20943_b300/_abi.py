@@ -141,6 +141,7 @@ SIGNATURES = {
     "airgs_stage_times": (I, [CTX, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64), ctypes.POINTER(I64)]),
     "airgs_stage_name": (ctypes.c_char_p, [I]),
     "airgs_measure_fp32_peak": (I, [CTX, ctypes.POINTER(ctypes.c_double)]),
+    "airgs_measure_smem_peak": (I, [CTX, ctypes.POINTER(ctypes.c_double)]),
     "airgs_kernel_launch_count": (I64, []),
     "airgs_blend_variant_count": (I, []),
     "airgs_blend_variant_name": (ctypes.c_char_p, [I]),

@@ -1127,6 +1127,17 @@ int airgs_measure_fp32_peak(airgs_ctx* ctx, double* tflops) {
   return AIRGS_OK;
 }
 
+int airgs_measure_smem_peak(airgs_ctx* ctx, double* tbs) {
+  if (!ctx || !tbs) return AIRGS_E_ARG;
+  float* scratch = nullptr;
+  int rc = dalloc(ctx, &scratch, smem_probe_words(ctx->num_sms));
+  if (rc) return rc;
+  const cudaError_t e = measure_smem_peak(ctx->stream, ctx->num_sms, scratch, tbs);
+  dfree(ctx, scratch);
+  if (e != cudaSuccess) return fail(ctx, AIRGS_E_CUDA, "shared-memory probe: %s", cudaGetErrorString(e));
+  return AIRGS_OK;
+}
+
 int64_t airgs_kernel_launch_count(void) { return g_launches.load(); }
 
 int airgs_blend_variant_count(void) { return blend_variant_count(); }

@@ -137,5 +137,7 @@ cudaError_t launch_project_bwd(cudaStream_t st, int64_t n, int sh_degree, const 
 
 cudaError_t measure_fp32_peak(cudaStream_t st, int num_sms, float* scratch, double* tflops);
 size_t fp32_probe_words(int num_sms);
+cudaError_t measure_smem_peak(cudaStream_t st, int num_sms, float* scratch, double* tbs);
+size_t smem_probe_words(int num_sms);
 
 }  // namespace airgs

@@ -455,6 +455,12 @@ class Rasterizer:
         self._check(self.lib.airgs_measure_fp32_peak(self.ctx, ctypes.byref(v)))
         return v.value
 
+    def measure_smem_peak(self) -> float:
+        """Measured shared-memory load throughput of this context's GPU, TB/s."""
+        v = ctypes.c_double(0.0)
+        self._check(self.lib.airgs_measure_smem_peak(self.ctx, ctypes.byref(v)))
+        return v.value
+
     @staticmethod
     def variant_names():
         lib = load_library()

@@ -416,6 +416,15 @@ def test_fp32_probe_reports_a_plausible_peak(rast):
     assert 10.0 < v < 200.0, v
 
 
+def test_smem_probe_reports_a_plausible_peak(rast):
+    """The shared-memory load probe the benchmark reports beside the derived
+    shared-memory peak (SMs x 128 B per clock): within a factor of two of it."""
+    v = rast.measure_smem_peak()
+    props = torch.cuda.get_device_properties(0)
+    derived = props.multi_processor_count * 128 * 2.0e9 / 1e12  # at about 2 GHz
+    assert 0.5 * derived < v < 2.0 * derived, (v, derived)
+
+
 @pytest.mark.parametrize("scene", ["plain_2k", "sh3_ragged", "needles", "dense_cluster"])
 def test_culled_lists_render_identically(scene):
     """Renders whose lists nothing observes (no saved state, no n_contrib) list a
