@@ -28,7 +28,9 @@ import torch
 
 from ._abi import AIRGS_DELTA_ANCHOR
 
-BYTES_PER_GAUSSIAN = 7 * 2  # seven 16-bit channels per Gaussian in the update maps
+UPDATE_CHANNELS = 7  # position offset (3) + rotation delta (4) per Gaussian (Sec. III-B, Eq. 3)
+BYTES_PER_GAUSSIAN = UPDATE_CHANNELS * 2  # seven 16-bit channels per Gaussian in the update maps
+BETA = 2.0  # the cliff multiplier beta of Algorithm 1 as the experiments set it (Sec. V)
 
 
 @dataclass

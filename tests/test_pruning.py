@@ -1,7 +1,8 @@
 """Usage-frequency pruning p(.) and pruning-level selection (Sec. III-C,
-Algorithm 1): Algorithm 1 against hand-worked cases and a linear-scan
-restatement, the oracle's p(.) / record update against their definitions, and
-the CUDA kernels against the oracle."""
+Algorithm 1): Algorithm 1 against a linear-scan restatement (its hand-worked
+cases are fixtures under tests/golden/, checked by test_golden.py), the
+oracle's p(.) / record update against their definitions, and the CUDA kernels
+against the oracle."""
 import math
 
 import numpy as np
@@ -13,27 +14,6 @@ from paper_2512_20943_b300.pruning import psnr, select_pruning_level
 
 
 # ---------------------------------------------------------------- Algorithm 1 (host)
-def test_algorithm1_cliff_and_budget():
-    # quality drops: -0.1, -0.2 (ratio 2, not > 2), -0.2 (1), -2.5 (12.5 > 2): cliff at level 4
-    q = [30.0, 29.9, 29.7, 29.5, 27.0, 26.9]
-    s = [10, 8, 6, 4, 2, 1]
-    space = list(zip(q, s))
-    assert select_pruning_level(space, beta=2, bandwidth=7 * 30, frame_rate=30) == 2  # lowest level with size <= 7
-    assert select_pruning_level(space, beta=2, bandwidth=100, frame_rate=1) == 0      # everything fits: no pruning
-    assert select_pruning_level(space, beta=2, bandwidth=3, frame_rate=1) == 4        # no candidate fits: the cliff level
-    assert select_pruning_level(space, beta=2, bandwidth=4, frame_rate=1) == 3
-    # with a larger beta there is no cliff and the last level fits
-    assert select_pruning_level(space, beta=20, bandwidth=1, frame_rate=1) == 5
-
-
-def test_algorithm1_zero_previous_drop_and_tiny_spaces():
-    assert select_pruning_level([(30.0, 5)], 2, 1, 1) == 0
-    # a flat step followed by any loss is a cliff
-    space = [(30.0, 10), (30.0, 8), (29.0, 6), (28.0, 4)]
-    assert select_pruning_level(space, 2, 7, 1) == 2  # nothing in {0, 1} fits: the cliff level
-    assert select_pruning_level(space, 2, 9, 1) == 1
-
-
 def _linear_reference(space, beta, B, R):
     """The same selection by a linear scan of the candidates."""
     q = [a for a, _ in space]
