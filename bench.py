@@ -16,6 +16,19 @@ time.  Synthetic data (the paper's captures are not available).
 Prints one JSON line (rank 0).  Under torchrun every rank runs an independent
 replica of the workload (the path has no data-path exchange here); the time is
 the max over ranks and the value the pixels of all ranks over that time.
+
+Besides the contract's keys the line carries: `stages` (each stage's CUDA-event
+time per launch and share, achieved GB/s of the HBM-bound stages); `roofline`
+for the dominant kernel (algorithmic TFLOP/s against the derived FP32 peak and
+the library's FFMA probe; `roofline.smem`: shared-memory TB/s against SMs x 128
+B/clock and the library's LDS probe; DRAM traffic and shared-memory bytes come
+from a committed ncu capture and are null once the kernel's sources change);
+`e2e` (the same steps fed from pinned host buffers through the double-buffered
+HostFeed, every loss read back); `cpu_baseline` (the FP64 oracle on a bounded
+sample, one host core); `serving` (served-view throughput and p50/p99 latency
+of the continuous-batching engine against a one-view-per-call loop).
+`--workload plain|per_frame|large` measures the other workload shapes the same
+way; `--impl reference` times the oracle instead.
 """
 from __future__ import annotations
 
