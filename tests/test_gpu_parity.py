@@ -509,3 +509,25 @@ def test_many_ragged_views_in_one_launch(variant):
     for k in ("means", "log_scales", "quats", "opacity_logit", "sh"):
         assert_grad_close(gr[k].cpu().numpy(), ref_g[k], k)
     res.state.release()
+
+
+def test_maximum_view_count(rast):
+    """AIRGS_MAX_VIEWS (256) views render in one launch and match the oracle;
+    one more is an argument error."""
+    from paper_2512_20943_b300 import AirGSError
+    from paper_2512_20943_b300._abi import AIRGS_MAX_VIEWS
+    g = synthetic.gaussians(300, 41, mean_mode="uniform", mean_scale=(1.0, 1.0, 1.0), log_scale=(-2.5, 0.4),
+                            sh_degree=1, sh_std=0.2)
+    rng = np.random.default_rng(42)
+    cams = [synthetic.camera(synthetic.sphere_pose(rng, 3.5), 9 + v % 8, 7 + v % 5, fov_x_deg=50.0)
+            for v in range(AIRGS_MAX_VIEWS)]
+    t, res = render_gpu(rast, g, cams, T=True)
+    ref = oracle.render(synthetic.widen(g), cams)
+    rgb = views_np(res.rgb, cams)
+    for v in range(len(cams)):
+        ok = ~ref["ambig"][v]
+        if ok.any():
+            assert np.abs(rgb[v] - ref["rgb"][v])[:, ok].max() < RGB_ATOL, v
+    assert max(r.max() for r in ref["rgb"]) > 0.1
+    with pytest.raises(AirGSError):
+        rast.render_gaussians(*params(t), cams + cams[:1])
