@@ -531,3 +531,33 @@ def test_maximum_view_count(rast):
     assert max(r.max() for r in ref["rgb"]) > 0.1
     with pytest.raises(AirGSError):
         rast.render_gaussians(*params(t), cams + cams[:1])
+
+
+@pytest.mark.parametrize("variant", [3, 6])
+def test_non_default_settings_match_oracle(variant):
+    """A coloured background, no low-pass dilation and other blending
+    thresholds (alpha clamp 0.9, skip below 0.01, stop below 1e-3), on the GPU
+    and in the oracle: images, T, n_contrib and gradients (the background
+    enters the colour still ahead of every pair)."""
+    from paper_2512_20943_b300 import RasterConfig, Rasterizer
+    st = dict(dilation=0.0, alpha_max=0.9, alpha_min=0.01, T_min=1e-3, bg=(0.2, 0.5, 0.9))
+    rast = Rasterizer(RasterConfig(blend_variant=variant, **st))
+    g, cams = small_sh3_scene()
+    ref = oracle.render(synthetic.widen(g), cams, **st)
+    t, res = render_gpu(rast, g, cams, T=True, n_contrib=True, save=True)
+    rgb, T, nc = views_np(res.rgb, cams), views_np(res.T, cams, 1), views_np(res.n_contrib, cams, 1)
+    for v in range(len(cams)):
+        ok = ~ref["ambig"][v]
+        assert ok.mean() > 0.97
+        assert np.abs(rgb[v] - ref["rgb"][v])[:, ok].max() < RGB_ATOL
+        assert np.abs(T[v] - ref["T"][v])[ok].max() < RGB_ATOL
+        assert np.array_equal(nc[v][ok], ref["n_contrib"][v][ok])
+        assert rgb[v].min() >= 0.2 * T[v].min() - 1e-6  # the background shows through
+    dL = masked_dL(cams, ref, 51)
+    flat = torch.from_numpy(np.concatenate([d.reshape(-1) for d in dL]).astype(np.float32)).cuda()
+    gr = rast.render_backward(res.state, flat)
+    torch.cuda.synchronize()
+    ref_g = oracle.render_backward(synthetic.widen(g), cams, dL, **st)
+    for k in ("means", "log_scales", "quats", "opacity_logit", "sh"):
+        assert_grad_close(gr[k].cpu().numpy(), ref_g[k], k)
+    res.state.release()
