@@ -561,3 +561,22 @@ def test_non_default_settings_match_oracle(variant):
     for k in ("means", "log_scales", "quats", "opacity_logit", "sh"):
         assert_grad_close(gr[k].cpu().numpy(), ref_g[k], k)
     res.state.release()
+
+
+def test_autograd_function_gradients_match_oracle(rast):
+    """The torch.autograd.Function around the library: a random linear loss of
+    the rendered images back-propagated by autograd gives the oracle's
+    gradients with respect to every raw parameter."""
+    from paper_2512_20943_b300 import rasterize
+    g, cams = small_sh3_scene()
+    t = to_cuda(g)
+    p = [x.clone().requires_grad_(True) for x in params(t)]
+    rgb = rasterize(rast, *p, cams)
+    ref = oracle.render(synthetic.widen(g), cams)
+    dL = masked_dL(cams, ref, 61)
+    w = torch.from_numpy(np.concatenate([d.reshape(-1) for d in dL]).astype(np.float32)).cuda()
+    (rgb * w).sum().backward()
+    ref_g = oracle.render_backward(synthetic.widen(g), cams, dL)
+    for name, x in zip(("means", "log_scales", "quats", "opacity_logit", "sh"), p):
+        assert x.grad is not None and x.grad.shape == x.shape, name
+        assert_grad_close(x.grad.cpu().numpy(), ref_g[name], name)
