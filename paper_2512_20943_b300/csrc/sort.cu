@@ -18,6 +18,8 @@
 // each 2048-key tile stably in shared memory (warp match/popc per 32-key
 // round) and writes it out digit-contiguously, which keeps the global writes
 // coalesced.  About RS_CTAS_PER_SM CTAs per SM keep loads in flight.
+#include <utility>
+
 #include "airgs_internal.cuh"
 #include "kernels.h"
 
@@ -32,6 +34,28 @@ constexpr int RS_ITEMS = AIRGS_RS_ITEMS;  // keys per thread per tile
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 constexpr int RS_RADIX = 256;
 constexpr int RS_CTAS_PER_SM = 8;
+
+// The radix kernels are launched with programmatic stream serialisation: a
+// launch may begin while the previous kernel on the stream finishes, and each
+// kernel's first act is to wait (griddepcontrol.wait) until that kernel has
+// completed and its memory is visible.  Only the launch latency overlaps.
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_serialised(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
+                                     Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 struct SortGeom {
   int64_t seg_len;    // keys per segment
@@ -50,6 +74,7 @@ __device__ __forceinline__ void cta_range(const SortGeom& g, int cta, int& seg, 
 
 __global__ void __launch_bounds__(RS_THREADS) k_rs_upsweep(const uint32_t* __restrict__ keys, SortGeom g, int shift,
                                                           uint32_t* __restrict__ counts) {
+  wait_prior_grid();
   __shared__ uint32_t hist[RS_WARPS][RS_RADIX];
   int tid = threadIdx.x, warp = tid >> 5;
   for (int k = tid; k < RS_WARPS * RS_RADIX; k += RS_THREADS) (&hist[0][0])[k] = 0;
@@ -76,6 +101,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_upsweep(const uint32_t* __res
 // One warp per (segment, digit) row: exclusive scan of the row's per-CTA counts
 // in place, row total -> totals[segment * RS_RADIX + digit].
 __global__ void __launch_bounds__(256) k_rs_spine(uint32_t* counts, uint32_t* totals, int ctas_seg, int rows) {
+  wait_prior_grid();
   const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (row >= rows) return;
   uint32_t* c = counts + (size_t)row * ctas_seg;
@@ -105,6 +131,7 @@ __global__ void __launch_bounds__(RS_THREADS, AIRGS_RS_MINB) k_rs_downsweep(cons
                                                             uint32_t* __restrict__ vals_out, SortGeom g, int shift,
                                                             const uint32_t* __restrict__ counts,
                                                             const uint32_t* __restrict__ totals) {
+  wait_prior_grid();
   __shared__ uint32_t s_keys[RS_TILE];
   __shared__ uint32_t s_vals[RS_TILE];
   __shared__ uint32_t s_warp_cnt[RS_WARPS][RS_RADIX];  // per-warp digit counts, then per-warp offsets
@@ -637,12 +664,17 @@ cudaError_t radix_sort_pairs(cudaStream_t st, int num_sms, uint32_t* keys_a, uin
   for (int pass = 0; pass < passes; ++pass) {
     int shift = 8 * pass;
     uint32_t* totals = scratch + (size_t)n_seg * RS_RADIX * g.ctas_seg;
-    k_rs_upsweep<<<grid, RS_THREADS, 0, st>>>(ki, g, shift, scratch);
-    k_rs_spine<<<(n_seg * RS_RADIX + 7) / 8, 256, 0, st>>>(scratch, totals, g.ctas_seg, n_seg * RS_RADIX);
-    k_rs_downsweep<<<grid, RS_THREADS, 0, st>>>(ki, (pass == 0 && identity_vals) ? nullptr : vi, ko, vo, g, shift,
-                                                 scratch, totals);
+    const uint32_t* vin = (pass == 0 && identity_vals) ? nullptr : vi;
+    cudaError_t e = launch_serialised(k_rs_upsweep, dim3(grid), dim3(RS_THREADS), st, (const uint32_t*)ki, g, shift,
+                                      scratch);
+    if (e == cudaSuccess)
+      e = launch_serialised(k_rs_spine, dim3((n_seg * RS_RADIX + 7) / 8), dim3(256), st, scratch, totals, g.ctas_seg,
+                            n_seg * RS_RADIX);
+    if (e == cudaSuccess)
+      e = launch_serialised(k_rs_downsweep, dim3(grid), dim3(RS_THREADS), st, (const uint32_t*)ki, vin, ko, vo, g,
+                            shift, (const uint32_t*)scratch, (const uint32_t*)totals);
     count_launches(3);
-    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     uint32_t* t = ki;
     ki = ko;
@@ -663,11 +695,15 @@ cudaError_t radix_sort_pass(cudaStream_t st, int num_sms, const uint32_t* keys_i
   if (n == 0) return cudaSuccess;
   SortGeom g = make_geom(n, 1, num_sms);
   uint32_t* totals = counts + (size_t)RS_RADIX * g.ctas_seg;
-  k_rs_upsweep<<<g.ctas_seg, RS_THREADS, 0, st>>>(keys_in, g, shift, counts);
-  k_rs_spine<<<(RS_RADIX + 7) / 8, 256, 0, st>>>(counts, totals, g.ctas_seg, RS_RADIX);
-  k_rs_downsweep<<<g.ctas_seg, RS_THREADS, 0, st>>>(keys_in, vals_in, keys_out, vals_out, g, shift, counts, totals);
+  cudaError_t e = launch_serialised(k_rs_upsweep, dim3(g.ctas_seg), dim3(RS_THREADS), st, keys_in, g, shift, counts);
+  if (e == cudaSuccess)
+    e = launch_serialised(k_rs_spine, dim3((RS_RADIX + 7) / 8), dim3(256), st, counts, totals, g.ctas_seg, RS_RADIX);
+  if (e == cudaSuccess)
+    e = launch_serialised(k_rs_downsweep, dim3(g.ctas_seg), dim3(RS_THREADS), st, keys_in, vals_in, keys_out,
+                          vals_out, g, shift, (const uint32_t*)counts, (const uint32_t*)totals);
   count_launches(3);
-  return cudaGetLastError();
+  if (e == cudaSuccess) e = cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_count_gather(cudaStream_t st, int64_t total, int64_t n, const uint32_t* order,
