@@ -9,6 +9,7 @@
 // reporting and replaying positions of the definition's list.
 #include "airgs_internal.cuh"
 #include "kernels.h"
+#include "launch.cuh"
 
 namespace airgs {
 
@@ -40,6 +41,7 @@ struct HalfArgs {
 __global__ void __launch_bounds__(HL_THREADS) k_half_sums(HalfArgs h, uint8_t* __restrict__ flags,
                                                           uint64_t* __restrict__ sums_top,
                                                           uint64_t* __restrict__ sums_bot) {
+  wait_prior_grid();
   __shared__ uint32_t s_t[HL_THREADS / 32], s_b[HL_THREADS / 32];
   const int64_t c0 = (int64_t)blockIdx.x * HL_CHUNK;
   const int lane = threadIdx.x & 31;
@@ -90,6 +92,7 @@ __global__ void __launch_bounds__(HL_THREADS) k_half_compact(HalfArgs h, const u
                                                              const uint64_t* __restrict__ off_bot,
                                                              uint64_t bot_base, uint2* __restrict__ hl,
                                                              uint2* __restrict__ hranges, int64_t n_tiles) {
+  wait_prior_grid();
   __shared__ uint32_t s_t[HL_THREADS / 32], s_b[HL_THREADS / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t p0 = (int64_t)blockIdx.x * HL_CHUNK + (int64_t)tid * HL_ITEMS;
@@ -163,14 +166,14 @@ cudaError_t launch_half_lists(cudaStream_t st, const uint32_t* keys, const uint3
   HalfArgs h{keys, ids, ranges, ranges, cams, n_views, proj, n, n_inst, log2f(alpha_min)};
   uint64_t* st_ = sums;               // [chunks + 1] top
   uint64_t* sb_ = sums + chunks + 1;  // [chunks + 1] bottom
-  k_half_sums<<<(unsigned)chunks, HL_THREADS, 0, st>>>(h, flags, st_, sb_);
-  cudaError_t e = launch_scan_spans(st, st_, chunks, st_ + chunks);
+  cudaError_t e = launch_serialised(k_half_sums, dim3((unsigned)chunks), dim3(HL_THREADS), 0, st, h, flags, st_, sb_);
+  if (e == cudaSuccess) e = launch_scan_spans(st, st_, chunks, st_ + chunks);
   if (e == cudaSuccess) e = launch_scan_spans(st, sb_, chunks, sb_ + chunks);
   if (e != cudaSuccess) return e;
-  k_half_compact<<<(unsigned)chunks, HL_THREADS, 0, st>>>(h, flags, st_, sb_, (uint64_t)n_inst, hl, hranges,
-                                                          n_tiles);
+  e = launch_serialised(k_half_compact, dim3((unsigned)chunks), dim3(HL_THREADS), 0, st, h, (const uint8_t*)flags,
+                        (const uint64_t*)st_, (const uint64_t*)sb_, (uint64_t)n_inst, hl, hranges, n_tiles);
   count_launches(2);
-  return cudaGetLastError();
+  return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 }  // namespace airgs

@@ -10,6 +10,7 @@
 //                   radius, tile rectangle, depth key, SH colour.
 #include "airgs_internal.cuh"
 #include "kernels.h"
+#include "launch.cuh"
 
 namespace airgs {
 
@@ -24,6 +25,7 @@ __global__ void __launch_bounds__(256) k_decode_apply(int64_t n, const uint16_t*
                                                       const float* __restrict__ base_means,
                                                       const float* __restrict__ base_quats, float* out_means,
                                                       float* out_quats) {
+  wait_prior_grid();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float v[7];
@@ -254,9 +256,10 @@ cudaError_t launch_decode_apply(cudaStream_t st, int64_t n, const uint16_t* map,
     dp.scale[c] = (float)(((double)hi[c] - (double)lo[c]) / 65535.0);
   }
   int blocks = (int)((n + 255) / 256);
-  k_decode_apply<<<blocks, 256, 0, st>>>(n, map, plane, dp, quat_add, base_means, base_quats, out_means, out_quats);
+  cudaError_t e = launch_serialised(k_decode_apply, dim3(blocks), dim3(256), 0, st, n, map, plane, dp, quat_add,
+                                    base_means, base_quats, out_means, out_quats);
   count_launches(1);
-  return cudaGetLastError();
+  return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 cudaError_t launch_project(cudaStream_t st, int64_t n, int sh_degree, const float* means, const float* log_scales,

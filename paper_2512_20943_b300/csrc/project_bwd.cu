@@ -14,6 +14,7 @@
 // Every gradient buffer is written once (overwrite), coalesced.
 #include "airgs_internal.cuh"
 #include "kernels.h"
+#include "launch.cuh"
 #include "sh_tile.cuh"
 
 namespace airgs {
@@ -87,6 +88,7 @@ __global__ void __launch_bounds__(PB_THREADS, AIRGS_PROJ_BWD_MINB) k_project_bwd
                                                      float* __restrict__ g_log_scales, float* __restrict__ g_quats,
                                                      float* __restrict__ g_opacity, float* __restrict__ g_sh,
                                                      float* __restrict__ dens_grad, uint32_t* __restrict__ dens_views) {
+  wait_prior_grid();
   constexpr int K = (DEG + 1) * (DEG + 1);
   constexpr int S = sh_tile_stride<DEG>();
   __shared__ float s_sh[PB_THREADS * S];
@@ -286,9 +288,11 @@ cudaError_t launch_project_bwd(cudaStream_t st, int64_t n, int sh_degree, const 
                                float* g_opacity, float* g_sh, float* dens_grad, uint32_t* dens_views) {
   if (n == 0) return cudaSuccess;
   int blocks = (int)((n + PB_THREADS - 1) / PB_THREADS);
-#define AIRGS_PB(D)                                                                                              \
-  k_project_bwd<D><<<blocks, PB_THREADS, 0, st>>>(n, means, log_scales, quats, opacity_logit, sh, cams, n_views, proj, \
-                                           grad, g_means, g_log_scales, g_quats, g_opacity, g_sh, dens_grad, dens_views)
+  cudaError_t e;
+#define AIRGS_PB(D)                                                                                                 \
+  e = launch_serialised(k_project_bwd<D>, dim3(blocks), dim3(PB_THREADS), 0, st, n, means, log_scales, quats,       \
+                        opacity_logit, sh, cams, n_views, proj, grad, g_means, g_log_scales, g_quats, g_opacity, g_sh, \
+                        dens_grad, dens_views)
   switch (sh_degree) {
     case 0: AIRGS_PB(0); break;
     case 1: AIRGS_PB(1); break;
@@ -297,7 +301,7 @@ cudaError_t launch_project_bwd(cudaStream_t st, int64_t n, int sh_degree, const 
   }
 #undef AIRGS_PB
   count_launches(1);
-  return cudaGetLastError();
+  return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 }  // namespace airgs

@@ -18,10 +18,9 @@
 // each 2048-key tile stably in shared memory (warp match/popc per 32-key
 // round) and writes it out digit-contiguously, which keeps the global writes
 // coalesced.  About RS_CTAS_PER_SM CTAs per SM keep loads in flight.
-#include <utility>
-
 #include "airgs_internal.cuh"
 #include "kernels.h"
+#include "launch.cuh"
 
 namespace airgs {
 
@@ -35,28 +34,8 @@ constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 constexpr int RS_RADIX = 256;
 constexpr int RS_CTAS_PER_SM = 8;
 
-// The radix kernels are launched with programmatic stream serialisation: a
-// launch may begin while the previous kernel on the stream finishes, and each
-// kernel's first act is to wait (griddepcontrol.wait) until that kernel has
-// completed and its memory is visible.  Only the launch latency overlaps.
-__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
-template <typename... KArgs, typename... Args>
-static cudaError_t launch_serialised(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
-                                     Args&&... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
-}
-
+// The radix kernels and the emission chain are launched with programmatic
+// stream serialisation (launch.cuh): each waits for its predecessor first.
 struct SortGeom {
   int64_t seg_len;    // keys per segment
   int n_seg;          // segments (views), each sorted independently
@@ -269,6 +248,7 @@ __global__ void __launch_bounds__(EM_THREADS) k_count_gather(int64_t total, int6
                                                             const uint32_t* __restrict__ tiles_touched,
                                                             uint32_t* __restrict__ counts_sorted,
                                                             uint64_t* __restrict__ chunk_sums) {
+  wait_prior_grid();
   __shared__ uint64_t s_w[EM_THREADS / 32];
   int64_t c0 = (int64_t)blockIdx.x * EM_CHUNK;
   uint64_t sum = 0;
@@ -295,6 +275,7 @@ __global__ void __launch_bounds__(EM_THREADS) k_count_gather(int64_t total, int6
 
 // Exclusive scan of the chunk sums (one CTA); total -> *total_out.
 __global__ void __launch_bounds__(1024) k_scan_spans(uint64_t* sums, int64_t n_chunks, uint64_t* total_out) {
+  wait_prior_grid();
   __shared__ uint64_t warp_sums[32];
   __shared__ uint64_t carry;
   int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -342,6 +323,7 @@ constexpr size_t EM_SMEM = 3 * EM_CHUNK * sizeof(float4) + EM_CHUNK * sizeof(flo
 
 __global__ void __launch_bounds__(1024) k_emit_pieces(const uint64_t* __restrict__ chunk_offsets, int64_t n_chunks,
                                                      uint32_t* __restrict__ piece_off) {
+  wait_prior_grid();
   __shared__ uint32_t warp_sums[32];
   __shared__ uint32_t carry;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -373,6 +355,7 @@ __global__ void __launch_bounds__(1024) k_emit_pieces(const uint64_t* __restrict
 // piece_chunk[b] = the chunk that owns piece b (one thread per chunk).
 __global__ void k_emit_piece_map(const uint32_t* __restrict__ piece_off, int64_t n_chunks,
                                  uint32_t* __restrict__ piece_chunk) {
+  wait_prior_grid();
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n_chunks) return;
   for (uint32_t b = piece_off[c]; b < piece_off[c + 1]; ++b) piece_chunk[b] = (uint32_t)c;
@@ -400,6 +383,7 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(int64_t total, int64_t n, c
                                                     const ProjRec* __restrict__ proj, const CamDev* __restrict__ cams,
                                                     float log2_amin, bool with_halves, int cull,
                                                     uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  wait_prior_grid();
   // dynamic shared memory (EM_SMEM bytes):
   extern __shared__ float4 em_smem[];
   float4* s_box = em_smem;                   // centre, alpha-box half-widths (-inf: never, +inf: unbounded)
@@ -621,6 +605,7 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(int64_t total, int64_t n, c
 }
 
 __global__ void k_tile_ranges(int64_t n_inst, const uint32_t* __restrict__ keys, uint2* __restrict__ ranges) {
+  wait_prior_grid();
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n_inst) return;
   uint32_t k = keys[p] & kKeyTileMask;
@@ -665,13 +650,13 @@ cudaError_t radix_sort_pairs(cudaStream_t st, int num_sms, uint32_t* keys_a, uin
     int shift = 8 * pass;
     uint32_t* totals = scratch + (size_t)n_seg * RS_RADIX * g.ctas_seg;
     const uint32_t* vin = (pass == 0 && identity_vals) ? nullptr : vi;
-    cudaError_t e = launch_serialised(k_rs_upsweep, dim3(grid), dim3(RS_THREADS), st, (const uint32_t*)ki, g, shift,
+    cudaError_t e = launch_serialised(k_rs_upsweep, dim3(grid), dim3(RS_THREADS), 0, st, (const uint32_t*)ki, g, shift,
                                       scratch);
     if (e == cudaSuccess)
-      e = launch_serialised(k_rs_spine, dim3((n_seg * RS_RADIX + 7) / 8), dim3(256), st, scratch, totals, g.ctas_seg,
+      e = launch_serialised(k_rs_spine, dim3((n_seg * RS_RADIX + 7) / 8), dim3(256), 0, st, scratch, totals, g.ctas_seg,
                             n_seg * RS_RADIX);
     if (e == cudaSuccess)
-      e = launch_serialised(k_rs_downsweep, dim3(grid), dim3(RS_THREADS), st, (const uint32_t*)ki, vin, ko, vo, g,
+      e = launch_serialised(k_rs_downsweep, dim3(grid), dim3(RS_THREADS), 0, st, (const uint32_t*)ki, vin, ko, vo, g,
                             shift, (const uint32_t*)scratch, (const uint32_t*)totals);
     count_launches(3);
     if (e == cudaSuccess) e = cudaGetLastError();
@@ -695,11 +680,11 @@ cudaError_t radix_sort_pass(cudaStream_t st, int num_sms, const uint32_t* keys_i
   if (n == 0) return cudaSuccess;
   SortGeom g = make_geom(n, 1, num_sms);
   uint32_t* totals = counts + (size_t)RS_RADIX * g.ctas_seg;
-  cudaError_t e = launch_serialised(k_rs_upsweep, dim3(g.ctas_seg), dim3(RS_THREADS), st, keys_in, g, shift, counts);
+  cudaError_t e = launch_serialised(k_rs_upsweep, dim3(g.ctas_seg), dim3(RS_THREADS), 0, st, keys_in, g, shift, counts);
   if (e == cudaSuccess)
-    e = launch_serialised(k_rs_spine, dim3((RS_RADIX + 7) / 8), dim3(256), st, counts, totals, g.ctas_seg, RS_RADIX);
+    e = launch_serialised(k_rs_spine, dim3((RS_RADIX + 7) / 8), dim3(256), 0, st, counts, totals, g.ctas_seg, RS_RADIX);
   if (e == cudaSuccess)
-    e = launch_serialised(k_rs_downsweep, dim3(g.ctas_seg), dim3(RS_THREADS), st, keys_in, vals_in, keys_out,
+    e = launch_serialised(k_rs_downsweep, dim3(g.ctas_seg), dim3(RS_THREADS), 0, st, keys_in, vals_in, keys_out,
                           vals_out, g, shift, (const uint32_t*)counts, (const uint32_t*)totals);
   count_launches(3);
   if (e == cudaSuccess) e = cudaGetLastError();
@@ -711,16 +696,16 @@ cudaError_t launch_count_gather(cudaStream_t st, int64_t total, int64_t n, const
                                 int64_t* n_chunks) {
   *n_chunks = (total + EM_CHUNK - 1) / EM_CHUNK;
   if (total == 0) return cudaSuccess;
-  k_count_gather<<<(unsigned)*n_chunks, EM_THREADS, 0, st>>>(total, n, order, tiles_touched, counts_sorted,
-                                                             chunk_sums);
+  cudaError_t e = launch_serialised(k_count_gather, dim3((unsigned)*n_chunks), dim3(EM_THREADS), 0, st, total, n,
+                                    order, tiles_touched, counts_sorted, chunk_sums);
   count_launches(1);
-  return cudaGetLastError();
+  return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 cudaError_t launch_scan_spans(cudaStream_t st, uint64_t* sums, int64_t n_chunks, uint64_t* total_out) {
-  k_scan_spans<<<1, 1024, 0, st>>>(sums, n_chunks, total_out);
+  cudaError_t e = launch_serialised(k_scan_spans, dim3(1), dim3(1024), 0, st, sums, n_chunks, total_out);
   count_launches(1);
-  return cudaGetLastError();
+  return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 // piece offsets [n_chunks + 1], then the piece -> chunk map [n_inst / EM_PIECE + n_chunks + 1]
@@ -738,12 +723,15 @@ cudaError_t launch_emit(cudaStream_t st, int64_t total, int64_t n, const uint32_
   // sum over chunks of ceil(count / EM_PIECE) <= n_inst / EM_PIECE + n_chunks; surplus CTAs return at once
   const int64_t grid = n_chunks + n_inst / EM_PIECE + 1;
   uint32_t* piece_chunk = piece_off + n_chunks + 1;
-  k_emit_pieces<<<1, 1024, 0, st>>>(chunk_offsets, n_chunks, piece_off);
-  k_emit_piece_map<<<(unsigned)((n_chunks + 255) / 256), 256, 0, st>>>(piece_off, n_chunks, piece_chunk);
+  cudaError_t e = launch_serialised(k_emit_pieces, dim3(1), dim3(1024), 0, st, chunk_offsets, n_chunks, piece_off);
+  if (e == cudaSuccess)
+    e = launch_serialised(k_emit_piece_map, dim3((unsigned)((n_chunks + 255) / 256)), dim3(256), 0, st,
+                          (const uint32_t*)piece_off, n_chunks, piece_chunk);
+  if (e != cudaSuccess) return e;
   // the attribute is per device: set it once for each device this process uses
   static bool smem_set[kMaxDevicesAttr] = {};
   int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev >= kMaxDevicesAttr || !smem_set[dev]) {
     e = cudaFuncSetAttribute(k_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EM_SMEM);
@@ -752,19 +740,19 @@ cudaError_t launch_emit(cudaStream_t st, int64_t total, int64_t n, const uint32_
     if (e != cudaSuccess) return e;
     if (dev < kMaxDevicesAttr) smem_set[dev] = true;
   }
-  k_emit<<<(unsigned)grid, EM_THREADS, EM_SMEM, st>>>(total, n, order, counts_sorted, chunk_offsets, piece_off,
-                                                       piece_chunk, n_chunks,
-                                                proj, cams, log2f(alpha_min), n_tiles <= (1ll << 24), cull ? 1 : 0, keys,
-                                                vals);
+  e = launch_serialised(k_emit, dim3((unsigned)grid), dim3(EM_THREADS), EM_SMEM, st, total, n, order, counts_sorted,
+                        chunk_offsets, (const uint32_t*)piece_off, (const uint32_t*)piece_chunk, n_chunks, proj, cams,
+                        log2f(alpha_min), n_tiles <= (1ll << 24), cull ? 1 : 0, keys, vals);
   count_launches(3);
-  return cudaGetLastError();
+  return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 cudaError_t launch_tile_ranges(cudaStream_t st, int64_t n_inst, const uint32_t* keys, uint2* ranges) {
   if (n_inst == 0) return cudaSuccess;
-  k_tile_ranges<<<(unsigned)((n_inst + 255) / 256), 256, 0, st>>>(n_inst, keys, ranges);
+  cudaError_t e = launch_serialised(k_tile_ranges, dim3((unsigned)((n_inst + 255) / 256)), dim3(256), 0, st, n_inst,
+                                    keys, ranges);
   count_launches(1);
-  return cudaGetLastError();
+  return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 }  // namespace airgs
