@@ -236,7 +236,10 @@ __global__ void __launch_bounds__(RS_THREADS, AIRGS_RS_MINB) k_rs_downsweep(cons
 
 // ------------------------------------------------------------------ instance emission
 constexpr int EM_THREADS = 256;
-constexpr int EM_ITEMS = 2;
+#ifndef AIRGS_EM_ITEMS
+#define AIRGS_EM_ITEMS 1  // 256-Gaussian chunks: 6 CTAs per SM (measured best of 1, 2)
+#endif
+constexpr int EM_ITEMS = AIRGS_EM_ITEMS;
 constexpr int EM_CHUNK = EM_THREADS * EM_ITEMS;
 
 int64_t emit_chunks(int64_t total) { return (total + EM_CHUNK - 1) / EM_CHUNK; }
@@ -315,7 +318,10 @@ __global__ void __launch_bounds__(1024) k_scan_spans(uint64_t* sums, int64_t n_c
 // scan over chunks of ceil(instances of chunk c / EM_PIECE) (one CTA), total
 // pieces in piece_off[n_chunks].  chunk_offsets holds the chunks' exclusive
 // instance offsets with the total in chunk_offsets[n_chunks].
-constexpr int EM_RUN = 8;                                     // instances per thread and piece
+#ifndef AIRGS_EM_RUN
+#define AIRGS_EM_RUN 8  // measured best of 4, 8
+#endif
+constexpr int EM_RUN = AIRGS_EM_RUN;                          // instances per thread and piece
 constexpr uint32_t EM_PIECE = (uint32_t)EM_THREADS * EM_RUN;  // instances per CTA
 constexpr int EM_STAGE = EM_THREADS * (EM_RUN + 1);            // padded staging rows (no bank conflicts)
 constexpr size_t EM_SMEM = 3 * EM_CHUNK * sizeof(float4) + EM_CHUNK * sizeof(float2) +
