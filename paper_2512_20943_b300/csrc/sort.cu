@@ -29,17 +29,21 @@ constexpr int RS_WARPS = RS_THREADS / 32;
 #ifndef AIRGS_RS_ITEMS
 #define AIRGS_RS_ITEMS 8
 #endif
-constexpr int RS_ITEMS = AIRGS_RS_ITEMS;  // keys per thread per tile
-constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+#ifndef AIRGS_RS_ITEMS_SEG
+#define AIRGS_RS_ITEMS_SEG 6  // measured best of 4, 6, 8 (more CTAs over the views' short segments)
+#endif
+constexpr int RS_ITEMS = AIRGS_RS_ITEMS;          // keys per thread per tile
+constexpr int RS_ITEMS_SEG = AIRGS_RS_ITEMS_SEG;  // the same for a sort of several segments (the per-view depth sort)
 constexpr int RS_RADIX = 256;
 constexpr int RS_CTAS_PER_SM = 8;
 
 // The radix kernels and the emission chain are launched with programmatic
 // stream serialisation (launch.cuh): each waits for its predecessor first.
 struct SortGeom {
+  int64_t tile;       // keys per CTA tile (RS_THREADS x keys per thread)
   int64_t seg_len;    // keys per segment
   int n_seg;          // segments (views), each sorted independently
-  int64_t tiles_seg;  // RS_TILE-key tiles per segment
+  int64_t tiles_seg;  // tiles per segment
   int ctas_seg;       // CTAs per segment
   int64_t tiles_cta;  // tiles handled by one CTA (contiguous)
 };
@@ -54,6 +58,7 @@ __device__ __forceinline__ void cta_range(const SortGeom& g, int cta, int& seg, 
 __global__ void __launch_bounds__(RS_THREADS) k_rs_upsweep(const uint32_t* __restrict__ keys, SortGeom g, int shift,
                                                           uint32_t* __restrict__ counts) {
   wait_prior_grid();
+  const int64_t RS_TILE = g.tile;
   __shared__ uint32_t hist[RS_WARPS][RS_RADIX];
   int tid = threadIdx.x, warp = tid >> 5;
   for (int k = tid; k < RS_WARPS * RS_RADIX; k += RS_THREADS) (&hist[0][0])[k] = 0;
@@ -104,6 +109,7 @@ __global__ void __launch_bounds__(256) k_rs_spine(uint32_t* counts, uint32_t* to
 #ifndef AIRGS_RS_MINB
 #define AIRGS_RS_MINB 5  // 48 registers, 5 CTAs per SM (measured best of 4 (unbounded), 5, 6, 8)
 #endif
+template <int RS_ITEMS>
 __global__ void __launch_bounds__(RS_THREADS, AIRGS_RS_MINB) k_rs_downsweep(const uint32_t* __restrict__ keys_in,
                                                             const uint32_t* __restrict__ vals_in,
                                                             uint32_t* __restrict__ keys_out,
@@ -111,6 +117,7 @@ __global__ void __launch_bounds__(RS_THREADS, AIRGS_RS_MINB) k_rs_downsweep(cons
                                                             const uint32_t* __restrict__ counts,
                                                             const uint32_t* __restrict__ totals) {
   wait_prior_grid();
+  constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
   __shared__ uint32_t s_keys[RS_TILE];
   __shared__ uint32_t s_vals[RS_TILE];
   __shared__ uint32_t s_warp_cnt[RS_WARPS][RS_RADIX];  // per-warp digit counts, then per-warp offsets
@@ -622,9 +629,10 @@ __global__ void k_tile_ranges(int64_t n_inst, const uint32_t* __restrict__ keys,
 // ------------------------------------------------------------------ host side
 static SortGeom make_geom(int64_t seg_len, int n_seg, int num_sms) {
   SortGeom g;
+  g.tile = (int64_t)RS_THREADS * (n_seg > 1 ? RS_ITEMS_SEG : RS_ITEMS);
   g.seg_len = seg_len;
   g.n_seg = n_seg;
-  g.tiles_seg = (seg_len + RS_TILE - 1) / RS_TILE;
+  g.tiles_seg = (seg_len + g.tile - 1) / g.tile;
   if (g.tiles_seg == 0) g.tiles_seg = 1;
   int target = max(1, (RS_CTAS_PER_SM * num_sms + n_seg - 1) / n_seg);
   g.tiles_cta = (g.tiles_seg + target - 1) / target;
@@ -662,8 +670,12 @@ cudaError_t radix_sort_pairs(cudaStream_t st, int num_sms, uint32_t* keys_a, uin
       e = launch_serialised(k_rs_spine, dim3((n_seg * RS_RADIX + 7) / 8), dim3(256), 0, st, scratch, totals, g.ctas_seg,
                             n_seg * RS_RADIX);
     if (e == cudaSuccess)
-      e = launch_serialised(k_rs_downsweep, dim3(grid), dim3(RS_THREADS), 0, st, (const uint32_t*)ki, vin, ko, vo, g,
-                            shift, (const uint32_t*)scratch, (const uint32_t*)totals);
+      e = (g.tile == (int64_t)RS_THREADS * RS_ITEMS
+               ? launch_serialised(k_rs_downsweep<RS_ITEMS>, dim3(grid), dim3(RS_THREADS), 0, st, (const uint32_t*)ki,
+                                   vin, ko, vo, g, shift, (const uint32_t*)scratch, (const uint32_t*)totals)
+               : launch_serialised(k_rs_downsweep<RS_ITEMS_SEG>, dim3(grid), dim3(RS_THREADS), 0, st,
+                                   (const uint32_t*)ki, vin, ko, vo, g, shift, (const uint32_t*)scratch,
+                                   (const uint32_t*)totals));
     count_launches(3);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -690,8 +702,8 @@ cudaError_t radix_sort_pass(cudaStream_t st, int num_sms, const uint32_t* keys_i
   if (e == cudaSuccess)
     e = launch_serialised(k_rs_spine, dim3((RS_RADIX + 7) / 8), dim3(256), 0, st, counts, totals, g.ctas_seg, RS_RADIX);
   if (e == cudaSuccess)
-    e = launch_serialised(k_rs_downsweep, dim3(g.ctas_seg), dim3(RS_THREADS), 0, st, keys_in, vals_in, keys_out,
-                          vals_out, g, shift, (const uint32_t*)counts, (const uint32_t*)totals);
+    e = launch_serialised(k_rs_downsweep<RS_ITEMS>, dim3(g.ctas_seg), dim3(RS_THREADS), 0, st, keys_in, vals_in,
+                          keys_out, vals_out, g, shift, (const uint32_t*)counts, (const uint32_t*)totals);
   count_launches(3);
   if (e == cudaSuccess) e = cudaGetLastError();
   return e;
