@@ -80,12 +80,12 @@ FP32_LANES_PER_SM = 128
 _BLEND_SOURCES = ("paper_2512_20943_b300/csrc/blend_cull.cu", "paper_2512_20943_b300/csrc/airgs_internal.cuh",
                   "paper_2512_20943_b300/csrc/kernels.h")
 NCU_TRAFFIC = {
-    "blend_bwd": {"bytes_per_launch": (640.500736 + 86.741504) * 1e6, "smem_bytes_per_launch": 419024757 * 128,
+    "blend_bwd": {"bytes_per_launch": (657.434624 + 92.624896) * 1e6, "smem_bytes_per_launch": 426793462 * 128,
                   "sources": _BLEND_SOURCES,
-                  "sha256": "157d5c483f84e4b55ad21bae33d37041bb6757cc84ae473774d915b948b5c380"},
-    "blend_fwd": {"bytes_per_launch": (225.171456 + 234.556416) * 1e6, "smem_bytes_per_launch": 82653512 * 128,
+                  "sha256": "fdd0a542b4ce5a2feffd84a9500508dbbbc7878ca6f3d400831609528d5adbd9"},
+    "blend_fwd": {"bytes_per_launch": (225.238272 + 234.169600) * 1e6, "smem_bytes_per_launch": 82653747 * 128,
                   "sources": _BLEND_SOURCES,
-                  "sha256": "157d5c483f84e4b55ad21bae33d37041bb6757cc84ae473774d915b948b5c380"},
+                  "sha256": "fdd0a542b4ce5a2feffd84a9500508dbbbc7878ca6f3d400831609528d5adbd9"},
 }
 
 

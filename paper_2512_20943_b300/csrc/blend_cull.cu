@@ -432,7 +432,7 @@ __device__ __forceinline__ void flush_deferred(float (*s_red)[kRedStride], const
 //   0 mx (x ln2), 1 my (x ln2), 2 A (x -1/2), 3 B (x -1), 4 C (x -1/2),
 //   5 opacity, 6-8 colour, 9 blend weight.
 #ifndef AIRGS_CULL_BWD_MINB
-#define AIRGS_CULL_BWD_MINB 24  // 80 registers: 24 warps per SM (measured best of 1, 20-32)
+#define AIRGS_CULL_BWD_MINB 28  // 72 registers: 28 warps per SM (measured best of 20, 24, 26, 28, 30, 32)
 #endif
 template <int NG, bool L1, bool IMP, bool COMPACT>
 __global__ void __launch_bounds__(32, COMPACT ? AIRGS_CULL_BWD_MINB : 1) k_blend_bwd_cull(BlendArgs a, BwdIn in) {
