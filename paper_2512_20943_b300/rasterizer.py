@@ -33,7 +33,8 @@ class RasterConfig:
     T_min: float = 1e-4
     bg: tuple = (0.0, 0.0, 0.0)
     blend_variant: int = -1  # -1: autotuned choice (default variant until tuned)
-    sort_mode: int = -1      # -1/0: global radix ordering; 1: per-tile ordering when lists fit a CTA
+    sort_mode: int = -1      # 0: global radix ordering; 1: per-tile ordering when lists fit a CTA; -1: per-tile for
+                             # batches of at most 65536 (view, Gaussian) pairs, radix above
     autotune_cache: str | None = None
     cull_lists: bool = True  # unobservable lists (no saved state, no n_contrib) hold only live tiles
 
