@@ -666,10 +666,11 @@ def run_serving(args, device):
     frames = FrameStream(maps, lo, hi, period_s=1.0 / 30.0)
     stream = synthetic.serving_requests(n_viewers=64, rate_hz=30.0, duration_s=args.serve_seconds, seed=4)
     budget = 24 * view_bytes(n, dict(width=1920, height=1080))
-    # warm-up: a few batches so that pools and kernels are ready
-    warm = make_requests([(0.0, 0, c) for _, _, c in stream[:16]])
-    ServingEngine(anchor, frames, budget, max_batch_views=64).run(warm, realtime=False)
+    # warm-up of the engine that then serves (as a server warms up before it
+    # takes traffic): a few batches so that its memory pools and kernels are ready
     eng = ServingEngine(anchor, frames, budget, max_batch_views=64)
+    warm = make_requests([(0.0, 0, c) for _, _, c in stream[:16]])
+    eng.run(warm, realtime=False)
     st_eng = eng.run(make_requests(stream), realtime=True)
     st_plain = run_plain_loop(anchor, frames, make_requests(stream), realtime=True)
     keep = ("n_requests", "completed", "rejected", "p50_ms", "p99_ms", "mean_ms", "views_per_s", "mpix_per_s",
