@@ -29,12 +29,12 @@ def window_loss(cams, windows, ref, seed):
     return out
 
 
-def check_windows(rgb_views, ref, windows):
+def check_windows(rgb_views, ref, windows, min_unflagged=0.95):
     for v, (x0, y0, x1, y1) in enumerate(windows):
         if x1 <= x0:
             continue
         ok = ~ref["ambig"][v][y0:y1, x0:x1]
-        assert ok.mean() > 0.95, v
+        assert ok.mean() > min_unflagged, v
         err = np.abs(rgb_views[v][:, y0:y1, x0:x1] - ref["rgb"][v][:, y0:y1, x0:x1])[:, ok].max()
         assert err < RGB_ATOL, (v, err)
 
@@ -93,6 +93,46 @@ def test_streaming_training_batch_full_size():
     run_case(rast, frame, cams, windows, seed=1)
 
 
+def test_streaming_step_fused_l1_full_size():
+    """The benchmark's step exactly as it runs (context anchor and frame state,
+    frame 0 decoded with mode PREV, 8 views at 1352x1014 rendered with saved
+    state, fused L1 backward with importance): the fused gradients equal the
+    explicit-gradient backward (which the oracle checks on windows above) up to
+    the order of the atomic additions; the loss is the mean absolute error of
+    the rendered images; the backward's blended-pair counts equal the forward's."""
+    from paper_2512_20943_b300 import AIRGS_DELTA_PREV, Rasterizer
+    g, arc = synthetic.streaming_scene()
+    cams = synthetic.streaming_views(arc, 0)
+    rast = Rasterizer()
+    rast.set_anchor(*params(to_cuda(g)))
+    m, lo, hi = synthetic.update_map(300_000, 1000, size=768)
+    rast.apply_frame_update(torch.from_numpy(m.view(np.int16)).cuda().view(torch.uint16), lo, hi,
+                            mode=AIRGS_DELTA_PREV, frame_id=0)
+    target = torch.from_numpy(np.concatenate([x.reshape(-1) for x in synthetic.target_images(cams, 1)])).cuda()
+    n = g["means"].shape[0]
+    res = rast.render(cams, importance=True, save=True)
+    iw, ic = torch.zeros(n, device="cuda"), torch.zeros(n, dtype=torch.int32, device="cuda")
+    loss, gr = rast.render_backward_l1(res.state, target, importance=(iw, ic))
+    dL = (torch.sign(res.rgb - target) / res.rgb.numel()).contiguous()
+    iw2, ic2 = torch.zeros_like(iw), torch.zeros_like(ic)
+    gr2 = rast.render_backward(res.state, dL, importance=(iw2, ic2))
+    torch.cuda.synchronize()
+    ref_loss = float(torch.abs(res.rgb.double() - target.double()).mean())
+    assert abs(float(loss) - ref_loss) <= 1e-5 * ref_loss
+    # two replays sum the same terms in different atomic orders: 1e-5 of the
+    # norm was exceeded (log-scale gradients cancel), so 1e-4, ten times inside
+    # the parity bar; elementwise the parity bar itself
+    for k in gr:
+        a, b = gr[k].double(), gr2[k].double()
+        assert float(torch.linalg.norm(a - b)) <= 1e-4 * float(torch.linalg.norm(b)), k
+        assert float((a - b).abs().max()) <= 1e-3 * float(b.abs().max()), k
+    assert torch.equal(ic, ic2) and torch.equal(ic, res.importance_cnt)
+    assert int(ic.sum()) > 0
+    torch.testing.assert_close(iw, iw2, rtol=1e-5, atol=1e-6)
+    torch.testing.assert_close(iw, res.importance_w, rtol=1e-5, atol=1e-6)
+    res.state.release()
+
+
 def test_per_frame_training_20_views_full_size():
     """200k Gaussians SH3, 20 views at 1352x1014 in one launch."""
     from paper_2512_20943_b300 import Rasterizer
@@ -125,3 +165,44 @@ def test_large_scene_16_views_4k_full_size():
     assert torch.equal(ic, res.importance_cnt)
     assert int(ic.sum()) > 0
     res.state.release()
+
+
+def test_serving_batch_full_size_culled_lists():
+    """500k-Gaussian SH3 serving scene with a streamed frame update applied, one
+    batch of three requests at 640x480, 1280x720 and 1920x1080 rendered the way
+    the serving engine renders them (caller-owned frame state, no saved state,
+    hence the culled lists): windows vs the oracle, which blends the full lists."""
+    from paper_2512_20943_b300 import Rasterizer
+    n = 500_000
+    g = synthetic.serving_scene(n)
+    upd = Rasterizer()
+    upd.set_anchor(*params(to_cuda(g)))
+    m, lo, hi = synthetic.update_map(n, 2000, size=768)
+    upd.apply_frame_update(torch.from_numpy(m.view(np.int16)).cuda().view(torch.uint16), lo, hi)
+    means_d, quats_d = upd.frame_state()
+    t = to_cuda(g)
+    t["means"], t["quats"] = means_d.clone(), quats_d.clone()
+    frame = dict(g, means=means_d.cpu().numpy(), quats=quats_d.cpu().numpy())
+    cams, seen = [], set()
+    for _, _, c in synthetic.serving_requests(n_viewers=64, rate_hz=30.0, duration_s=0.5, seed=4):
+        key = (int(c["width"]), int(c["height"]))
+        if key not in seen:
+            seen.add(key)
+            cams.append(c)
+    assert sorted(seen) == sorted(synthetic.SERVING_SIZES)
+    res = Rasterizer().render_gaussians(*params(t), cams, T=True)
+    torch.cuda.synchronize()
+    # per view, a window at the centre, where the scene is densest, and one at the
+    # bottom-right corner (1080 rows end in a ragged half tile row); the oracle
+    # takes each view twice, once per window
+    windows = [(c["width"] // 2 - 32, c["height"] // 2 - 32, c["width"] // 2 + 32, c["height"] // 2 + 32)
+               for c in cams]
+    windows += [(c["width"] - 64, c["height"] - 64, c["width"], c["height"]) for c in cams]
+    ref = oracle.render(synthetic.widen(frame), cams + cams, windows=windows)
+    rgb, Tv = views_np(res.rgb, cams), views_np(res.T, cams, 1)
+    # hundreds of Gaussians deep at 500k, more pixels hold a pair the oracle flags
+    # as within rounding of a threshold (up to 12 % of a window)
+    check_windows(rgb + rgb, ref, windows, min_unflagged=0.8)
+    for v, (x0, y0, x1, y1) in enumerate(windows):
+        ok = ~ref["ambig"][v][y0:y1, x0:x1]
+        assert np.abs(Tv[v % 3][y0:y1, x0:x1] - ref["T"][v][y0:y1, x0:x1])[ok].max() < RGB_ATOL
