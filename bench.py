@@ -17,10 +17,13 @@ Prints one JSON line (rank 0).  Under torchrun every rank runs an independent
 replica of the workload (the path has no data-path exchange here); the time is
 the max over ranks and the value the pixels of all ranks over that time.
 
-Besides the contract's keys the line carries: `stages` (each stage's CUDA-event
-time per launch and share, achieved GB/s of the HBM-bound stages); `roofline`
-for the dominant kernel (algorithmic TFLOP/s against the derived FP32 peak and
-the library's FFMA probe; `roofline.smem`: shared-memory TB/s against SMs x 128
+Inside the timed region only the two blend stages are bracketed by CUDA events
+(their live times give the roofline); a second pass of a few steps with every
+stage bracketed gives the breakdown.  Besides the contract's keys the line
+carries: `stages` (from that pass: each stage's CUDA-event time per launch and
+share, achieved GB/s of the HBM-bound stages; the blend stages also with their
+timed-region times); `roofline` for the dominant kernel (algorithmic TFLOP/s
+against the derived FP32 peak and the library's FFMA probe; `roofline.smem`: shared-memory TB/s against SMs x 128
 B/clock and the library's LDS probe; DRAM traffic and shared-memory bytes come
 from a committed ncu capture and are null once the kernel's sources change);
 `e2e` (the same steps fed from pinned host buffers through the double-buffered
@@ -79,6 +82,8 @@ FP32_LANES_PER_SM = 128
 # was built from: once those change the counters no longer describe it (null).
 _BLEND_SOURCES = ("paper_2512_20943_b300/csrc/blend_cull.cu", "paper_2512_20943_b300/csrc/airgs_internal.cuh",
                   "paper_2512_20943_b300/csrc/kernels.h")
+PROFILE_STEPS = 10  # steps of the per-stage profiling pass after the timed region
+
 NCU_TRAFFIC = {
     "blend_bwd": {"bytes_per_launch": (657.434624 + 92.624896) * 1e6, "smem_bytes_per_launch": 426793462 * 128,
                   "sources": _BLEND_SOURCES,
@@ -363,23 +368,26 @@ def run_ours(args):
         with torch.cuda.stream(stream):
             rast.autotune(wl.views(0)[1])
 
-    # warm-up
+    # clock sampling starts first (nvidia-smi takes a moment), then the warm-up
+    # steps, so that the timed region follows busy steps instead of an idle pause
+    sampler = ClockSampler(device.index)
+    sampler.start()
+    time.sleep(0.3)
     with torch.cuda.stream(stream):
         for t in range(args.warmup):
             train_step(rast, wl, t, (imp_w, imp_c))
     stream.synchronize()
 
-    # timed region: per-step CUDA events on the library's stream
+    # timed region: per-step CUDA events on the library's stream; inside it only
+    # the two blend stages carry events (the dominant kernels' live times for the
+    # roofline), the per-stage breakdown comes from a second pass below
     blended0 = int(imp_c.sum(dtype=torch.int64))
-    rast.set_profiling(True)
+    rast.set_profiling(True, blend_only=True)
     rast.stage_times()  # clear
-    sampler = ClockSampler(device.index)
     launches0 = Rasterizer.kernel_launch_count()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    sampler.start()
-    time.sleep(0.3)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     wall0 = time.perf_counter()
     with torch.cuda.stream(stream):
@@ -394,9 +402,17 @@ def run_ours(args):
         torch.distributed.barrier()
     clocks = sampler.stop()
     launches = Rasterizer.kernel_launch_count() - launches0
+    timed = rast.stage_times()
+    blended = (int(imp_c.sum(dtype=torch.int64)) - blended0) / args.steps  # blended pairs per step
+    # per-stage breakdown: the same frames again with every stage bracketed
+    n_prof = min(args.steps, PROFILE_STEPS)
+    rast.set_profiling(True)
+    rast.stage_times()
+    with torch.cuda.stream(stream):
+        for k in range(n_prof):
+            train_step(rast, wl, args.warmup + k, (imp_w, imp_c))
     stages = rast.stage_times()
     rast.set_profiling(False)
-    blended = (int(imp_c.sum(dtype=torch.int64)) - blended0) / args.steps  # blended pairs per step
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     total_ms = barrier_max(world, total_ms, device)
@@ -420,33 +436,35 @@ def run_ours(args):
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
     n_sms = torch.cuda.get_device_properties(device).multi_processor_count
     fp32_peak = n_sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FMA = 2 flops
-    ms = stages["ms"]
-    nl = stages["launches"]
+    ms, nl = stages["ms"], stages["launches"]          # every stage, the profiling pass
+    ms_t, nl_t = timed["ms"], timed["launches"]        # the blend stages, the timed region
     dom = max(ms, key=lambda k: ms[k])
     stage_lines = {}
     for name in ms:
         if nl[name] == 0:
             continue
-        stage_lines[name] = {"ms_per_launch": ms[name] / nl[name], "launches": nl[name],
+        stage_lines[name] = {"ms_per_launch": ms[name] / nl[name], "launches_per_step": nl[name] / n_prof,
                              "share": ms[name] / max(1e-9, sum(ms.values()))}
+        if nl_t[name]:
+            stage_lines[name]["ms_per_launch_timed_region"] = ms_t[name] / nl_t[name]
     # Blend work (algorithmic): the definition's pairs (list entries up to each
     # pixel's termination, counted by the kernels) times the test flops, plus the
     # blended pairs (the importance counts) times the blend flops.  The culling
     # variants decide most definition pairs per 8x4 block without per-pair
     # arithmetic; the lane evaluations they do issue are reported beside.
-    def rate(flops, name):
-        return flops / (ms[name] / 1e3) / 1e12 if ms[name] else 0.0
-    alg = {"blend_fwd": stages["pairs_forward"] * FLOPS_TEST + blended * args.steps * FLOPS_BLEND_FWD,
-           "blend_bwd": stages["pairs_backward"] * FLOPS_TEST + blended * args.steps * FLOPS_BLEND_BWD}
-    issued = {"blend_fwd": stages["issued_forward"] * FLOPS_ISSUED_FWD,
-              "blend_bwd": stages["issued_backward"] * FLOPS_ISSUED_BWD}
+    def rate(flops, name):  # over the blend stage's live event time in the timed region
+        return flops / (ms_t[name] / 1e3) / 1e12 if ms_t[name] else 0.0
+    alg = {"blend_fwd": timed["pairs_forward"] * FLOPS_TEST + blended * args.steps * FLOPS_BLEND_FWD,
+           "blend_bwd": timed["pairs_backward"] * FLOPS_TEST + blended * args.steps * FLOPS_BLEND_BWD}
+    issued = {"blend_fwd": timed["issued_forward"] * FLOPS_ISSUED_FWD,
+              "blend_bwd": timed["issued_backward"] * FLOPS_ISSUED_BWD}
     for name, key in (("blend_fwd", "forward"), ("blend_bwd", "backward")):
         if name in stage_lines:
-            n_l = max(1, nl[name])
+            n_l = max(1, nl_t[name])
             stage_lines[name]["tflops_algorithmic"] = rate(alg[name], name)
             stage_lines[name]["tflops_issued_lanes"] = rate(issued[name], name)
-            stage_lines[name]["definition_pairs_per_launch"] = stages["pairs_" + key] / n_l
-            stage_lines[name]["issued_evals_per_launch"] = stages["issued_" + key] / n_l
+            stage_lines[name]["definition_pairs_per_launch"] = timed["pairs_" + key] / n_l
+            stage_lines[name]["issued_evals_per_launch"] = timed["issued_" + key] / n_l
             stage_lines[name]["blended_pairs_per_launch"] = blended * args.steps / n_l
     add_stage_bandwidths(stage_lines, ms, nl, N_GAUSS, VIEWS_PER_STEP, probe["n_instances"],
                          bits_for_tiles(VIEWS_PER_STEP * math.ceil(WIDTH / 16) * math.ceil(HEIGHT / 16)))
@@ -470,7 +488,7 @@ def run_ours(args):
         # ncu capture (wavefronts x 128 B) over the live CUDA-event time of a launch
         smem_bytes = dominant_smem_bytes(dom)
         smem_peak = n_sms * 128 * sm_max * 1e6 / 1e12
-        smem_tbs = smem_bytes / (ms[dom] / max(1, nl[dom]) / 1e3) / 1e12 if smem_bytes else None
+        smem_tbs = smem_bytes / (ms_t[dom] / max(1, nl_t[dom]) / 1e3) / 1e12 if smem_bytes else None
         roof["smem"] = {"achieved": smem_tbs, "unit": "TB/s", "peak": smem_peak,
                         "peak_source": f"derived: {n_sms} SMs x 128 B/clock x {sm_max:.0f} MHz",
                         "frac": smem_tbs / smem_peak if smem_tbs else None,
@@ -499,12 +517,14 @@ def run_ours(args):
         "clocks": clocks,
         "roofline": roof,
         "stages": stage_lines,
+        "stages_pass": f"{n_prof} further steps of the same frames with every stage bracketed by CUDA events "
+                       "(inside the timed region only the blend stages are)",
         "blend_variant": probe["variant"],
         "instances_per_step": probe["n_instances"],
-        "pairs_per_step": {"blended": blended, "forward": stages["pairs_forward"] / args.steps,
-                           "backward": stages["pairs_backward"] / args.steps,
-                           "issued_forward": stages["issued_forward"] / args.steps,
-                           "issued_backward": stages["issued_backward"] / args.steps},
+        "pairs_per_step": {"blended": blended, "forward": timed["pairs_forward"] / args.steps,
+                           "backward": timed["pairs_backward"] / args.steps,
+                           "issued_forward": timed["issued_forward"] / args.steps,
+                           "issued_backward": timed["issued_backward"] / args.steps},
     }
     if e2e is not None:
         line["e2e"] = e2e
@@ -573,20 +593,22 @@ def run_config(args):
             rast.render_backward_l1(res.state, target, importance=imp)
             res.state.release()
 
+    # as in the streaming step: sampling first, warm-up, a timed region whose only
+    # events bracket the blend stages, then a per-stage profiling pass
+    sampler = ClockSampler(device.index)
+    sampler.start()
+    time.sleep(0.3)
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             step()
     stream.synchronize()
     blended0 = int(imp[1].sum(dtype=torch.int64)) if imp is not None else 0
-    rast.set_profiling(True)
+    rast.set_profiling(True, blend_only=True)
     rast.stage_times()
-    sampler = ClockSampler(device.index)
     launches0 = Rasterizer.kernel_launch_count()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    sampler.start()
-    time.sleep(0.3)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with torch.cuda.stream(stream):
         for k in range(args.steps):
@@ -597,14 +619,26 @@ def run_config(args):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     launches = Rasterizer.kernel_launch_count() - launches0
+    timed = rast.stage_times()
+    blended = (int(imp[1].sum(dtype=torch.int64)) - blended0) / args.steps if imp is not None else None
+    n_prof = min(args.steps, PROFILE_STEPS)
+    rast.set_profiling(True)
+    rast.stage_times()
+    with torch.cuda.stream(stream):
+        for _ in range(n_prof):
+            step()
     stages = rast.stage_times()
     rast.set_profiling(False)
     total_ms = barrier_max(world, sum(a.elapsed_time(b) for a, b in ev), device)
     px = sum(int(c["width"]) * int(c["height"]) for c in cams)
     value = whole_job_value(world, px, args.steps, total_ms)
     ms, nl = stages["ms"], stages["launches"]
-    stage_lines = {name: {"ms_per_launch": ms[name] / nl[name], "launches": nl[name],
+    ms_t, nl_t = timed["ms"], timed["launches"]
+    stage_lines = {name: {"ms_per_launch": ms[name] / nl[name], "launches_per_step": nl[name] / n_prof,
                           "share": ms[name] / max(1e-9, sum(ms.values()))} for name in ms if nl[name]}
+    for name in stage_lines:
+        if nl_t[name]:
+            stage_lines[name]["ms_per_launch_timed_region"] = ms_t[name] / nl_t[name]
     with torch.cuda.stream(stream):
         res = rast.render_gaussians(*p, cams, save=True)
         st = rast.stats(res.state)
@@ -623,18 +657,19 @@ def run_config(args):
         "config": {"workload": WORKLOADS[kind], "global_batch": len(cams) * world, "seq_len": px // len(cams),
                    "parallelism": f"replicas x{world}" if world > 1 else "none"},
         "gpu_launches": launches, "clocks": clocks, "stages": stage_lines,
+        "stages_pass": f"{n_prof} further steps with every stage bracketed by CUDA events (inside the timed "
+                       "region only the blend stages are)",
         "blend_variant": Rasterizer.variant_names()[st["blend_variant"]], "instances_per_step": st["n_instances"],
     }
-    blended = (int(imp[1].sum(dtype=torch.int64)) - blended0) / args.steps if imp is not None else None
     for name, key, fl in (("blend_fwd", "forward", FLOPS_BLEND_FWD), ("blend_bwd", "backward", FLOPS_BLEND_BWD)):
-        if name in stage_lines and blended is not None:
-            flops = stages["pairs_" + key] * FLOPS_TEST + blended * args.steps * fl
-            t_s = ms[name] / 1e3
+        if name in stage_lines and blended is not None and ms_t[name]:
+            flops = timed["pairs_" + key] * FLOPS_TEST + blended * args.steps * fl
+            t_s = ms_t[name] / 1e3  # the blend stage's live event time in the timed region
             stage_lines[name]["tflops_algorithmic"] = flops / t_s / 1e12
             stage_lines[name]["frac_fp32_peak"] = flops / t_s / 1e12 / fp32_peak
         if name in stage_lines:
-            stage_lines[name]["definition_pairs_per_launch"] = stages["pairs_" + key] / max(1, nl[name])
-            stage_lines[name]["issued_evals_per_launch"] = stages["issued_" + key] / max(1, nl[name])
+            stage_lines[name]["definition_pairs_per_launch"] = timed["pairs_" + key] / max(1, nl_t[name])
+            stage_lines[name]["issued_evals_per_launch"] = timed["issued_" + key] / max(1, nl_t[name])
     if backward and "tflops_algorithmic" in stage_lines.get("blend_bwd", {}):
         bw = stage_lines["blend_bwd"]
         line["roofline"] = {"bound": "alu", "achieved": bw["tflops_algorithmic"], "peak": fp32_peak, "unit": "TFLOP/s",

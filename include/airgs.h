@@ -320,11 +320,14 @@ int airgs_sort_pairs_noalloc(const uint32_t* keys_in, const uint32_t* vals_in, u
  * path if set.  Returns the chosen variant in *variant. */
 int airgs_autotune(airgs_ctx* ctx, const airgs_camera* cams, int n_views, int* variant);
 
-/* Per-stage device timing.  With profiling on, each pipeline stage (decode,
- * projection, depth sort, scan+emit, tile sort, ranges, blend forward, blend
- * backward, projection backward) is bracketed by CUDA events on the context's
- * stream, and the blend kernels also add their evaluated pairs to a context
- * counter.  airgs_stage_times synchronises, writes the summed milliseconds and
+/* Per-stage device timing.  With profiling level AIRGS_PROFILE_ALL, each
+ * pipeline stage (decode, projection, depth sort, scan+emit, tile sort, ranges,
+ * blend forward, blend backward, projection backward) is bracketed by CUDA
+ * events on the context's stream; with AIRGS_PROFILE_BLEND only the two blend
+ * stages are (two event pairs per training step instead of nine, so the rest of
+ * the pipeline runs as it does unprofiled); with either level the blend kernels
+ * also add their evaluated pairs to a context counter.  airgs_set_profiling
+ * returns AIRGS_E_ARG for any other level than the three below.  airgs_stage_times synchronises, writes the summed milliseconds and
  * the number of timed launches of each stage since the previous readout into
  * ms[AIRGS_NUM_STAGES] / launches[AIRGS_NUM_STAGES], and into pairs[4] (each
  * nullable) the forward and backward pair totals of the definition (list
@@ -332,6 +335,9 @@ int airgs_autotune(airgs_ctx* ctx, const airgs_camera* cams, int n_views, int* v
  * backward lane evaluations the culling kernels actually issued (0 for
  * variants that do not count them); then clears them. */
 #define AIRGS_NUM_STAGES 9
+#define AIRGS_PROFILE_OFF 0
+#define AIRGS_PROFILE_ALL 1
+#define AIRGS_PROFILE_BLEND 2
 int airgs_set_profiling(airgs_ctx* ctx, int enabled);
 int airgs_stage_times(airgs_ctx* ctx, double* ms, int64_t* launches, int64_t* pairs);
 const char* airgs_stage_name(int stage);

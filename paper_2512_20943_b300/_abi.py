@@ -26,8 +26,12 @@ ERROR_NAMES = {
 AIRGS_DELTA_PREV = 0
 AIRGS_DELTA_ANCHOR = 1
 AIRGS_QUAT_ADD = 2
+AIRGS_UPDATE_CHANNELS = 7
 AIRGS_MAX_VIEWS = 256
 AIRGS_NUM_STAGES = 9
+AIRGS_PROFILE_OFF = 0
+AIRGS_PROFILE_ALL = 1
+AIRGS_PROFILE_BLEND = 2
 AIRGS_NOALLOC_SORT_MAX_PAIRS = 1 << 20
 
 

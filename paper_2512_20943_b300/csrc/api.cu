@@ -57,7 +57,7 @@ struct airgs_ctx {
   std::string last_error;
   std::map<std::string, int> tuned;  // autotune choices
   // profiling: (stage, start, end) event triples awaiting readout
-  bool profiling = false;
+  int profiling = AIRGS_PROFILE_OFF;
   unsigned long long* d_pair_total = nullptr;  // [4] forward, backward pairs; forward, backward issued evaluations
   std::vector<cudaEvent_t> event_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
@@ -222,13 +222,14 @@ struct StageScope {
   int stage;
   cudaEvent_t e0 = nullptr;
   StageScope(airgs_ctx* c, int s) : ctx(c), stage(s) {
-    if (ctx->profiling) {
+    if (ctx->profiling == AIRGS_PROFILE_ALL ||
+        (ctx->profiling == AIRGS_PROFILE_BLEND && (s == ST_BLEND_FWD || s == ST_BLEND_BWD))) {
       e0 = take_event(ctx);
       cudaEventRecord(e0, ctx->stream);
     }
   }
   ~StageScope() {
-    if (ctx->profiling && e0) {
+    if (e0) {
       cudaEvent_t e1 = take_event(ctx);
       cudaEventRecord(e1, ctx->stream);
       ctx->pending.push_back({stage, {e0, e1}});
@@ -1082,12 +1083,15 @@ int airgs_l3dgs_loss(airgs_ctx* ctx, const airgs_camera* cams, int n_views, cons
 
 int airgs_set_profiling(airgs_ctx* ctx, int enabled) {
   if (!ctx) return AIRGS_E_ARG;
+  if (enabled != AIRGS_PROFILE_OFF && enabled != AIRGS_PROFILE_ALL && enabled != AIRGS_PROFILE_BLEND)
+    return fail(ctx, AIRGS_E_ARG, "profiling level %d: expected 0 (off), 1 (every stage) or 2 (blend stages)",
+                enabled);
   if (enabled && !ctx->d_pair_total) {
     int rc = dalloc(ctx, &ctx->d_pair_total, 4);
     if (rc) return rc;
     CK(cudaMemsetAsync(ctx->d_pair_total, 0, 4 * sizeof(unsigned long long), ctx->stream));
   }
-  ctx->profiling = enabled != 0;
+  ctx->profiling = enabled;
   return AIRGS_OK;
 }
 

@@ -429,9 +429,12 @@ class Rasterizer:
         self._check(self.lib.airgs_autotune(self.ctx, camera_array(cams), len(cams), ctypes.byref(v)))
         return v.value
 
-    def set_profiling(self, enabled: bool = True):
-        """Time each pipeline stage with CUDA events on the context's stream."""
-        self._check(self.lib.airgs_set_profiling(self.ctx, 1 if enabled else 0))
+    def set_profiling(self, enabled: bool = True, blend_only: bool = False):
+        """Time each pipeline stage with CUDA events on the context's stream
+        (blend_only: only the blend forward and backward stages)."""
+        level = (_abi.AIRGS_PROFILE_BLEND if blend_only else _abi.AIRGS_PROFILE_ALL) if enabled else \
+            _abi.AIRGS_PROFILE_OFF
+        self._check(self.lib.airgs_set_profiling(self.ctx, level))
 
     def stage_times(self) -> dict:
         """Per-stage device milliseconds and launch counts since the previous

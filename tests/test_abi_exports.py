@@ -36,6 +36,16 @@ def test_binding_declares_the_header(lib_path):
     _abi.load_library()  # resolves every symbol with its signature
 
 
+def test_binding_constants_equal_the_header():
+    """Every integer constant the header defines has the same value in the binding."""
+    from paper_2512_20943_b300 import _abi
+    text = open(os.path.join(ROOT, "include", "airgs.h")).read()
+    consts = dict(re.findall(r"#define\s+(AIRGS_[A-Z0-9_]+)\s+(\(?-?[0-9][0-9 <()-]*\)?)", text))
+    assert {"AIRGS_E_ARG", "AIRGS_PROFILE_BLEND", "AIRGS_MAX_VIEWS"} <= set(consts)
+    for name, expr in consts.items():
+        assert getattr(_abi, name) == eval(expr, {}), name  # plain integer literals and shifts only
+
+
 def test_variant_table_without_gpu(lib_path):
     from paper_2512_20943_b300 import _abi
     lib = _abi.load_library()

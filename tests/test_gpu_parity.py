@@ -605,3 +605,38 @@ def test_small_batch_default_ordering_equals_radix(variant):
         assert_grad_close(ga[k].cpu().numpy(), gb[k].cpu().numpy(), k)
     a.state.release()
     b.state.release()
+
+
+def test_profiling_levels():
+    """Level 1 brackets every stage, level 2 (the benchmark's timed region) only
+    the two blend stages; both count the blend kernels' pairs; off times
+    nothing; any other level is an argument error."""
+    from paper_2512_20943_b300 import AirGSError, RasterConfig, Rasterizer
+    rast = Rasterizer(RasterConfig(sort_mode=0))
+    g, cams = small_sh3_scene()
+    t = to_cuda(g)
+
+    def step():
+        res = rast.render_gaussians(*params(t), cams, save=True)
+        rast.render_backward(res.state, torch.ones_like(res.rgb))
+        res.state.release()
+        return rast.stage_times()
+
+    for level in ("all", "blend"):
+        rast.set_profiling(True, blend_only=level == "blend")
+        rast.stage_times()
+        st = step()
+        timed = {k for k, v in st["launches"].items() if v}
+        if level == "blend":
+            assert timed == {"blend_fwd", "blend_bwd"}
+        else:
+            assert {"project_sh", "depth_sort", "scan_emit", "tile_sort", "blend_fwd", "blend_bwd",
+                    "project_bwd"} <= timed
+        assert all(st["ms"][k] > 0 for k in timed)
+        assert st["pairs_forward"] > 0 and st["pairs_backward"] > 0
+    rast.set_profiling(False)
+    rast.stage_times()
+    st = step()
+    assert not any(st["launches"].values()) and st["pairs_forward"] == 0
+    with pytest.raises(AirGSError):
+        rast._check(rast.lib.airgs_set_profiling(rast.ctx, 3))
