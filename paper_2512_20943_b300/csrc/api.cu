@@ -54,6 +54,11 @@ struct airgs_ctx {
   float *c_means = nullptr, *c_quats = nullptr;
   int64_t frame_id = -1;
   uint64_t* h_pinned = nullptr;  // small pinned host buffer for counters
+  // pinned staging of the cameras a render uploads (two slots, each reused once
+  // the copy out of it has run: a copy from pinned memory is a plain DMA)
+  CamDev* h_cam_ring = nullptr;  // [2][AIRGS_MAX_VIEWS]
+  cudaEvent_t cam_copied[2] = {nullptr, nullptr};
+  int cam_slot = 0;
   std::string last_error;
   std::map<std::string, int> tuned;  // autotune choices
   // profiling: (stage, start, end) event triples awaiting readout
@@ -76,8 +81,10 @@ struct airgs_state {
   int32_t* ncontrib = nullptr; // [pixels]
   uint2* hl = nullptr;         // half-tile lists (variant with half-tile warps), nullable
   uint2* hranges = nullptr;    // [2][tiles]
-  int* work = nullptr;         // [2] work counters (forward, backward)
-  unsigned long long* pairs = nullptr;  // [2] pair counters (forward, backward)
+  // [4] device counters, 8 bytes each: forward pairs, forward work queue,
+  // backward pairs, backward work queue (int in the low half); the backward's
+  // two are adjacent, so one memset resets them
+  unsigned long long* counters = nullptr;
   const float* rgb = nullptr;  // caller's forward output
   int64_t n_inst = 0, n_tiles = 0, n_pixels = 0;
   int variant = 0;
@@ -296,11 +303,17 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
   ALLOC(s->proj, V * N);
   ALLOC(s->ranges, s->n_tiles);
   ALLOC(s->ncontrib, s->n_pixels);
-  ALLOC(s->work, 2);
-  ALLOC(s->pairs, 2);
-  CK(cudaMemcpyAsync(s->d_cams, s->h_cams.data(), V * sizeof(CamDev), cudaMemcpyHostToDevice, st));
-  CK(cudaMemsetAsync(s->work, 0, 2 * sizeof(int), st));
-  CK(cudaMemsetAsync(s->pairs, 0, 2 * sizeof(unsigned long long), st));
+  ALLOC(s->counters, 4);
+  {
+    const int slot = ctx->cam_slot;
+    CK(cudaEventSynchronize(ctx->cam_copied[slot]));  // the slot's previous copy (complete unless just enqueued)
+    CamDev* staged = ctx->h_cam_ring + (size_t)slot * AIRGS_MAX_VIEWS;
+    std::copy(s->h_cams.begin(), s->h_cams.end(), staged);
+    CK(cudaMemcpyAsync(s->d_cams, staged, V * sizeof(CamDev), cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(ctx->cam_copied[slot], st));
+    ctx->cam_slot = slot ^ 1;
+  }
+  CK(cudaMemsetAsync(s->counters, 0, 4 * sizeof(unsigned long long), st));
   CK(cudaMemsetAsync(s->ranges, 0, s->n_tiles * sizeof(uint2), st));
   RasterParams rp = raster_params(ctx->cfg);
 
@@ -473,8 +486,8 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
   a.n_views = n_views;
   a.n_tiles = s->n_tiles;
   a.rp = rp;
-  a.work_counter = s->work;
-  a.pair_counter = s->pairs;
+  a.work_counter = reinterpret_cast<int*>(s->counters + 1);
+  a.pair_counter = s->counters;
   a.pair_total = ctx->profiling ? ctx->d_pair_total : nullptr;
   a.exec_total = ctx->profiling ? ctx->d_pair_total + 2 : nullptr;
   a.hl = s->hl;
@@ -524,8 +537,7 @@ int backward_impl(airgs_ctx* ctx, airgs_state* s, const float* dL, const float* 
     ~G() { dfree(c, p); }
   } gguard{ctx, grad};
   CK(cudaMemsetAsync(grad, 0, (size_t)s->n_views * s->n * sizeof(GradRec), st));
-  CK(cudaMemsetAsync(s->work + 1, 0, sizeof(int), st));
-  CK(cudaMemsetAsync(s->pairs + 1, 0, sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(s->counters + 2, 0, 2 * sizeof(unsigned long long), st));
   BlendArgs a;
   a.proj = s->proj;
   a.n = s->n;
@@ -535,8 +547,8 @@ int backward_impl(airgs_ctx* ctx, airgs_state* s, const float* dL, const float* 
   a.n_views = s->n_views;
   a.n_tiles = s->n_tiles;
   a.rp = raster_params(ctx->cfg);
-  a.work_counter = s->work + 1;
-  a.pair_counter = s->pairs + 1;
+  a.work_counter = reinterpret_cast<int*>(s->counters + 3);
+  a.pair_counter = s->counters + 2;
   a.pair_total = ctx->profiling ? ctx->d_pair_total + 1 : nullptr;
   a.exec_total = ctx->profiling ? ctx->d_pair_total + 3 : nullptr;
   a.hl = s->hl;
@@ -652,8 +664,14 @@ int airgs_create(airgs_ctx** out, const airgs_config* cfg, void* stream) {
     e = cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &thr);
   }
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_pinned, 128);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_cam_ring, 2 * AIRGS_MAX_VIEWS * sizeof(CamDev));
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ctx->cam_copied[k], cudaEventDisableTiming);
   if (e != cudaSuccess) {
     cudaGetLastError();
+    for (cudaEvent_t ev : ctx->cam_copied)
+      if (ev) cudaEventDestroy(ev);
+    if (ctx->h_cam_ring) cudaFreeHost(ctx->h_cam_ring);
+    if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     delete ctx;
     return AIRGS_E_CUDA;
@@ -669,6 +687,9 @@ int airgs_destroy(airgs_ctx* ctx) {
   dfree(ctx, ctx->d_pair_total);
   cudaStreamSynchronize(ctx->stream);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+  if (ctx->h_cam_ring) cudaFreeHost(ctx->h_cam_ring);
+  for (cudaEvent_t ev : ctx->cam_copied)
+    if (ev) cudaEventDestroy(ev);
   for (auto& p : ctx->pending) ctx->event_pool.insert(ctx->event_pool.end(), {p.second.first, p.second.second});
   for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
@@ -830,13 +851,14 @@ int airgs_release_state(airgs_ctx* ctx, airgs_state* state) {
 
 int airgs_state_stats(airgs_ctx* ctx, const airgs_state* s, airgs_stats* out) {
   if (!ctx || !s || !out) return AIRGS_E_ARG;
-  CK(cudaMemcpyAsync(ctx->h_pinned, s->pairs, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->h_pinned, s->counters, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                     ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   out->n_instances = s->n_inst;
   out->n_tiles = s->n_tiles;
   out->n_pixels = s->n_pixels;
   out->pairs_forward = (int64_t)ctx->h_pinned[0];
-  out->pairs_backward = (int64_t)ctx->h_pinned[1];
+  out->pairs_backward = (int64_t)ctx->h_pinned[2];
   out->blend_variant = s->variant;
   return AIRGS_OK;
 }

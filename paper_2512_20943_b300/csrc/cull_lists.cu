@@ -167,8 +167,7 @@ cudaError_t launch_half_lists(cudaStream_t st, const uint32_t* keys, const uint3
   uint64_t* st_ = sums;               // [chunks + 1] top
   uint64_t* sb_ = sums + chunks + 1;  // [chunks + 1] bottom
   cudaError_t e = launch_serialised(k_half_sums, dim3((unsigned)chunks), dim3(HL_THREADS), 0, st, h, flags, st_, sb_);
-  if (e == cudaSuccess) e = launch_scan_spans(st, st_, chunks, st_ + chunks);
-  if (e == cudaSuccess) e = launch_scan_spans(st, sb_, chunks, sb_ + chunks);
+  if (e == cudaSuccess) e = launch_scan_spans(st, st_, chunks, st_ + chunks, sb_, sb_ + chunks);
   if (e != cudaSuccess) return e;
   e = launch_serialised(k_half_compact, dim3((unsigned)chunks), dim3(HL_THREADS), 0, st, h, (const uint8_t*)flags,
                         (const uint64_t*)st_, (const uint64_t*)sb_, (uint64_t)n_inst, hl, hranges, n_tiles);

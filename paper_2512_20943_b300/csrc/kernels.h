@@ -44,7 +44,10 @@ cudaError_t radix_sort_pass(cudaStream_t st, int num_sms, const uint32_t* keys_i
 cudaError_t launch_count_gather(cudaStream_t st, int64_t total, int64_t n, const uint32_t* order,
                                 const uint32_t* tiles_touched, uint32_t* counts_sorted, uint64_t* chunk_sums,
                                 int64_t* n_chunks);
-cudaError_t launch_scan_spans(cudaStream_t st, uint64_t* sums, int64_t n_chunks, uint64_t* total_out);
+// Exclusive scan in place of n_chunks sums (and of a second array of the same
+// length when sums2 is given, in the same launch); totals -> total_out(2).
+cudaError_t launch_scan_spans(cudaStream_t st, uint64_t* sums, int64_t n_chunks, uint64_t* total_out,
+                              uint64_t* sums2 = nullptr, uint64_t* total_out2 = nullptr);
 size_t emit_piece_words(int64_t total, int64_t n_inst);
 int64_t emit_chunks(int64_t total);  // depth-order chunks of the count/scan/emit kernels
 cudaError_t launch_emit(cudaStream_t st, int64_t total, int64_t n, const uint32_t* order,

@@ -283,21 +283,32 @@ __global__ void __launch_bounds__(EM_THREADS) k_count_gather(int64_t total, int6
   }
 }
 
-// Exclusive scan of the chunk sums (one CTA); total -> *total_out.
-__global__ void __launch_bounds__(1024) k_scan_spans(uint64_t* sums, int64_t n_chunks, uint64_t* total_out) {
+// Exclusive scan in place of one or two arrays of n_chunks chunk sums, one CTA
+// per array (blockIdx.x picks it); each array's total -> its total pointer.
+// Every thread scans SP_ITEMS consecutive values per round, so a round covers
+// SP_THREADS x SP_ITEMS values and the CTA's serial rounds stay few.
+constexpr int SP_THREADS = 1024;
+constexpr int SP_ITEMS = 8;
+__global__ void __launch_bounds__(SP_THREADS) k_scan_spans(uint64_t* sums0, uint64_t* sums1, int64_t n_chunks,
+                                                          uint64_t* total0, uint64_t* total1) {
   wait_prior_grid();
-  __shared__ uint64_t warp_sums[32];
-  __shared__ uint64_t carry;
-  int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) carry = 0;
-  __syncthreads();
-  for (int64_t base = 0; base < n_chunks; base += 1024) {
-    int64_t idx = base + tid;
-    uint64_t v = idx < n_chunks ? sums[idx] : 0;
-    uint64_t x = v;
+  uint64_t* sums = blockIdx.x ? sums1 : sums0;
+  __shared__ uint64_t warp_sums[SP_THREADS / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint64_t carry = 0;  // the same in every thread
+  for (int64_t base = 0; base < n_chunks; base += (int64_t)SP_THREADS * SP_ITEMS) {
+    const int64_t i0 = base + (int64_t)tid * SP_ITEMS;
+    uint64_t v[SP_ITEMS];
+    uint64_t local = 0;
+#pragma unroll
+    for (int j = 0; j < SP_ITEMS; ++j) {
+      v[j] = i0 + j < n_chunks ? sums[i0 + j] : 0ull;
+      local += v[j];
+    }
+    uint64_t x = local;  // inclusive scan of the thread totals within the warp
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
     }
     if (lane == 31) warp_sums[warp] = x;
@@ -306,19 +317,22 @@ __global__ void __launch_bounds__(1024) k_scan_spans(uint64_t* sums, int64_t n_c
       uint64_t ws = warp_sums[lane];
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        uint64_t y = __shfl_up_sync(0xffffffffu, ws, o);
+        const uint64_t y = __shfl_up_sync(0xffffffffu, ws, o);
         if (lane >= o) ws += y;
       }
-      warp_sums[lane] = ws;
+      warp_sums[lane] = ws;  // inclusive over the warps
     }
     __syncthreads();
-    uint64_t excl = carry + (warp ? warp_sums[warp - 1] : 0) + x - v;
-    if (idx < n_chunks) sums[idx] = excl;
-    __syncthreads();
-    if (tid == 1023) carry = excl + v;
-    __syncthreads();
+    uint64_t run = carry + (warp ? warp_sums[warp - 1] : 0ull) + x - local;
+#pragma unroll
+    for (int j = 0; j < SP_ITEMS; ++j) {
+      if (i0 + j < n_chunks) sums[i0 + j] = run;
+      run += v[j];
+    }
+    carry += warp_sums[SP_THREADS / 32 - 1];
+    __syncthreads();  // warp_sums is rewritten by the next round
   }
-  if (tid == 0) *total_out = carry;
+  if (tid == 0) *(blockIdx.x ? total1 : total0) = carry;
 }
 
 // Pieces of at most EM_PIECE instances per chunk: piece_off[c] = exclusive
@@ -334,19 +348,23 @@ constexpr int EM_STAGE = EM_THREADS * (EM_RUN + 1);            // padded staging
 constexpr size_t EM_SMEM = 3 * EM_CHUNK * sizeof(float4) + EM_CHUNK * sizeof(float2) +
                            (2 * EM_CHUNK + 4) * sizeof(uint32_t) + 2 * EM_STAGE * sizeof(uint32_t);
 
-__global__ void __launch_bounds__(1024) k_emit_pieces(const uint64_t* __restrict__ chunk_offsets, int64_t n_chunks,
-                                                     uint32_t* __restrict__ piece_off) {
+__global__ void __launch_bounds__(SP_THREADS) k_emit_pieces(const uint64_t* __restrict__ chunk_offsets,
+                                                           int64_t n_chunks, uint32_t* __restrict__ piece_off) {
   wait_prior_grid();
-  __shared__ uint32_t warp_sums[32];
-  __shared__ uint32_t carry;
+  __shared__ uint32_t warp_sums[SP_THREADS / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) carry = 0;
-  __syncthreads();
-  for (int64_t base = 0; base < n_chunks; base += 1024) {
-    const int64_t c = base + tid;
-    const uint32_t v =
-        c < n_chunks ? (uint32_t)((chunk_offsets[c + 1] - chunk_offsets[c] + EM_PIECE - 1) / EM_PIECE) : 0u;
-    uint32_t x = v;
+  uint32_t carry = 0;  // the same in every thread
+  for (int64_t base = 0; base < n_chunks; base += (int64_t)SP_THREADS * SP_ITEMS) {
+    const int64_t c0 = base + (int64_t)tid * SP_ITEMS;
+    uint32_t v[SP_ITEMS];
+    uint32_t local = 0;
+#pragma unroll
+    for (int j = 0; j < SP_ITEMS; ++j) {
+      const int64_t c = c0 + j;
+      v[j] = c < n_chunks ? (uint32_t)((chunk_offsets[c + 1] - chunk_offsets[c] + EM_PIECE - 1) / EM_PIECE) : 0u;
+      local += v[j];
+    }
+    uint32_t x = local;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -354,12 +372,23 @@ __global__ void __launch_bounds__(1024) k_emit_pieces(const uint64_t* __restrict
     }
     if (lane == 31) warp_sums[warp] = x;
     __syncthreads();
-    uint32_t wb = 0;
-    for (int w = 0; w < warp; ++w) wb += warp_sums[w];
-    const uint32_t excl = carry + wb + x - v;
-    if (c < n_chunks) piece_off[c] = excl;
+    if (warp == 0) {
+      uint32_t ws = warp_sums[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, ws, o);
+        if (lane >= o) ws += y;
+      }
+      warp_sums[lane] = ws;
+    }
     __syncthreads();
-    if (tid == 1023) carry = excl + v;
+    uint32_t run = carry + (warp ? warp_sums[warp - 1] : 0u) + x - local;
+#pragma unroll
+    for (int j = 0; j < SP_ITEMS; ++j) {
+      if (c0 + j < n_chunks) piece_off[c0 + j] = run;
+      run += v[j];
+    }
+    carry += warp_sums[SP_THREADS / 32 - 1];
     __syncthreads();
   }
   if (tid == 0) piece_off[n_chunks] = carry;
@@ -720,8 +749,10 @@ cudaError_t launch_count_gather(cudaStream_t st, int64_t total, int64_t n, const
   return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
-cudaError_t launch_scan_spans(cudaStream_t st, uint64_t* sums, int64_t n_chunks, uint64_t* total_out) {
-  cudaError_t e = launch_serialised(k_scan_spans, dim3(1), dim3(1024), 0, st, sums, n_chunks, total_out);
+cudaError_t launch_scan_spans(cudaStream_t st, uint64_t* sums, int64_t n_chunks, uint64_t* total_out,
+                              uint64_t* sums2, uint64_t* total_out2) {
+  cudaError_t e = launch_serialised(k_scan_spans, dim3(sums2 ? 2 : 1), dim3(SP_THREADS), 0, st, sums, sums2, n_chunks,
+                                    total_out, total_out2);
   count_launches(1);
   return e == cudaSuccess ? cudaGetLastError() : e;
 }
@@ -741,7 +772,8 @@ cudaError_t launch_emit(cudaStream_t st, int64_t total, int64_t n, const uint32_
   // sum over chunks of ceil(count / EM_PIECE) <= n_inst / EM_PIECE + n_chunks; surplus CTAs return at once
   const int64_t grid = n_chunks + n_inst / EM_PIECE + 1;
   uint32_t* piece_chunk = piece_off + n_chunks + 1;
-  cudaError_t e = launch_serialised(k_emit_pieces, dim3(1), dim3(1024), 0, st, chunk_offsets, n_chunks, piece_off);
+  cudaError_t e = launch_serialised(k_emit_pieces, dim3(1), dim3(SP_THREADS), 0, st, chunk_offsets, n_chunks,
+                                    piece_off);
   if (e == cudaSuccess)
     e = launch_serialised(k_emit_piece_map, dim3((unsigned)((n_chunks + 255) / 256)), dim3(256), 0, st,
                           (const uint32_t*)piece_off, n_chunks, piece_chunk);
