@@ -59,6 +59,7 @@ struct airgs_ctx {
   CamDev* h_cam_ring = nullptr;  // [2][AIRGS_MAX_VIEWS]
   cudaEvent_t cam_copied[2] = {nullptr, nullptr};
   int cam_slot = 0;
+  cudaEvent_t count_ready = nullptr;  // the instance count has reached h_pinned
   std::string last_error;
   std::map<std::string, int> tuned;  // autotune choices
   // profiling: (stage, start, end) event triples awaiting readout
@@ -81,6 +82,8 @@ struct airgs_state {
   int32_t* ncontrib = nullptr; // [pixels]
   uint2* hl = nullptr;         // half-tile lists (variant with half-tile warps), nullable
   uint2* hranges = nullptr;    // [2][tiles]
+  GradRec* grad = nullptr;     // [V][N] blend-backward accumulators, zeroed during the render (saved states)
+  bool grad_zeroed = false;    // grad holds zeros (not yet used by a backward)
   // [4] device counters, 8 bytes each: forward pairs, forward work queue,
   // backward pairs, backward work queue (int in the low half); the backward's
   // two are adjacent, so one memset resets them
@@ -299,6 +302,17 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
     if (r_) return r_;                         \
     s->owned.push_back((void*)(ptr));          \
   } while (0)
+  // A state saved for a backward gets its gradient accumulators here, zeroed
+  // while the host waits for the instance count (the GPU would otherwise idle
+  // through that round trip); the backward then skips its own memset.
+#define PREFILL_GRAD()                                                                  \
+  do {                                                                                  \
+    if (saved && !s->grad && N > 0) {                                                   \
+      ALLOC(s->grad, V * N);                                                            \
+      CK(cudaMemsetAsync(s->grad, 0, (size_t)V * N * sizeof(GradRec), st));            \
+      s->grad_zeroed = true;                                                            \
+    }                                                                                   \
+  } while (0)
   ALLOC(s->d_cams, V);
   ALLOC(s->proj, V * N);
   ALLOC(s->ranges, s->n_tiles);
@@ -369,7 +383,9 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
       }
       CK(cudaMemcpyAsync(ctx->h_pinned, csum + chunks, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
       CK(cudaMemcpyAsync(ctx->h_pinned + 1, info, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
+      CK(cudaEventRecord(ctx->count_ready, st));
+      PREFILL_GRAD();
+      CK(cudaEventSynchronize(ctx->count_ready));
       n_inst = (int64_t)ctx->h_pinned[0];
       const uint32_t longest = (uint32_t)(ctx->h_pinned[1] & 0xFFFFFFFFu);
       const int64_t n_big = (int64_t)(ctx->h_pinned[1] >> 32);
@@ -419,7 +435,9 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
         CK(launch_scan_spans(st, chunk, nc2, chunk + n_chunks));
       }
       CK(cudaMemcpyAsync(ctx->h_pinned, chunk + n_chunks, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
+      CK(cudaEventRecord(ctx->count_ready, st));
+      PREFILL_GRAD();
+      CK(cudaEventSynchronize(ctx->count_ready));
       n_inst = (int64_t)ctx->h_pinned[0];
       if (n_inst >= (int64_t)0xFFFF0000ll)
         return fail(ctx, AIRGS_E_CAPACITY, "%lld tile instances exceed the 32-bit list limit", (long long)n_inst);
@@ -504,6 +522,7 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
     StageScope sc(ctx, ST_BLEND_FWD);
     CK(launch_blend_fwd(st, s->variant, ctx->num_sms, a, o));
   }
+#undef PREFILL_GRAD
 #undef ALLOC
 #undef TALLOC
   if (saved) {
@@ -528,15 +547,21 @@ int backward_impl(airgs_ctx* ctx, airgs_state* s, const float* dL, const float* 
   cudaStream_t st = ctx->stream;
   if (loss_out) CK(cudaMemsetAsync(loss_out, 0, sizeof(float), st));
   if (s->n == 0) return AIRGS_OK;
-  GradRec* grad = nullptr;
-  int rc = dalloc(ctx, &grad, (size_t)s->n_views * s->n);
-  if (rc) return rc;
+  // the accumulators the render zeroed for this state, else a temporary
+  GradRec* grad = s->grad;
   struct G {
     airgs_ctx* c;
     void* p;
     ~G() { dfree(c, p); }
-  } gguard{ctx, grad};
-  CK(cudaMemsetAsync(grad, 0, (size_t)s->n_views * s->n * sizeof(GradRec), st));
+  } gguard{ctx, nullptr};
+  if (!grad) {
+    int rc = dalloc(ctx, &grad, (size_t)s->n_views * s->n);
+    if (rc) return rc;
+    gguard.p = grad;
+  }
+  if (!(grad == s->grad && s->grad_zeroed))
+    CK(cudaMemsetAsync(grad, 0, (size_t)s->n_views * s->n * sizeof(GradRec), st));
+  if (grad == s->grad) s->grad_zeroed = false;  // a second backward of the state zeroes them again
   CK(cudaMemsetAsync(s->counters + 2, 0, 2 * sizeof(unsigned long long), st));
   BlendArgs a;
   a.proj = s->proj;
@@ -666,10 +691,12 @@ int airgs_create(airgs_ctx** out, const airgs_config* cfg, void* stream) {
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_pinned, 128);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_cam_ring, 2 * AIRGS_MAX_VIEWS * sizeof(CamDev));
   for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ctx->cam_copied[k], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->count_ready, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     cudaGetLastError();
     for (cudaEvent_t ev : ctx->cam_copied)
       if (ev) cudaEventDestroy(ev);
+    if (ctx->count_ready) cudaEventDestroy(ctx->count_ready);
     if (ctx->h_cam_ring) cudaFreeHost(ctx->h_cam_ring);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
@@ -690,6 +717,7 @@ int airgs_destroy(airgs_ctx* ctx) {
   if (ctx->h_cam_ring) cudaFreeHost(ctx->h_cam_ring);
   for (cudaEvent_t ev : ctx->cam_copied)
     if (ev) cudaEventDestroy(ev);
+  if (ctx->count_ready) cudaEventDestroy(ctx->count_ready);
   for (auto& p : ctx->pending) ctx->event_pool.insert(ctx->event_pool.end(), {p.second.first, p.second.second});
   for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
