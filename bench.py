@@ -85,12 +85,12 @@ _BLEND_SOURCES = ("paper_2512_20943_b300/csrc/blend_cull.cu", "paper_2512_20943_
 PROFILE_STEPS = 10  # steps of the per-stage profiling pass after the timed region
 
 NCU_TRAFFIC = {
-    "blend_bwd": {"bytes_per_launch": (657.434624 + 92.624896) * 1e6, "smem_bytes_per_launch": 426793462 * 128,
+    "blend_bwd": {"bytes_per_launch": (657.871616 + 92.626944) * 1e6, "smem_bytes_per_launch": 426798009 * 128,
                   "sources": _BLEND_SOURCES,
-                  "sha256": "fdd0a542b4ce5a2feffd84a9500508dbbbc7878ca6f3d400831609528d5adbd9"},
-    "blend_fwd": {"bytes_per_launch": (225.238272 + 234.169600) * 1e6, "smem_bytes_per_launch": 82653747 * 128,
+                  "sha256": "6d777966f8e6cc249eb063f470d32dc7cf0580f66bdb9dd3a679bec4ed20496d"},
+    "blend_fwd": {"bytes_per_launch": (225.070592 + 233.461248) * 1e6, "smem_bytes_per_launch": 82653493 * 128,
                   "sources": _BLEND_SOURCES,
-                  "sha256": "fdd0a542b4ce5a2feffd84a9500508dbbbc7878ca6f3d400831609528d5adbd9"},
+                  "sha256": "6d777966f8e6cc249eb063f470d32dc7cf0580f66bdb9dd3a679bec4ed20496d"},
 }
 
 
