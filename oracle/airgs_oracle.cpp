@@ -473,8 +473,9 @@ PixelResult blend_pixel(const BlendView& bv, const TileLists& tl, int u, int v, 
   pr.ambig = false;
   int tile = (v / kTile) * tl.TW + (u / kTile);
   double px = u + 0.5, py = v + 0.5;
-  double prev_depth = -1;
-  int prev_id = -1;
+  double prev_depth = 0;  // the previous list entry: its depth and whether it blended here
+  bool have_prev = false, prev_sig = false;
+  bool last_tied = false;  // the latest blended entry is a near tie of a neighbour that does not blend
   for (int64_t k = tl.start[tile]; k < tl.end[tile]; ++k) {
     int32_t i = tl.ids[k];
     int pos = (int)(k - tl.start[tile]);
@@ -483,26 +484,50 @@ PixelResult blend_pixel(const BlendView& bv, const TileLists& tl, int u, int v, 
     double A = bv.conic[3 * i], B = bv.conic[3 * i + 1], Cc = bv.conic[3 * i + 2];
     double power = -0.5 * (A * dx * dx + Cc * dy * dy) - B * dx * dy;
     if (std::fabs(power) <= st.tol_rel) pr.ambig = true;
-    if (power > 0) continue;
-    double G = std::exp(power);
-    double alpha = std::min(st.alpha_max, bv.opacity[i] * G);
-    if (std::fabs(alpha - st.alpha_min) <= st.tol_rel * st.alpha_min) pr.ambig = true;
-    // the alpha_max clamp decides whether o and G receive gradient
-    if (std::fabs(bv.opacity[i] * G - st.alpha_max) <= st.tol_rel * st.alpha_max) pr.ambig = true;
-    if (alpha < st.alpha_min) continue;
-    double test = pr.T * (1 - alpha);
-    if (std::fabs(test - st.T_min) <= st.tol_stop * st.T_min) pr.ambig = true;
-    if (test < st.T_min) break;
-    // two blended Gaussians whose depths a single-precision projection could
-    // order differently
-    if (prev_id >= 0 && std::fabs(bv.depth[i] - prev_depth) <= st.tol_depth * std::fabs(bv.depth[i])) pr.ambig = true;
-    prev_depth = bv.depth[i];
-    prev_id = i;
+    bool sig = false, stop = false;  // sig: the entry blends or stops the pixel
+    double G = 0, alpha = 0, test = 0;
+    if (!(power > 0)) {
+      G = std::exp(power);
+      alpha = std::min(st.alpha_max, bv.opacity[i] * G);
+      if (std::fabs(alpha - st.alpha_min) <= st.tol_rel * st.alpha_min) pr.ambig = true;
+      // the alpha_max clamp decides whether o and G receive gradient
+      if (std::fabs(bv.opacity[i] * G - st.alpha_max) <= st.tol_rel * st.alpha_max) pr.ambig = true;
+      if (!(alpha < st.alpha_min)) {
+        test = pr.T * (1 - alpha);
+        if (std::fabs(test - st.T_min) <= st.tol_stop * st.T_min) pr.ambig = true;
+        sig = true;
+        stop = test < st.T_min;
+      }
+    }
+    // Two neighbouring list entries closer in depth than a single-precision key
+    // resolves may come in the other order there.  When both blend or stop this
+    // pixel, the blend depends on that rounding; when only one blends, its list
+    // position does, which matters if it is the pixel's last blended entry
+    // (n_contrib).
+    const double d = bv.depth[i];
+    const bool tie = have_prev && std::fabs(d - prev_depth) <= st.tol_depth * std::fabs(d);
+    if (tie && sig && prev_sig) pr.ambig = true;
+    if (tie && !sig && prev_sig) last_tied = true;
+    const bool tie_nonsig_prev = tie && sig && !prev_sig;
+    have_prev = true;
+    prev_depth = d;
+    prev_sig = sig;
+    if (!sig) continue;
+    if (stop) {
+      // the entry after the one that stops the pixel could come first
+      if (k + 1 < tl.end[tile]) {
+        const double dn = bv.depth[tl.ids[k + 1]];
+        if (std::fabs(dn - d) <= st.tol_depth * std::fabs(dn)) pr.ambig = true;
+      }
+      break;
+    }
+    last_tied = tie_nonsig_prev;  // this entry is now the latest blended one
     for (int ch = 0; ch < 3; ++ch) pr.C[ch] += bv.rgb[3 * i + ch] * alpha * pr.T;
     on_blend(pos, i, alpha, pr.T, G);
     pr.T = test;
     pr.n_contrib = pos + 1;
   }
+  if (last_tied) pr.ambig = true;
   for (int ch = 0; ch < 3; ++ch) pr.C[ch] += pr.T * st.bg[ch];
   return pr;
 }

@@ -271,6 +271,33 @@ def test_termination_stack():
     assert list(out["importance_cnt"]) == [int(c) for c in out["importance_cnt"]]
 
 
+def test_depth_near_ties_flag_the_pixels_they_decide():
+    """Two list entries closer in depth than a single-precision key resolves
+    (relative 1e-8) are flagged at a pixel where both blend (their order
+    changes the blend) or where one of them is the pixel's last blended entry
+    (its position is n_contrib); 1e-3 apart they are not; a near tie of two
+    entries too faint to blend, or of a blended entry that is not the last, moves
+    no output and is not flagged."""
+    cam = axis_camera(W=32, H=32, f=64.0, dist=4.0)
+    cam["cx"] = cam["cy"] = 16.5
+
+    def pair(dz, p_front, p_back):
+        # centres a little off the pixel centre, so that no power sits at 0
+        return concat([one_gaussian([0.02, 0, 0.0], [math.log(0.08)] * 3, [1, 0, 0, 0], logit(p_front), [1, 0, 0]),
+                       one_gaussian([0.02, 0, dz], [math.log(0.08)] * 3, [1, 0, 0, 0], logit(p_back), [0, 1, 0])])
+
+    assert oracle.render(pair(4e-8, 0.5, 0.5), [cam])["ambig"][0][16, 16]      # both blend
+    assert oracle.render(pair(4e-8, 0.5, 0.001), [cam])["ambig"][0][16, 16]    # the last blended entry's position
+    assert not oracle.render(pair(4e-3, 0.5, 0.5), [cam])["ambig"][0][16, 16]  # resolved in single precision
+    assert not oracle.render(pair(4e-8, 0.001, 0.001), [cam])["ambig"][0][16, 16]  # neither blends
+    # a blended entry tied with a faint one, then another blended entry: the
+    # tie moves no output of the pixel (n_contrib is the later entry's)
+    later = one_gaussian([0.02, 0, 0.1], [math.log(0.08)] * 3, [1, 0, 0, 0], logit(0.5), [0, 0, 1])
+    g3 = concat([pair(4e-8, 0.5, 0.001), later])
+    out = oracle.render(g3, [cam])
+    assert out["n_contrib"][0][16, 16] == 3 and not out["ambig"][0][16, 16]
+
+
 def test_permutation_invariance():
     g, cams = synthetic.plain_forward_scene()
     g = synthetic.widen(g)
