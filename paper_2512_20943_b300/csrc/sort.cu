@@ -409,9 +409,12 @@ __global__ void k_emit_piece_map(const uint32_t* __restrict__ piece_off, int64_t
 // instances) of a chunk of EM_CHUNK consecutive depth-order positions, so that
 // no CTA carries much more work than another however uneven the counts are
 // (nearby Gaussians, which come first in depth order, cover many tiles).  The
-// CTA scans the chunk's counts into list offsets and describes the Gaussians
-// that own the piece's instances in shared memory (one per thread: first key,
-// rectangle, alpha box and terms of the exact half test).  Thread t then
+// CTA scans the chunk's counts into list offsets (thread t holds Gaussian t of
+// the chunk, whose id it loads first so that the scan hides that load), finds
+// the owners of the piece's first and last instances (each thread tests its own
+// Gaussian's offset range), and describes the Gaussians that own the piece's
+// instances in shared memory (first key, rectangle, alpha box and terms of the
+// exact half test).  Thread t then
 // produces the piece's instances t*EM_RUN .. +EM_RUN: one binary search for
 // the owner of the first, then tile by tile (row-major stepping, no division
 // past the first), moving to the next Gaussian when the offsets say so; the
@@ -445,6 +448,10 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(int64_t total, int64_t n, c
   const int64_t chunk = piece_chunk[b];
   const uint32_t piece = b - piece_off[chunk];
   const int64_t c0 = chunk * EM_CHUNK;
+  // the chunk's Gaussian ids in depth order (thread t: Gaussian t), loaded now so
+  // that describing the piece's Gaussians below waits for one global load
+  static_assert(EM_ITEMS == 1 && EM_CHUNK == EM_THREADS, "one Gaussian per thread");
+  const uint32_t my_gid = c0 + tid < total ? __ldg(order + c0 + tid) : 0u;
   // chunk offsets: blocked, thread t scans chunk positions t*EM_ITEMS .. +EM_ITEMS
   uint32_t cnt[EM_ITEMS];
   uint32_t local = 0;
@@ -483,17 +490,18 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(int64_t total, int64_t n, c
     }
     return lo;
   };
-  if (tid == 0) {
-    s_g0 = owner(p0, 0, EM_CHUNK - 1);
-    s_g1 = owner(p1 - 1, 0, EM_CHUNK - 1);
+  {  // owners of the piece's first and last instances: the g with s_off[g] <= i < s_off[g + 1]
+    const uint32_t lo = s_off[tid], hi = s_off[tid + 1];
+    if (lo <= p0 && p0 < hi) s_g0 = tid;
+    if (lo <= p1 - 1 && p1 - 1 < hi) s_g1 = tid;
   }
   __syncthreads();
   const int g0 = s_g0, g1 = s_g1;
-  for (int g = g0 + tid; g <= g1; g += EM_THREADS) {
-    if (s_off[g + 1] == s_off[g]) continue;  // no instances
+  for (int g = tid; g <= g1; g += EM_THREADS) {
+    if (g < g0 || s_off[g + 1] == s_off[g]) continue;  // not in the piece, or no instances
     const int64_t p = c0 + g;
     const int v = (total < (int64_t)0xFFFFFFFFll) ? (int)((uint32_t)p / (uint32_t)n) : (int)(p / n);
-    const uint32_t gid = __ldg(order + p);
+    const uint32_t gid = my_gid;
     const CamDev& cam = cams[v];
     const ProjRec* rec = proj + (size_t)v * n + gid;
     const float4 ra = __ldg(&rec->a), rb = __ldg(&rec->b);
