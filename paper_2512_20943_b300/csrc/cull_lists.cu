@@ -96,6 +96,19 @@ __global__ void __launch_bounds__(HL_THREADS) k_half_compact(HalfArgs h, const u
   __shared__ uint32_t s_t[HL_THREADS / 32], s_b[HL_THREADS / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t p0 = (int64_t)blockIdx.x * HL_CHUNK + (int64_t)tid * HL_ITEMS;
+  // every global load this thread needs is issued before the scan, so that
+  // their latencies overlap it (the ranges wait only for the keys)
+  const uint64_t cta_top = off_top[blockIdx.x], cta_bot = off_bot[blockIdx.x];
+  uint32_t tiles[HL_ITEMS], gids[HL_ITEMS];
+  uint2 rgs[HL_ITEMS];
+#pragma unroll
+  for (int k = 0; k < HL_ITEMS; ++k) {
+    const int64_t p = p0 + k;
+    tiles[k] = p < h.n_inst ? h.keys[p] & kKeyTileMask : 0u;
+    gids[k] = p < h.n_inst ? h.ids[p] : 0u;
+  }
+#pragma unroll
+  for (int k = 0; k < HL_ITEMS; ++k) rgs[k] = p0 + k < h.n_inst ? h.ranges[tiles[k]] : make_uint2(0u, 0u);
   unsigned f[HL_ITEMS];
   uint32_t lt = 0, lb = 0;
 #pragma unroll
@@ -123,18 +136,8 @@ __global__ void __launch_bounds__(HL_THREADS) k_half_compact(HalfArgs h, const u
     wt += s_t[w];
     wb += s_b[w];
   }
-  uint64_t ot = off_top[blockIdx.x] + wt + xt - lt;
-  uint64_t ob = bot_base + off_bot[blockIdx.x] + wb + xb - lb;
-  uint32_t tiles[HL_ITEMS], gids[HL_ITEMS];
-  uint2 rgs[HL_ITEMS];
-#pragma unroll
-  for (int k = 0; k < HL_ITEMS; ++k) {  // all loads first, so that they overlap
-    const int64_t p = p0 + k;
-    tiles[k] = p < h.n_inst ? h.keys[p] & kKeyTileMask : 0u;
-    gids[k] = p < h.n_inst ? h.ids[p] : 0u;
-  }
-#pragma unroll
-  for (int k = 0; k < HL_ITEMS; ++k) rgs[k] = p0 + k < h.n_inst ? h.ranges[tiles[k]] : make_uint2(0u, 0u);
+  uint64_t ot = cta_top + wt + xt - lt;
+  uint64_t ob = bot_base + cta_bot + wb + xb - lb;
 #pragma unroll
   for (int k = 0; k < HL_ITEMS; ++k) {
     const int64_t p = p0 + k;
