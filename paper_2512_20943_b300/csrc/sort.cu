@@ -253,24 +253,35 @@ int64_t emit_chunks(int64_t total) { return (total + EM_CHUNK - 1) / EM_CHUNK; }
 
 // counts_sorted[p] = tiles_touched of the Gaussian at depth-order position p;
 // chunk_sums[b] = sum over chunk b.
-__global__ void __launch_bounds__(EM_THREADS) k_count_gather(int64_t total, int64_t n,
+constexpr int CG_THREADS = 64;                    // a chunk's positions over 64 threads,
+constexpr int CG_ITEMS = EM_CHUNK / CG_THREADS;   // so that each thread's gathers overlap
+__global__ void __launch_bounds__(CG_THREADS) k_count_gather(int64_t total, int64_t n,
                                                             const uint32_t* __restrict__ order,
                                                             const uint32_t* __restrict__ tiles_touched,
                                                             uint32_t* __restrict__ counts_sorted,
                                                             uint64_t* __restrict__ chunk_sums) {
   wait_prior_grid();
-  __shared__ uint64_t s_w[EM_THREADS / 32];
-  int64_t c0 = (int64_t)blockIdx.x * EM_CHUNK;
+  __shared__ uint64_t s_w[CG_THREADS / 32];
+  const int64_t c0 = (int64_t)blockIdx.x * EM_CHUNK;
+  uint32_t gid[CG_ITEMS];
+#pragma unroll
+  for (int j = 0; j < CG_ITEMS; ++j) {
+    const int64_t p = c0 + j * CG_THREADS + threadIdx.x;
+    gid[j] = p < total ? __ldg(order + p) : 0u;
+  }
+  uint32_t cnt[CG_ITEMS];
+#pragma unroll
+  for (int j = 0; j < CG_ITEMS; ++j) {
+    const int64_t p = c0 + j * CG_THREADS + threadIdx.x;
+    const int64_t v = total < (int64_t)0xFFFFFFFFll ? (int64_t)((uint32_t)p / (uint32_t)n) : p / n;
+    cnt[j] = p < total ? __ldg(tiles_touched + v * n + gid[j]) : 0u;
+  }
   uint64_t sum = 0;
 #pragma unroll
-  for (int j = 0; j < EM_ITEMS; ++j) {
-    int64_t p = c0 + j * EM_THREADS + threadIdx.x;
-    if (p < total) {
-      int64_t v = p / n;
-      uint32_t cnt = __ldg(tiles_touched + v * n + __ldg(order + p));
-      counts_sorted[p] = cnt;
-      sum += cnt;
-    }
+  for (int j = 0; j < CG_ITEMS; ++j) {
+    const int64_t p = c0 + j * CG_THREADS + threadIdx.x;
+    if (p < total) counts_sorted[p] = cnt[j];
+    sum += cnt[j];
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
@@ -278,7 +289,7 @@ __global__ void __launch_bounds__(EM_THREADS) k_count_gather(int64_t total, int6
   __syncthreads();
   if (threadIdx.x == 0) {
     uint64_t s = 0;
-    for (int w = 0; w < EM_THREADS / 32; ++w) s += s_w[w];
+    for (int w = 0; w < CG_THREADS / 32; ++w) s += s_w[w];
     chunk_sums[blockIdx.x] = s;
   }
 }
@@ -751,7 +762,7 @@ cudaError_t launch_count_gather(cudaStream_t st, int64_t total, int64_t n, const
                                 int64_t* n_chunks) {
   *n_chunks = (total + EM_CHUNK - 1) / EM_CHUNK;
   if (total == 0) return cudaSuccess;
-  cudaError_t e = launch_serialised(k_count_gather, dim3((unsigned)*n_chunks), dim3(EM_THREADS), 0, st, total, n,
+  cudaError_t e = launch_serialised(k_count_gather, dim3((unsigned)*n_chunks), dim3(CG_THREADS), 0, st, total, n,
                                     order, tiles_touched, counts_sorted, chunk_sums);
   count_launches(1);
   return e == cudaSuccess ? cudaGetLastError() : e;
