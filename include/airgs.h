@@ -304,11 +304,13 @@ int airgs_sort_pairs(airgs_ctx* ctx, const uint32_t* keys_in, const uint32_t* va
  *   stream              cudaStream_t the work is enqueued on (NULL = legacy)
  * Needs no context and calls no allocator: its scratch is a fixed device
  * array of 2 * AIRGS_NOALLOC_SORT_MAX_PAIRS + 262144 uint32 words (about 9 MB)
- * that every GPU loading the library holds until the process exits.  The
- * first call on a device looks up that array's device address (make it before
- * any stream capture).  All calls share the array: calls that overlap on the
- * GPU (other streams, other threads) race and must be serialised by the
- * caller.  Returns AIRGS_E_CAPACITY if n > AIRGS_NOALLOC_SORT_MAX_PAIRS,
+ * that every GPU loading the library holds until the process exits.  Every
+ * call looks up that array's device address on the current device (a host-side
+ * lookup that allocates nothing, so the address stays right after
+ * cudaDeviceReset or under another context); the first call in a context may
+ * load the library's device code, so make it before any stream capture.  All
+ * calls share the array: calls that overlap on the GPU (other streams, other
+ * threads) race and must be serialised by the caller.  Returns AIRGS_E_CAPACITY if n > AIRGS_NOALLOC_SORT_MAX_PAIRS,
  * AIRGS_E_ARG for bad arguments, AIRGS_E_CUDA if a launch fails. */
 #define AIRGS_NOALLOC_SORT_MAX_PAIRS (1 << 20)
 int airgs_sort_pairs_noalloc(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,

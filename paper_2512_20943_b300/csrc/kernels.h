@@ -38,8 +38,10 @@ cudaError_t radix_sort_pairs(cudaStream_t st, int num_sms, uint32_t* keys_a, uin
                              uint32_t* vals_b, int64_t seg_len, int n_seg, int key_bits, bool identity_vals,
                              uint32_t* scratch, bool* result_in_b);
 
+// One pass: the digit of bits [shift, min(shift + 8, key_bits)).
 cudaError_t radix_sort_pass(cudaStream_t st, int num_sms, const uint32_t* keys_in, const uint32_t* vals_in,
-                            uint32_t* keys_out, uint32_t* vals_out, int64_t n, int shift, uint32_t* counts);
+                            uint32_t* keys_out, uint32_t* vals_out, int64_t n, int shift, int key_bits,
+                            uint32_t* counts);
 
 cudaError_t launch_count_gather(cudaStream_t st, int64_t total, int64_t n, const uint32_t* order,
                                 const uint32_t* tiles_touched, uint32_t* counts_sorted, uint64_t* chunk_sums,

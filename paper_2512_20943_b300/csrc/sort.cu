@@ -55,8 +55,15 @@ __device__ __forceinline__ void cta_range(const SortGeom& g, int cta, int& seg, 
   t1 = min(t0 + g.tiles_cta, g.tiles_seg);
 }
 
+// Digit of a pass: bits [shift, min(shift + 8, key_bits)) of the key, so that
+// the bits above key_bits (flags kept in the same word) never take part.
+static inline uint32_t radix_digit_mask(int key_bits, int shift) {
+  const int w = key_bits - shift;
+  return w >= 8 ? 0xFFu : (1u << w) - 1u;
+}
+
 __global__ void __launch_bounds__(RS_THREADS) k_rs_upsweep(const uint32_t* __restrict__ keys, SortGeom g, int shift,
-                                                          uint32_t* __restrict__ counts) {
+                                                          uint32_t dmask, uint32_t* __restrict__ counts) {
   wait_prior_grid();
   const int64_t RS_TILE = g.tile;
   __shared__ uint32_t hist[RS_WARPS][RS_RADIX];
@@ -69,7 +76,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_upsweep(const uint32_t* __res
   int64_t base = (int64_t)seg * g.seg_len;
   int64_t e0 = t0 * RS_TILE, e1 = min(t1 * RS_TILE, g.seg_len);
   for (int64_t e = e0 + tid; e < e1; e += RS_THREADS) {
-    uint32_t d = (__ldg(keys + base + e) >> shift) & 0xFF;
+    uint32_t d = (__ldg(keys + base + e) >> shift) & dmask;
     atomicAdd(&hist[warp][d], 1u);
   }
   __syncthreads();
@@ -114,7 +121,7 @@ __global__ void __launch_bounds__(RS_THREADS, AIRGS_RS_MINB) k_rs_downsweep(cons
                                                             const uint32_t* __restrict__ vals_in,
                                                             uint32_t* __restrict__ keys_out,
                                                             uint32_t* __restrict__ vals_out, SortGeom g, int shift,
-                                                            const uint32_t* __restrict__ counts,
+                                                            uint32_t dmask, const uint32_t* __restrict__ counts,
                                                             const uint32_t* __restrict__ totals) {
   wait_prior_grid();
   constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
@@ -171,7 +178,7 @@ __global__ void __launch_bounds__(RS_THREADS, AIRGS_RS_MINB) k_rs_downsweep(cons
       const int p = warp * (RS_ITEMS * 32) + j * 32 + lane;
       const bool valid = p < tile_n;
       const uint32_t k = key[j];
-      uint32_t d = valid ? ((k >> shift) & 0xFF) : RS_RADIX;  // invalid keys form their own class
+      uint32_t d = valid ? ((k >> shift) & dmask) : RS_RADIX;  // invalid keys form their own class
       uint32_t peers = __match_any_sync(0xffffffffu, d);
       uint32_t before = 0;
       if (valid) before = s_warp_cnt[warp][d];
@@ -219,7 +226,7 @@ __global__ void __launch_bounds__(RS_THREADS, AIRGS_RS_MINB) k_rs_downsweep(cons
     for (int j = 0; j < RS_ITEMS; ++j) {
       int p = warp * (RS_ITEMS * 32) + j * 32 + lane;
       if (p < tile_n) {
-        uint32_t d = (key[j] >> shift) & 0xFF;
+        uint32_t d = (key[j] >> shift) & dmask;
         uint32_t pos = s_local[d] + s_warp_cnt[warp][d] + rank[j];
         s_keys[pos] = key[j];
         s_vals[pos] = val[j];
@@ -230,7 +237,7 @@ __global__ void __launch_bounds__(RS_THREADS, AIRGS_RS_MINB) k_rs_downsweep(cons
     // coalesced write-out: consecutive threads write consecutive positions of a digit run
     for (int p = tid; p < tile_n; p += RS_THREADS) {
       uint32_t k = s_keys[p];
-      uint32_t d = (k >> shift) & 0xFF;
+      uint32_t d = (k >> shift) & dmask;
       uint32_t dst = s_offset[d] + (uint32_t)p - s_local[d];
       keys_out[base + dst] = k;
       vals_out[base + dst] = s_vals[p];
@@ -710,19 +717,20 @@ cudaError_t radix_sort_pairs(cudaStream_t st, int num_sms, uint32_t* keys_a, uin
   uint32_t *ki = keys_a, *vi = vals_a, *ko = keys_b, *vo = vals_b;
   for (int pass = 0; pass < passes; ++pass) {
     int shift = 8 * pass;
+    const uint32_t dmask = radix_digit_mask(key_bits, shift);
     uint32_t* totals = scratch + (size_t)n_seg * RS_RADIX * g.ctas_seg;
     const uint32_t* vin = (pass == 0 && identity_vals) ? nullptr : vi;
     cudaError_t e = launch_serialised(k_rs_upsweep, dim3(grid), dim3(RS_THREADS), 0, st, (const uint32_t*)ki, g, shift,
-                                      scratch);
+                                      dmask, scratch);
     if (e == cudaSuccess)
       e = launch_serialised(k_rs_spine, dim3((n_seg * RS_RADIX + 7) / 8), dim3(256), 0, st, scratch, totals, g.ctas_seg,
                             n_seg * RS_RADIX);
     if (e == cudaSuccess)
       e = (g.tile == (int64_t)RS_THREADS * RS_ITEMS
                ? launch_serialised(k_rs_downsweep<RS_ITEMS>, dim3(grid), dim3(RS_THREADS), 0, st, (const uint32_t*)ki,
-                                   vin, ko, vo, g, shift, (const uint32_t*)scratch, (const uint32_t*)totals)
+                                   vin, ko, vo, g, shift, dmask, (const uint32_t*)scratch, (const uint32_t*)totals)
                : launch_serialised(k_rs_downsweep<RS_ITEMS_SEG>, dim3(grid), dim3(RS_THREADS), 0, st,
-                                   (const uint32_t*)ki, vin, ko, vo, g, shift, (const uint32_t*)scratch,
+                                   (const uint32_t*)ki, vin, ko, vo, g, shift, dmask, (const uint32_t*)scratch,
                                    (const uint32_t*)totals));
     count_launches(3);
     if (e == cudaSuccess) e = cudaGetLastError();
@@ -738,20 +746,23 @@ cudaError_t radix_sort_pairs(cudaStream_t st, int num_sms, uint32_t* keys_a, uin
   return cudaSuccess;
 }
 
-// One 8-bit pass (bits [shift, shift + 8)) of the same radix sort over a single
+// One pass (the digit of bits [shift, min(shift + 8, key_bits))) of the same radix sort over a single
 // segment, reading (keys_in, vals_in) and writing (keys_out, vals_out);
 // `counts` must hold radix_scratch_bytes(n, 1, num_sms) bytes.
 cudaError_t radix_sort_pass(cudaStream_t st, int num_sms, const uint32_t* keys_in, const uint32_t* vals_in,
-                            uint32_t* keys_out, uint32_t* vals_out, int64_t n, int shift, uint32_t* counts) {
+                            uint32_t* keys_out, uint32_t* vals_out, int64_t n, int shift, int key_bits,
+                            uint32_t* counts) {
   if (n == 0) return cudaSuccess;
   SortGeom g = make_geom(n, 1, num_sms);
+  const uint32_t dmask = radix_digit_mask(key_bits, shift);
   uint32_t* totals = counts + (size_t)RS_RADIX * g.ctas_seg;
-  cudaError_t e = launch_serialised(k_rs_upsweep, dim3(g.ctas_seg), dim3(RS_THREADS), 0, st, keys_in, g, shift, counts);
+  cudaError_t e =
+      launch_serialised(k_rs_upsweep, dim3(g.ctas_seg), dim3(RS_THREADS), 0, st, keys_in, g, shift, dmask, counts);
   if (e == cudaSuccess)
     e = launch_serialised(k_rs_spine, dim3((RS_RADIX + 7) / 8), dim3(256), 0, st, counts, totals, g.ctas_seg, RS_RADIX);
   if (e == cudaSuccess)
     e = launch_serialised(k_rs_downsweep<RS_ITEMS>, dim3(g.ctas_seg), dim3(RS_THREADS), 0, st, keys_in, vals_in,
-                          keys_out, vals_out, g, shift, (const uint32_t*)counts, (const uint32_t*)totals);
+                          keys_out, vals_out, g, shift, dmask, (const uint32_t*)counts, (const uint32_t*)totals);
   count_launches(3);
   if (e == cudaSuccess) e = cudaGetLastError();
   return e;

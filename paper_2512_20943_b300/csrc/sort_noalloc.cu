@@ -11,8 +11,6 @@
 // process exits.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "airgs.h"
 #include "airgs_internal.cuh"
 #include "kernels.h"
@@ -22,41 +20,11 @@ namespace {
 constexpr int64_t kMaxPairs = AIRGS_NOALLOC_SORT_MAX_PAIRS;
 constexpr size_t kCountWords = 256 * 1024;  // digit counts: 256 digits x up to 1024 CTAs
 constexpr size_t kScratchWords = 2 * kMaxPairs + kCountWords;
-constexpr int kMaxDevices = 64;
 
 }  // namespace
 
 // Shared by every call on a device; holds the previous call's contents.
 static __device__ __align__(256) uint32_t g_sort_scratch[kScratchWords];
-
-namespace {
-
-// Device address of g_sort_scratch per device (the symbol's name in host code
-// is only a host-side stand-in), and the SM count used to size the grid.
-uint32_t* g_scratch_addr[kMaxDevices];
-int g_num_sms[kMaxDevices];
-std::mutex g_setup_mu;
-
-// Once per device, with that device current.
-int setup_device(int dev) {
-  std::lock_guard<std::mutex> lock(g_setup_mu);
-  if (g_scratch_addr[dev]) return AIRGS_OK;
-  void* p = nullptr;
-  if (cudaGetSymbolAddress(&p, g_sort_scratch) != cudaSuccess) {
-    cudaGetLastError();
-    return AIRGS_E_CUDA;
-  }
-  int sms = 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-    cudaGetLastError();
-    return AIRGS_E_CUDA;
-  }
-  g_num_sms[dev] = sms;
-  g_scratch_addr[dev] = static_cast<uint32_t*>(p);
-  return AIRGS_OK;
-}
-
-}  // namespace
 
 extern "C" int airgs_sort_pairs_noalloc(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
                                         uint32_t* vals_out, int64_t n, int key_bits, void* stream) {
@@ -64,21 +32,26 @@ extern "C" int airgs_sort_pairs_noalloc(const uint32_t* keys_in, const uint32_t*
   if (n > kMaxPairs) return AIRGS_E_CAPACITY;
   if (n == 0) return AIRGS_OK;
   if (!keys_in || !vals_in || !keys_out || !vals_out) return AIRGS_E_ARG;
+  // The array's name is only a host-side stand-in: its device address is
+  // looked up on every call, with the caller's device current.  The lookup is a
+  // host-side table read that allocates nothing, and doing it per call keeps
+  // the address right under whatever context is current (a cached address
+  // would dangle after cudaDeviceReset, which loads the module again).  The
+  // first call in a context may load the library's device code: make it before
+  // any stream capture.
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
+  void* p = nullptr;
+  int sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetSymbolAddress(&p, g_sort_scratch) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || p == nullptr ||
+      sms <= 0) {
     cudaGetLastError();
     return AIRGS_E_CUDA;
   }
-  if (dev < 0 || dev >= kMaxDevices) return AIRGS_E_ARG;
-  if (!g_scratch_addr[dev]) {
-    int rc = setup_device(dev);
-    if (rc != AIRGS_OK) return rc;
-  }
-  const int sms = g_num_sms[dev];
   if (airgs::radix_scratch_bytes(n, 1, sms) > kCountWords * sizeof(uint32_t)) return AIRGS_E_CAPACITY;
-  uint32_t* sk = g_scratch_addr[dev];      // scratch keys  [kMaxPairs]
-  uint32_t* sv = sk + kMaxPairs;           // scratch values [kMaxPairs]
-  uint32_t* counts = sk + 2 * kMaxPairs;   // digit counts, fully rewritten by every pass
+  uint32_t* sk = static_cast<uint32_t*>(p);  // scratch keys  [kMaxPairs]
+  uint32_t* sv = sk + kMaxPairs;             // scratch values [kMaxPairs]
+  uint32_t* counts = sk + 2 * kMaxPairs;     // digit counts, fully rewritten by every pass
   cudaStream_t st = static_cast<cudaStream_t>(stream);
 
   // Ping-pong so that the last pass writes the caller's outputs and the inputs
@@ -87,10 +60,10 @@ extern "C" int airgs_sort_pairs_noalloc(const uint32_t* keys_in, const uint32_t*
   const uint32_t* ki = keys_in;
   const uint32_t* vi = vals_in;
   bool to_out = (passes % 2) == 1;
-  for (int p = 0; p < passes; ++p) {
+  for (int pass = 0; pass < passes; ++pass) {
     uint32_t* ko = to_out ? keys_out : sk;
     uint32_t* vo = to_out ? vals_out : sv;
-    cudaError_t e = airgs::radix_sort_pass(st, sms, ki, vi, ko, vo, n, 8 * p, counts);
+    cudaError_t e = airgs::radix_sort_pass(st, sms, ki, vi, ko, vo, n, 8 * pass, key_bits, counts);
     if (e != cudaSuccess) return AIRGS_E_CUDA;
     ki = ko;
     vi = vo;

@@ -263,6 +263,21 @@ def test_radix_sort_stable_bit_exact(rast, n, bits):
     assert np.array_equal(vo.cpu().numpy().view(np.uint32), vals[order])
 
 
+@pytest.mark.parametrize("n,bits", [(200_003, 17), (65_537, 5), (100_000, 30)])
+def test_radix_sort_ignores_bits_above_key_bits(rast, n, bits):
+    """Only bits [0, key_bits) order the pairs (the tile sort keeps flags in the
+    top bits of its keys); the keys come out whole."""
+    rng = np.random.default_rng(n + bits)
+    keys = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
+    vals = np.arange(n, dtype=np.uint32)
+    ko, vo = rast.sort_pairs(torch.from_numpy(keys.view(np.int32)).cuda(),
+                             torch.from_numpy(vals.view(np.int32)).cuda(), bits)
+    torch.cuda.synchronize()
+    order = np.argsort(keys & np.uint32((1 << bits) - 1), kind="stable")
+    assert np.array_equal(ko.cpu().numpy().view(np.uint32), keys[order])
+    assert np.array_equal(vo.cpu().numpy().view(np.uint32), vals[order])
+
+
 @pytest.mark.parametrize("variant", VARIANTS)
 def test_permutation_invariance_gpu(variant):
     rast = rast_variant(variant)
