@@ -517,3 +517,53 @@ def test_l1_gradient_sign_and_scale():
     assert abs(loss - (0.1 + 0.2 + 0.5) / 6) < 1e-15
     assert np.array_equal(np.sign(gr[0]), [[[1, 0]], [[-1, 0]], [[0, 1]]])
     assert np.allclose(np.abs(gr[0])[gr[0] != 0], 1 / 6)
+
+
+# ---------------------------------------------------------------- densification statistic
+def test_densification_statistic_per_view_norms_and_binned_views():
+    """Sec. III-B densifies where the view-space positional gradient is large;
+    the statistic is the sum over views of |dL/d mean2d| with the count of views
+    in which the Gaussian is binned.  One Gaussian, five cameras:
+      A, B  see it from different directions (random linear loss on both),
+      C     has it behind the camera (culled),
+      D     has it in front but off the image (no tile: not binned),
+      E     bins it, but the loss has no weight there (zero gradient, still a view).
+    dL/d mean2d of a view is pinned without the adjoint: shifting that camera's
+    principal point by h moves only that view's projected centre by h (mean2d =
+    f t/z + c), so a central difference of the forward loss in cx / cy gives it.
+    The statistic must be |v_A| + |v_B| (not |v_A + v_B|), the count 3 (A, B, E)."""
+    g = one_gaussian([0.1, -0.05, 0.2], [math.log(0.12), math.log(0.08), math.log(0.1)],
+                     [0.9, 0.3, -0.2, 0.25], logit(0.6), [0.8, 0.3, 0.5])
+    cams = [synthetic.camera((0.0, 0.0, -3.0), 40, 36, fov_x_deg=50.0),           # A
+            synthetic.camera((2.2, -1.0, -1.6), 36, 40, fov_x_deg=55.0),          # B
+            synthetic.camera((0.0, 0.0, 3.0), 32, 32, fov_x_deg=50.0, target=(0.0, 0.0, 6.0)),   # C
+            synthetic.camera((0.0, 0.0, -3.0), 32, 32, fov_x_deg=30.0, target=(4.0, 0.0, 0.0)),  # D
+            synthetic.camera((-1.5, 0.5, -2.5), 30, 30, fov_x_deg=50.0)]          # E
+    vis = [oracle.project(g, c) for c in cams]
+    assert [bool(p["visible"][0]) for p in vis] == [True, True, False, False, True]
+    assert vis[3]["depth"][0] > cams[3]["near"]  # D: in front of the camera, yet not binned
+    rng = np.random.default_rng(5)
+    wts = [rng.standard_normal((3, c["height"], c["width"])) for c in cams]
+    wts[4][:] = 0.0
+    L0, out = loss_and_weights(g, cams, wts)
+    assert not any(a.any() for a in out["ambig"])
+    h = 1e-6
+    v = []
+    for k, c in enumerate(cams):
+        comp = []
+        for key in ("cx", "cy"):
+            cp = [dict(x) for x in cams]
+            cp[k][key] = c[key] + h
+            Lp, _ = loss_and_weights(g, cp, wts)
+            cp[k][key] = c[key] - h
+            Lm, _ = loss_and_weights(g, cp, wts)
+            comp.append((Lp - Lm) / (2 * h))
+        v.append(np.array(comp))
+    assert np.linalg.norm(v[0]) > 1e-2 and np.linalg.norm(v[1]) > 1e-2
+    assert all(np.abs(v[k]).max() == 0.0 for k in (2, 3, 4))
+    want = np.linalg.norm(v[0]) + np.linalg.norm(v[1])
+    # the two readings differ clearly on this scene
+    assert abs(want - np.linalg.norm(v[0] + v[1])) > 0.05 * want
+    got = oracle.render_backward(g, cams, wts, densify=True)
+    assert abs(got["densify_grad"][0] - want) < 1e-6 * max(1.0, want), (got["densify_grad"][0], want)
+    assert int(got["densify_views"][0]) == 3
