@@ -3,23 +3,24 @@
 The dense pruning-level space S_t^d lists, for pruning levels 0 %, 10 %, ...,
 100 % of the Gaussians (lowest usage frequency first), the reconstruction
 quality and the transmitted size of the pruned delta d'_t = p(D_t - D'_{t-1}).
-Algorithm 1 keeps the levels before the first quality "cliff" (a drop more
-than beta times the previous drop) and binary-searches that candidate list,
-whose sizes decrease with the level, for the lowest level whose size fits the
-per-frame budget B / R.
+The selection of Algorithm 1 admits the levels before the first quality
+"cliff" (a drop more than beta times the drop before it) and returns the
+least pruned admissible level whose size fits the per-frame budget B / R;
+sizes do not increase with the level, so that level is found by bisection.
 
 Quality is the PSNR of the pruned frame against the unpruned one, rendered by
 the library for a set of views; every rendering, pruning, delta and error step
 runs in libairgs kernels.  Only the level loop and Algorithm 1 (a few
 comparisons) run on the host.
 
-Readings where the listing is silent: a previous drop of exactly 0 makes any
+Readings where the section is silent: a previous drop of exactly 0 makes any
 later quality loss a cliff; when no candidate level fits the budget the result
 is the cliff level if a cliff was found, else the last candidate (the most
 pruning the candidates allow).
 """
 from __future__ import annotations
 
+import bisect
 import math
 from dataclasses import dataclass
 
@@ -41,42 +42,44 @@ class Level:
 
 
 def _is_cliff(drop: float, previous: float, beta: float) -> bool:
+    """A quality change is a cliff when it is more than beta times the drop
+    before it (both changes are non-positive); after a flat step any loss is."""
     if previous == 0.0:
         return drop < 0.0
     return drop / previous > beta
 
 
+def first_cliff(quality, beta: float):
+    """Index of the first level whose quality change is a cliff relative to the
+    change before it (the first change stands in for its own predecessor), or
+    None when the space has no cliff."""
+    changes = [b - a for a, b in zip(quality, quality[1:])]  # changes[k]: level k -> k + 1
+    for k, change in enumerate(changes):
+        if _is_cliff(change, changes[max(k - 1, 0)], beta):
+            return k + 1
+    return None
+
+
 def select_pruning_level(space, beta: float, bandwidth: float, frame_rate: float) -> int:
-    """Algorithm 1: the pruning level (index into `space`, a list of
-    (quality, size) pairs ordered by increasing pruning) for bandwidth B and
-    target frame rate R."""
-    q = [float(s[0]) for s in space]
+    """Pruning level of Sec. III-C (Algorithm 1): `space` lists (quality, size)
+    per level, ordered by increasing pruning, so sizes do not increase.  The
+    admissible levels are those before the first quality cliff; of those, the
+    result is the least pruned one whose transmitted size fits the per-frame
+    budget B / R, located by bisection over the admissible sizes (a
+    non-increasing sequence).  If no admissible level fits, the result is the
+    cliff level when there is one, else the most pruned admissible level."""
+    quality = [float(s[0]) for s in space]
     size = [float(s[1]) for s in space]
-    if not q:
+    if not quality:
         raise ValueError("empty pruning-level space")
-    candidates = [0]
-    cliff = None
-    if len(q) > 1:
-        previous = q[1] - q[0]
-        for i in range(1, len(q)):
-            drop = q[i] - q[i - 1]
-            if _is_cliff(drop, previous, beta):
-                cliff = i
-                break
-            candidates.append(i)
-            previous = drop
+    cliff = first_cliff(quality, beta)
+    admissible = cliff if cliff is not None else len(quality)  # levels [0, admissible)
     budget = bandwidth / frame_rate
-    chosen = cliff if cliff is not None else candidates[-1]
-    lo, hi = 0, len(candidates) - 1
-    while lo <= hi:
-        mid = (lo + hi) // 2
-        level = candidates[mid]
-        if size[level] <= budget:
-            chosen = level
-            hi = mid - 1
-        else:
-            lo = mid + 1
-    return chosen
+    # "fits the budget" goes from False to True along non-increasing sizes
+    first_fit = bisect.bisect_left(range(admissible), True, key=lambda level: size[level] <= budget)
+    if first_fit < admissible:
+        return first_fit
+    return cliff if cliff is not None else admissible - 1
 
 
 def psnr(sse: float, n_values: int) -> float:
