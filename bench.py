@@ -80,7 +80,8 @@ FP32_LANES_PER_SM = 128
 # dominant kernels from one ncu capture of this workload (the summary and the
 # command are under profiles/), keyed to the SHA-256 of the sources the kernel
 # was built from: once those change the counters no longer describe it (null).
-_BLEND_SOURCES = ("paper_2512_20943_b300/csrc/blend_cull.cu", "paper_2512_20943_b300/csrc/airgs_internal.cuh",
+_BLEND_SOURCES = ("paper_2512_20943_b300/csrc/blend_fwd.cu", "paper_2512_20943_b300/csrc/blend_bwd.cu",
+                  "paper_2512_20943_b300/csrc/blend_common.cuh", "paper_2512_20943_b300/csrc/airgs_internal.cuh",
                   "paper_2512_20943_b300/csrc/kernels.h")
 PROFILE_STEPS = 10  # steps of the per-stage profiling pass after the timed region
 
@@ -358,7 +359,7 @@ def run_ours(args):
     n_frames = args.warmup + args.steps
     wl = Workload(n_frames, device)
     stream = torch.cuda.Stream()
-    rast = Rasterizer(RasterConfig(blend_variant=args.variant, sort_mode=args.sort_mode), stream=stream)
+    rast = Rasterizer(RasterConfig(kernel_shape=args.shape, sort_mode=args.sort_mode), stream=stream)
     p = wl.params
     with torch.cuda.stream(stream):
         rast.set_anchor(p["means"], p["log_scales"], p["quats"], p["opacity_logit"], p["sh"])
@@ -419,12 +420,12 @@ def run_ours(args):
     px_step = VIEWS_PER_STEP * WIDTH * HEIGHT
     value = whole_job_value(world, px_step, args.steps, total_ms)
 
-    # one untimed render to read the variant and list sizes the timed steps used
+    # one untimed render to read the kernel shape and list sizes the timed steps used
     with torch.cuda.stream(stream):
         res = rast.render(wl.views(args.warmup)[1], save=True)
         st = rast.stats(res.state)
         res.state.release()
-    probe = {"variant": Rasterizer.variant_names()[st["blend_variant"]], "n_instances": st["n_instances"]}
+    probe = {"shape": Rasterizer.shape_names()[st["kernel_shape"]], "n_instances": st["n_instances"]}
 
     # end to end through the public API with host buffers
     e2e = None
@@ -450,7 +451,7 @@ def run_ours(args):
     # Blend work (algorithmic): the definition's pairs (list entries up to each
     # pixel's termination, counted by the kernels) times the test flops, plus the
     # blended pairs (the importance counts) times the blend flops.  The culling
-    # variants decide most definition pairs per 8x4 block without per-pair
+    # kernels decide most definition pairs per 8x4 block without per-pair
     # arithmetic; the lane evaluations they do issue are reported beside.
     def rate(flops, name):  # over the blend stage's live event time in the timed region
         return flops / (ms_t[name] / 1e3) / 1e12 if ms_t[name] else 0.0
@@ -519,7 +520,7 @@ def run_ours(args):
         "stages": stage_lines,
         "stages_pass": f"{n_prof} further steps of the same frames with every stage bracketed by CUDA events "
                        "(inside the timed region only the blend stages are)",
-        "blend_variant": probe["variant"],
+        "kernel_shape": probe["shape"],
         "instances_per_step": probe["n_instances"],
         "pairs_per_step": {"blended": blended, "forward": timed["pairs_forward"] / args.steps,
                            "backward": timed["pairs_backward"] / args.steps,
@@ -544,7 +545,7 @@ WORKLOADS = {
     "per_frame": "per-frame training step: 200k Gaussians SH3, 20 views at 1352x1014 in one launch, fused L1 backward "
                  "with importance accumulation",
     "large": "large scene: 2M Gaussians SH3, 16 views at 3840x2160 in one launch, fused L1 backward with "
-             "importance accumulation, blend variant autotuned",
+             "importance accumulation, kernel shape autotuned",
 }
 
 
@@ -575,7 +576,7 @@ def run_config(args):
     p = [torch.from_numpy(np.ascontiguousarray(g[k])).to(device)
          for k in ("means", "log_scales", "quats", "opacity_logit", "sh")]
     stream = torch.cuda.Stream()
-    rast = Rasterizer(RasterConfig(blend_variant=args.variant, sort_mode=args.sort_mode), stream=stream)
+    rast = Rasterizer(RasterConfig(kernel_shape=args.shape, sort_mode=args.sort_mode), stream=stream)
     target = None
     if backward:
         target = torch.from_numpy(np.concatenate([x.reshape(-1) for x in synthetic.target_images(cams, 1)])).to(device)
@@ -659,7 +660,7 @@ def run_config(args):
         "gpu_launches": launches, "clocks": clocks, "stages": stage_lines,
         "stages_pass": f"{n_prof} further steps with every stage bracketed by CUDA events (inside the timed "
                        "region only the blend stages are)",
-        "blend_variant": Rasterizer.variant_names()[st["blend_variant"]], "instances_per_step": st["n_instances"],
+        "kernel_shape": Rasterizer.shape_names()[st["kernel_shape"]], "instances_per_step": st["n_instances"],
     }
     for name, key, fl in (("blend_fwd", "forward", FLOPS_BLEND_FWD), ("blend_bwd", "backward", FLOPS_BLEND_BWD)):
         if name in stage_lines and blended is not None and ms_t[name]:
@@ -775,8 +776,8 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="length of the served request stream")
-    ap.add_argument("--autotune", action="store_true", help="time every blend variant first and keep the fastest")
-    ap.add_argument("--variant", type=int, default=-1, help="blend kernel variant (-1: autotuned choice or default)")
+    ap.add_argument("--autotune", action="store_true", help="search the kernel shapes first and keep the fastest")
+    ap.add_argument("--shape", type=int, default=-1, help="kernel shape (-1: autotuned choice or shape 0)")
     ap.add_argument("--sort-mode", type=int, default=-1,
                     help="0: global radix ordering; 1: per-tile ordering when lists fit; -1: per-tile for small batches")
     ap.add_argument("--workload", choices=["streaming"] + sorted(WORKLOADS), default="streaming",

@@ -73,7 +73,8 @@ typedef struct {
   float alpha_min; /* 1/255 */
   float T_min;     /* 1e-4 */
   float bg[3];     /* background colour, added as T_final * bg (black) */
-  int blend_variant;          /* -1: autotuned per workload, else a fixed kernel variant */
+  int kernel_shape;           /* -1: autotuned per workload (shape 0 until tuned), else a fixed index
+                                 into the compiled kernel shapes (airgs_shape_count / airgs_shape_name) */
   int sort_mode;              /* 0: global two-stage radix ordering; 1: per-tile ordering (lists
                                  sorted in shared memory) when every list fits one CTA; -1 (default):
                                  per-tile for batches of at most 65536 (view, Gaussian) pairs, where
@@ -109,7 +110,7 @@ typedef struct {
   int64_t n_pixels;      /* pixels over all views */
   int64_t pairs_forward; /* (pixel, list entry) pairs evaluated by the forward, up to termination */
   int64_t pairs_backward;/* pairs replayed by the backward (list positions < n_contrib) */
-  int blend_variant;     /* kernel variant the forward ran */
+  int kernel_shape;      /* kernel shape the render ran */
 } airgs_stats;
 
 /* Fill *cfg with the defaults above. */
@@ -316,11 +317,21 @@ int airgs_sort_pairs(airgs_ctx* ctx, const uint32_t* keys_in, const uint32_t* va
 int airgs_sort_pairs_noalloc(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
                              uint32_t* vals_out, int64_t n, int key_bits, void* stream);
 
-/* Autotune the blend kernel variant for this workload shape (n Gaussians of
- * the current frame, the given cameras) by timing every variant; the choice
- * is cached per (n, total pixels, n_views) and written to the config's cache
- * path if set.  Returns the chosen variant in *variant. */
-int airgs_autotune(airgs_ctx* ctx, const airgs_camera* cams, int n_views, int* variant);
+/* Autotune the kernel shape for this workload (n Gaussians of the current
+ * frame, the given cameras): a coordinate search over the compiled shapes --
+ * first the blend backward's (staged entries per batch, warps per SM), then
+ * the blend forward's, then the radix sort's keys per thread -- timing the
+ * training step as it runs (render with saved state, then the fused L1
+ * backward with usage-frequency accumulation, against a constant target) with
+ * CUDA events on the context's stream, best of 3 repetitions after one
+ * warm-up.  Shape 0 is always among the candidates, so the choice is never
+ * slower than it by the timing.  The choice is cached per (n, total pixels,
+ * n_views), used by later renders of that workload when kernel_shape is -1,
+ * and written to the config's cache path if set.  *shape receives the choice;
+ * ms_default / ms_best (nullable) the step times of shape 0 and of the
+ * choice.  Synchronises the context's stream. */
+int airgs_autotune(airgs_ctx* ctx, const airgs_camera* cams, int n_views, int* shape, float* ms_default,
+                   float* ms_best);
 
 /* Per-stage device timing.  With profiling level AIRGS_PROFILE_ALL, each
  * pipeline stage (decode, projection, depth sort, scan+emit, tile sort, ranges,
@@ -329,13 +340,14 @@ int airgs_autotune(airgs_ctx* ctx, const airgs_camera* cams, int n_views, int* v
  * stages are (two event pairs per training step instead of nine, so the rest of
  * the pipeline runs as it does unprofiled); with either level the blend kernels
  * also add their evaluated pairs to a context counter.  airgs_set_profiling
- * returns AIRGS_E_ARG for any other level than the three below.  airgs_stage_times synchronises, writes the summed milliseconds and
- * the number of timed launches of each stage since the previous readout into
+ * returns AIRGS_E_ARG for any other level than the three below.
+ * airgs_stage_times synchronises, writes the summed milliseconds and the
+ * number of timed launches of each stage since the previous readout into
  * ms[AIRGS_NUM_STAGES] / launches[AIRGS_NUM_STAGES], and into pairs[4] (each
  * nullable) the forward and backward pair totals of the definition (list
  * entries up to termination / below n_contrib) followed by the forward and
- * backward lane evaluations the culling kernels actually issued (0 for
- * variants that do not count them); then clears them. */
+ * backward lane evaluations the blend kernels actually issued (32 per 8x4
+ * pixel block they evaluate); then clears them. */
 #define AIRGS_NUM_STAGES 9
 #define AIRGS_PROFILE_OFF 0
 #define AIRGS_PROFILE_ALL 1
@@ -363,9 +375,12 @@ int airgs_measure_smem_peak(airgs_ctx* ctx, double* tbs);
 /* Process-wide number of kernel launches the library has issued. */
 int64_t airgs_kernel_launch_count(void);
 
-/* Number of blend kernel variants and a short name of each. */
-int airgs_blend_variant_count(void);
-const char* airgs_blend_variant_name(int variant);
+/* Number of compiled kernel shapes and a short name of each ("fwd B/W bwd
+ * B/W keys K": staged entries per batch and warps per SM of the blend forward
+ * and backward, radix keys per thread of the instance sort).  Shape 0 is the
+ * default. */
+int airgs_shape_count(void);
+const char* airgs_shape_name(int shape);
 
 #ifdef __cplusplus
 }

@@ -42,7 +42,7 @@ class airgs_config(ctypes.Structure):
         ("alpha_min", ctypes.c_float),
         ("T_min", ctypes.c_float),
         ("bg", ctypes.c_float * 3),
-        ("blend_variant", ctypes.c_int),
+        ("kernel_shape", ctypes.c_int),
         ("sort_mode", ctypes.c_int),
         ("autotune_cache", ctypes.c_char_p),
         ("cull_lists", ctypes.c_int),
@@ -98,7 +98,7 @@ class airgs_stats(ctypes.Structure):
         ("n_pixels", ctypes.c_int64),
         ("pairs_forward", ctypes.c_int64),
         ("pairs_backward", ctypes.c_int64),
-        ("blend_variant", ctypes.c_int),
+        ("kernel_shape", ctypes.c_int),
     ]
 
 
@@ -140,15 +140,16 @@ SIGNATURES = {
     "airgs_state_tile_lists": (I, [CTX, STATE, I, P, P]),
     "airgs_sort_pairs": (I, [CTX, P, P, P, P, I64, I]),
     "airgs_sort_pairs_noalloc": (I, [P, P, P, P, I64, I, P]),
-    "airgs_autotune": (I, [CTX, ctypes.POINTER(airgs_camera), I, ctypes.POINTER(I)]),
+    "airgs_autotune": (I, [CTX, ctypes.POINTER(airgs_camera), I, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_float),
+                           ctypes.POINTER(ctypes.c_float)]),
     "airgs_set_profiling": (I, [CTX, I]),
     "airgs_stage_times": (I, [CTX, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64), ctypes.POINTER(I64)]),
     "airgs_stage_name": (ctypes.c_char_p, [I]),
     "airgs_measure_fp32_peak": (I, [CTX, ctypes.POINTER(ctypes.c_double)]),
     "airgs_measure_smem_peak": (I, [CTX, ctypes.POINTER(ctypes.c_double)]),
     "airgs_kernel_launch_count": (I64, []),
-    "airgs_blend_variant_count": (I, []),
-    "airgs_blend_variant_name": (ctypes.c_char_p, [I]),
+    "airgs_shape_count": (I, []),
+    "airgs_shape_name": (ctypes.c_char_p, [I]),
 }
 
 _lib = None

@@ -80,7 +80,7 @@ struct airgs_state {
   uint32_t* ids = nullptr;     // sorted instance values
   uint2* ranges = nullptr;     // [tiles]
   int32_t* ncontrib = nullptr; // [pixels]
-  uint2* hl = nullptr;         // half-tile lists (variant with half-tile warps), nullable
+  uint2* hl = nullptr;         // half-tile lists, nullable (lists of 2^28 entries or more: the full lists)
   uint2* hranges = nullptr;    // [2][tiles]
   GradRec* grad = nullptr;     // [V][N] blend-backward accumulators, zeroed during the render (saved states)
   bool grad_zeroed = false;    // grad holds zeros (not yet used by a backward)
@@ -90,7 +90,7 @@ struct airgs_state {
   unsigned long long* counters = nullptr;
   const float* rgb = nullptr;  // caller's forward output
   int64_t n_inst = 0, n_tiles = 0, n_pixels = 0;
-  int variant = 0;
+  int shape = 0;               // kernel shape (shape_parts) the render ran and the backward runs
   std::vector<void*> owned;    // device allocations to free on release
 };
 
@@ -247,23 +247,44 @@ struct StageScope {
   }
 };
 
+}  // namespace
+
+const char* airgs::shape_name(int shape) {
+  struct Names {
+    char s[kShapes][48];
+    Names() {
+      const int fwd[kFwdShapes][2] = {{32, 32}, {16, 32}, {64, 32}, {32, 28}, {32, 24}};
+      const int bwd[kBwdShapes][2] = {{32, 28}, {16, 28}, {64, 28}, {32, 24}, {32, 32}};
+      for (int i = 0; i < kShapes; ++i) {
+        const ShapeParts p = shape_parts(i);
+        snprintf(s[i], sizeof(s[i]), "fwd %d/%d bwd %d/%d keys %d", fwd[p.fwd][0], fwd[p.fwd][1], bwd[p.bwd][0],
+                 bwd[p.bwd][1], sort_keys_of(p.sort));
+      }
+    }
+  };
+  static const Names names;  // built once (thread-safe initialisation of a local static)
+  return (shape >= 0 && shape < kShapes) ? names.s[shape] : "";
+}
+
+namespace {
+
 std::string tune_key(int64_t n, int64_t pixels, int views) {
   std::ostringstream os;
   os << n << ":" << pixels << ":" << views;
   return os.str();
 }
 
-int choose_variant(airgs_ctx* ctx, int64_t n, int64_t pixels, int views) {
-  if (ctx->cfg.blend_variant >= 0 && ctx->cfg.blend_variant < blend_variant_count()) return ctx->cfg.blend_variant;
+int choose_shape(airgs_ctx* ctx, int64_t n, int64_t pixels, int views) {
+  if (ctx->cfg.kernel_shape >= 0 && ctx->cfg.kernel_shape < kShapes) return ctx->cfg.kernel_shape;
   auto it = ctx->tuned.find(tune_key(n, pixels, views));
   if (it != ctx->tuned.end()) return it->second;
-  return 6;  // half-tile warps with block culling and compacted staging unless tuned otherwise
+  return 0;  // the default shape unless tuned otherwise
 }
 
 // Forward pipeline: project -> depth sort -> emit -> tile sort -> ranges -> blend.
 int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* cams, int n_views, float* rgb_out,
                 float* T_out, int32_t* nc_out, float* imp_w, uint32_t* imp_cnt, airgs_state** saved,
-                int forced_variant) {
+                int forced_shape) {
   if (saved) *saved = nullptr;
   int rc = check_gaussians(ctx, g);
   if (rc) return rc;
@@ -293,7 +314,8 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
   s->opacity = g->opacity_logit;
   s->sh = g->sh;
   s->rgb = rgb_out;
-  s->variant = forced_variant >= 0 ? forced_variant : choose_variant(ctx, N, s->n_pixels, n_views);
+  s->shape = forced_shape >= 0 ? forced_shape : choose_shape(ctx, N, s->n_pixels, n_views);
+  const ShapeParts parts = shape_parts(s->shape);
   cudaStream_t st = ctx->stream;
 
 #define ALLOC(ptr, count)                      \
@@ -448,7 +470,8 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
         TALLOC(ikeys_b, n_inst);
         TALLOC(ivals_b, n_inst);
         ALLOC(ivals_a, n_inst);  // may end up holding the sorted values
-        TALLOC(rs2, radix_scratch_bytes(n_inst, 1, ctx->num_sms) / sizeof(uint32_t) + 1);
+        const int sort_keys = sort_keys_of(parts.sort);
+        TALLOC(rs2, radix_scratch_bytes(n_inst, 1, ctx->num_sms, sort_keys) / sizeof(uint32_t) + 1);
         {
           StageScope sc(ctx, ST_EMIT);
           TALLOC(pieces, emit_piece_words(V * N, n_inst));
@@ -459,7 +482,7 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
         {
           StageScope sc(ctx, ST_TILE_SORT);
           CK(radix_sort_pairs(st, ctx->num_sms, ikeys_a, ivals_a, ikeys_b, ivals_b, n_inst, 1,
-                              bits_for(s->n_tiles), false, rs2, &in_b2));
+                              bits_for(s->n_tiles), false, rs2, &in_b2, sort_keys));
         }
         const uint32_t* skeys = in_b2 ? ikeys_b : ikeys_a;
         if (in_b2) {
@@ -471,7 +494,7 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
         } else {
           s->ids = ivals_a;
         }
-        const bool half_lists = (s->variant == 5 || s->variant == 6) && n_inst < (1ll << 28);
+        const bool half_lists = n_inst < (1ll << 28);
         if (!half_lists) {  // (the half-list pass writes the ranges itself)
           StageScope sc(ctx, ST_RANGES);
           CK(launch_tile_ranges(st, n_inst, skeys, s->ranges));
@@ -520,7 +543,7 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
   o.imp_cnt = imp_cnt;
   {
     StageScope sc(ctx, ST_BLEND_FWD);
-    CK(launch_blend_fwd(st, s->variant, ctx->num_sms, a, o));
+    CK(launch_blend_fwd(st, parts.fwd, ctx->num_sms, a, o));
   }
 #undef PREFILL_GRAD
 #undef ALLOC
@@ -591,7 +614,7 @@ int backward_impl(airgs_ctx* ctx, airgs_state* s, const float* dL, const float* 
   in.imp_cnt = imp_cnt;
   if (s->n_inst > 0) {
     StageScope sc(ctx, ST_BLEND_BWD);
-    CK(launch_blend_bwd(st, s->variant, ctx->num_sms, a, in));
+    CK(launch_blend_bwd(st, shape_parts(s->shape).bwd, ctx->num_sms, a, in));
   }
   StageScope sc(ctx, ST_PROJECT_BWD);
   CK(launch_project_bwd(st, s->n, s->sh_degree, s->means, s->log_scales, s->quats, s->opacity, s->sh, s->d_cams,
@@ -630,7 +653,7 @@ void load_tune_cache(airgs_ctx* ctx) {
   std::string key;
   int v;
   while (f >> key >> v)
-    if (v >= 0 && v < blend_variant_count()) ctx->tuned[key] = v;
+    if (v >= 0 && v < kShapes) ctx->tuned[key] = v;
 }
 
 void save_tune_cache(airgs_ctx* ctx) {
@@ -651,7 +674,7 @@ void airgs_default_config(airgs_config* c) {
   c->alpha_min = 1.0f / 255.0f;
   c->T_min = 1e-4f;
   c->bg[0] = c->bg[1] = c->bg[2] = 0.f;
-  c->blend_variant = -1;
+  c->kernel_shape = -1;
   c->sort_mode = -1;
   c->autotune_cache = nullptr;
   c->cull_lists = 1;
@@ -887,7 +910,7 @@ int airgs_state_stats(airgs_ctx* ctx, const airgs_state* s, airgs_stats* out) {
   out->n_pixels = s->n_pixels;
   out->pairs_forward = (int64_t)ctx->h_pinned[0];
   out->pairs_backward = (int64_t)ctx->h_pinned[2];
-  out->blend_variant = s->variant;
+  out->kernel_shape = s->shape;
   return AIRGS_OK;
 }
 
@@ -975,7 +998,8 @@ int airgs_sort_pairs(airgs_ctx* ctx, const uint32_t* keys_in, const uint32_t* va
   return AIRGS_OK;
 }
 
-int airgs_autotune(airgs_ctx* ctx, const airgs_camera* cams, int n_views, int* variant) {
+int airgs_autotune(airgs_ctx* ctx, const airgs_camera* cams, int n_views, int* shape, float* ms_default,
+                   float* ms_best) {
   if (!ctx) return AIRGS_E_ARG;
   if (ctx->sh_degree < 0) return fail(ctx, AIRGS_E_STATE, "set_anchor first");
   std::vector<CamDev> tmp;
@@ -983,46 +1007,81 @@ int airgs_autotune(airgs_ctx* ctx, const airgs_camera* cams, int n_views, int* v
   int rc = build_cams(ctx, cams, n_views, tmp, nt, np);
   if (rc) return rc;
   airgs_gaussians g = frame_gaussians(ctx);
-  float *rgb = nullptr, *dL = nullptr, *gm = nullptr, *gl = nullptr, *gq = nullptr, *go = nullptr, *gs = nullptr;
-  int K = (ctx->sh_degree + 1) * (ctx->sh_degree + 1);
-  int64_t n = std::max<int64_t>(ctx->n, 1);
-  if ((rc = dalloc(ctx, &rgb, 3 * np)) || (rc = dalloc(ctx, &dL, 3 * np)) || (rc = dalloc(ctx, &gm, 3 * n)) ||
+  const int K = (ctx->sh_degree + 1) * (ctx->sh_degree + 1);
+  const int64_t n = std::max<int64_t>(ctx->n, 1);
+  // the buffers of a training step: image, a constant target, parameter gradients, usage frequency, loss
+  float *rgb = nullptr, *target = nullptr, *gm = nullptr, *gl = nullptr, *gq = nullptr, *go = nullptr,
+        *gs = nullptr, *impw = nullptr, *loss = nullptr;
+  uint32_t* impc = nullptr;
+  struct Free {
+    airgs_ctx* c;
+    std::vector<void*> p;
+    ~Free() {
+      for (void* q : p) dfree(c, q);
+    }
+  } fr{ctx, {}};
+  if ((rc = dalloc(ctx, &rgb, 3 * np)) || (rc = dalloc(ctx, &target, 3 * np)) || (rc = dalloc(ctx, &gm, 3 * n)) ||
       (rc = dalloc(ctx, &gl, 3 * n)) || (rc = dalloc(ctx, &gq, 4 * n)) || (rc = dalloc(ctx, &go, n)) ||
-      (rc = dalloc(ctx, &gs, (size_t)K * 3 * n)))
+      (rc = dalloc(ctx, &gs, (size_t)K * 3 * n)) || (rc = dalloc(ctx, &impw, n)) || (rc = dalloc(ctx, &impc, n)) ||
+      (rc = dalloc(ctx, &loss, 1)))
     return rc;
-  CK(cudaMemsetAsync(dL, 0, 12 * np, ctx->stream));
+  fr.p = {rgb, target, gm, gl, gq, go, gs, impw, impc, loss};
+  CK(cudaMemsetAsync(target, 0x3F, 12 * np, ctx->stream));  // every channel 0x3F3F3F3F = 0.747
+  CK(cudaMemsetAsync(impw, 0, 4 * n, ctx->stream));
+  CK(cudaMemsetAsync(impc, 0, 4 * n, ctx->stream));
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  int best = 0;
-  float best_ms = 1e30f;
-  for (int v = 0; v < blend_variant_count() && rc == AIRGS_OK; ++v) {
-    float ms_sum = 0.f;
-    for (int rep = 0; rep < 3 && rc == AIRGS_OK; ++rep) {
-      // one forward + backward with this variant (the first repetition warms up)
+  // one training step with the given shape: best of 3 timed repetitions after a warm-up
+  auto time_shape = [&](int shp, float& ms) -> int {
+    ms = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
       airgs_state* s = nullptr;
       cudaEventRecord(e0, ctx->stream);
-      rc = render_impl(ctx, &g, cams, n_views, rgb, nullptr, nullptr, nullptr, nullptr, &s, v);
-      if (rc == AIRGS_OK) rc = backward_impl(ctx, s, dL, nullptr, nullptr, gm, gl, gq, go, gs, nullptr, nullptr);
+      int r = render_impl(ctx, &g, cams, n_views, rgb, nullptr, nullptr, nullptr, nullptr, &s, shp);
+      if (r == AIRGS_OK) r = backward_impl(ctx, s, nullptr, target, loss, gm, gl, gq, go, gs, impw, impc);
       cudaEventRecord(e1, ctx->stream);
-      cudaEventSynchronize(e1);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (rep > 0) ms_sum += ms;
+      const cudaError_t e = cudaEventSynchronize(e1);
       release_state(ctx, s);
+      if (r != AIRGS_OK) return r;
+      if (e != cudaSuccess) return fail(ctx, AIRGS_E_CUDA, "autotune: %s", cudaGetErrorString(e));
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (rep > 0) ms = std::min(ms, t);
     }
-    if (rc == AIRGS_OK && ms_sum < best_ms) {
-      best_ms = ms_sum;
-      best = v;
+    return AIRGS_OK;
+  };
+  // coordinate search from shape 0: the backward's shapes, then the forward's,
+  // then the sort's keys per thread, each with the other parts at the best so far
+  ShapeParts best{0, 0, 0};
+  float best_ms = 0.f, def_ms = 0.f;
+  rc = time_shape(0, def_ms);
+  best_ms = def_ms;
+  for (int axis = 0; axis < 3 && rc == AIRGS_OK; ++axis) {
+    const int count = axis == 0 ? kBwdShapes : axis == 1 ? kFwdShapes : kSortShapes;
+    const ShapeParts base = best;
+    for (int c = 0; c < count && rc == AIRGS_OK; ++c) {
+      ShapeParts p = base;
+      int& slot = axis == 0 ? p.bwd : axis == 1 ? p.fwd : p.sort;
+      if (slot == c) continue;  // already timed
+      slot = c;
+      float ms = 0.f;
+      rc = time_shape(shape_index(p.fwd, p.bwd, p.sort), ms);
+      if (rc == AIRGS_OK && ms < best_ms) {
+        best_ms = ms;
+        best = p;
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  for (void* p : {(void*)rgb, (void*)dL, (void*)gm, (void*)gl, (void*)gq, (void*)go, (void*)gs}) dfree(ctx, p);
   if (rc) return rc;
-  ctx->tuned[tune_key(ctx->n, np, n_views)] = best;
+  const int chosen = shape_index(best.fwd, best.bwd, best.sort);
+  ctx->tuned[tune_key(ctx->n, np, n_views)] = chosen;
   save_tune_cache(ctx);
-  if (variant) *variant = best;
+  if (shape) *shape = chosen;
+  if (ms_default) *ms_default = def_ms;
+  if (ms_best) *ms_best = best_ms;
   return AIRGS_OK;
 }
 
@@ -1200,7 +1259,7 @@ int airgs_measure_smem_peak(airgs_ctx* ctx, double* tbs) {
 
 int64_t airgs_kernel_launch_count(void) { return g_launches.load(); }
 
-int airgs_blend_variant_count(void) { return blend_variant_count(); }
-const char* airgs_blend_variant_name(int variant) { return blend_variant_name(variant); }
+int airgs_shape_count(void) { return kShapes; }
+const char* airgs_shape_name(int shape) { return shape_name(shape); }
 
 }  // extern "C"

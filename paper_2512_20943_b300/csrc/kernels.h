@@ -33,10 +33,12 @@ cudaError_t launch_scatter(cudaStream_t st, int64_t total, int64_t n, const Proj
 cudaError_t launch_sort_tiles(cudaStream_t st, int64_t n_tiles, const uint2* ranges, const uint32_t* big_list,
                               int64_t n_big, const uint2* pairs, uint32_t* vals);
 
-size_t radix_scratch_bytes(int64_t seg_len, int n_seg, int num_sms);
+// keys: radix keys per thread (6, 8 or 12; 0 = the default for the segment
+// count); the scratch size and the sort must be given the same value.
+size_t radix_scratch_bytes(int64_t seg_len, int n_seg, int num_sms, int keys = 0);
 cudaError_t radix_sort_pairs(cudaStream_t st, int num_sms, uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b,
                              uint32_t* vals_b, int64_t seg_len, int n_seg, int key_bits, bool identity_vals,
-                             uint32_t* scratch, bool* result_in_b);
+                             uint32_t* scratch, bool* result_in_b, int keys = 0);
 
 // One pass: the digit of bits [shift, min(shift + 8, key_bits)).
 cudaError_t radix_sort_pass(cudaStream_t st, int num_sms, const uint32_t* keys_in, const uint32_t* vals_in,
@@ -96,7 +98,7 @@ struct BlendArgs {
   int* work_counter;
   unsigned long long* pair_counter;
   unsigned long long* pair_total;  // nullable: cumulative counter of the context
-  unsigned long long* exec_total;  // nullable: cumulative lane evaluations actually issued (culling variants)
+  unsigned long long* exec_total;  // nullable: cumulative lane evaluations actually issued (32 per block)
   const uint2* hl;                 // nullable: half-tile lists of (Gaussian id, full-list position | block mask)
   uint2* hl_mut;                   // the same lists, written by the compacting forward (block masks)
   const uint2* hranges;            // [2][tiles] ranges into hl (top halves, then bottom halves)
@@ -123,16 +125,27 @@ struct BwdIn {
   uint32_t* imp_cnt;
 };
 
-int blend_variant_count();
-const char* blend_variant_name(int v);
-cudaError_t launch_blend_fwd(cudaStream_t st, int variant, int num_sms, const BlendArgs& a, const FwdOut& o);
-cudaError_t launch_blend_bwd(cudaStream_t st, int variant, int num_sms, const BlendArgs& a, const BwdIn& in);
-cudaError_t launch_blend_fwd_cull(cudaStream_t st, int num_sms, int blocks_per_warp, bool compact, const BlendArgs& a,
-                                  const FwdOut& o);
-cudaError_t launch_blend_bwd_cull(cudaStream_t st, int num_sms, int blocks_per_warp, bool compact, const BlendArgs& a,
-                                  const BwdIn& in);
-cudaError_t launch_blend_fwd_warp(cudaStream_t st, int num_sms, const BlendArgs& a, const FwdOut& o);
-cudaError_t launch_blend_bwd_warp(cudaStream_t st, int num_sms, const BlendArgs& a, const BwdIn& in);
+// Kernel shapes the autotuner searches: compiled instantiations of the blend
+// forward and backward (staged list entries per batch, warps per SM: the
+// register bound) and keys per thread of the instances' radix sort.  A shape
+// index packs (forward f, backward b, sort k) as f + kFwdShapes (b +
+// kBwdShapes k); shape 0 (every part 0) is the default.
+constexpr int kFwdShapes = 5;   // forward (batch, warps): (32, 32) (16, 32) (64, 32) (32, 28) (32, 24)
+constexpr int kBwdShapes = 5;   // backward (batch, warps): (32, 28) (16, 28) (64, 28) (32, 24) (32, 32)
+constexpr int kSortShapes = 3;  // instance sort keys per thread: 8, 6, 12
+constexpr int kShapes = kFwdShapes * kBwdShapes * kSortShapes;
+struct ShapeParts {
+  int fwd, bwd, sort;
+};
+inline ShapeParts shape_parts(int shape) {
+  if (shape < 0 || shape >= kShapes) shape = 0;
+  return ShapeParts{shape % kFwdShapes, (shape / kFwdShapes) % kBwdShapes, shape / (kFwdShapes * kBwdShapes)};
+}
+inline int shape_index(int fwd, int bwd, int sort) { return fwd + kFwdShapes * (bwd + kBwdShapes * sort); }
+inline int sort_keys_of(int sort_shape) { return sort_shape == 1 ? 6 : sort_shape == 2 ? 12 : 8; }
+const char* shape_name(int shape);
+cudaError_t launch_blend_fwd(cudaStream_t st, int fwd_shape, int num_sms, const BlendArgs& a, const FwdOut& o);
+cudaError_t launch_blend_bwd(cudaStream_t st, int bwd_shape, int num_sms, const BlendArgs& a, const BwdIn& in);
 
 cudaError_t launch_project_bwd(cudaStream_t st, int64_t n, int sh_degree, const float* means,
                                const float* log_scales, const float* quats, const float* opacity_logit,

@@ -682,9 +682,16 @@ __global__ void k_tile_ranges(int64_t n_inst, const uint32_t* __restrict__ keys,
 }
 
 // ------------------------------------------------------------------ host side
-static SortGeom make_geom(int64_t seg_len, int n_seg, int num_sms) {
+// keys: keys per thread of a CTA tile (6, 8 or 12; 0 = the default for the
+// segment count).
+static int radix_keys(int n_seg, int keys) {
+  if (keys == 6 || keys == 8 || keys == 12) return keys;
+  return n_seg > 1 ? RS_ITEMS_SEG : RS_ITEMS;
+}
+
+static SortGeom make_geom(int64_t seg_len, int n_seg, int num_sms, int keys = 0) {
   SortGeom g;
-  g.tile = (int64_t)RS_THREADS * (n_seg > 1 ? RS_ITEMS_SEG : RS_ITEMS);
+  g.tile = (int64_t)RS_THREADS * radix_keys(n_seg, keys);
   g.seg_len = seg_len;
   g.n_seg = n_seg;
   g.tiles_seg = (seg_len + g.tile - 1) / g.tile;
@@ -696,8 +703,8 @@ static SortGeom make_geom(int64_t seg_len, int n_seg, int num_sms) {
 }
 
 // counts [n_seg][RS_RADIX][ctas_seg], then totals [n_seg][RS_RADIX]
-size_t radix_scratch_bytes(int64_t seg_len, int n_seg, int num_sms) {
-  SortGeom g = make_geom(seg_len, n_seg, num_sms);
+size_t radix_scratch_bytes(int64_t seg_len, int n_seg, int num_sms, int keys) {
+  SortGeom g = make_geom(seg_len, n_seg, num_sms, keys);
   return (size_t)n_seg * RS_RADIX * (g.ctas_seg + 1) * sizeof(uint32_t);
 }
 
@@ -708,10 +715,11 @@ size_t radix_scratch_bytes(int64_t seg_len, int n_seg, int num_sms) {
 // used as a buffer by later passes).
 cudaError_t radix_sort_pairs(cudaStream_t st, int num_sms, uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b,
                              uint32_t* vals_b, int64_t seg_len, int n_seg, int key_bits, bool identity_vals,
-                             uint32_t* scratch, bool* result_in_b) {
+                             uint32_t* scratch, bool* result_in_b, int keys) {
   *result_in_b = false;
   if (seg_len == 0 || n_seg == 0) return cudaSuccess;
-  SortGeom g = make_geom(seg_len, n_seg, num_sms);
+  SortGeom g = make_geom(seg_len, n_seg, num_sms, keys);
+  const int kpt = radix_keys(n_seg, keys);
   int grid = g.ctas_seg * n_seg;
   int passes = (key_bits + 7) / 8;
   uint32_t *ki = keys_a, *vi = vals_a, *ko = keys_b, *vo = vals_b;
@@ -725,13 +733,11 @@ cudaError_t radix_sort_pairs(cudaStream_t st, int num_sms, uint32_t* keys_a, uin
     if (e == cudaSuccess)
       e = launch_serialised(k_rs_spine, dim3((n_seg * RS_RADIX + 7) / 8), dim3(256), 0, st, scratch, totals, g.ctas_seg,
                             n_seg * RS_RADIX);
-    if (e == cudaSuccess)
-      e = (g.tile == (int64_t)RS_THREADS * RS_ITEMS
-               ? launch_serialised(k_rs_downsweep<RS_ITEMS>, dim3(grid), dim3(RS_THREADS), 0, st, (const uint32_t*)ki,
-                                   vin, ko, vo, g, shift, dmask, (const uint32_t*)scratch, (const uint32_t*)totals)
-               : launch_serialised(k_rs_downsweep<RS_ITEMS_SEG>, dim3(grid), dim3(RS_THREADS), 0, st,
-                                   (const uint32_t*)ki, vin, ko, vo, g, shift, dmask, (const uint32_t*)scratch,
-                                   (const uint32_t*)totals));
+    if (e == cudaSuccess) {
+      auto down = kpt == 12 ? k_rs_downsweep<12> : kpt == 8 ? k_rs_downsweep<8> : k_rs_downsweep<6>;
+      e = launch_serialised(down, dim3(grid), dim3(RS_THREADS), 0, st, (const uint32_t*)ki, vin, ko, vo, g, shift,
+                            dmask, (const uint32_t*)scratch, (const uint32_t*)totals);
+    }
     count_launches(3);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return e;

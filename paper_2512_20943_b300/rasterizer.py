@@ -32,7 +32,7 @@ class RasterConfig:
     alpha_min: float = 1.0 / 255.0
     T_min: float = 1e-4
     bg: tuple = (0.0, 0.0, 0.0)
-    blend_variant: int = -1  # -1: autotuned choice (default variant until tuned)
+    kernel_shape: int = -1   # -1: the autotuned choice for the workload (shape 0 until tuned), else a fixed shape
     sort_mode: int = -1      # 0: global radix ordering; 1: per-tile ordering when lists fit a CTA; -1: per-tile for
                              # batches of at most 65536 (view, Gaussian) pairs, radix above
     autotune_cache: str | None = None
@@ -43,7 +43,7 @@ class RasterConfig:
         c.dilation, c.alpha_max, c.alpha_min, c.T_min = self.dilation, self.alpha_max, self.alpha_min, self.T_min
         for k in range(3):
             c.bg[k] = float(self.bg[k])
-        c.blend_variant = int(self.blend_variant)
+        c.kernel_shape = int(self.kernel_shape)
         c.sort_mode = int(self.sort_mode)
         c.autotune_cache = self.autotune_cache.encode() if self.autotune_cache else None
         c.cull_lists = 1 if self.cull_lists else 0
@@ -394,7 +394,7 @@ class Rasterizer:
         s = airgs_stats()
         self._check(self.lib.airgs_state_stats(self.ctx, state.handle, ctypes.byref(s)))
         return dict(n_instances=s.n_instances, n_tiles=s.n_tiles, n_pixels=s.n_pixels,
-                    pairs_forward=s.pairs_forward, pairs_backward=s.pairs_backward, blend_variant=s.blend_variant)
+                    pairs_forward=s.pairs_forward, pairs_backward=s.pairs_backward, kernel_shape=s.kernel_shape)
 
     def state_projection(self, state: RenderState, view: int):
         n = state.n
@@ -424,10 +424,15 @@ class Rasterizer:
                                               key_bits))
         return ko, vo
 
-    def autotune(self, cams) -> int:
-        v = ctypes.c_int()
-        self._check(self.lib.airgs_autotune(self.ctx, camera_array(cams), len(cams), ctypes.byref(v)))
-        return v.value
+    def autotune(self, cams, report: bool = False):
+        """Search the compiled kernel shapes for this workload (the current
+        frame's Gaussians, these cameras) by timing training steps; later
+        renders of the workload use the choice.  Returns the shape index, or
+        with report=True (shape, ms of shape 0, ms of the choice)."""
+        v, t0, t1 = ctypes.c_int(), ctypes.c_float(), ctypes.c_float()
+        self._check(self.lib.airgs_autotune(self.ctx, camera_array(cams), len(cams), ctypes.byref(v),
+                                            ctypes.byref(t0), ctypes.byref(t1)))
+        return (v.value, t0.value, t1.value) if report else v.value
 
     def set_profiling(self, enabled: bool = True, blend_only: bool = False):
         """Time each pipeline stage with CUDA events on the context's stream
@@ -466,9 +471,10 @@ class Rasterizer:
         return v.value
 
     @staticmethod
-    def variant_names():
+    def shape_names():
+        """Names of the compiled kernel shapes (index 0 is the default)."""
         lib = load_library()
-        return [lib.airgs_blend_variant_name(i).decode() for i in range(lib.airgs_blend_variant_count())]
+        return [lib.airgs_shape_name(i).decode() for i in range(lib.airgs_shape_count())]
 
 
 # ---------------------------------------------------------------- autograd

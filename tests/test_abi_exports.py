@@ -46,12 +46,16 @@ def test_binding_constants_equal_the_header():
         assert getattr(_abi, name) == eval(expr, {}), name  # plain integer literals and shifts only
 
 
-def test_variant_table_without_gpu(lib_path):
+def test_shape_table_without_gpu(lib_path):
+    """Shape 0 is the default; every shape has a distinct name naming its
+    forward and backward (batch/warps) and the sort's keys per thread."""
     from paper_2512_20943_b300 import _abi
     lib = _abi.load_library()
-    n = lib.airgs_blend_variant_count()
-    assert n >= 3
-    assert all(lib.airgs_blend_variant_name(i) for i in range(n))
+    n = lib.airgs_shape_count()
+    names = [lib.airgs_shape_name(i).decode() for i in range(n)]
+    assert n == 75 and len(set(names)) == n
+    assert names[0] == "fwd 32/32 bwd 32/28 keys 8"
+    assert lib.airgs_shape_name(n) == b"" and lib.airgs_shape_name(-1) == b""
 
 
 def test_create_without_gpu_fails_cleanly(lib_path):

@@ -145,19 +145,21 @@ def test_per_frame_training_20_views_full_size():
 
 def test_large_scene_16_views_4k_full_size():
     """2M Gaussians SH3, 16 views at 3840x2160 in one launch with importance,
-    after autotuning the blend variant; forward windows and gradients on one."""
+    after autotuning the kernel shape; forward windows and gradients on one."""
     from paper_2512_20943_b300 import Rasterizer
     g, cams = synthetic.large_scene()
     rast = Rasterizer()
     t = to_cuda(g)
     rast.set_anchor(*params(t))
-    variant = rast.autotune(cams)
-    assert 0 <= variant < len(Rasterizer.variant_names())
+    shape, ms_default, ms_best = rast.autotune(cams, report=True)
+    assert 0 <= shape < len(Rasterizer.shape_names())
+    assert 0.0 < ms_best <= ms_default
     windows = [no_window()] * 16
     windows[8] = (1880, 1040, 1944, 1104)
     run_case(rast, g, cams, windows, seed=3)
     # usage frequency over all 16 views: forward and backward replay agree
     res = rast.render_gaussians(*params(t), cams, importance=True, save=True)
+    assert rast.stats(res.state)["kernel_shape"] == shape  # later renders of the workload run the choice
     iw = torch.zeros_like(res.importance_w)
     ic = torch.zeros_like(res.importance_cnt)
     rast.render_backward(res.state, torch.zeros_like(res.rgb), importance=(iw, ic))
