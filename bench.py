@@ -27,9 +27,13 @@ against the derived FP32 peak and the library's FFMA probe; `roofline.smem`: sha
 B/clock and the library's LDS probe; DRAM traffic and shared-memory bytes come
 from a committed ncu capture and are null once the kernel's sources change);
 `e2e` (the same steps fed from pinned host buffers through the double-buffered
-HostFeed, every loss read back); `cpu_baseline` (the FP64 oracle on a bounded
-sample, one host core); `serving` (served-view throughput and p50/p99 latency
-of the continuous-batching engine against a one-view-per-call loop).
+HostFeed, every loss read back); `serving` (served-view throughput and p50/p99
+latency of the continuous-batching engine against a one-view-per-call loop,
+over a 10-second request stream); `configs` (the plain 2k forward, the
+per-frame 200k x 20-view step and the large 2M x 16 x 4K step with its kernel
+shape autotuned, each timed the same way with its roofline fraction);
+`cpu_baseline` (the FP64 oracle on this host: single-threaded, and on all
+cores through its OpenMP timing build, for configs 1-3).
 `--workload plain|per_frame|large` measures the other workload shapes the same
 way; `--impl reference` times the oracle instead.
 """
@@ -253,32 +257,71 @@ def train_step(rast, wl, frame, imp, map_tensor=None, target=None):
 
 
 # ---------------------------------------------------------------- CPU baseline (oracle)
-def oracle_sample(wl_g, arc, view, frame_map, lo, hi, crop):
-    """fwd+bwd of the oracle on a centred crop x crop window of one view,
-    after decoding/applying one frame; returns (seconds, pixels)."""
+def _crop(cam, w, h):
+    """The centred w x h window of a camera (principal point moved with it)."""
+    c = dict(cam)
+    c["cx"] = c["cx"] - (c["width"] - w) / 2.0
+    c["cy"] = c["cy"] - (c["height"] - h) / 2.0
+    c["width"], c["height"] = w, h
+    return c
+
+
+def oracle_step(kind, impl, crop=None, frame_map=None, lo=None, hi=None, g=None, cams=None):
+    """One sample of a workload on the FP64 oracle: (seconds, pixels).  kind
+    "plain": the forward of config 1's scene; "train": decode/apply of one
+    update map (when given) and the forward + L1 backward of the given view(s).
+    impl: the oracle module (single-threaded) or its OpenMP timing build."""
     import oracle
-    g = synthetic.widen(wl_g)
+    w = synthetic.widen(g)
     t0 = time.perf_counter()
-    m, q = oracle.decode_apply(frame_map, lo.astype(np.float64), hi.astype(np.float64), g["means"], g["quats"])
-    g["means"], g["quats"] = m, q
-    cam = dict(arc[view])
-    cam["cx"] = cam["cx"] - (cam["width"] - crop) / 2.0
-    cam["cy"] = cam["cy"] - (cam["height"] - crop) / 2.0
-    cam["width"] = cam["height"] = crop
-    out = oracle.render(g, [cam])
-    tgt = np.random.default_rng(1).uniform(0, 1, (3, crop, crop))
-    _, dL = oracle.l1_loss_grad(out["rgb"], [tgt])
-    oracle.render_backward(g, [cam], dL)
-    return time.perf_counter() - t0, crop * crop
+    if frame_map is not None:
+        w["means"], w["quats"] = oracle.decode_apply(frame_map, lo.astype(np.float64), hi.astype(np.float64),
+                                                     w["means"], w["quats"])
+    if crop is not None:
+        cams = [_crop(c, min(crop, c["width"]), min(crop, c["height"])) for c in cams]
+    out = impl.render(w, cams)
+    if kind == "train":
+        tgt = [np.random.default_rng(1).uniform(0, 1, (3, c["height"], c["width"])) for c in cams]
+        _, dL = oracle.l1_loss_grad(out["rgb"], tgt)
+        impl.render_backward(w, cams, dL)
+    return time.perf_counter() - t0, sum(int(c["width"]) * int(c["height"]) for c in cams)
 
 
 def cpu_baseline_line(crop=512):
-    g, arc = synthetic.streaming_scene(N_GAUSS, 0)
+    """The FP64 oracle timed on this host: single-threaded as it stands (the
+    checker, on 512x512 crops so that it stays within seconds) and through its
+    OpenMP timing build on all the host's cores (full views), for config 1 in
+    full (plain 2k forward at 128x128), config 2 for one view (200k SH3, fwd + L1
+    bwd) and config 3 for one frame and one view (300k SH3, decode/apply + fwd +
+    L1 bwd).  value = config 3 on all cores, in the headline metric's unit."""
+    import oracle
+    from oracle import timing
+    cores = os.cpu_count()
+    usable = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else cores
+    g1, c1 = synthetic.plain_forward_scene()
+    g2, arc2 = synthetic.per_frame_training_scene()
+    g3, arc3 = synthetic.streaming_scene(N_GAUSS, 0)
     m, lo, hi = synthetic.update_map(N_GAUSS, 1000, size=MAP_SIZE)
-    secs, px = oracle_sample(g, arc, 0, m, lo, hi, crop)
-    return {"value": px / secs / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"frame 0 decode/apply + fwd+bwd (L1) of view 0 cropped to the central {crop}x{crop} "
-                      f"window, 300k Gaussians SH3, FP64 single-threaded; {secs:.1f} s"}
+    samples = {
+        "config1": dict(kind="plain", g=g1, cams=c1),
+        "config2": dict(kind="train", g=g2, cams=arc2[:1]),
+        "config3": dict(kind="train", g=g3, cams=arc3[:1], frame_map=m, lo=lo, hi=hi),
+    }
+    res = {"single_thread": {}, "all_cores": {}}
+    for name, kw in samples.items():
+        crop1 = None if name == "config1" else crop
+        secs, px = oracle_step(impl=oracle, crop=crop1, **kw)
+        res["single_thread"][name] = {"mpix_per_s": px / secs / 1e6, "seconds": secs, "pixels": px,
+                                      "sample": "full" if crop1 is None else f"centred {crop}x{crop} crop"}
+        secs, px = oracle_step(impl=timing, **kw)
+        res["all_cores"][name] = {"mpix_per_s": px / secs / 1e6, "seconds": secs, "pixels": px, "sample": "full"}
+    value = res["all_cores"]["config3"]["mpix_per_s"]
+    return {"value": value, "unit": UNIT, "cores": cores, "usable_cores": usable, "threads": timing.threads(),
+            "kind": "oracle",
+            "sample": "config 3: frame 0's 768x768 uint16 map decoded/applied to the 300k SH3 anchor, then fwd + "
+                      "L1 bwd of view 0 (1352x1014) on all host cores (OpenMP timing build of the oracle's source); "
+                      "single_thread/all_cores give configs 1-3 (config 1 forward only)",
+            **res}
 
 
 def run_reference(args):
@@ -291,7 +334,8 @@ def run_reference(args):
     for step in range(args.warmup + args.steps):
         m, lo, hi = synthetic.update_map(N_GAUSS, 1000 + step, size=MAP_SIZE)
         view = (VIEWS_PER_STEP * step) % len(arc)
-        secs, px = oracle_sample(g, arc, view, m, lo, hi, crop)
+        import oracle
+        secs, px = oracle_step("train", oracle, crop=crop, frame_map=m, lo=lo, hi=hi, g=g, cams=[arc[view]])
         if step >= args.warmup:
             times.append(secs)
             pix += px
@@ -304,7 +348,7 @@ def run_reference(args):
         "config": {"workload": "streaming training, 300k Gaussians SH3, 8 views 1352x1014 per step, "
                                "768x768 uint16 update maps; each reference step is one view cropped to 256x256",
                    "global_batch": 1, "seq_len": crop * crop, "parallelism": "none"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
                          "sample": f"per step: decode/apply one frame + fwd+bwd of one view cropped to {crop}x{crop}"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -531,6 +575,13 @@ def run_ours(args):
         line["e2e"] = e2e
     if not args.no_serving and world == 1:
         line["serving"] = run_serving(args, device)
+    if not args.no_configs and world == 1:
+        # the other workload shapes, each measured like the streaming step (plain 2k forward,
+        # per-frame 200k x 20 views, large 2M x 16 x 4K with the kernel shape autotuned)
+        line["configs"] = {}
+        for kind, (k_steps, k_warm) in CONFIG_STEPS.items():
+            c = measure_workload(kind, k_steps, k_warm, device=device)
+            line["configs"][kind] = {k: c[k] for k in CONFIG_KEEP if k in c}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_line()
     if rank == 0:
@@ -549,22 +600,15 @@ WORKLOADS = {
 }
 
 
-def run_config(args):
-    """The other workload shapes with the same timing, stage profiling and
-    roofline (one GPU; replicas under torchrun like the streaming step).  A step
-    is one batched render (plain) or render + fused L1 backward (per-frame,
-    large) of all the workload's views."""
+def measure_workload(kind, steps, warmup, shape=-1, sort_mode=-1, autotune=False, world=1, device=None):
+    """One of the other workload shapes, timed like the streaming step: a step
+    is one batched render (plain) or render + fused L1 backward with importance
+    (per-frame, large) of all the workload's views; CUDA events on the
+    library's stream around each step, nvidia-smi clocks sampled through the
+    warm-up and the timed region, a per-stage profiling pass after it.
+    Returns the bench-line fields of the workload."""
     import torch
-    world, rank, local = dist_setup()
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    else:
-        torch.cuda.set_device(0)
-    device = torch.device("cuda", torch.cuda.current_device())
     from paper_2512_20943_b300 import RasterConfig, Rasterizer
-    kind = args.workload
     if kind == "plain":
         g, cams = synthetic.plain_forward_scene()
     elif kind == "per_frame":
@@ -576,17 +620,20 @@ def run_config(args):
     p = [torch.from_numpy(np.ascontiguousarray(g[k])).to(device)
          for k in ("means", "log_scales", "quats", "opacity_logit", "sh")]
     stream = torch.cuda.Stream()
-    rast = Rasterizer(RasterConfig(kernel_shape=args.shape, sort_mode=args.sort_mode), stream=stream)
+    rast = Rasterizer(RasterConfig(kernel_shape=shape, sort_mode=sort_mode), stream=stream)
     target = None
     if backward:
         target = torch.from_numpy(np.concatenate([x.reshape(-1) for x in synthetic.target_images(cams, 1)])).to(device)
     imp = None
     if backward:  # importance counts also give the blended pairs of the roofline
         imp = (torch.zeros(n, dtype=torch.float32, device=device), torch.zeros(n, dtype=torch.int32, device=device))
+    tuned = None
     with torch.cuda.stream(stream):
-        if kind == "large" or args.autotune:
+        if kind == "large" or autotune:
             rast.set_anchor(*p)
-            rast.autotune(cams)
+            shp, ms0, ms1 = rast.autotune(cams, report=True)
+            tuned = {"shape": Rasterizer.shape_names()[shp], "ms_shape0": ms0, "ms_chosen": ms1,
+                     "search": "coordinate search over the compiled shapes, training step timed (best of 3)"}
 
     def step():
         res = rast.render_gaussians(*p, cams, save=backward)
@@ -600,7 +647,7 @@ def run_config(args):
     sampler.start()
     time.sleep(0.3)
     with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             step()
     stream.synchronize()
     blended0 = int(imp[1].sum(dtype=torch.int64)) if imp is not None else 0
@@ -610,9 +657,9 @@ def run_config(args):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     with torch.cuda.stream(stream):
-        for k in range(args.steps):
+        for k in range(steps):
             ev[k][0].record(stream)
             step()
             ev[k][1].record(stream)
@@ -621,8 +668,8 @@ def run_config(args):
     clocks = sampler.stop()
     launches = Rasterizer.kernel_launch_count() - launches0
     timed = rast.stage_times()
-    blended = (int(imp[1].sum(dtype=torch.int64)) - blended0) / args.steps if imp is not None else None
-    n_prof = min(args.steps, PROFILE_STEPS)
+    blended = (int(imp[1].sum(dtype=torch.int64)) - blended0) / steps if imp is not None else None
+    n_prof = min(steps, PROFILE_STEPS)
     rast.set_profiling(True)
     rast.stage_times()
     with torch.cuda.stream(stream):
@@ -632,7 +679,7 @@ def run_config(args):
     rast.set_profiling(False)
     total_ms = barrier_max(world, sum(a.elapsed_time(b) for a, b in ev), device)
     px = sum(int(c["width"]) * int(c["height"]) for c in cams)
-    value = whole_job_value(world, px, args.steps, total_ms)
+    value = whole_job_value(world, px, steps, total_ms)
     ms, nl = stages["ms"], stages["launches"]
     ms_t, nl_t = timed["ms"], timed["launches"]
     stage_lines = {name: {"ms_per_launch": ms[name] / nl[name], "launches_per_step": nl[name] / n_prof,
@@ -644,6 +691,10 @@ def run_config(args):
         res = rast.render_gaussians(*p, cams, save=True)
         st = rast.stats(res.state)
         res.state.release()
+        if blended is None:  # a forward-only step: its blended pairs from one untimed render with importance
+            probe = rast.render_gaussians(*p, cams, importance=True)
+            blended = float(probe.importance_cnt.sum(dtype=torch.int64))
+            del probe
     n_tiles = sum(math.ceil(int(c["width"]) / 16) * math.ceil(int(c["height"]) / 16) for c in cams)
     add_stage_bandwidths(stage_lines, ms, nl, n, len(cams), st["n_instances"], bits_for_tiles(n_tiles),
                          sh_floats=3 * (int(g["sh_degree"]) + 1) ** 2)
@@ -653,7 +704,7 @@ def run_config(args):
     fp32_peak = n_sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     line = {
         "metric": ("fwd+bwd" if backward else "fwd") + " Mpix/s", "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "steps": steps, "warmup": warmup, "ms_per_step": total_ms / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOADS[kind], "global_batch": len(cams) * world, "seq_len": px // len(cams),
                    "parallelism": f"replicas x{world}" if world > 1 else "none"},
@@ -662,26 +713,60 @@ def run_config(args):
                        "region only the blend stages are)",
         "kernel_shape": Rasterizer.shape_names()[st["kernel_shape"]], "instances_per_step": st["n_instances"],
     }
+    if tuned:
+        line["autotune"] = tuned
     for name, key, fl in (("blend_fwd", "forward", FLOPS_BLEND_FWD), ("blend_bwd", "backward", FLOPS_BLEND_BWD)):
         if name in stage_lines and blended is not None and ms_t[name]:
-            flops = timed["pairs_" + key] * FLOPS_TEST + blended * args.steps * fl
+            flops = timed["pairs_" + key] * FLOPS_TEST + blended * steps * fl
             t_s = ms_t[name] / 1e3  # the blend stage's live event time in the timed region
             stage_lines[name]["tflops_algorithmic"] = flops / t_s / 1e12
             stage_lines[name]["frac_fp32_peak"] = flops / t_s / 1e12 / fp32_peak
         if name in stage_lines:
             stage_lines[name]["definition_pairs_per_launch"] = timed["pairs_" + key] / max(1, nl_t[name])
             stage_lines[name]["issued_evals_per_launch"] = timed["issued_" + key] / max(1, nl_t[name])
-    if backward and "tflops_algorithmic" in stage_lines.get("blend_bwd", {}):
-        bw = stage_lines["blend_bwd"]
-        line["roofline"] = {"bound": "alu", "achieved": bw["tflops_algorithmic"], "peak": fp32_peak, "unit": "TFLOP/s",
-                            "frac": bw["frac_fp32_peak"], "traffic": None, "kernel": "k_blend_bwd_cull",
+    dom = max(stage_lines, key=lambda k: stage_lines[k]["share"])
+    if dom in ("blend_bwd", "blend_fwd") and "tflops_algorithmic" in stage_lines[dom]:
+        bl = stage_lines[dom]
+        line["roofline"] = {"bound": "alu", "achieved": bl["tflops_algorithmic"], "peak": fp32_peak,
+                            "unit": "TFLOP/s", "frac": bl["frac_fp32_peak"], "traffic": None,
+                            "kernel": "k_blend_bwd" if dom == "blend_bwd" else "k_blend_fwd",
                             "peak_source": f"derived: {n_sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                            f"{sm_max:g} MHz", "traffic_note": "no ncu capture of this workload"}
+    else:
+        gbs = stage_lines[dom].get("gbs")
+        line["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                            "frac": (gbs / peaks["hbm_gbs"]) if gbs else None, "traffic": None, "kernel": dom}
+    line["dominant_stage"] = dom
+    del rast, p, target, imp
+    torch.cuda.empty_cache()
+    return line
+
+
+def run_config(args):
+    """The other workload shapes with the same timing, stage profiling and
+    roofline (one GPU; replicas under torchrun like the streaming step)."""
+    import torch
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    device = torch.device("cuda", torch.cuda.current_device())
+    line = measure_workload(args.workload, args.steps, args.warmup, args.shape, args.sort_mode, args.autotune, world,
+                            device)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+# steps of the other workload shapes inside the default run (their timed work stays a few seconds)
+CONFIG_STEPS = {"plain": (20, 5), "per_frame": (10, 3), "large": (3, 3)}
+CONFIG_KEEP = ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "clocks", "roofline", "dominant_stage",
+               "kernel_shape", "autotune", "config", "gpu_launches")
 
 
 def run_serving(args, device):
@@ -775,7 +860,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serve-seconds", type=float, default=3.0, help="length of the served request stream")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the served request stream")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other workload shapes in the default line")
     ap.add_argument("--autotune", action="store_true", help="search the kernel shapes first and keep the fastest")
     ap.add_argument("--shape", type=int, default=-1, help="kernel shape (-1: autotuned choice or shape 0)")
     ap.add_argument("--sort-mode", type=int, default=-1,

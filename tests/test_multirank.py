@@ -49,6 +49,6 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
     monkeypatch.setenv("RANK", "1")
     monkeypatch.setenv("WORLD_SIZE", "2")
     called = []
-    monkeypatch.setattr(bench, "oracle_sample", lambda *a, **k: called.append(1))
+    monkeypatch.setattr(bench, "oracle_step", lambda *a, **k: called.append(1))
     assert bench.main(["--impl", "reference", "--steps", "1", "--warmup", "3"]) == 0
     assert called == []

@@ -567,3 +567,28 @@ def test_densification_statistic_per_view_norms_and_binned_views():
     got = oracle.render_backward(g, cams, wts, densify=True)
     assert abs(got["densify_grad"][0] - want) < 1e-6 * max(1.0, want), (got["densify_grad"][0], want)
     assert int(got["densify_views"][0]) == 3
+
+
+# ---------------------------------------------------------------- the OpenMP timing build of the oracle
+def test_openmp_timing_build_computes_the_oracle():
+    """The benchmark times the oracle on all host cores through a separate
+    OpenMP build of the same source: its forward must equal the oracle's bit
+    for bit and its adjoint up to the order of additions."""
+    from oracle import timing
+    g, cams = fd_scene(21)
+    cams = cams + [synthetic.camera((0.4, 0.3, -3.2), 53, 37, fov_x_deg=50.0)]
+    ref = oracle.render(g, cams)
+    got = timing.render(g, cams)
+    for v in range(len(cams)):
+        assert np.array_equal(got["rgb"][v], ref["rgb"][v])
+        assert np.array_equal(got["T"][v], ref["T"][v])
+        assert np.array_equal(got["n_contrib"][v], ref["n_contrib"][v])
+    assert got["pairs"] == ref["pairs"]
+    assert np.array_equal(got["importance_cnt"], ref["importance_cnt"])
+    assert np.allclose(got["importance_w"], ref["importance_w"], rtol=1e-12, atol=1e-15)
+    rng = np.random.default_rng(4)
+    dL = [rng.standard_normal((3, c["height"], c["width"])) for c in cams]
+    gr, gw = oracle.render_backward(g, cams, dL), timing.render_backward(g, cams, dL)
+    for k in gr:
+        assert np.allclose(gw[k], gr[k], rtol=1e-10, atol=1e-12 * np.abs(gr[k]).max()), k
+    assert timing.threads() >= 1
