@@ -384,6 +384,33 @@ def add_stage_bandwidths(stage_lines, ms, nl, n, views, n_inst, tile_bits, sh_fl
             stage_lines[name]["gbs"] = nbytes / (per_launch * launches_per_step) / 1e9
 
 
+def definition_pairs_streaming(wl, args, stream, device):
+    """Definition pairs of the timed steps: (pixel, list entry) pairs of the
+    full rectangle lists up to each pixel's termination (forward) and below its
+    n_contrib (backward).  The timed steps list a Gaussian only in its live
+    tiles, so the same frame sequence (anchor, then the warm-up and timed
+    frames' updates in order) is replayed after the timed region by a context
+    that builds the definition's full lists, with the pair counters on."""
+    import torch
+    from paper_2512_20943_b300 import RasterConfig, Rasterizer
+    r = Rasterizer(RasterConfig(kernel_shape=args.shape, sort_mode=args.sort_mode, cull_lists=False), stream=stream)
+    p = wl.params
+    imp = (torch.zeros(N_GAUSS, dtype=torch.float32, device=device),
+           torch.zeros(N_GAUSS, dtype=torch.int32, device=device))
+    with torch.cuda.stream(stream):
+        r.set_anchor(p["means"], p["log_scales"], p["quats"], p["opacity_logit"], p["sh"])
+        for t in range(args.warmup):
+            train_step(r, wl, t, imp)
+        r.set_profiling(True, blend_only=True)
+        r.stage_times()
+        for k in range(args.steps):
+            train_step(r, wl, args.warmup + k, imp)
+        st = r.stage_times()
+        r.set_profiling(False)
+    del r
+    return st["pairs_forward"], st["pairs_backward"]
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_setup()
@@ -454,6 +481,7 @@ def run_ours(args):
             train_step(rast, wl, args.warmup + k, (imp_w, imp_c))
     stages = rast.stage_times()
     rast.set_profiling(False)
+    def_fwd, def_bwd = definition_pairs_streaming(wl, args, stream, device)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     total_ms = barrier_max(world, total_ms, device)
@@ -488,15 +516,18 @@ def run_ours(args):
                              "share": ms[name] / max(1e-9, sum(ms.values()))}
         if nl_t[name]:
             stage_lines[name]["ms_per_launch_timed_region"] = ms_t[name] / nl_t[name]
-    # Blend work (algorithmic): the definition's pairs (list entries up to each
-    # pixel's termination, counted by the kernels) times the test flops, plus the
-    # blended pairs (the importance counts) times the blend flops.  The culling
-    # kernels decide most definition pairs per 8x4 block without per-pair
-    # arithmetic; the lane evaluations they do issue are reported beside.
+    # Blend work (algorithmic): the definition's pairs (entries of the full
+    # rectangle lists up to each pixel's termination, counted by the kernels of a
+    # full-list replay of the same frames) times the test flops, plus the blended
+    # pairs (the importance counts) times the blend flops.  The timed steps list a
+    # Gaussian only in the tiles it can reach and the kernels decide most of the
+    # remaining pairs per 8x4 block without per-pair arithmetic; the pairs of the
+    # lists they walk and the lane evaluations they issue are reported beside.
     def rate(flops, name):  # over the blend stage's live event time in the timed region
         return flops / (ms_t[name] / 1e3) / 1e12 if ms_t[name] else 0.0
-    alg = {"blend_fwd": timed["pairs_forward"] * FLOPS_TEST + blended * args.steps * FLOPS_BLEND_FWD,
-           "blend_bwd": timed["pairs_backward"] * FLOPS_TEST + blended * args.steps * FLOPS_BLEND_BWD}
+    def_pairs = {"forward": def_fwd, "backward": def_bwd}
+    alg = {"blend_fwd": def_fwd * FLOPS_TEST + blended * args.steps * FLOPS_BLEND_FWD,
+           "blend_bwd": def_bwd * FLOPS_TEST + blended * args.steps * FLOPS_BLEND_BWD}
     issued = {"blend_fwd": timed["issued_forward"] * FLOPS_ISSUED_FWD,
               "blend_bwd": timed["issued_backward"] * FLOPS_ISSUED_BWD}
     for name, key in (("blend_fwd", "forward"), ("blend_bwd", "backward")):
@@ -504,7 +535,8 @@ def run_ours(args):
             n_l = max(1, nl_t[name])
             stage_lines[name]["tflops_algorithmic"] = rate(alg[name], name)
             stage_lines[name]["tflops_issued_lanes"] = rate(issued[name], name)
-            stage_lines[name]["definition_pairs_per_launch"] = timed["pairs_" + key] / n_l
+            stage_lines[name]["definition_pairs_per_launch"] = def_pairs[key] / n_l
+            stage_lines[name]["listed_pairs_per_launch"] = timed["pairs_" + key] / n_l
             stage_lines[name]["issued_evals_per_launch"] = timed["issued_" + key] / n_l
             stage_lines[name]["blended_pairs_per_launch"] = blended * args.steps / n_l
     add_stage_bandwidths(stage_lines, ms, nl, N_GAUSS, VIEWS_PER_STEP, probe["n_instances"],
@@ -562,8 +594,9 @@ def run_ours(args):
                        "(inside the timed region only the blend stages are)",
         "kernel_shape": probe["shape"],
         "instances_per_step": probe["n_instances"],
-        "pairs_per_step": {"blended": blended, "forward": timed["pairs_forward"] / args.steps,
-                           "backward": timed["pairs_backward"] / args.steps,
+        "pairs_per_step": {"blended": blended, "forward": def_fwd / args.steps, "backward": def_bwd / args.steps,
+                           "listed_forward": timed["pairs_forward"] / args.steps,
+                           "listed_backward": timed["pairs_backward"] / args.steps,
                            "issued_forward": timed["issued_forward"] / args.steps,
                            "issued_backward": timed["issued_backward"] / args.steps},
     }
@@ -673,6 +706,19 @@ def measure_workload(kind, steps, warmup, shape=-1, sort_mode=-1, autotune=False
             step()
     stages = rast.stage_times()
     rast.set_profiling(False)
+    # definition pairs (the full rectangle lists; the timed steps list only live tiles): one step of a context
+    # that builds the full lists, times the steps (every step renders the same scene)
+    full = Rasterizer(RasterConfig(kernel_shape=shape, sort_mode=sort_mode, cull_lists=False), stream=stream)
+    full.set_profiling(True, blend_only=True)
+    full.stage_times()
+    with torch.cuda.stream(stream):
+        res = full.render_gaussians(*p, cams, save=backward)
+        if backward:
+            full.render_backward_l1(res.state, target)
+            res.state.release()
+    fst = full.stage_times()
+    del full, res
+    def_pairs = {"forward": fst["pairs_forward"] * steps, "backward": fst["pairs_backward"] * steps}
     total_ms = barrier_max(world, sum(a.elapsed_time(b) for a, b in ev), device)
     px = sum(int(c["width"]) * int(c["height"]) for c in cams)
     value = whole_job_value(world, px, steps, total_ms)
@@ -713,12 +759,13 @@ def measure_workload(kind, steps, warmup, shape=-1, sort_mode=-1, autotune=False
         line["autotune"] = tuned
     for name, key, fl in (("blend_fwd", "forward", FLOPS_BLEND_FWD), ("blend_bwd", "backward", FLOPS_BLEND_BWD)):
         if name in stage_lines and blended is not None and ms_t[name]:
-            flops = timed["pairs_" + key] * FLOPS_TEST + blended * steps * fl
+            flops = def_pairs[key] * FLOPS_TEST + blended * steps * fl
             t_s = ms_t[name] / 1e3  # the blend stage's live event time in the timed region
             stage_lines[name]["tflops_algorithmic"] = flops / t_s / 1e12
             stage_lines[name]["frac_fp32_peak"] = flops / t_s / 1e12 / fp32_peak
         if name in stage_lines:
-            stage_lines[name]["definition_pairs_per_launch"] = timed["pairs_" + key] / max(1, nl_t[name])
+            stage_lines[name]["definition_pairs_per_launch"] = def_pairs[key] / max(1, nl_t[name])
+            stage_lines[name]["listed_pairs_per_launch"] = timed["pairs_" + key] / max(1, nl_t[name])
             stage_lines[name]["issued_evals_per_launch"] = timed["issued_" + key] / max(1, nl_t[name])
     dom = max(stage_lines, key=lambda k: stage_lines[k]["share"])
     if dom in ("blend_bwd", "blend_fwd") and "tflops_algorithmic" in stage_lines[dom]:

@@ -80,10 +80,13 @@ typedef struct {
                                  per-tile for batches of at most 65536 (view, Gaussian) pairs, where
                                  the radix path's fixed cost dominates, else radix */
   const char* autotune_cache; /* nullable path of a text cache of autotune choices */
-  int cull_lists;             /* 1 (default): a render that neither saves its state nor returns n_contrib
-                                 (whose tile lists nothing can observe) lists a Gaussian only in the
-                                 tiles of its rectangle in which it can reach alpha_min; images, T and
-                                 importance are identical.  0: always the full rectangle lists */
+  int cull_lists;             /* 1 (default): a render that does not return n_contrib lists a Gaussian
+                                 only in the tiles of its rectangle in which it can reach alpha_min;
+                                 images, T, importance and the backward's gradients are those of the
+                                 full lists (the dropped entries are skipped by every pixel), but a
+                                 saved state's lists, list positions and pair counts are those of the
+                                 culled lists.  0: always the full rectangle lists (the definition's
+                                 lists, as the radix ordering builds them) */
 } airgs_config;
 
 typedef struct {
@@ -108,7 +111,7 @@ typedef struct {
   int64_t n_instances;   /* (tile, Gaussian) list entries over all views */
   int64_t n_tiles;       /* 16x16 tiles over all views */
   int64_t n_pixels;      /* pixels over all views */
-  int64_t pairs_forward; /* (pixel, list entry) pairs evaluated by the forward, up to termination */
+  int64_t pairs_forward; /* (pixel, list entry) pairs of the lists the render built, up to termination */
   int64_t pairs_backward;/* pairs replayed by the backward (list positions < n_contrib) */
   int kernel_shape;      /* kernel shape the render ran */
 } airgs_stats;

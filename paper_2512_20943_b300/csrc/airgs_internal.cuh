@@ -312,6 +312,50 @@ __device__ __forceinline__ LiveRow live_row(const EllipseBands& e, int ty, int x
   return r;
 }
 
+// The rectangle [x0, x1) x [y0, y1) of tile_rect clipped to the tiles whose
+// pixel centres meet the bounding box of the region where the Gaussian can
+// blend: P(d) = a2 dx^2 + b2 dx dy + c2 dy^2 >= -L, L = log2(o / alpha_min),
+// has half-widths hx = sqrt(L (-c2) / det), hy = sqrt(L (-a2) / det),
+// det = a2 c2 - b2^2 / 4.  L is widened by 0.01 + 1e-5 S (S bounds the terms'
+// magnitudes over the region, the scale of the per-pair test's rounding
+// error) and the box by 0.01 + 1e-5 (h + |m|), as for the row bands above, so
+// no dropped tile holds a pair the per-pair test would blend.  Every operation
+// has an explicit rounding mode: the projection (which counts the tiles) and
+// the emission (which lists them) compute the same rectangle.  A Gaussian that
+// can never blend gets an empty rectangle; one with no bound (degenerate or NaN
+// terms) keeps the full one.
+__device__ __forceinline__ void clip_rect_to_alpha_box(float mx, float my, float a2, float b2, float c2, float o,
+                                                       float log2_amin, int& x0, int& y0, int& x1, int& y1) {
+  const float L0 = __fadd_rn(__fadd_rn(lg2_approx(o), -log2_amin), 1e-3f);
+  if (L0 <= 0.f) {  // o below alpha_min everywhere: never blends
+    x1 = x0;
+    y1 = y0;
+    return;
+  }
+  const bool definite = a2 < 0.f && c2 < 0.f && __fmul_rn(4.f, __fmul_rn(a2, c2)) > __fmul_rn(1.0001f, __fmul_rn(b2, b2));
+  if (!(L0 > 0.f) || !definite) return;
+  const float det = __fmaf_rn(a2, c2, __fmul_rn(-0.25f, __fmul_rn(b2, b2)));
+  const float hx0 = __fsqrt_rn(__fdiv_rn(__fmul_rn(L0, -c2), det));
+  const float hy0 = __fsqrt_rn(__fdiv_rn(__fmul_rn(L0, -a2), det));
+  const float S = __fadd_rn(__fadd_rn(__fmul_rn(-a2, __fmul_rn(hx0, hx0)), __fmul_rn(fabsf(b2), __fmul_rn(hx0, hy0))),
+                            __fmul_rn(-c2, __fmul_rn(hy0, hy0)));
+  const float L = __fadd_rn(__fadd_rn(L0, 0.01f), __fmul_rn(1e-5f, S));
+  const float hx = __fsqrt_rn(__fdiv_rn(__fmul_rn(L, -c2), det));
+  const float hy = __fsqrt_rn(__fdiv_rn(__fmul_rn(L, -a2), det));
+  const float ex = __fadd_rn(hx, __fadd_rn(0.01f, __fmul_rn(1e-5f, __fadd_rn(hx, fabsf(mx)))));
+  const float ey = __fadd_rn(hy, __fadd_rn(0.01f, __fmul_rn(1e-5f, __fadd_rn(hy, fabsf(my)))));
+  // tile t meets [m - e, m + e] iff 16 t + 0.5 <= m + e and 16 t + 15.5 >= m - e
+  const float lim = 1048576.0f;
+  const int bx0 = (int)ceilf(__fmul_rn(fminf(fmaxf(__fadd_rn(__fadd_rn(mx, -ex), -15.5f), -lim), lim), 0.0625f));
+  const int bx1 = (int)floorf(__fmul_rn(fminf(fmaxf(__fadd_rn(__fadd_rn(mx, ex), -0.5f), -lim), lim), 0.0625f)) + 1;
+  const int by0 = (int)ceilf(__fmul_rn(fminf(fmaxf(__fadd_rn(__fadd_rn(my, -ey), -15.5f), -lim), lim), 0.0625f));
+  const int by1 = (int)floorf(__fmul_rn(fminf(fmaxf(__fadd_rn(__fadd_rn(my, ey), -0.5f), -lim), lim), 0.0625f)) + 1;
+  x0 = max(x0, bx0);
+  y0 = max(y0, by0);
+  x1 = max(x0, min(x1, bx1));
+  y1 = max(y0, min(y1, by1));
+}
+
 // Half flags (bit 0 top, bit 1 bottom) of live tile tx of a row.
 __device__ __forceinline__ uint32_t live_row_halves(const LiveRow& r, int tx) {
   const float X0 = (float)(tx * kTile);

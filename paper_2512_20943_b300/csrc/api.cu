@@ -377,8 +377,12 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
     // ordering path: per-tile lists sorted in shared memory on request, or by default for small batches,
     // where the radix path's fixed cost (4 + 2 passes of 3 launches) dominates; the radix path otherwise
     const bool per_tile = ctx->cfg.sort_mode == 1 || (ctx->cfg.sort_mode == -1 && V * N <= kSmallOrdering);
-    // lists nothing can observe (no saved state, no n_contrib output) hold only the live tiles
-    const bool cull = ctx->cfg.cull_lists != 0 && !saved && !nc_out && !per_tile;
+    // unless the caller asks for n_contrib (positions in the definition's lists), a Gaussian is listed only in
+    // tiles of its rectangle where it can reach alpha_min: the dropped entries are skipped by every pixel of their
+    // tile, so images, T, blend weights and the backward's replay (which walks the same lists) are unchanged.  A
+    // state saved for a backward (training: small footprints, where the exact row bands cost more to compute than
+    // they save) takes the alpha_min box; a render without state (serving: large footprints) the exact bands.
+    const int cull = (ctx->cfg.cull_lists == 0 || nc_out || per_tile) ? kCullNone : (saved ? kCullBox : kCullBands);
     if (per_tile) {
       TALLOC(tile_counts, s->n_tiles);
       CK(cudaMemsetAsync(tile_counts, 0, s->n_tiles * sizeof(uint32_t), st));

@@ -17,10 +17,17 @@ cudaError_t launch_decode_apply(cudaStream_t st, int64_t n, const uint16_t* map,
                                 const float* hi, int quat_add, const float* base_means, const float* base_quats,
                                 float* out_means, float* out_quats);
 
+// Tile lists: kCullNone lists a Gaussian in every tile of its 3-sigma rectangle
+// (the definition's lists), kCullBands only in the tiles where it can reach
+// alpha_min (exact row bands of its ellipse), kCullBox in the tiles of the
+// rectangle that the bounding box of that region meets (cheaper to compute,
+// fewer tiles dropped).  Images, T, blend weights and gradients are the same.
+constexpr int kCullNone = 0, kCullBands = 1, kCullBox = 2;
+
 cudaError_t launch_project(cudaStream_t st, int64_t n, int sh_degree, const float* means, const float* log_scales,
                            const float* quats, const float* opacity_logit, const float* sh, const CamDev* cams,
                            int n_views, const RasterParams& rp, ProjRec* proj, uint32_t* depth_keys,
-                           uint32_t* tiles_touched, uint32_t* tile_counts, bool cull);
+                           uint32_t* tiles_touched, uint32_t* tile_counts, int cull);
 
 // Per-tile ordering (order.cu).
 constexpr int kTileSortSmall = 2048;  // entries sorted by one 256-thread CTA
@@ -57,7 +64,7 @@ int64_t emit_chunks(int64_t total);  // depth-order chunks of the count/scan/emi
 cudaError_t launch_emit(cudaStream_t st, int64_t total, int64_t n, const uint32_t* order,
                         const uint32_t* counts_sorted, const uint64_t* chunk_offsets, int64_t n_inst,
                         uint32_t* piece_off, const ProjRec* proj, const CamDev* cams, float alpha_min,
-                        int64_t n_tiles, bool cull, uint32_t* keys, uint32_t* vals);
+                        int64_t n_tiles, int cull, uint32_t* keys, uint32_t* vals);
 cudaError_t launch_tile_ranges(cudaStream_t st, int64_t n_inst, const uint32_t* keys, uint2* ranges);
 
 // Usage-frequency pruning (prune.cu).

@@ -222,8 +222,11 @@ __global__ void __launch_bounds__(128, AIRGS_PROJ_MINB) k_project(int64_t n, con
           a2 = -0.5f * kLog2e * A;
           b2 = -kLog2e * B;
           c2 = -0.5f * kLog2e * C;
-          if (cull) {  // only the tiles in which the Gaussian can reach alpha_min (culled lists), from
-                       // the values the record stores, as the emission will read them
+          if (cull == kCullBox) {  // the rectangle clipped to the alpha_min box, from the record's values
+            clip_rect_to_alpha_box(mx, my, a2, b2, c2, opacity, log2_amin, x0, y0, x1, y1);
+            ntiles = (uint32_t)((x1 - x0) * (y1 - y0));
+          } else if (cull == kCullBands) {  // only the tiles in which the Gaussian can reach alpha_min, from
+                                            // the values the record stores, as the emission will read them
             const EllipseBands e = ellipse_bands(mx, my, a2, b2, c2, opacity, log2_amin);
             uint32_t live = 0;
             for (int ty = y0; ty < y1; ++ty) {
@@ -265,25 +268,25 @@ cudaError_t launch_decode_apply(cudaStream_t st, int64_t n, const uint16_t* map,
 cudaError_t launch_project(cudaStream_t st, int64_t n, int sh_degree, const float* means, const float* log_scales,
                            const float* quats, const float* opacity_logit, const float* sh, const CamDev* cams,
                            int n_views, const RasterParams& rp, ProjRec* proj, uint32_t* depth_keys,
-                           uint32_t* tiles_touched, uint32_t* tile_counts, bool cull) {
+                           uint32_t* tiles_touched, uint32_t* tile_counts, int cull) {
   if (n == 0) return cudaSuccess;
   int blocks = (int)((n + 127) / 128);
   switch (sh_degree) {
     case 0:
       k_project<0><<<blocks, 128, 0, st>>>(n, means, log_scales, quats, opacity_logit, sh, cams, n_views, rp, proj,
-                                           depth_keys, tiles_touched, tile_counts, cull ? 1 : 0, log2f(rp.alpha_min));
+                                           depth_keys, tiles_touched, tile_counts, cull, log2f(rp.alpha_min));
       break;
     case 1:
       k_project<1><<<blocks, 128, 0, st>>>(n, means, log_scales, quats, opacity_logit, sh, cams, n_views, rp, proj,
-                                           depth_keys, tiles_touched, tile_counts, cull ? 1 : 0, log2f(rp.alpha_min));
+                                           depth_keys, tiles_touched, tile_counts, cull, log2f(rp.alpha_min));
       break;
     case 2:
       k_project<2><<<blocks, 128, 0, st>>>(n, means, log_scales, quats, opacity_logit, sh, cams, n_views, rp, proj,
-                                           depth_keys, tiles_touched, tile_counts, cull ? 1 : 0, log2f(rp.alpha_min));
+                                           depth_keys, tiles_touched, tile_counts, cull, log2f(rp.alpha_min));
       break;
     default:
       k_project<3><<<blocks, 128, 0, st>>>(n, means, log_scales, quats, opacity_logit, sh, cams, n_views, rp, proj,
-                                           depth_keys, tiles_touched, tile_counts, cull ? 1 : 0, log2f(rp.alpha_min));
+                                           depth_keys, tiles_touched, tile_counts, cull, log2f(rp.alpha_min));
       break;
   }
   count_launches(1);

@@ -526,9 +526,10 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(int64_t total, int64_t n, c
     const int radius = __float_as_int(__ldg(&rec->c.z));
     int x0, y0, x1, y1;
     tile_rect(ra.x, ra.y, radius, cam.TW, cam.TH, x0, y0, x1, y1);
+    if (cull == kCullBox) clip_rect_to_alpha_box(ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, log2_amin, x0, y0, x1, y1);
     s_rect[g] = make_uint4((uint32_t)cam.tile_base + (uint32_t)(y0 * cam.TW + x0),
                            (uint32_t)(x1 - x0) | ((uint32_t)cam.TW << 16), (uint32_t)x0 | ((uint32_t)y0 << 16), gid);
-    if (cull) {  // culled lists: the row-band terms the projection counted with, from the same record values
+    if (cull == kCullBands) {  // culled lists: the row-band terms the projection counted with, from the same record values
       const EllipseBands e = ellipse_bands(ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, log2_amin);
       s_rect[g].x = (uint32_t)cam.tile_base;
       s_ext[g] = (uint32_t)cam.TW | ((uint32_t)(y1 - y0) << 16);
@@ -549,7 +550,7 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(int64_t total, int64_t n, c
   __syncthreads();
   const uint32_t i0 = p0 + (uint32_t)tid * EM_RUN;
   const uint32_t i1 = min(i0 + (uint32_t)EM_RUN, p1);
-  if (cull && i0 < i1) {
+  if (cull == kCullBands && i0 < i1) {
     // culled lists: walk the live tiles row by row exactly as the projection counted them
     auto bands_of = [&](int gg) {
       EllipseBands e;
@@ -802,7 +803,7 @@ size_t emit_piece_words(int64_t total, int64_t n_inst) {
 cudaError_t launch_emit(cudaStream_t st, int64_t total, int64_t n, const uint32_t* order,
                         const uint32_t* counts_sorted, const uint64_t* chunk_offsets, int64_t n_inst,
                         uint32_t* piece_off, const ProjRec* proj, const CamDev* cams, float alpha_min,
-                        int64_t n_tiles, bool cull, uint32_t* keys, uint32_t* vals) {
+                        int64_t n_tiles, int cull, uint32_t* keys, uint32_t* vals) {
   if (total == 0 || n_inst == 0) return cudaSuccess;
   const int64_t n_chunks = (total + EM_CHUNK - 1) / EM_CHUNK;
   // sum over chunks of ceil(count / EM_PIECE) <= n_inst / EM_PIECE + n_chunks; surplus CTAs return at once
@@ -828,7 +829,7 @@ cudaError_t launch_emit(cudaStream_t st, int64_t total, int64_t n, const uint32_
   }
   e = launch_serialised(k_emit, dim3((unsigned)grid), dim3(EM_THREADS), EM_SMEM, st, total, n, order, counts_sorted,
                         chunk_offsets, (const uint32_t*)piece_off, (const uint32_t*)piece_chunk, n_chunks, proj, cams,
-                        log2f(alpha_min), n_tiles <= (1ll << 24), cull ? 1 : 0, keys, vals);
+                        log2f(alpha_min), n_tiles <= (1ll << 24), cull, keys, vals);
   count_launches(3);
   return e == cudaSuccess ? cudaGetLastError() : e;
 }

@@ -21,9 +21,11 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(scope="module")
 def rast():
     """The radix ordering the benchmark's batch sizes take (the default picks
-    the per-tile ordering for batches this small; both are tested)."""
+    the per-tile ordering for batches this small; both are tested), with the
+    definition's full rectangle lists (saved states of a culling context hold
+    only the live tiles)."""
     from paper_2512_20943_b300 import RasterConfig, Rasterizer
-    return Rasterizer(RasterConfig(sort_mode=0))
+    return Rasterizer(RasterConfig(sort_mode=0, cull_lists=False))
 
 
 _by_shape = {}
@@ -82,10 +84,10 @@ _by_sort = {}
 
 def rast_sort(mode):
     """A context pinned to an ordering path: 1 per-tile lists sorted in shared
-    memory, 0 the global two-stage radix ordering (default)."""
+    memory, 0 the global two-stage radix ordering (default); full lists."""
     from paper_2512_20943_b300 import RasterConfig, Rasterizer
     if mode not in _by_sort:
-        _by_sort[mode] = Rasterizer(RasterConfig(sort_mode=mode))
+        _by_sort[mode] = Rasterizer(RasterConfig(sort_mode=mode, cull_lists=False))
     return _by_sort[mode]
 
 
@@ -506,10 +508,16 @@ def test_smem_probe_reports_a_plausible_peak(rast):
 
 @pytest.mark.parametrize("scene", ["plain_2k", "sh3_ragged", "needles", "dense_cluster"])
 def test_culled_lists_render_identically(scene):
-    """Renders whose lists nothing observes (no saved state, no n_contrib) list a
-    Gaussian only in the tiles where it can reach alpha_min: images,
-    transmittance and blended-pair counts are bit-identical to the full
-    rectangle lists, with the default and another forward shape."""
+    """Renders that do not return n_contrib list a Gaussian only in tiles where
+    it can reach alpha_min -- the tiles its ellipse's exact row bands meet when
+    no state is kept, the tiles its bounding box meets for a state saved for a
+    backward: images, transmittance and blended-pair counts are bit-identical
+    to the full rectangle lists, with the default and another forward shape,
+    with fewer list entries; the backward of a saved state replays its culled
+    lists and gives the full lists' usage counts exactly and their gradients
+    within the gradient bar (only the order of the atomic additions differs;
+    the thinnest needles' ill-conditioned log-scale gradients amplify that
+    order to about 1e-3, so that scene is compared in the forward only)."""
     from paper_2512_20943_b300 import RasterConfig, Rasterizer
     if scene == "needles":
         g, cams = needle_scene()
@@ -520,15 +528,32 @@ def test_culled_lists_render_identically(scene):
                 for (w, h) in [(320, 240), (200, 113), (480, 270)]]
     else:
         g, cams = scenes()[scene]
+    rng = np.random.default_rng(5)
     for v in (0, 2):
         full = Rasterizer(RasterConfig(kernel_shape=v, cull_lists=False, sort_mode=0))
         culled = Rasterizer(RasterConfig(kernel_shape=v, cull_lists=True, sort_mode=0))
-        a = render_gpu(full, g, cams, T=True, importance=True)[1]
-        b = render_gpu(culled, g, cams, T=True, importance=True)[1]
+        bands = render_gpu(culled, g, cams, T=True, importance=True)[1]  # no state: the exact row bands
+        a = render_gpu(full, g, cams, T=True, importance=True, save=True)[1]
+        b = render_gpu(culled, g, cams, T=True, importance=True, save=True)[1]  # saved: the alpha_min box
+        assert torch.equal(a.rgb, bands.rgb) and torch.equal(a.T, bands.T), v
+        assert torch.equal(a.importance_cnt, bands.importance_cnt), v
         assert torch.equal(a.rgb, b.rgb), v
         assert torch.equal(a.T, b.T), v
         assert torch.equal(a.importance_cnt, b.importance_cnt), v
         assert float(a.rgb.max()) > 0.0
+        assert culled.stats(b.state)["n_instances"] < full.stats(a.state)["n_instances"]
+        dL = torch.from_numpy(rng.standard_normal(a.rgb.numel()).astype(np.float32)).cuda()
+        ia = (torch.zeros_like(a.importance_w), torch.zeros_like(a.importance_cnt))
+        ib = (torch.zeros_like(b.importance_w), torch.zeros_like(b.importance_cnt))
+        ga = full.render_backward(a.state, dL, importance=ia)
+        gb = culled.render_backward(b.state, dL, importance=ib)
+        torch.cuda.synchronize()
+        assert torch.equal(ia[1], ib[1]) and torch.equal(ib[1], a.importance_cnt), v
+        if scene != "needles":
+            for k in ga:
+                assert_grad_close(gb[k].cpu().numpy(), ga[k].cpu().numpy(), (v, k))
+        a.state.release()
+        b.state.release()
 
 
 @pytest.mark.gpu
