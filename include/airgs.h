@@ -323,7 +323,8 @@ int airgs_sort_pairs_noalloc(const uint32_t* keys_in, const uint32_t* vals_in, u
 /* Autotune the kernel shape for this workload (n Gaussians of the current
  * frame, the given cameras): a coordinate search over the compiled shapes --
  * first the blend backward's (staged entries per batch, warps per SM), then
- * the blend forward's, then the radix sort's keys per thread -- timing the
+ * the blend forward's, then the radix sort's keys per thread, then the
+ * emission's instances per thread -- timing the
  * training step as it runs (render with saved state, then the fused L1
  * backward with usage-frequency accumulation, against a constant target) with
  * CUDA events on the context's stream, best of 3 repetitions after one
@@ -379,9 +380,9 @@ int airgs_measure_smem_peak(airgs_ctx* ctx, double* tbs);
 int64_t airgs_kernel_launch_count(void);
 
 /* Number of compiled kernel shapes and a short name of each ("fwd B/W bwd
- * B/W keys K": staged entries per batch and warps per SM of the blend forward
- * and backward, radix keys per thread of the instance sort).  Shape 0 is the
- * default. */
+ * B/W keys K run R": staged entries per batch and warps per SM of the blend
+ * forward and backward, radix keys per thread of the instance sort, instances
+ * per thread of the emission).  Shape 0 is the default. */
 int airgs_shape_count(void);
 const char* airgs_shape_name(int shape);
 

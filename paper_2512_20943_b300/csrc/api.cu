@@ -257,8 +257,8 @@ const char* airgs::shape_name(int shape) {
       const int bwd[kBwdShapes][2] = {{32, 28}, {16, 28}, {64, 28}, {32, 24}, {32, 32}};
       for (int i = 0; i < kShapes; ++i) {
         const ShapeParts p = shape_parts(i);
-        snprintf(s[i], sizeof(s[i]), "fwd %d/%d bwd %d/%d keys %d", fwd[p.fwd][0], fwd[p.fwd][1], bwd[p.bwd][0],
-                 bwd[p.bwd][1], sort_keys_of(p.sort));
+        snprintf(s[i], sizeof(s[i]), "fwd %d/%d bwd %d/%d keys %d run %d", fwd[p.fwd][0], fwd[p.fwd][1],
+                 bwd[p.bwd][0], bwd[p.bwd][1], sort_keys_of(p.sort), emit_run_of(p.emit));
       }
     }
   };
@@ -480,7 +480,7 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
           StageScope sc(ctx, ST_EMIT);
           TALLOC(pieces, emit_piece_words(V * N, n_inst));
           CK(launch_emit(st, V * N, N, order, counts_sorted, chunk, n_inst, pieces, s->proj, s->d_cams,
-                         ctx->cfg.alpha_min, s->n_tiles, cull, ikeys_a, ivals_a));
+                         ctx->cfg.alpha_min, s->n_tiles, cull, emit_run_of(parts.emit), ikeys_a, ivals_a));
         }
         bool in_b2 = false;
         {
@@ -1056,21 +1056,22 @@ int airgs_autotune(airgs_ctx* ctx, const airgs_camera* cams, int n_views, int* s
     return AIRGS_OK;
   };
   // coordinate search from shape 0: the backward's shapes, then the forward's,
-  // then the sort's keys per thread, each with the other parts at the best so far
-  ShapeParts best{0, 0, 0};
+  // then the sort's keys per thread, then the emission's run length, each with
+  // the other parts at the best so far
+  ShapeParts best{0, 0, 0, 0};
   float best_ms = 0.f, def_ms = 0.f;
   rc = time_shape(0, def_ms);
   best_ms = def_ms;
-  for (int axis = 0; axis < 3 && rc == AIRGS_OK; ++axis) {
-    const int count = axis == 0 ? kBwdShapes : axis == 1 ? kFwdShapes : kSortShapes;
+  for (int axis = 0; axis < 4 && rc == AIRGS_OK; ++axis) {
+    const int count = axis == 0 ? kBwdShapes : axis == 1 ? kFwdShapes : axis == 2 ? kSortShapes : kEmitShapes;
     const ShapeParts base = best;
     for (int c = 0; c < count && rc == AIRGS_OK; ++c) {
       ShapeParts p = base;
-      int& slot = axis == 0 ? p.bwd : axis == 1 ? p.fwd : p.sort;
+      int& slot = axis == 0 ? p.bwd : axis == 1 ? p.fwd : axis == 2 ? p.sort : p.emit;
       if (slot == c) continue;  // already timed
       slot = c;
       float ms = 0.f;
-      rc = time_shape(shape_index(p.fwd, p.bwd, p.sort), ms);
+      rc = time_shape(shape_index(p.fwd, p.bwd, p.sort, p.emit), ms);
       if (rc == AIRGS_OK && ms < best_ms) {
         best_ms = ms;
         best = p;
@@ -1080,7 +1081,7 @@ int airgs_autotune(airgs_ctx* ctx, const airgs_camera* cams, int n_views, int* s
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
-  const int chosen = shape_index(best.fwd, best.bwd, best.sort);
+  const int chosen = shape_index(best.fwd, best.bwd, best.sort, best.emit);
   ctx->tuned[tune_key(ctx->n, np, n_views)] = chosen;
   save_tune_cache(ctx);
   if (shape) *shape = chosen;

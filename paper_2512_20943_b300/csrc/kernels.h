@@ -64,7 +64,7 @@ int64_t emit_chunks(int64_t total);  // depth-order chunks of the count/scan/emi
 cudaError_t launch_emit(cudaStream_t st, int64_t total, int64_t n, const uint32_t* order,
                         const uint32_t* counts_sorted, const uint64_t* chunk_offsets, int64_t n_inst,
                         uint32_t* piece_off, const ProjRec* proj, const CamDev* cams, float alpha_min,
-                        int64_t n_tiles, int cull, uint32_t* keys, uint32_t* vals);
+                        int64_t n_tiles, int cull, int run, uint32_t* keys, uint32_t* vals);
 cudaError_t launch_tile_ranges(cudaStream_t st, int64_t n_inst, const uint32_t* keys, uint2* ranges);
 
 // Usage-frequency pruning (prune.cu).
@@ -134,22 +134,28 @@ struct BwdIn {
 
 // Kernel shapes the autotuner searches: compiled instantiations of the blend
 // forward and backward (staged list entries per batch, warps per SM: the
-// register bound) and keys per thread of the instances' radix sort.  A shape
-// index packs (forward f, backward b, sort k) as f + kFwdShapes (b +
-// kBwdShapes k); shape 0 (every part 0) is the default.
+// register bound), keys per thread of the instances' radix sort and the
+// emission's instances per thread.  A shape index packs (forward f, backward
+// b, sort k, emission e) as f + kFwdShapes (b + kBwdShapes (k + kSortShapes e));
+// shape 0 (every part 0) is the default.
 constexpr int kFwdShapes = 5;   // forward (batch, warps): (32, 32) (16, 32) (64, 32) (32, 28) (32, 24)
 constexpr int kBwdShapes = 5;   // backward (batch, warps): (32, 28) (16, 28) (64, 28) (32, 24) (32, 32)
 constexpr int kSortShapes = 3;  // instance sort keys per thread: 8, 6, 12
-constexpr int kShapes = kFwdShapes * kBwdShapes * kSortShapes;
+constexpr int kEmitShapes = 3;  // emission instances per thread and piece: 8, 4, 16
+constexpr int kShapes = kFwdShapes * kBwdShapes * kSortShapes * kEmitShapes;
 struct ShapeParts {
-  int fwd, bwd, sort;
+  int fwd, bwd, sort, emit;
 };
 inline ShapeParts shape_parts(int shape) {
   if (shape < 0 || shape >= kShapes) shape = 0;
-  return ShapeParts{shape % kFwdShapes, (shape / kFwdShapes) % kBwdShapes, shape / (kFwdShapes * kBwdShapes)};
+  return ShapeParts{shape % kFwdShapes, (shape / kFwdShapes) % kBwdShapes,
+                    (shape / (kFwdShapes * kBwdShapes)) % kSortShapes, shape / (kFwdShapes * kBwdShapes * kSortShapes)};
 }
-inline int shape_index(int fwd, int bwd, int sort) { return fwd + kFwdShapes * (bwd + kBwdShapes * sort); }
+inline int shape_index(int fwd, int bwd, int sort, int emit) {
+  return fwd + kFwdShapes * (bwd + kBwdShapes * (sort + kSortShapes * emit));
+}
 inline int sort_keys_of(int sort_shape) { return sort_shape == 1 ? 6 : sort_shape == 2 ? 12 : 8; }
+inline int emit_run_of(int emit_shape) { return emit_shape == 1 ? 4 : emit_shape == 2 ? 16 : 8; }
 const char* shape_name(int shape);
 cudaError_t launch_blend_fwd(cudaStream_t st, int fwd_shape, int num_sms, const BlendArgs& a, const FwdOut& o);
 cudaError_t launch_blend_bwd(cudaStream_t st, int bwd_shape, int num_sms, const BlendArgs& a, const BwdIn& in);

@@ -357,15 +357,18 @@ __global__ void __launch_bounds__(SP_THREADS) k_scan_spans(uint64_t* sums0, uint
 // scan over chunks of ceil(instances of chunk c / EM_PIECE) (one CTA), total
 // pieces in piece_off[n_chunks].  chunk_offsets holds the chunks' exclusive
 // instance offsets with the total in chunk_offsets[n_chunks].
-#ifndef AIRGS_EM_RUN
-#define AIRGS_EM_RUN 8  // measured best of 4, 8
-#endif
-constexpr int EM_RUN = AIRGS_EM_RUN;                          // instances per thread and piece
-constexpr uint32_t EM_PIECE = (uint32_t)EM_THREADS * EM_RUN;  // instances per CTA
-constexpr int EM_STAGE = EM_THREADS * (EM_RUN + 1);            // padded staging rows (no bank conflicts)
-constexpr size_t EM_SMEM = 3 * EM_CHUNK * sizeof(float4) + EM_CHUNK * sizeof(float2) +
-                           (2 * EM_CHUNK + 4) * sizeof(uint32_t) + 2 * EM_STAGE * sizeof(uint32_t);
+// RUN: instances per thread and piece (4, 8 or 16: a kernel-shape parameter);
+// a piece is EM_THREADS x RUN instances, one CTA.
+template <int RUN>
+struct EmitGeom {
+  static constexpr uint32_t PIECE = (uint32_t)EM_THREADS * RUN;  // instances per CTA
+  static constexpr int STAGE = EM_THREADS * (RUN + 1);            // padded staging rows (no bank conflicts)
+  static constexpr size_t SMEM = 3 * EM_CHUNK * sizeof(float4) + EM_CHUNK * sizeof(float2) +
+                                 (2 * EM_CHUNK + 4) * sizeof(uint32_t) + 2 * STAGE * sizeof(uint32_t);
+};
+constexpr uint32_t EM_MIN_PIECE = EmitGeom<4>::PIECE;  // the smallest piece (bounds the piece count)
 
+template <int RUN>
 __global__ void __launch_bounds__(SP_THREADS) k_emit_pieces(const uint64_t* __restrict__ chunk_offsets,
                                                            int64_t n_chunks, uint32_t* __restrict__ piece_off) {
   wait_prior_grid();
@@ -379,7 +382,8 @@ __global__ void __launch_bounds__(SP_THREADS) k_emit_pieces(const uint64_t* __re
 #pragma unroll
     for (int j = 0; j < SP_ITEMS; ++j) {
       const int64_t c = c0 + j;
-      v[j] = c < n_chunks ? (uint32_t)((chunk_offsets[c + 1] - chunk_offsets[c] + EM_PIECE - 1) / EM_PIECE) : 0u;
+      constexpr uint32_t PIECE = EmitGeom<RUN>::PIECE;
+      v[j] = c < n_chunks ? (uint32_t)((chunk_offsets[c + 1] - chunk_offsets[c] + PIECE - 1) / PIECE) : 0u;
       local += v[j];
     }
     uint32_t x = local;
@@ -438,6 +442,7 @@ __global__ void k_emit_piece_map(const uint32_t* __restrict__ piece_off, int64_t
 // past the first), moving to the next Gaussian when the offsets say so; the
 // run goes to shared memory (rows padded to EM_RUN + 1 words) and the CTA
 // writes the piece out coalesced.
+template <int RUN>
 __global__ void __launch_bounds__(EM_THREADS) k_emit(int64_t total, int64_t n, const uint32_t* __restrict__ order,
                                                     const uint32_t* __restrict__ counts_sorted,
                                                     const uint64_t* __restrict__ chunk_offsets,
@@ -447,7 +452,10 @@ __global__ void __launch_bounds__(EM_THREADS) k_emit(int64_t total, int64_t n, c
                                                     float log2_amin, bool with_halves, int cull,
                                                     uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
   wait_prior_grid();
-  // dynamic shared memory (EM_SMEM bytes):
+  constexpr uint32_t EM_PIECE = EmitGeom<RUN>::PIECE;
+  constexpr int EM_STAGE = EmitGeom<RUN>::STAGE;
+  constexpr int EM_RUN = RUN;
+  // dynamic shared memory (EmitGeom<RUN>::SMEM bytes):
   extern __shared__ float4 em_smem[];
   float4* s_box = em_smem;                   // centre, alpha-box half-widths (-inf: never, +inf: unbounded)
   float4* s_quad = s_box + EM_CHUNK;         // a2, b2, c2 (a2 = 0: no exact test), L = log2(o / alpha_min)
@@ -794,22 +802,25 @@ cudaError_t launch_scan_spans(cudaStream_t st, uint64_t* sums, int64_t n_chunks,
   return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
-// piece offsets [n_chunks + 1], then the piece -> chunk map [n_inst / EM_PIECE + n_chunks + 1]
+// piece offsets [n_chunks + 1], then the piece -> chunk map [n_inst / piece + n_chunks + 1]
+// (sized for the smallest piece, so that every run length fits)
 size_t emit_piece_words(int64_t total, int64_t n_inst) {
   const int64_t n_chunks = (total + EM_CHUNK - 1) / EM_CHUNK;
-  return (size_t)(2 * n_chunks + n_inst / EM_PIECE + 2);
+  return (size_t)(2 * n_chunks + n_inst / EM_MIN_PIECE + 2);
 }
 
-cudaError_t launch_emit(cudaStream_t st, int64_t total, int64_t n, const uint32_t* order,
-                        const uint32_t* counts_sorted, const uint64_t* chunk_offsets, int64_t n_inst,
-                        uint32_t* piece_off, const ProjRec* proj, const CamDev* cams, float alpha_min,
-                        int64_t n_tiles, int cull, uint32_t* keys, uint32_t* vals) {
-  if (total == 0 || n_inst == 0) return cudaSuccess;
+template <int RUN>
+static cudaError_t emit_launch(cudaStream_t st, int64_t total, int64_t n, const uint32_t* order,
+                               const uint32_t* counts_sorted, const uint64_t* chunk_offsets, int64_t n_inst,
+                               uint32_t* piece_off, const ProjRec* proj, const CamDev* cams, float alpha_min,
+                               int64_t n_tiles, int cull, uint32_t* keys, uint32_t* vals) {
+  constexpr uint32_t PIECE = EmitGeom<RUN>::PIECE;
+  constexpr size_t SMEM = EmitGeom<RUN>::SMEM;
   const int64_t n_chunks = (total + EM_CHUNK - 1) / EM_CHUNK;
-  // sum over chunks of ceil(count / EM_PIECE) <= n_inst / EM_PIECE + n_chunks; surplus CTAs return at once
-  const int64_t grid = n_chunks + n_inst / EM_PIECE + 1;
+  // sum over chunks of ceil(count / piece) <= n_inst / piece + n_chunks; surplus CTAs return at once
+  const int64_t grid = n_chunks + n_inst / PIECE + 1;
   uint32_t* piece_chunk = piece_off + n_chunks + 1;
-  cudaError_t e = launch_serialised(k_emit_pieces, dim3(1), dim3(SP_THREADS), 0, st, chunk_offsets, n_chunks,
+  cudaError_t e = launch_serialised(k_emit_pieces<RUN>, dim3(1), dim3(SP_THREADS), 0, st, chunk_offsets, n_chunks,
                                     piece_off);
   if (e == cudaSuccess)
     e = launch_serialised(k_emit_piece_map, dim3((unsigned)((n_chunks + 255) / 256)), dim3(256), 0, st,
@@ -821,17 +832,33 @@ cudaError_t launch_emit(cudaStream_t st, int64_t total, int64_t n, const uint32_
   e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev >= kMaxDevicesAttr || !smem_set[dev]) {
-    e = cudaFuncSetAttribute(k_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EM_SMEM);
+    e = cudaFuncSetAttribute(k_emit<RUN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
     if (e == cudaSuccess)  // several CTAs per SM rather than the largest L1
-      e = cudaFuncSetAttribute(k_emit, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+      e = cudaFuncSetAttribute(k_emit<RUN>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     if (dev < kMaxDevicesAttr) smem_set[dev] = true;
   }
-  e = launch_serialised(k_emit, dim3((unsigned)grid), dim3(EM_THREADS), EM_SMEM, st, total, n, order, counts_sorted,
-                        chunk_offsets, (const uint32_t*)piece_off, (const uint32_t*)piece_chunk, n_chunks, proj, cams,
-                        log2f(alpha_min), n_tiles <= (1ll << 24), cull, keys, vals);
+  e = launch_serialised(k_emit<RUN>, dim3((unsigned)grid), dim3(EM_THREADS), SMEM, st, total, n, order,
+                        counts_sorted, chunk_offsets, (const uint32_t*)piece_off, (const uint32_t*)piece_chunk,
+                        n_chunks, proj, cams, log2f(alpha_min), n_tiles <= (1ll << 24), cull, keys, vals);
   count_launches(3);
   return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
+cudaError_t launch_emit(cudaStream_t st, int64_t total, int64_t n, const uint32_t* order,
+                        const uint32_t* counts_sorted, const uint64_t* chunk_offsets, int64_t n_inst,
+                        uint32_t* piece_off, const ProjRec* proj, const CamDev* cams, float alpha_min,
+                        int64_t n_tiles, int cull, int run, uint32_t* keys, uint32_t* vals) {
+  if (total == 0 || n_inst == 0) return cudaSuccess;
+  if (run == 4)
+    return emit_launch<4>(st, total, n, order, counts_sorted, chunk_offsets, n_inst, piece_off, proj, cams,
+                          alpha_min, n_tiles, cull, keys, vals);
+  if (run == 16)
+    return emit_launch<16>(st, total, n, order, counts_sorted, chunk_offsets, n_inst, piece_off, proj, cams,
+                           alpha_min, n_tiles, cull, keys, vals);
+  return emit_launch<8>(st, total, n, order, counts_sorted, chunk_offsets, n_inst, piece_off, proj, cams, alpha_min,
+                        n_tiles, cull, keys, vals);
 }
 
 cudaError_t launch_tile_ranges(cudaStream_t st, int64_t n_inst, const uint32_t* keys, uint2* ranges) {

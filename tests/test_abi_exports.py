@@ -48,13 +48,14 @@ def test_binding_constants_equal_the_header():
 
 def test_shape_table_without_gpu(lib_path):
     """Shape 0 is the default; every shape has a distinct name naming its
-    forward and backward (batch/warps) and the sort's keys per thread."""
+    forward and backward (batch/warps), the sort's keys per thread and the
+    emission's instances per thread."""
     from paper_2512_20943_b300 import _abi
     lib = _abi.load_library()
     n = lib.airgs_shape_count()
     names = [lib.airgs_shape_name(i).decode() for i in range(n)]
-    assert n == 75 and len(set(names)) == n
-    assert names[0] == "fwd 32/32 bwd 32/28 keys 8"
+    assert n == 225 and len(set(names)) == n
+    assert names[0] == "fwd 32/32 bwd 32/28 keys 8 run 8"
     assert lib.airgs_shape_name(n) == b"" and lib.airgs_shape_name(-1) == b""
 
 

@@ -35,7 +35,8 @@ def rast_shape(shape):
     """A context pinned to one compiled kernel shape (radix ordering, half-tile
     lists).  Shape 0 is the default; 1-4 change the blend forward's staging
     batch / warps per SM, 5, 10, 15, 20 the backward's, 25 and 50 the instance
-    sort's keys per thread (Rasterizer.shape_names())."""
+    sort's keys per thread, 75 and 150 the emission's instances per thread
+    (Rasterizer.shape_names())."""
     from paper_2512_20943_b300 import RasterConfig, Rasterizer
     if shape not in _by_shape:
         _by_shape[shape] = Rasterizer(RasterConfig(kernel_shape=shape, sort_mode=0))
@@ -45,7 +46,8 @@ def rast_shape(shape):
 FWD_SHAPES = [0, 1, 2, 3, 4]      # forward (batch, warps) axis, the rest at shape 0
 BWD_SHAPES = [0, 5, 10, 15, 20]   # backward axis
 SORT_SHAPES = [0, 25, 50]         # instance-sort keys per thread axis
-SHAPES = sorted(set(FWD_SHAPES + BWD_SHAPES + SORT_SHAPES))
+EMIT_SHAPES = [0, 75, 150]        # emission instances-per-thread axis
+SHAPES = sorted(set(FWD_SHAPES + BWD_SHAPES + SORT_SHAPES + EMIT_SHAPES))
 
 
 def render_gpu(rast, g, cams, **kw):
@@ -127,7 +129,7 @@ def test_tile_lists_match_fp64_sets(rast, name):
     res.state.release()
 
 
-@pytest.mark.parametrize("shape", sorted(set(FWD_SHAPES + SORT_SHAPES)))
+@pytest.mark.parametrize("shape", sorted(set(FWD_SHAPES + SORT_SHAPES + EMIT_SHAPES)))
 @pytest.mark.parametrize("name", ["plain_2k", "sh3_ragged"])
 def test_forward_matches_oracle(name, shape):
     rast = rast_shape(shape)
