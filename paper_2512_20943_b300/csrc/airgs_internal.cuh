@@ -45,10 +45,16 @@ constexpr int kFlagClampShift = 1;  // bits 1..3: colour channel clamped at 0
 constexpr int kFlagGuardX = 16;     // x/z outside the frustum guard
 constexpr int kFlagGuardY = 32;
 
-// Per (view, Gaussian) gradient record accumulated by the blend backward:
-//   a = {dL/dmx, dL/dmy, dL/dA, dL/dB}
-//   b = {dL/dC, dL/dopacity, dL/dr, dL/dg}
+// Per (view, Gaussian) record of the sums the blend backward accumulates over
+// the Gaussian's replayed pairs, with d = mean2d - pixel and t = dL/dalpha G on
+// unclamped pairs:
+//   a = {S_x = sum t dx, S_y = sum t dy, S_xx = sum t dx^2, S_xy = sum t dx dy}
+//   b = {S_yy = sum t dy^2, S_t = sum t, dL/dr, dL/dg}
 //   c = {dL/db, 0, 0, 0}
+// The projection adjoint turns them into the 2D gradients: with
+// power2 = a2 dx^2 + b2 dx dy + c2 dy^2 = log2(e) power and dL/dpower = o t,
+// dL/dmean2d = o ln2 (2 a2 S_x + b2 S_y, b2 S_x + 2 c2 S_y),
+// dL/dA = -o S_xx / 2, dL/dB = -o S_xy, dL/dC = -o S_yy / 2, dL/dopacity = S_t.
 struct __align__(16) GradRec {
   float4 a, b, c;
 };
@@ -58,6 +64,15 @@ struct __align__(16) GradRec {
 // these helpers, with explicit rounding intrinsics, so that the backward's
 // replay takes exactly the forward's skip / blend / stop decisions and
 // reproduces its running sums bit for bit.
+// a / b with the hardware reciprocal, subnormal inputs and results flushed to
+// zero (the blend backward divides the colour still ahead by 1 - alpha, which
+// lies in [1 - alpha_max, 1]).
+__device__ __forceinline__ float div_approx_ftz(float a, float b) {
+  float q;
+  asm("div.approx.ftz.f32 %0, %1, %2;" : "=f"(q) : "f"(a), "f"(b));
+  return q;
+}
+
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));

@@ -1,27 +1,34 @@
 // Blend backward (sm_103a): the adjoint of the blend forward by a per-tile
-// front-to-back replay, one warp per 16x8 half tile, persistent over an atomic
-// queue of all (view, half tile) items of a batch.  No per-pixel list is
-// stored: each pixel replays its list up to n_contrib with the forward's exact
-// arithmetic, recomputing the transmittance T_i.  With R_i the colour still
-// ahead after entry i (C_final - P_i, background included):
+// front-to-back replay, persistent over an atomic queue of all (view, item)
+// work items of a batch.  No per-pixel list is stored: each pixel replays its
+// list up to n_contrib with the forward's exact arithmetic, recomputing the
+// transmittance T_i.  With R_i the colour still ahead after entry i
+// (C_final - P_i, background included):
 //     dC/dalpha_i = c_i T_i - R_i / (1 - alpha_i),   dC/dc_i = alpha_i T_i,
 // chained through alpha = o G, G = exp(power) to the opacity, the 2D mean and
 // the conic; a clamped alpha (o G > alpha_max) passes no gradient to o or G.
 //
-// Staging uses the forward's exact block masks (stored in the half-list
-// entries) restricted to the blocks whose largest n_contrib lies beyond the
-// entry's position.  Each entry's ten per-lane sums
+// Two replays share the per-entry arithmetic (replay_entry):
+//  - k_blend_bwd: one warp per 16x8 half tile (four 8x4 blocks, a lane's four
+//    pixels), walking the half's compacted list with the forward's exact block
+//    masks stored in its entries;
+//  - k_blend_bwd_tile: one warp per 16x16 tile (eight 8x4 blocks, a lane's
+//    eight pixels), walking the tile's full list with each entry's exact block
+//    mask computed while staging; an entry reaching both halves of a tile is
+//    reduced once instead of twice.
+// Either way an entry's mask is restricted to the blocks whose largest
+// n_contrib lies beyond its position.  Each entry's ten per-lane sums
 //   0 S_x = sum t dx, 1 S_y = sum t dy, 2 sum t dx^2, 3 sum t dx dy,
 //   4 sum t dy^2, 5 sum t, 6-8 colour, 9 blend weight
-// (t = dL/dalpha G on unclamped pairs) plus its blended-pair count are
-// deferred into a per-warp shared-memory table of three entries, reduced by one
-// row sum per lane (a transpose through shared memory) and flushed with one
-// scalar red.global.add per sum; with power2 = a2 dx^2 + b2 dx dy + c2 dy^2
-// and dL/dpower = o t the mean gradient is o ln2 (2 a2 S_x + b2 S_y,
-// b2 S_x + 2 c2 S_y).  With L1 the image gradient sign(C - target)/(3 sum H W)
-// and the loss are computed from the forward's image and the target in the
-// kernel; with IMP the blend weights and counts of the replay are the
-// Gaussians' usage frequency.
+// (t = dL/dalpha G on unclamped pairs) are deferred into a per-warp
+// shared-memory table of three entries, reduced by one row sum per lane (a
+// transpose through shared memory) and flushed with one scalar red.global.add
+// per sum into the Gaussian's gradient record (the projection adjoint applies
+// the 2D coefficients); the entry's blended-pair count is a warp vote per
+// block.  With L1 the image gradient sign(C - target)/(3 sum H W) and the loss
+// are computed from the forward's image and the target in the kernel; with IMP
+// the blend weights and counts of the replay are the Gaussians' usage
+// frequency.
 #include "blend_common.cuh"
 
 namespace airgs {
@@ -29,21 +36,20 @@ namespace airgs {
 namespace {
 
 // Table rows 10 f + q hold, per lane (column), sum q of the f-th deferred
-// Gaussian; row 30 holds the lanes' blended-pair counts of the three Gaussians
-// packed in 8-bit fields (at most 4 pixels per lane and 128 per half tile, so
-// the packed sums are integers below 2^24 and exact in single precision).
-// Lane s sums row s with eight 16-byte loads (rows padded to 36 floats: each
-// 8-lane phase of a 16-byte load touches 32 different banks) and sends it with
-// one scalar reduction.
+// Gaussian.  Lane r < 10 nf sums row r with eight 16-byte loads (rows padded
+// to 36 floats: each 8-lane phase of a 16-byte load touches 32 different
+// banks) and sends it with one scalar reduction: sums 0-8 to the record's
+// floats 0-8, sum 9 (the blend weight) to the usage weight.
 constexpr int kDeferG = 3;
 constexpr int kRedStride = 36;
+constexpr int kRedRows = kDeferG * 10;
 
 template <bool IMP>
-__device__ __forceinline__ void flush_deferred(float (*s_red)[kRedStride], const uint32_t* s_fid, const float4* s_fcon,
-                                               int nf, uint32_t cpack, GradRec* gradv, const BwdIn& in, int lane) {
-  if (IMP) s_red[30][lane] = (float)cpack;
+__device__ __forceinline__ void flush_deferred(float (*s_red)[kRedStride], const uint32_t* s_fid,
+                                               const uint32_t* s_fcnt, int nf, GradRec* gradv, const BwdIn& in,
+                                               int lane, int f, int q) {
   __syncwarp();
-  const int row = lane < 31 ? lane : 30;
+  const int row = lane < kRedRows ? lane : kRedRows - 1;
   const float4* rp = reinterpret_cast<const float4*>(&s_red[row][0]);
   float4 s = rp[0];
   float2 s01 = make_float2(s.x, s.y), s23 = make_float2(s.z, s.w);
@@ -55,186 +61,126 @@ __device__ __forceinline__ void flush_deferred(float (*s_red)[kRedStride], const
   }
   const float2 s4 = __fadd2_rn(s01, s23);
   const float sum = s4.x + s4.y;
-  const float other = __shfl_xor_sync(kAll, sum, 1);  // S_y for the S_x lane and vice versa
-  const int f = lane / 10, q = lane - 10 * f;
   if (lane < 10 * nf && (IMP || q < 9)) {
-    // GradRec floats 0-8: mean2d, conic A (x -1/2), B (x -1), C (x -1/2), opacity,
-    // colour; sum 9 (the blend weight) goes to the importance weights.  One
-    // branch-free coefficient pair per lane: value = ca sum + cb other.
     const uint32_t id = s_fid[f];
-    const float4 cf = s_fcon[f];  // (a2, b2, c2, o)
-    const float o = cf.w, lo = kLn2 * cf.w;
-    const float ca = q == 0 ? 2.f * lo * cf.x : q == 1 ? 2.f * lo * cf.z : q == 3 ? -o : q < 5 ? -0.5f * o : 1.f;
-    const float cb = q < 2 ? lo * cf.y : 0.f;
-    const float val = fmaf(ca, sum, cb * other);
     float* dst = q < 9 ? reinterpret_cast<float*>(gradv + id) + q : in.imp_w + id;
-    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(dst), "f"(val) : "memory");
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(dst), "f"(sum) : "memory");
   }
-  if (IMP) {
-    const uint32_t packed = (uint32_t)__shfl_sync(kAll, sum, 30);
-    if (lane < nf) {
-      const uint32_t c = (packed >> (8 * lane)) & 0xFFu;
-      asm volatile("red.global.add.u32 [%0], %1;" ::"l"(in.imp_cnt + s_fid[lane]), "r"(c) : "memory");
-    }
-  }
+  if (IMP && lane < nf)
+    asm volatile("red.global.add.u32 [%0], %1;" ::"l"(in.imp_cnt + s_fid[lane]), "r"(s_fcnt[lane]) : "memory");
   __syncwarp();  // the table is refilled after this
 }
 
-}  // namespace
+// Replays one staged entry over the blocks of mask m (block k = 2 by + bx of
+// ROWS block rows; the lane's pixel of block k sits at (pxb[bx], pyb[by])) with
+// the forward's arithmetic: updates each pixel's T and colour still ahead (gC,
+// dotted with the image gradient g), returns the lane's ten sums in acc and,
+// with IMP, the warp's blended-pair count in cnt (warp-uniform).
+template <int ROWS, bool IMP>
+__device__ __forceinline__ void replay_entry(const float4 ga, const float4 gb, float cb, int pos1, unsigned m,
+                                             const float (&pxb)[2], const float (&pyb)[ROWS], float alpha_max,
+                                             float alpha_min, float (&T)[2 * ROWS], float (&gC)[2 * ROWS],
+                                             const float (&g0)[2 * ROWS], const float (&g1)[2 * ROWS],
+                                             const float (&g2)[2 * ROWS], const int (&nc)[2 * ROWS],
+                                             float (&acc)[10], int& cnt) {
+  const float dxb[2] = {__fsub_rn(ga.x, pxb[0]), __fsub_rn(ga.x, pxb[1])};
+  float2 a01 = make_float2(0.f, 0.f), a24 = a01, a67 = a01;
+  float a3 = 0.f, a5 = 0.f, a8 = 0.f, a9 = 0.f;
+  cnt = 0;
+#pragma unroll
+  for (int by = 0; by < ROWS; ++by) {
+    if (!((m >> (2 * by)) & 3u)) continue;  // warp-uniform
+    float dy, b2dy, c2dy2;  // shared by the row's two blocks
+    row_terms(ga.y, pyb[by], ga.w, gb.x, dy, b2dy, c2dy2);
+#pragma unroll
+    for (int bx = 0; bx < 2; ++bx) {
+      const int k = 2 * by + bx;
+      if (!((m >> k) & 1u)) continue;  // warp-uniform
+      const float dx = dxb[bx];
+      const float p2 = power2_of(dx, ga.z, b2dy, c2dy2);
+      const float G = ex2_approx(p2);
+      const float oG = __fmul_rn(gb.y, G);
+      const float alpha = alpha_of(gb.y, G, alpha_max);
+      // pair (pixel, entry) replayed iff pos1 <= n_contrib and the forward blended it
+      const bool valid = (pos1 <= nc[k]) && !(p2 > 0.f) && !(alpha < alpha_min);
+      const float ae = valid ? alpha : 0.f;
+      const float w = __fmul_rn(ae, T[k]);
+      const float gc = g0[k] * gb.z + g1[k] * gb.w + g2[k] * cb;
+      // independent sums in pairs: one packed FP32x2 operation each
+      a67 = __ffma2_rn(make_float2(w, w), make_float2(g0[k], g1[k]), a67);
+      a8 = fmaf(w, g2[k], a8);
+      // gC[k] holds the colour still ahead of the replay, R = gC - gP
+      gC[k] = fmaf(-gc, w, gC[k]);
+      const float om = __fsub_rn(1.0f, ae);
+      const float dL_dalpha = T[k] * gc - div_approx_ftz(gC[k], om);
+      T[k] = __fmul_rn(T[k], om);
+      // t = dL/dalpha G on unclamped replayed pairs, whose ae equals o G
+      // exactly (a clamped pair has ae = alpha_max < o G, a skipped one 0)
+      const float tt = dL_dalpha * (ae == oG ? G : 0.f);
+      a5 += tt;
+      const float2 d2 = make_float2(dx, dy);
+      const float2 td = __fmul2_rn(make_float2(tt, tt), d2);  // (t dx, t dy)
+      a01 = __fadd2_rn(a01, td);
+      a24 = __ffma2_rn(td, d2, a24);                           // (t dx^2, t dy^2)
+      a3 = fmaf(td.x, dy, a3);
+      if (IMP) {
+        a9 += w;
+        cnt += __popc(__ballot_sync(kAll, valid));
+      }
+    }
+  }
+  acc[0] = a01.x;
+  acc[1] = a01.y;
+  acc[2] = a24.x;
+  acc[3] = a3;
+  acc[4] = a24.y;
+  acc[5] = a5;
+  acc[6] = a67.x;
+  acc[7] = a67.y;
+  acc[8] = a8;
+  acc[9] = a9;
+}
 
-template <bool L1, bool IMP, int CB, int MINB>
-__global__ void __launch_bounds__(32, MINB) k_blend_bwd(BlendArgs a, BwdIn in) {
-  __shared__ __align__(16) float s_red[kDeferG * 10 + 1][kRedStride];
-  __shared__ uint32_t s_fid[kDeferG];
-  __shared__ float4 s_fcon[kDeferG];  // (a2, b2, c2, o) of the deferred Gaussians
-  __shared__ float4 s_a[CB];
-  __shared__ float4 s_b[CB];
-  __shared__ StageMeta s_meta[CB];
-
-  const int lane = threadIdx.x;
-  const float alpha_max = a.rp.alpha_max, alpha_min = a.rp.alpha_min;
-  const float log2_amin = log2f(alpha_min);
-  const int lx = lane & 7, ly = lane >> 3;
-  unsigned long long pairs = 0, executed = 0;
-  float loss_acc = 0.f;
-
-  while (true) {
-    const int work = cull_fetch(a.work_counter);
-    if (work >= a.n_tiles * 2) break;
-    const int item = work >> 1, part = work & 1;
-    const int v = view_of_tile_cams(a.cams, a.n_views, item);
-    const CamDev& cam = a.cams[v];
-    const int lt = item - (int)__ldg(&a.cams[v].tile_base);
-    const int X0 = (lt % cam.TW) * kTile, Y0 = (lt / cam.TW) * kTile + part * (kTile / 2);
-    const float pxb[2] = {(float)(X0 + lx) + 0.5f, (float)(X0 + 8 + lx) + 0.5f};
-    const float pyb[2] = {(float)(Y0 + ly) + 0.5f, (float)(Y0 + 4 + ly) + 0.5f};  // the two block rows
+// Per-pixel state of a replay at the start of an item: T = 1, the image
+// gradient g (from the L1 target or the given dL/dC), gC = g . C_final and
+// n_contrib (0 outside the image); adds the pixel's list length to `pairs` and
+// |C - target| to the loss.
+template <bool L1>
+__device__ __forceinline__ void load_pixel(const BwdIn& in, const CamDev& cam, int x, int y, float& T, float& gC,
+                                           float& g0, float& g1, float& g2, int& nc, unsigned long long& pairs,
+                                           float& loss_acc) {
+  T = 1.f;
+  g0 = g1 = g2 = gC = 0.f;
+  nc = 0;
+  if (x < cam.W && y < cam.H) {
     const int64_t HW = (int64_t)cam.W * cam.H;
     const int64_t base3 = 3 * cam.pix_base;
-
-    float T[kBlocks], gC[kBlocks], g0[kBlocks], g1[kBlocks], g2[kBlocks];
-    int nc[kBlocks], gmax[kBlocks];
+    const int64_t pix = (int64_t)y * cam.W + x;
+    float cf[3], gg[3];
 #pragma unroll
-    for (int k = 0; k < kBlocks; ++k) {
-      const int x = X0 + 8 * (k & 1) + lx, y = Y0 + 4 * (k >> 1) + ly;
-      T[k] = 1.f;
-      g0[k] = g1[k] = g2[k] = gC[k] = 0.f;
-      nc[k] = 0;
-      if (x < cam.W && y < cam.H) {
-        const int64_t pix = (int64_t)y * cam.W + x;
-        float cf[3], gg[3];
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-          cf[ch] = in.rgb[base3 + ch * HW + pix];
-          if (L1) {
-            const float d = cf[ch] - in.target[base3 + ch * HW + pix];
-            gg[ch] = d > 0.f ? in.inv_norm : (d < 0.f ? -in.inv_norm : 0.f);
-            loss_acc += fabsf(d);
-          } else {
-            gg[ch] = in.dL[base3 + ch * HW + pix];
-          }
-        }
-        g0[k] = gg[0];
-        g1[k] = gg[1];
-        g2[k] = gg[2];
-        gC[k] = gg[0] * cf[0] + gg[1] * cf[1] + gg[2] * cf[2];
-        nc[k] = in.ncontrib[cam.pix_base + pix];
-        pairs += (unsigned long long)nc[k];
+    for (int ch = 0; ch < 3; ++ch) {
+      cf[ch] = in.rgb[base3 + ch * HW + pix];
+      if (L1) {
+        const float d = cf[ch] - in.target[base3 + ch * HW + pix];
+        gg[ch] = d > 0.f ? in.inv_norm : (d < 0.f ? -in.inv_norm : 0.f);
+        loss_acc += fabsf(d);
+      } else {
+        gg[ch] = in.dL[base3 + ch * HW + pix];
       }
-      gmax[k] = (int)__reduce_max_sync(kAll, (unsigned)nc[k]);  // warp-uniform
     }
-    int maxnc = 0;
-#pragma unroll
-    for (int k = 0; k < kBlocks; ++k) maxnc = max(maxnc, gmax[k]);
-    const uint2 range = a.ranges[item];
-    const bool use_hl = a.hl != nullptr;  // this half's compacted list
-    uint2 er = make_uint2(range.x, range.x + (uint32_t)maxnc);
-    if (use_hl) er = a.hranges[(int64_t)part * a.n_tiles + item];
-    const ProjRec* projv = a.proj + (size_t)v * a.n;
-    GradRec* gradv = in.grad + (size_t)v * a.n;
-    uint32_t exec_groups = 0;
-    bool past_end = false;
-    int ns = 0;          // deferred Gaussians in the table
-    uint32_t cpack = 0;  // this lane's packed pair counts of those
-
-    for (uint32_t b0 = er.x; b0 < er.y && !past_end; b0 += CB) {
-      const int nb = stage_compact<true>(a, use_hl, b0, (int)min((uint32_t)CB, er.y - b0), range.x, projv, log2_amin,
-                                         (float)X0, (float)Y0, gmax, maxnc, (1u << kBlocks) - 1u, s_a, s_b, s_meta,
-                                         past_end, exec_groups);
-      for (int j = 0; j < nb; ++j) {
-        const StageMeta me = s_meta[j];
-        const int pos1 = (int)me.pos1;  // pair (pixel, entry) replayed iff pos1 <= n_contrib
-        const unsigned m = me.mask;
-        const float4 ga = s_a[j];
-        const float4 gb = s_b[j];
-        const float cb = me.c;
-        const float dxb[2] = {__fsub_rn(ga.x, pxb[0]), __fsub_rn(ga.x, pxb[1])};
-        float acc[10];
-        int cnt = 0;
-        float2 a01 = make_float2(0.f, 0.f), a24 = a01, a67 = a01;
-        acc[3] = acc[5] = acc[8] = acc[9] = 0.f;
-#pragma unroll
-        for (int by = 0; by < 2; ++by) {
-          if (!((m >> (2 * by)) & 3u)) continue;  // warp-uniform
-          float dy, b2dy, c2dy2;  // shared by the row's two blocks
-          row_terms(ga.y, pyb[by], ga.w, gb.x, dy, b2dy, c2dy2);
-#pragma unroll
-          for (int bx = 0; bx < 2; ++bx) {
-            const int k = 2 * by + bx;
-            if (!((m >> k) & 1u)) continue;  // warp-uniform
-            const float dx = dxb[bx];
-            const float p2 = power2_of(dx, ga.z, b2dy, c2dy2);
-            const float G = ex2_approx(p2);
-            const float oG = __fmul_rn(gb.y, G);
-            const float alpha = alpha_of(gb.y, G, alpha_max);
-            const bool valid = (pos1 <= nc[k]) && !(p2 > 0.f) && !(alpha < alpha_min);
-            const float ae = valid ? alpha : 0.f;
-            const bool graded = valid && (oG <= alpha_max);
-            const float w = __fmul_rn(ae, T[k]);
-            const float gc = g0[k] * gb.z + g1[k] * gb.w + g2[k] * cb;
-            // independent sums in pairs: one packed FP32x2 operation each
-            a67 = __ffma2_rn(make_float2(w, w), make_float2(g0[k], g1[k]), a67);
-            acc[8] = fmaf(w, g2[k], acc[8]);
-            // gC[k] holds the colour still ahead of the replay, R = gC - gP
-            gC[k] = fmaf(-gc, w, gC[k]);
-            const float om = __fsub_rn(1.0f, ae);
-            const float dL_dalpha = T[k] * gc - __fdividef(gC[k], om);
-            T[k] = __fmul_rn(T[k], om);
-            // t = dL/dalpha G on unclamped pairs; dL/dpower = o t, o applied at the flush
-            const float tt = dL_dalpha * (graded ? G : 0.f);
-            acc[5] += tt;
-            const float2 d2 = make_float2(dx, dy);
-            const float2 td = __fmul2_rn(make_float2(tt, tt), d2);  // (t dx, t dy)
-            a01 = __fadd2_rn(a01, td);
-            a24 = __ffma2_rn(td, d2, a24);                           // (t dx^2, t dy^2)
-            acc[3] = fmaf(td.x, dy, acc[3]);
-            if (IMP) acc[9] += w;
-            cnt += valid ? 1 : 0;
-          }
-        }
-        acc[0] = a01.x;
-        acc[1] = a01.y;
-        acc[2] = a24.x;
-        acc[4] = a24.y;
-        acc[6] = a67.x;
-        acc[7] = a67.y;
-        // every compacted entry has a live block: defer without a vote
-#pragma unroll
-        for (int q = 0; q < 10; ++q) s_red[ns * 10 + q][lane] = acc[q];
-        if (IMP) cpack += (uint32_t)cnt << (8 * ns);
-        // every lane stores the same values (one shared-memory word each, no branch)
-        s_fid[ns] = me.id;
-        s_fcon[ns] = make_float4(ga.z, ga.w, gb.x, gb.y);
-        if (++ns == kDeferG) {
-          flush_deferred<IMP>(s_red, s_fid, s_fcon, ns, cpack, gradv, in, lane);
-          ns = 0;
-          cpack = 0;
-        }
-      }
-      __syncwarp();
-    }
-    if (ns > 0) flush_deferred<IMP>(s_red, s_fid, s_fcon, ns, cpack, gradv, in, lane);
-    executed += exec_groups;
+    g0 = gg[0];
+    g1 = gg[1];
+    g2 = gg[2];
+    gC = gg[0] * cf[0] + gg[1] * cf[1] + gg[2] * cf[2];
+    nc = in.ncontrib[cam.pix_base + pix];
+    pairs += (unsigned long long)nc;
   }
+}
+
+// Adds the warp's statistics to the launch counters and, with L1, its loss.
+template <bool L1>
+__device__ __forceinline__ void finish_counters(const BlendArgs& a, const BwdIn& in, unsigned long long pairs,
+                                                unsigned long long executed, float loss_acc, int lane) {
   for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(kAll, pairs, o);
   for (int o = 16; o > 0; o >>= 1) executed += __shfl_xor_sync(kAll, executed, o);
   executed *= 32ull;  // 32 lane evaluations per block
@@ -251,40 +197,257 @@ __global__ void __launch_bounds__(32, MINB) k_blend_bwd(BlendArgs a, BwdIn in) {
   }
 }
 
-namespace {
+}  // namespace
 
 template <bool L1, bool IMP, int CB, int MINB>
-cudaError_t bwd_launch(cudaStream_t st, int num_sms, const BlendArgs& a, const BwdIn& in) {
-  cudaError_t e = prefer_shared(k_blend_bwd<L1, IMP, CB, MINB>);
+__global__ void __launch_bounds__(32, MINB) k_blend_bwd(BlendArgs a, BwdIn in) {
+  __shared__ __align__(16) float s_red[kRedRows][kRedStride];
+  __shared__ uint32_t s_fid[kDeferG];
+  __shared__ uint32_t s_fcnt[kDeferG];
+  __shared__ float4 s_a[CB];
+  __shared__ float4 s_b[CB];
+  __shared__ StageMeta s_meta[CB];
+
+  const int lane = threadIdx.x;
+  const int ff = lane / 10, fq = lane - 10 * ff;  // the table row this lane flushes
+  const float alpha_max = a.rp.alpha_max, alpha_min = a.rp.alpha_min;
+  const float log2_amin = log2f(alpha_min);
+  const int lx = lane & 7, ly = lane >> 3;
+  unsigned long long pairs = 0, executed = 0;
+  float loss_acc = 0.f;
+
+  while (true) {
+    const int work = cull_fetch(a.work_counter);
+    if (work >= a.n_tiles * 2) break;
+    const int item = work >> 1, part = work & 1;
+    const int v = view_of_tile_cams(a.cams, a.n_views, item);
+    const CamDev& cam = a.cams[v];
+    const int lt = item - (int)__ldg(&a.cams[v].tile_base);
+    const int X0 = (lt % cam.TW) * kTile, Y0 = (lt / cam.TW) * kTile + part * (kTile / 2);
+    const float pxb[2] = {(float)(X0 + lx) + 0.5f, (float)(X0 + 8 + lx) + 0.5f};
+    const float pyb[2] = {(float)(Y0 + ly) + 0.5f, (float)(Y0 + 4 + ly) + 0.5f};  // the two block rows
+
+    float T[kBlocks], gC[kBlocks], g0[kBlocks], g1[kBlocks], g2[kBlocks];
+    int nc[kBlocks], gmax[kBlocks];
+#pragma unroll
+    for (int k = 0; k < kBlocks; ++k) {
+      load_pixel<L1>(in, cam, X0 + 8 * (k & 1) + lx, Y0 + 4 * (k >> 1) + ly, T[k], gC[k], g0[k], g1[k], g2[k], nc[k],
+                     pairs, loss_acc);
+      gmax[k] = (int)__reduce_max_sync(kAll, (unsigned)nc[k]);  // warp-uniform
+    }
+    int maxnc = 0;
+#pragma unroll
+    for (int k = 0; k < kBlocks; ++k) maxnc = max(maxnc, gmax[k]);
+    const uint2 range = a.ranges[item];
+    const bool use_hl = a.hl != nullptr;  // this half's compacted list
+    uint2 er = make_uint2(range.x, range.x + (uint32_t)maxnc);
+    if (use_hl) er = a.hranges[(int64_t)part * a.n_tiles + item];
+    const ProjRec* projv = a.proj + (size_t)v * a.n;
+    GradRec* gradv = in.grad + (size_t)v * a.n;
+    uint32_t exec_groups = 0;
+    bool past_end = false;
+    int ns = 0;  // deferred Gaussians in the table
+
+    for (uint32_t b0 = er.x; b0 < er.y && !past_end; b0 += CB) {
+      const int nb = stage_compact<true>(a, use_hl, b0, (int)min((uint32_t)CB, er.y - b0), range.x, projv, log2_amin,
+                                         (float)X0, (float)Y0, gmax, maxnc, (1u << kBlocks) - 1u, s_a, s_b, s_meta,
+                                         past_end, exec_groups);
+      for (int j = 0; j < nb; ++j) {
+        const StageMeta me = s_meta[j];
+        const float4 ga = s_a[j];
+        const float4 gb = s_b[j];
+        float acc[10];
+        int cnt;
+        replay_entry<2, IMP>(ga, gb, me.c, (int)me.pos1, me.mask, pxb, pyb, alpha_max, alpha_min, T, gC, g0, g1, g2,
+                             nc, acc, cnt);
+        // every compacted entry has a live block: defer without a vote
+#pragma unroll
+        for (int q = 0; q < 10; ++q) s_red[ns * 10 + q][lane] = acc[q];
+        // every lane stores the same values (one shared-memory word each, no branch)
+        s_fid[ns] = me.id;
+        if (IMP) s_fcnt[ns] = (uint32_t)cnt;
+        if (++ns == kDeferG) {
+          flush_deferred<IMP>(s_red, s_fid, s_fcnt, ns, gradv, in, lane, ff, fq);
+          ns = 0;
+        }
+      }
+      __syncwarp();
+    }
+    if (ns > 0) flush_deferred<IMP>(s_red, s_fid, s_fcnt, ns, gradv, in, lane, ff, fq);
+    executed += exec_groups;
+  }
+  finish_counters<L1>(a, in, pairs, executed, loss_acc, lane);
+}
+
+// ------------------------------------------------------------------ full-tile replay
+constexpr int kTileBlocks = 8;  // 8x4 blocks of a 16x16 tile, block k = 2 by + bx, by 0..3
+
+// Stages the full-list entries [b0, b0 + nb) of a tile, keeping in list order
+// those whose exact block mask, restricted to the blocks whose largest
+// n_contrib (s_gmax) lies beyond the entry's position, is non-zero.
+__device__ __forceinline__ int stage_tile(const BlendArgs& a, uint32_t b0, int nb, uint32_t list0,
+                                          const ProjRec* projv, float log2_amin, float X0, float Y0,
+                                          const int* s_gmax, float4* s_a, float4* s_b, StageMeta* s_meta,
+                                          uint32_t& groups) {
+  const int lane = threadIdx.x & 31;
+  int kept = 0;
+  for (int j0 = 0; j0 < nb; j0 += 32) {
+    const int j = j0 + lane;
+    unsigned msk = 0u;
+    float4 ga = make_float4(0.f, 0.f, 0.f, 0.f), gb = ga;
+    float gc = 0.f;
+    uint32_t id = 0u, pos = 0u;
+    if (j < nb) {
+      id = __ldg(a.ids + b0 + j);
+      pos = b0 + j - list0;
+      unsigned live = 0u;
+#pragma unroll
+      for (int k = 0; k < kTileBlocks; ++k) live |= ((int)pos < s_gmax[k] ? 1u : 0u) << k;
+      if (live) {
+        const ProjRec* r = projv + id;
+        ga = __ldg(&r->a);
+        gb = __ldg(&r->b);
+        gc = __ldg(&r->c.x);
+        msk = block_mask_exact(ga, gb, log2_amin, X0, Y0, live);
+      }
+    }
+    const unsigned bal = __ballot_sync(kAll, msk != 0u);
+    if (msk) {
+      const int d = kept + __popc(bal & ((1u << lane) - 1u));
+      s_a[d] = ga;
+      s_b[d] = gb;
+      s_meta[d] = StageMeta{pos + 1u, msk, gc, id};
+      groups += __popc(msk);
+    }
+    kept += __popc(bal);
+  }
+  __syncwarp();
+  return kept;
+}
+
+template <bool L1, bool IMP, int CB, int MINB>
+__global__ void __launch_bounds__(32, MINB) k_blend_bwd_tile(BlendArgs a, BwdIn in) {
+  __shared__ __align__(16) float s_red[kRedRows][kRedStride];
+  __shared__ uint32_t s_fid[kDeferG];
+  __shared__ uint32_t s_fcnt[kDeferG];
+  __shared__ float4 s_a[CB];
+  __shared__ float4 s_b[CB];
+  __shared__ StageMeta s_meta[CB];
+  __shared__ int s_gmax[kTileBlocks];  // largest n_contrib of each block
+
+  const int lane = threadIdx.x;
+  const int ff = lane / 10, fq = lane - 10 * ff;
+  const float alpha_max = a.rp.alpha_max, alpha_min = a.rp.alpha_min;
+  const float log2_amin = log2f(alpha_min);
+  const int lx = lane & 7, ly = lane >> 3;
+  unsigned long long pairs = 0, executed = 0;
+  float loss_acc = 0.f;
+
+  while (true) {
+    const int item = cull_fetch(a.work_counter);
+    if (item >= a.n_tiles) break;
+    const int v = view_of_tile_cams(a.cams, a.n_views, item);
+    const CamDev& cam = a.cams[v];
+    const int lt = item - (int)__ldg(&a.cams[v].tile_base);
+    const int X0 = (lt % cam.TW) * kTile, Y0 = (lt / cam.TW) * kTile;
+    const float pxb[2] = {(float)(X0 + lx) + 0.5f, (float)(X0 + 8 + lx) + 0.5f};
+    float pyb[kTileBlocks / 2];
+#pragma unroll
+    for (int by = 0; by < kTileBlocks / 2; ++by) pyb[by] = (float)(Y0 + 4 * by + ly) + 0.5f;
+
+    float T[kTileBlocks], gC[kTileBlocks], g0[kTileBlocks], g1[kTileBlocks], g2[kTileBlocks];
+    int nc[kTileBlocks];
+    int maxnc = 0;
+#pragma unroll
+    for (int k = 0; k < kTileBlocks; ++k) {
+      load_pixel<L1>(in, cam, X0 + 8 * (k & 1) + lx, Y0 + 4 * (k >> 1) + ly, T[k], gC[k], g0[k], g1[k], g2[k], nc[k],
+                     pairs, loss_acc);
+      const int gm = (int)__reduce_max_sync(kAll, (unsigned)nc[k]);  // warp-uniform
+      if (lane == k) s_gmax[k] = gm;
+      maxnc = max(maxnc, gm);
+    }
+    __syncwarp();
+    const uint2 range = a.ranges[item];
+    const uint32_t end = range.x + (uint32_t)maxnc;  // no entry at or beyond maxnc is replayed
+    const ProjRec* projv = a.proj + (size_t)v * a.n;
+    GradRec* gradv = in.grad + (size_t)v * a.n;
+    uint32_t exec_groups = 0;
+    int ns = 0;
+
+    for (uint32_t b0 = range.x; b0 < end; b0 += CB) {
+      const int nb = stage_tile(a, b0, (int)min((uint32_t)CB, end - b0), range.x, projv, log2_amin, (float)X0,
+                                (float)Y0, s_gmax, s_a, s_b, s_meta, exec_groups);
+      for (int j = 0; j < nb; ++j) {
+        const StageMeta me = s_meta[j];
+        const float4 ga = s_a[j];
+        const float4 gb = s_b[j];
+        float acc[10];
+        int cnt;
+        replay_entry<kTileBlocks / 2, IMP>(ga, gb, me.c, (int)me.pos1, me.mask, pxb, pyb, alpha_max, alpha_min, T,
+                                           gC, g0, g1, g2, nc, acc, cnt);
+#pragma unroll
+        for (int q = 0; q < 10; ++q) s_red[ns * 10 + q][lane] = acc[q];
+        s_fid[ns] = me.id;
+        if (IMP) s_fcnt[ns] = (uint32_t)cnt;
+        if (++ns == kDeferG) {
+          flush_deferred<IMP>(s_red, s_fid, s_fcnt, ns, gradv, in, lane, ff, fq);
+          ns = 0;
+        }
+      }
+      __syncwarp();
+    }
+    if (ns > 0) flush_deferred<IMP>(s_red, s_fid, s_fcnt, ns, gradv, in, lane, ff, fq);
+    executed += exec_groups;
+  }
+  finish_counters<L1>(a, in, pairs, executed, loss_acc, lane);
+}
+
+namespace {
+
+template <class K>
+cudaError_t launch_persistent(K kernel, int64_t items, cudaStream_t st, int num_sms, const BlendArgs& a,
+                              const BwdIn& in) {
+  cudaError_t e = prefer_shared(kernel);
   if (e != cudaSuccess) return e;
-  const int grid = persistent_grid(k_blend_bwd<L1, IMP, CB, MINB>, num_sms, a.n_tiles * 2, e);
+  const int grid = persistent_grid(kernel, num_sms, items, e);
   if (e != cudaSuccess) return e;
-  if (grid > 0) k_blend_bwd<L1, IMP, CB, MINB><<<grid, 32, 0, st>>>(a, in);
+  if (grid > 0) kernel<<<grid, 32, 0, st>>>(a, in);
   count_launches(1);
   return cudaGetLastError();
 }
 
-template <int CB, int MINB>
+template <bool TILE, bool L1, bool IMP, int CB, int MINB>
+cudaError_t bwd_launch(cudaStream_t st, int num_sms, const BlendArgs& a, const BwdIn& in) {
+  if constexpr (TILE)
+    return launch_persistent(k_blend_bwd_tile<L1, IMP, CB, MINB>, a.n_tiles, st, num_sms, a, in);
+  else
+    return launch_persistent(k_blend_bwd<L1, IMP, CB, MINB>, a.n_tiles * 2, st, num_sms, a, in);
+}
+
+template <bool TILE, int CB, int MINB>
 cudaError_t bwd_dispatch(cudaStream_t st, int num_sms, const BlendArgs& a, const BwdIn& in) {
   const bool l1 = in.target != nullptr, imp = in.imp_w != nullptr;
   if (l1)
-    return imp ? bwd_launch<true, true, CB, MINB>(st, num_sms, a, in)
-               : bwd_launch<true, false, CB, MINB>(st, num_sms, a, in);
-  return imp ? bwd_launch<false, true, CB, MINB>(st, num_sms, a, in)
-             : bwd_launch<false, false, CB, MINB>(st, num_sms, a, in);
+    return imp ? bwd_launch<TILE, true, true, CB, MINB>(st, num_sms, a, in)
+               : bwd_launch<TILE, true, false, CB, MINB>(st, num_sms, a, in);
+  return imp ? bwd_launch<TILE, false, true, CB, MINB>(st, num_sms, a, in)
+             : bwd_launch<TILE, false, false, CB, MINB>(st, num_sms, a, in);
 }
 
 }  // namespace
 
-// The compiled backward shapes (kBwdShapes in kernels.h): staged entries per
-// batch and warps per SM (the register bound).
+// The compiled backward shapes (kBwdShapes in kernels.h): item (half or full
+// tile), staged entries per batch and warps per SM (the register bound).
 cudaError_t launch_blend_bwd(cudaStream_t st, int shape, int num_sms, const BlendArgs& a, const BwdIn& in) {
   switch (shape) {
-    case 1: return bwd_dispatch<16, 28>(st, num_sms, a, in);
-    case 2: return bwd_dispatch<64, 28>(st, num_sms, a, in);
-    case 3: return bwd_dispatch<32, 24>(st, num_sms, a, in);
-    case 4: return bwd_dispatch<32, 32>(st, num_sms, a, in);
-    default: return bwd_dispatch<32, 28>(st, num_sms, a, in);
+    case 1: return bwd_dispatch<false, 16, 28>(st, num_sms, a, in);
+    case 2: return bwd_dispatch<false, 64, 28>(st, num_sms, a, in);
+    case 3: return bwd_dispatch<false, 32, 24>(st, num_sms, a, in);
+    case 4: return bwd_dispatch<false, 32, 32>(st, num_sms, a, in);
+    case 5: return bwd_dispatch<true, 32, 20>(st, num_sms, a, in);
+    case 6: return bwd_dispatch<true, 32, 24>(st, num_sms, a, in);
+    case 7: return bwd_dispatch<true, 32, 16>(st, num_sms, a, in);
+    default: return bwd_dispatch<false, 32, 28>(st, num_sms, a, in);
   }
 }
 

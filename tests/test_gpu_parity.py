@@ -33,20 +33,23 @@ _by_shape = {}
 
 def rast_shape(shape):
     """A context pinned to one compiled kernel shape (radix ordering, half-tile
-    lists).  Shape 0 is the default; 1-4 change the blend forward's staging
-    batch / warps per SM, 5, 10, 15, 20 the backward's, 25 and 50 the instance
-    sort's keys per thread, 75 and 150 the emission's instances per thread
-    (Rasterizer.shape_names())."""
+    lists).  Shape 0 is the default; a shape index packs (forward f, backward
+    b, sort k, emission e) as f + NF (b + NB (k + NS e)): the forward's staging
+    batch / warps per SM, the backward's (half-tile replays, then full-tile
+    replays), the instance sort's keys per thread and the emission's instances
+    per thread (Rasterizer.shape_names())."""
     from paper_2512_20943_b300 import RasterConfig, Rasterizer
     if shape not in _by_shape:
         _by_shape[shape] = Rasterizer(RasterConfig(kernel_shape=shape, sort_mode=0))
     return _by_shape[shape]
 
 
-FWD_SHAPES = [0, 1, 2, 3, 4]      # forward (batch, warps) axis, the rest at shape 0
-BWD_SHAPES = [0, 5, 10, 15, 20]   # backward axis
-SORT_SHAPES = [0, 25, 50]         # instance-sort keys per thread axis
-EMIT_SHAPES = [0, 75, 150]        # emission instances-per-thread axis
+NF, NB, NS, NE = 5, 8, 3, 3      # compiled forward, backward, sort and emission shapes
+FWD_SHAPES = list(range(NF))                       # forward (batch, warps) axis, the rest at shape 0
+BWD_SHAPES = [NF * b for b in range(NB)]           # backward axis (5-7: full-tile replays)
+TILE_BWD_SHAPES = [NF * b for b in range(5, NB)]
+SORT_SHAPES = [NF * NB * k for k in range(NS)]     # instance-sort keys per thread axis
+EMIT_SHAPES = [NF * NB * NS * e for e in range(NE)]  # emission instances-per-thread axis
 SHAPES = sorted(set(FWD_SHAPES + BWD_SHAPES + SORT_SHAPES + EMIT_SHAPES))
 
 
@@ -424,7 +427,47 @@ def test_shapes_agree(scene):
     assert int(o0.importance_cnt.sum()) > 0
 
 
-@pytest.mark.parametrize("shape", [0, 10])
+def large_faint_scene():
+    """A few dozen large, faint Gaussians: each covers whole 16x16 tiles with
+    every pixel blending it (a full-tile replay's entry counts up to 256
+    blended pairs in one tile, beyond 8 bits) and no pixel saturates."""
+    g = synthetic.gaussians(24, 5, mean_mode="uniform", mean_scale=(0.6, 0.5, 0.3), log_scale=(-0.9, 0.15),
+                            sh_degree=1)
+    g["opacity_logit"][:] = -2.0
+    cams = [synthetic.camera((0.0, 0.0, -4.0), 100, 70, fov_x_deg=50.0),
+            synthetic.camera((0.4, -0.3, -3.6), 53, 37, fov_x_deg=55.0)]
+    return g, cams
+
+
+@pytest.mark.parametrize("shape", [0] + TILE_BWD_SHAPES)
+def test_large_gaussians_backward_counts_and_gradients(shape):
+    """Usage counts accumulated by the backward replay equal the forward's
+    (and the oracle's) when one entry blends all 256 pixels of a tile, and the
+    gradients match the oracle's."""
+    rast = rast_shape(shape)
+    g, cams = large_faint_scene()
+    ref = oracle.render(synthetic.widen(g), cams)
+    t, res = render_gpu(rast, g, cams, importance=True, save=True)
+    c = res.importance_cnt.cpu().numpy()
+    assert c.max() > 2 * 256  # several full tiles per Gaussian
+    ok = ref["gauss_ambig"] == 0
+    assert np.array_equal(c[ok], ref["importance_cnt"][ok])
+    iw = torch.zeros_like(res.importance_w)
+    ic = torch.zeros_like(res.importance_cnt)
+    dL = masked_dL(cams, ref, 31)
+    flat = torch.from_numpy(np.concatenate([d.reshape(-1) for d in dL]).astype(np.float32)).cuda()
+    gr = rast.render_backward(res.state, flat, importance=(iw, ic))
+    torch.cuda.synchronize()
+    assert np.array_equal(ic.cpu().numpy(), c)
+    w = res.importance_w.cpu().numpy()
+    assert np.abs(iw.cpu().numpy() - w).max() < 1e-4 * max(1.0, w.max())
+    ref_g = oracle.render_backward(synthetic.widen(g), cams, dL)
+    for k in ("means", "log_scales", "quats", "opacity_logit", "sh"):
+        assert_grad_close(gr[k].cpu().numpy(), ref_g[k], k)
+    res.state.release()
+
+
+@pytest.mark.parametrize("shape", [0, 10, 25])
 def test_needles_backward_matches_oracle(shape):
     rast = rast_shape(shape)
     g, cams = needle_scene(thin=-3.5, long=-2.0)
