@@ -48,9 +48,10 @@ constexpr int kFlagGuardY = 32;
 // Per (view, Gaussian) record of the sums the blend backward accumulates over
 // the Gaussian's replayed pairs, with d = mean2d - pixel and t = dL/dalpha G on
 // unclamped pairs:
-//   a = {S_x = sum t dx, S_y = sum t dy, S_xx = sum t dx^2, S_xy = sum t dx dy}
-//   b = {S_yy = sum t dy^2, S_t = sum t, dL/dr, dL/dg}
+//   a = {S_x = sum t dx, S_y = sum t dy, S_xx = sum t dx^2, S_yy = sum t dy^2}
+//   b = {S_xy = sum t dx dy, S_t = sum t, dL/dr, dL/dg}
 //   c = {dL/db, 0, 0, 0}
+// (the order of the backward's accumulator pairs)
 // The projection adjoint turns them into the 2D gradients: with
 // power2 = a2 dx^2 + b2 dx dy + c2 dy^2 = log2(e) power and dL/dpower = o t,
 // dL/dmean2d = o ln2 (2 a2 S_x + b2 S_y, b2 S_x + 2 c2 S_y),

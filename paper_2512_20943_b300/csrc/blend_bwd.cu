@@ -17,15 +17,16 @@
 //    mask computed while staging; an entry reaching both halves of a tile is
 //    reduced once instead of twice.
 // Either way an entry's mask is restricted to the blocks whose largest
-// n_contrib lies beyond its position.  Each entry's ten per-lane sums
-//   0 S_x = sum t dx, 1 S_y = sum t dy, 2 sum t dx^2, 3 sum t dx dy,
-//   4 sum t dy^2, 5 sum t, 6-8 colour, 9 blend weight
+// n_contrib lies beyond its position.  Each entry's ten per-lane sums, in five
+// pairs
+//   (S_x = sum t dx, S_y = sum t dy), (sum t dx^2, sum t dy^2),
+//   (sum t dx dy, sum t), (colour r, g), (colour b, blend weight)
 // (t = dL/dalpha G on unclamped pairs) are deferred into a per-warp
-// shared-memory table of three entries, reduced by one row sum per lane (a
-// transpose through shared memory) and flushed with one scalar red.global.add
-// per sum into the Gaussian's gradient record (the projection adjoint applies
-// the 2D coefficients); the entry's blended-pair count is a warp vote per
-// block.  With L1 the image gradient sign(C - target)/(3 sum H W) and the loss
+// shared-memory table of three entries with one 8-byte store per pair, reduced
+// by two lanes per pair (a transpose through shared memory) and flushed with one
+// scalar red.global.add per sum into the Gaussian's gradient record (the
+// projection adjoint applies the 2D coefficients); the entry's blended-pair
+// count is a warp reduction of the lanes' counts.  With L1 the image gradient sign(C - target)/(3 sum H W) and the loss
 // are computed from the forward's image and the target in the kernel; with IMP
 // the blend weights and counts of the replay are the Gaussians' usage
 // frequency.
@@ -35,58 +36,72 @@ namespace airgs {
 
 namespace {
 
-// Table rows 10 f + q hold, per lane (column), sum q of the f-th deferred
-// Gaussian.  Lane r < 10 nf sums row r with eight 16-byte loads (rows padded
-// to 36 floats: each 8-lane phase of a 16-byte load touches 32 different
-// banks) and sends it with one scalar reduction: sums 0-8 to the record's
-// floats 0-8, sum 9 (the blend weight) to the usage weight.
+// Row 5 f + p of the table holds, per lane, sum pair p of the f-th deferred
+// Gaussian: lanes 0-15 at float2 slots 0-15, lanes 16-31 at slots 18-33 (rows
+// of 36 float2 = 72 words, 8 banks apart; the 16-byte gap before the upper
+// half puts the two halves 4 banks apart, so each 8-lane phase of the flush's
+// 16-byte loads touches 32 different banks).  In the flush lanes 2i and 2i+1
+// sum row i over lanes 0-15 and 16-31 (eight 16-byte loads each), trade the
+// component the other one owns with one shuffle, and send sum 2p + h (h = lane
+// parity) with one scalar reduction: sums 0-8 to the record's floats 0-8, sum 9
+// (the blend weight) to the usage weight.
 constexpr int kDeferG = 3;
-constexpr int kRedStride = 36;
-constexpr int kRedRows = kDeferG * 10;
+constexpr int kPairRows = kDeferG * 5;
+constexpr int kPairStride = 36;  // float2 slots per row
+
+__device__ __forceinline__ int table_slot(int lane) { return lane + ((lane >> 4) << 1); }
 
 template <bool IMP>
-__device__ __forceinline__ void flush_deferred(float (*s_red)[kRedStride], const uint32_t* s_fid,
-                                               const uint32_t* s_fcnt, int nf, GradRec* gradv, const BwdIn& in,
-                                               int lane, int f, int q) {
+__device__ __forceinline__ void flush_deferred(float2 (*s_tab)[kPairStride], const uint2* s_fmeta, int nf,
+                                               GradRec* gradv, const BwdIn& in, int lane) {
   __syncwarp();
-  const int row = lane < kRedRows ? lane : kRedRows - 1;
-  const float4* rp = reinterpret_cast<const float4*>(&s_red[row][0]);
-  float4 s = rp[0];
-  float2 s01 = make_float2(s.x, s.y), s23 = make_float2(s.z, s.w);
+  const int row = lane < 2 * kPairRows ? lane >> 1 : kPairRows - 1, h = lane & 1;
+  const float4* rp = reinterpret_cast<const float4*>(&s_tab[row][18 * h]);
+  float4 u = rp[0];
+  float2 s0 = make_float2(u.x, u.y), s1 = make_float2(u.z, u.w);
 #pragma unroll
-  for (int i = 1; i < 8; ++i) {  // row sums as packed FP32x2 additions
-    const float4 u = rp[i];
-    s01 = __fadd2_rn(s01, make_float2(u.x, u.y));
-    s23 = __fadd2_rn(s23, make_float2(u.z, u.w));
+  for (int i = 1; i < 8; ++i) {  // the half row's 16 pairs as packed FP32x2 additions
+    u = rp[i];
+    s0 = __fadd2_rn(s0, make_float2(u.x, u.y));
+    s1 = __fadd2_rn(s1, make_float2(u.z, u.w));
   }
-  const float2 s4 = __fadd2_rn(s01, s23);
-  const float sum = s4.x + s4.y;
+  const float2 ps = __fadd2_rn(s0, s1);
+  const float other = __shfl_xor_sync(kAll, h ? ps.x : ps.y, 1);
+  const float sum = (h ? ps.y : ps.x) + other;
+  const int f = row / 5, q = 2 * (row - 5 * f) + h;
   if (lane < 10 * nf && (IMP || q < 9)) {
-    const uint32_t id = s_fid[f];
-    float* dst = q < 9 ? reinterpret_cast<float*>(gradv + id) + q : in.imp_w + id;
+    const uint2 fm = s_fmeta[f];  // (Gaussian id, blended pairs)
+    float* dst = q < 9 ? reinterpret_cast<float*>(gradv + fm.x) + q : in.imp_w + fm.x;
     asm volatile("red.global.add.f32 [%0], %1;" ::"l"(dst), "f"(sum) : "memory");
+    if (IMP && q == 9) asm volatile("red.global.add.u32 [%0], %1;" ::"l"(in.imp_cnt + fm.x), "r"(fm.y) : "memory");
   }
-  if (IMP && lane < nf)
-    asm volatile("red.global.add.u32 [%0], %1;" ::"l"(in.imp_cnt + s_fid[lane]), "r"(s_fcnt[lane]) : "memory");
   __syncwarp();  // the table is refilled after this
+}
+
+// Defers one replayed entry into slot ns of the table.
+__device__ __forceinline__ void defer_entry(float2 (*s_tab)[kPairStride], uint2* s_fmeta, int ns, int slot,
+                                            const float2 (&acc)[5], uint32_t id, int cnt) {
+#pragma unroll
+  for (int p = 0; p < 5; ++p) s_tab[5 * ns + p][slot] = acc[p];
+  // every lane stores the same value (one shared-memory word pair, no branch)
+  s_fmeta[ns] = make_uint2(id, (uint32_t)cnt);
 }
 
 // Replays one staged entry over the blocks of mask m (block k = 2 by + bx of
 // ROWS block rows; the lane's pixel of block k sits at (pxb[bx], pyb[by])) with
 // the forward's arithmetic: updates each pixel's T and colour still ahead (gC,
-// dotted with the image gradient g), returns the lane's ten sums in acc and,
-// with IMP, the warp's blended-pair count in cnt (warp-uniform).
+// dotted with the image gradient g), returns the lane's ten sums in five pairs
+// (acc) and, with IMP, the warp's blended-pair count in cnt (warp-uniform).
 template <int ROWS, bool IMP>
 __device__ __forceinline__ void replay_entry(const float4 ga, const float4 gb, float cb, int pos1, unsigned m,
                                              const float (&pxb)[2], const float (&pyb)[ROWS], float alpha_max,
                                              float alpha_min, float (&T)[2 * ROWS], float (&gC)[2 * ROWS],
                                              const float (&g0)[2 * ROWS], const float (&g1)[2 * ROWS],
                                              const float (&g2)[2 * ROWS], const int (&nc)[2 * ROWS],
-                                             float (&acc)[10], int& cnt) {
+                                             float2 (&acc)[5], int& cnt) {
   const float dxb[2] = {__fsub_rn(ga.x, pxb[0]), __fsub_rn(ga.x, pxb[1])};
-  float2 a01 = make_float2(0.f, 0.f), a24 = a01, a67 = a01;
-  float a3 = 0.f, a5 = 0.f, a8 = 0.f, a9 = 0.f;
-  cnt = 0;
+  float2 a01 = make_float2(0.f, 0.f), a24 = a01, a35 = a01, a67 = a01, a89 = a01;
+  int lcnt = 0;
 #pragma unroll
   for (int by = 0; by < ROWS; ++by) {
     if (!((m >> (2 * by)) & 3u)) continue;  // warp-uniform
@@ -108,7 +123,7 @@ __device__ __forceinline__ void replay_entry(const float4 ga, const float4 gb, f
       const float gc = g0[k] * gb.z + g1[k] * gb.w + g2[k] * cb;
       // independent sums in pairs: one packed FP32x2 operation each
       a67 = __ffma2_rn(make_float2(w, w), make_float2(g0[k], g1[k]), a67);
-      a8 = fmaf(w, g2[k], a8);
+      a89.x = fmaf(w, g2[k], a89.x);
       // gC[k] holds the colour still ahead of the replay, R = gC - gP
       gC[k] = fmaf(-gc, w, gC[k]);
       const float om = __fsub_rn(1.0f, ae);
@@ -117,28 +132,24 @@ __device__ __forceinline__ void replay_entry(const float4 ga, const float4 gb, f
       // t = dL/dalpha G on unclamped replayed pairs, whose ae equals o G
       // exactly (a clamped pair has ae = alpha_max < o G, a skipped one 0)
       const float tt = dL_dalpha * (ae == oG ? G : 0.f);
-      a5 += tt;
+      a35.y += tt;
       const float2 d2 = make_float2(dx, dy);
       const float2 td = __fmul2_rn(make_float2(tt, tt), d2);  // (t dx, t dy)
       a01 = __fadd2_rn(a01, td);
       a24 = __ffma2_rn(td, d2, a24);                           // (t dx^2, t dy^2)
-      a3 = fmaf(td.x, dy, a3);
+      a35.x = fmaf(td.x, dy, a35.x);
       if (IMP) {
-        a9 += w;
-        cnt += __popc(__ballot_sync(kAll, valid));
+        a89.y += w;
+        if (valid) ++lcnt;
       }
     }
   }
-  acc[0] = a01.x;
-  acc[1] = a01.y;
-  acc[2] = a24.x;
-  acc[3] = a3;
-  acc[4] = a24.y;
-  acc[5] = a5;
-  acc[6] = a67.x;
-  acc[7] = a67.y;
-  acc[8] = a8;
-  acc[9] = a9;
+  acc[0] = a01;
+  acc[1] = a24;
+  acc[2] = a35;
+  acc[3] = a67;
+  acc[4] = a89;
+  cnt = IMP ? (int)__reduce_add_sync(kAll, (unsigned)lcnt) : 0;
 }
 
 // Per-pixel state of a replay at the start of an item: T = 1, the image
@@ -201,15 +212,14 @@ __device__ __forceinline__ void finish_counters(const BlendArgs& a, const BwdIn&
 
 template <bool L1, bool IMP, int CB, int MINB>
 __global__ void __launch_bounds__(32, MINB) k_blend_bwd(BlendArgs a, BwdIn in) {
-  __shared__ __align__(16) float s_red[kRedRows][kRedStride];
-  __shared__ uint32_t s_fid[kDeferG];
-  __shared__ uint32_t s_fcnt[kDeferG];
+  __shared__ __align__(16) float2 s_tab[kPairRows][kPairStride];
+  __shared__ uint2 s_fmeta[kDeferG];  // (Gaussian id, blended pairs) of the deferred entries
   __shared__ float4 s_a[CB];
   __shared__ float4 s_b[CB];
   __shared__ StageMeta s_meta[CB];
 
   const int lane = threadIdx.x;
-  const int ff = lane / 10, fq = lane - 10 * ff;  // the table row this lane flushes
+  const int slot = table_slot(lane);
   const float alpha_max = a.rp.alpha_max, alpha_min = a.rp.alpha_min;
   const float log2_amin = log2f(alpha_min);
   const int lx = lane & 7, ly = lane >> 3;
@@ -256,24 +266,20 @@ __global__ void __launch_bounds__(32, MINB) k_blend_bwd(BlendArgs a, BwdIn in) {
         const StageMeta me = s_meta[j];
         const float4 ga = s_a[j];
         const float4 gb = s_b[j];
-        float acc[10];
+        float2 acc[5];
         int cnt;
         replay_entry<2, IMP>(ga, gb, me.c, (int)me.pos1, me.mask, pxb, pyb, alpha_max, alpha_min, T, gC, g0, g1, g2,
                              nc, acc, cnt);
         // every compacted entry has a live block: defer without a vote
-#pragma unroll
-        for (int q = 0; q < 10; ++q) s_red[ns * 10 + q][lane] = acc[q];
-        // every lane stores the same values (one shared-memory word each, no branch)
-        s_fid[ns] = me.id;
-        if (IMP) s_fcnt[ns] = (uint32_t)cnt;
+        defer_entry(s_tab, s_fmeta, ns, slot, acc, me.id, cnt);
         if (++ns == kDeferG) {
-          flush_deferred<IMP>(s_red, s_fid, s_fcnt, ns, gradv, in, lane, ff, fq);
+          flush_deferred<IMP>(s_tab, s_fmeta, ns, gradv, in, lane);
           ns = 0;
         }
       }
       __syncwarp();
     }
-    if (ns > 0) flush_deferred<IMP>(s_red, s_fid, s_fcnt, ns, gradv, in, lane, ff, fq);
+    if (ns > 0) flush_deferred<IMP>(s_tab, s_fmeta, ns, gradv, in, lane);
     executed += exec_groups;
   }
   finish_counters<L1>(a, in, pairs, executed, loss_acc, lane);
@@ -327,16 +333,15 @@ __device__ __forceinline__ int stage_tile(const BlendArgs& a, uint32_t b0, int n
 
 template <bool L1, bool IMP, int CB, int MINB>
 __global__ void __launch_bounds__(32, MINB) k_blend_bwd_tile(BlendArgs a, BwdIn in) {
-  __shared__ __align__(16) float s_red[kRedRows][kRedStride];
-  __shared__ uint32_t s_fid[kDeferG];
-  __shared__ uint32_t s_fcnt[kDeferG];
+  __shared__ __align__(16) float2 s_tab[kPairRows][kPairStride];
+  __shared__ uint2 s_fmeta[kDeferG];  // (Gaussian id, blended pairs) of the deferred entries
   __shared__ float4 s_a[CB];
   __shared__ float4 s_b[CB];
   __shared__ StageMeta s_meta[CB];
   __shared__ int s_gmax[kTileBlocks];  // largest n_contrib of each block
 
   const int lane = threadIdx.x;
-  const int ff = lane / 10, fq = lane - 10 * ff;
+  const int slot = table_slot(lane);
   const float alpha_max = a.rp.alpha_max, alpha_min = a.rp.alpha_min;
   const float log2_amin = log2f(alpha_min);
   const int lx = lane & 7, ly = lane >> 3;
@@ -381,22 +386,19 @@ __global__ void __launch_bounds__(32, MINB) k_blend_bwd_tile(BlendArgs a, BwdIn 
         const StageMeta me = s_meta[j];
         const float4 ga = s_a[j];
         const float4 gb = s_b[j];
-        float acc[10];
+        float2 acc[5];
         int cnt;
         replay_entry<kTileBlocks / 2, IMP>(ga, gb, me.c, (int)me.pos1, me.mask, pxb, pyb, alpha_max, alpha_min, T,
                                            gC, g0, g1, g2, nc, acc, cnt);
-#pragma unroll
-        for (int q = 0; q < 10; ++q) s_red[ns * 10 + q][lane] = acc[q];
-        s_fid[ns] = me.id;
-        if (IMP) s_fcnt[ns] = (uint32_t)cnt;
+        defer_entry(s_tab, s_fmeta, ns, slot, acc, me.id, cnt);
         if (++ns == kDeferG) {
-          flush_deferred<IMP>(s_red, s_fid, s_fcnt, ns, gradv, in, lane, ff, fq);
+          flush_deferred<IMP>(s_tab, s_fmeta, ns, gradv, in, lane);
           ns = 0;
         }
       }
       __syncwarp();
     }
-    if (ns > 0) flush_deferred<IMP>(s_red, s_fid, s_fcnt, ns, gradv, in, lane, ff, fq);
+    if (ns > 0) flush_deferred<IMP>(s_tab, s_fmeta, ns, gradv, in, lane);
     executed += exec_groups;
   }
   finish_counters<L1>(a, in, pairs, executed, loss_acc, lane);
