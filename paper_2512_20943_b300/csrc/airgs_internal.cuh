@@ -49,9 +49,10 @@ constexpr int kFlagGuardY = 32;
 // the Gaussian's replayed pairs, with d = mean2d - pixel and t = dL/dalpha G on
 // unclamped pairs:
 //   a = {S_x = sum t dx, S_y = sum t dy, S_xx = sum t dx^2, S_yy = sum t dy^2}
-//   b = {S_xy = sum t dx dy, S_t = sum t, dL/dr, dL/dg}
-//   c = {dL/db, 0, 0, 0}
-// (the order of the backward's accumulator pairs)
+//   b = {S_t = sum t, 0, dL/dr, dL/dg}
+//   c = {dL/db, S_xy = sum t dx dy, 0, 0}
+// (the order of the backward's accumulator pairs; float 5 is the pair slot of
+// the blend weight, which goes to the usage weight instead)
 // The projection adjoint turns them into the 2D gradients: with
 // power2 = a2 dx^2 + b2 dx dy + c2 dy^2 = log2(e) power and dL/dpower = o t,
 // dL/dmean2d = o ln2 (2 a2 S_x + b2 S_y, b2 S_x + 2 c2 S_y),
@@ -65,13 +66,13 @@ struct __align__(16) GradRec {
 // these helpers, with explicit rounding intrinsics, so that the backward's
 // replay takes exactly the forward's skip / blend / stop decisions and
 // reproduces its running sums bit for bit.
-// a / b with the hardware reciprocal, subnormal inputs and results flushed to
-// zero (the blend backward divides the colour still ahead by 1 - alpha, which
-// lies in [1 - alpha_max, 1]).
-__device__ __forceinline__ float div_approx_ftz(float a, float b) {
-  float q;
-  asm("div.approx.ftz.f32 %0, %1, %2;" : "=f"(q) : "f"(a), "f"(b));
-  return q;
+// 1 / b by the hardware reciprocal, subnormals flushed to zero (the blend
+// backward divides the colour still ahead by 1 - alpha, which lies in
+// [1 - alpha_max, 1]).
+__device__ __forceinline__ float rcp_approx_ftz(float b) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(b));
+  return r;
 }
 
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -95,7 +96,10 @@ __device__ __forceinline__ float power2_of(float dx, float a2, float b2dy, float
 
 __device__ __forceinline__ float alpha_of(float o, float G, float alpha_max) { return fminf(alpha_max, __fmul_rn(o, G)); }
 
-__device__ __forceinline__ float transmit(float T, float alpha) { return __fmul_rn(T, __fsub_rn(1.0f, alpha)); }
+// T (1 - alpha) evaluated as T - w with the pair's blend weight w = alpha T (one
+// subtraction, the weight being computed for the colour anyway).
+__device__ __forceinline__ float blend_weight(float alpha, float T) { return __fmul_rn(alpha, T); }
+__device__ __forceinline__ float transmit(float T, float w) { return __fsub_rn(T, w); }
 
 // Tile rectangle of a footprint centred at (mx, my) with integer radius r: the
 // tiles whose 16-pixel span meets [m - r, m + r], computed exactly from

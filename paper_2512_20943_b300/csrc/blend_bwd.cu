@@ -20,7 +20,7 @@
 // n_contrib lies beyond its position.  Each entry's ten per-lane sums, in five
 // pairs
 //   (S_x = sum t dx, S_y = sum t dy), (sum t dx^2, sum t dy^2),
-//   (sum t dx dy, sum t), (colour r, g), (colour b, blend weight)
+//   (sum t, blend weight), (colour r, g), (colour b, sum t dx dy)
 // (t = dL/dalpha G on unclamped pairs) are deferred into a per-warp
 // shared-memory table of three entries with one 8-byte store per pair, reduced
 // by two lanes per pair (a transpose through shared memory) and flushed with one
@@ -43,8 +43,8 @@ namespace {
 // 16-byte loads touches 32 different banks).  In the flush lanes 2i and 2i+1
 // sum row i over lanes 0-15 and 16-31 (eight 16-byte loads each), trade the
 // component the other one owns with one shuffle, and send sum 2p + h (h = lane
-// parity) with one scalar reduction: sums 0-8 to the record's floats 0-8, sum 9
-// (the blend weight) to the usage weight.
+// parity) with one scalar reduction: sum q to the record's float q, except sum
+// 5 (the blend weight), which goes to the usage weight.
 constexpr int kDeferG = 3;
 constexpr int kPairRows = kDeferG * 5;
 constexpr int kPairStride = 36;  // float2 slots per row
@@ -69,11 +69,11 @@ __device__ __forceinline__ void flush_deferred(float2 (*s_tab)[kPairStride], con
   const float other = __shfl_xor_sync(kAll, h ? ps.x : ps.y, 1);
   const float sum = (h ? ps.y : ps.x) + other;
   const int f = row / 5, q = 2 * (row - 5 * f) + h;
-  if (lane < 10 * nf && (IMP || q < 9)) {
+  if (lane < 10 * nf && (IMP || q != 5)) {
     const uint2 fm = s_fmeta[f];  // (Gaussian id, blended pairs)
-    float* dst = q < 9 ? reinterpret_cast<float*>(gradv + fm.x) + q : in.imp_w + fm.x;
+    float* dst = q != 5 ? reinterpret_cast<float*>(gradv + fm.x) + q : in.imp_w + fm.x;
     asm volatile("red.global.add.f32 [%0], %1;" ::"l"(dst), "f"(sum) : "memory");
-    if (IMP && q == 9) asm volatile("red.global.add.u32 [%0], %1;" ::"l"(in.imp_cnt + fm.x), "r"(fm.y) : "memory");
+    if (IMP && q == 5) asm volatile("red.global.add.u32 [%0], %1;" ::"l"(in.imp_cnt + fm.x), "r"(fm.y) : "memory");
   }
   __syncwarp();  // the table is refilled after this
 }
@@ -100,7 +100,7 @@ __device__ __forceinline__ void replay_entry(const float4 ga, const float4 gb, f
                                              const float (&g2)[2 * ROWS], const int (&nc)[2 * ROWS],
                                              float2 (&acc)[5], int& cnt) {
   const float dxb[2] = {__fsub_rn(ga.x, pxb[0]), __fsub_rn(ga.x, pxb[1])};
-  float2 a01 = make_float2(0.f, 0.f), a24 = a01, a35 = a01, a67 = a01, a89 = a01;
+  float2 a01 = make_float2(0.f, 0.f), a24 = a01, a59 = a01, a67 = a01, a83 = a01;
   int lcnt = 0;
 #pragma unroll
   for (int by = 0; by < ROWS; ++by) {
@@ -119,36 +119,36 @@ __device__ __forceinline__ void replay_entry(const float4 ga, const float4 gb, f
       // pair (pixel, entry) replayed iff pos1 <= n_contrib and the forward blended it
       const bool valid = (pos1 <= nc[k]) && !(p2 > 0.f) && !(alpha < alpha_min);
       const float ae = valid ? alpha : 0.f;
-      const float w = __fmul_rn(ae, T[k]);
+      const float w = blend_weight(ae, T[k]);
       const float gc = g0[k] * gb.z + g1[k] * gb.w + g2[k] * cb;
       // independent sums in pairs: one packed FP32x2 operation each
       a67 = __ffma2_rn(make_float2(w, w), make_float2(g0[k], g1[k]), a67);
-      a89.x = fmaf(w, g2[k], a89.x);
+      a83.x = fmaf(w, g2[k], a83.x);
       // gC[k] holds the colour still ahead of the replay, R = gC - gP
       gC[k] = fmaf(-gc, w, gC[k]);
-      const float om = __fsub_rn(1.0f, ae);
-      const float dL_dalpha = T[k] * gc - div_approx_ftz(gC[k], om);
-      T[k] = __fmul_rn(T[k], om);
+      const float dL_dalpha = fmaf(-gC[k], rcp_approx_ftz(__fsub_rn(1.0f, ae)), T[k] * gc);
+      T[k] = transmit(T[k], w);
       // t = dL/dalpha G on unclamped replayed pairs, whose ae equals o G
       // exactly (a clamped pair has ae = alpha_max < o G, a skipped one 0)
       const float tt = dL_dalpha * (ae == oG ? G : 0.f);
-      a35.y += tt;
       const float2 d2 = make_float2(dx, dy);
       const float2 td = __fmul2_rn(make_float2(tt, tt), d2);  // (t dx, t dy)
       a01 = __fadd2_rn(a01, td);
       a24 = __ffma2_rn(td, d2, a24);                           // (t dx^2, t dy^2)
-      a35.x = fmaf(td.x, dy, a35.x);
+      a83.y = fmaf(td.x, dy, a83.y);
       if (IMP) {
-        a89.y += w;
+        a59 = __fadd2_rn(a59, make_float2(tt, w));
         if (valid) ++lcnt;
+      } else {
+        a59.x += tt;
       }
     }
   }
   acc[0] = a01;
   acc[1] = a24;
-  acc[2] = a35;
+  acc[2] = a59;
   acc[3] = a67;
-  acc[4] = a89;
+  acc[4] = a83;
   cnt = IMP ? (int)__reduce_add_sync(kAll, (unsigned)lcnt) : 0;
 }
 

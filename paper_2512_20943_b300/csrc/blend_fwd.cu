@@ -98,11 +98,11 @@ __global__ void __launch_bounds__(32, MINB) k_blend_fwd(BlendArgs a, FwdOut out)
             const float p2 = power2_of(dx, ga.z, b2dy, c2dy2);
             const float G = ex2_approx(p2);
             const float alpha = alpha_of(gb.y, G, alpha_max);
-            const float Tn = transmit(T[k], alpha);
+            const float w = blend_weight(alpha, T[k]);
+            const float Tn = transmit(T[k], w);
             const bool valid = (stop_at[k] < 0) && !(p2 > 0.f) && !(alpha < alpha_min);
             const bool stop = valid && (Tn < T_min);
             const bool blend = valid && !stop;
-            const float w = __fmul_rn(alpha, T[k]);
             if (blend) {
               C01[k] = __ffma2_rn(make_float2(gb.z, gb.w), make_float2(w, w), C01[k]);
               C2[k] = __fmaf_rn(cb, w, C2[k]);

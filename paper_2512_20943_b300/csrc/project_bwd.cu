@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(PB_THREADS, AIRGS_PROJ_BWD_MINB) k_project_bwd
       const float op2 = rec.b.y, lo = kLn2 * op2;
       const float gmx = lo * fmaf(2.f * rec.a.z, gr.a.x, rec.a.w * gr.a.y);
       const float gmy = lo * fmaf(rec.a.w, gr.a.x, 2.f * rec.b.x * gr.a.y);
-      const float gA = -0.5f * op2 * gr.a.z, gB = -op2 * gr.b.x, gC = -0.5f * op2 * gr.a.w, go = gr.b.y;
+      const float gA = -0.5f * op2 * gr.a.z, gB = -op2 * gr.c.y, gC = -0.5f * op2 * gr.a.w, go = gr.b.x;
       ++dviews;
       dgrad += sqrtf(gmx * gmx + gmy * gmy);
       const float grgb[3] = {gr.b.z, gr.b.w, gr.c.x};
