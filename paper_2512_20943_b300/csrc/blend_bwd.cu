@@ -188,23 +188,40 @@ __device__ __forceinline__ void load_pixel(const BwdIn& in, const CamDev& cam, i
   }
 }
 
-// Adds the warp's statistics to the launch counters and, with L1, its loss.
+// The warp's running statistics, kept in shared memory so that no register
+// holds them through the replay: replayed pairs and, with L1, the loss.
+struct WarpTotals {
+  unsigned long long pairs;
+  float loss;
+};
+
+// Adds an item's replayed pairs and loss to the warp's totals (at the item's
+// start).
 template <bool L1>
-__device__ __forceinline__ void finish_counters(const BlendArgs& a, const BwdIn& in, unsigned long long pairs,
-                                                unsigned long long executed, float loss_acc, int lane) {
+__device__ __forceinline__ void item_counters(WarpTotals& t, unsigned long long pairs, float loss_acc, int lane) {
   for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(kAll, pairs, o);
-  for (int o = 16; o > 0; o >>= 1) executed += __shfl_xor_sync(kAll, executed, o);
-  executed *= 32ull;  // 32 lane evaluations per block
-  if (lane == 0) {
-    if (pairs) {
-      atomicAdd(a.pair_counter, pairs);
-      if (a.pair_total) atomicAdd(a.pair_total, pairs);
-    }
-    if (a.exec_total && executed) atomicAdd(a.exec_total, executed);
-  }
-  if (L1 && in.loss) {
+  if (L1)
     for (int o = 16; o > 0; o >>= 1) loss_acc += __shfl_xor_sync(kAll, loss_acc, o);
-    if (lane == 0) atomicAdd(in.loss, loss_acc * in.inv_norm);
+  if (lane == 0) {
+    t.pairs += pairs;
+    if (L1) t.loss += loss_acc;
+  }
+}
+
+// Adds the warp's totals and issued block evaluations (32 lane evaluations
+// each) to the launch counters.
+template <bool L1>
+__device__ __forceinline__ void finish_counters(const BlendArgs& a, const BwdIn& in, const WarpTotals& t,
+                                                uint32_t groups, int lane) {
+  unsigned long long executed = groups;
+  for (int o = 16; o > 0; o >>= 1) executed += __shfl_xor_sync(kAll, executed, o);
+  if (lane == 0) {
+    if (a.exec_total && executed) atomicAdd(a.exec_total, 32ull * executed);
+    if (t.pairs) {
+      atomicAdd(a.pair_counter, t.pairs);
+      if (a.pair_total) atomicAdd(a.pair_total, t.pairs);
+    }
+    if (L1 && in.loss) atomicAdd(in.loss, t.loss * in.inv_norm);
   }
 }
 
@@ -217,14 +234,16 @@ __global__ void __launch_bounds__(32, MINB) k_blend_bwd(BlendArgs a, BwdIn in) {
   __shared__ float4 s_a[CB];
   __shared__ float4 s_b[CB];
   __shared__ StageMeta s_meta[CB];
+  __shared__ int s_gmax[kBlocks];  // largest n_contrib of each block
+  __shared__ WarpTotals s_tot;
 
   const int lane = threadIdx.x;
   const int slot = table_slot(lane);
   const float alpha_max = a.rp.alpha_max, alpha_min = a.rp.alpha_min;
   const float log2_amin = log2f(alpha_min);
   const int lx = lane & 7, ly = lane >> 3;
-  unsigned long long pairs = 0, executed = 0;
-  float loss_acc = 0.f;
+  uint32_t exec_groups = 0;
+  if (lane == 0) s_tot = WarpTotals{0ull, 0.f};
 
   while (true) {
     const int work = cull_fetch(a.work_counter);
@@ -238,29 +257,34 @@ __global__ void __launch_bounds__(32, MINB) k_blend_bwd(BlendArgs a, BwdIn in) {
     const float pyb[2] = {(float)(Y0 + ly) + 0.5f, (float)(Y0 + 4 + ly) + 0.5f};  // the two block rows
 
     float T[kBlocks], gC[kBlocks], g0[kBlocks], g1[kBlocks], g2[kBlocks];
-    int nc[kBlocks], gmax[kBlocks];
-#pragma unroll
-    for (int k = 0; k < kBlocks; ++k) {
-      load_pixel<L1>(in, cam, X0 + 8 * (k & 1) + lx, Y0 + 4 * (k >> 1) + ly, T[k], gC[k], g0[k], g1[k], g2[k], nc[k],
-                     pairs, loss_acc);
-      gmax[k] = (int)__reduce_max_sync(kAll, (unsigned)nc[k]);  // warp-uniform
-    }
+    int nc[kBlocks];
     int maxnc = 0;
+    {
+      unsigned long long pairs = 0;
+      float loss_acc = 0.f;
 #pragma unroll
-    for (int k = 0; k < kBlocks; ++k) maxnc = max(maxnc, gmax[k]);
+      for (int k = 0; k < kBlocks; ++k) {
+        load_pixel<L1>(in, cam, X0 + 8 * (k & 1) + lx, Y0 + 4 * (k >> 1) + ly, T[k], gC[k], g0[k], g1[k], g2[k],
+                       nc[k], pairs, loss_acc);
+        const int gm = (int)__reduce_max_sync(kAll, (unsigned)nc[k]);  // warp-uniform
+        if (lane == k) s_gmax[k] = gm;
+        maxnc = max(maxnc, gm);
+      }
+      item_counters<L1>(s_tot, pairs, loss_acc, lane);
+    }
+    __syncwarp();
     const uint2 range = a.ranges[item];
     const bool use_hl = a.hl != nullptr;  // this half's compacted list
     uint2 er = make_uint2(range.x, range.x + (uint32_t)maxnc);
     if (use_hl) er = a.hranges[(int64_t)part * a.n_tiles + item];
     const ProjRec* projv = a.proj + (size_t)v * a.n;
     GradRec* gradv = in.grad + (size_t)v * a.n;
-    uint32_t exec_groups = 0;
     bool past_end = false;
     int ns = 0;  // deferred Gaussians in the table
 
     for (uint32_t b0 = er.x; b0 < er.y && !past_end; b0 += CB) {
       const int nb = stage_compact<true>(a, use_hl, b0, (int)min((uint32_t)CB, er.y - b0), range.x, projv, log2_amin,
-                                         (float)X0, (float)Y0, gmax, maxnc, (1u << kBlocks) - 1u, s_a, s_b, s_meta,
+                                         (float)X0, (float)Y0, s_gmax, maxnc, (1u << kBlocks) - 1u, s_a, s_b, s_meta,
                                          past_end, exec_groups);
       for (int j = 0; j < nb; ++j) {
         const StageMeta me = s_meta[j];
@@ -280,9 +304,9 @@ __global__ void __launch_bounds__(32, MINB) k_blend_bwd(BlendArgs a, BwdIn in) {
       __syncwarp();
     }
     if (ns > 0) flush_deferred<IMP>(s_tab, s_fmeta, ns, gradv, in, lane);
-    executed += exec_groups;
   }
-  finish_counters<L1>(a, in, pairs, executed, loss_acc, lane);
+  __syncwarp();
+  finish_counters<L1>(a, in, s_tot, exec_groups, lane);
 }
 
 // ------------------------------------------------------------------ full-tile replay
@@ -339,14 +363,15 @@ __global__ void __launch_bounds__(32, MINB) k_blend_bwd_tile(BlendArgs a, BwdIn 
   __shared__ float4 s_b[CB];
   __shared__ StageMeta s_meta[CB];
   __shared__ int s_gmax[kTileBlocks];  // largest n_contrib of each block
+  __shared__ WarpTotals s_tot;
 
   const int lane = threadIdx.x;
   const int slot = table_slot(lane);
   const float alpha_max = a.rp.alpha_max, alpha_min = a.rp.alpha_min;
   const float log2_amin = log2f(alpha_min);
   const int lx = lane & 7, ly = lane >> 3;
-  unsigned long long pairs = 0, executed = 0;
-  float loss_acc = 0.f;
+  uint32_t exec_groups = 0;
+  if (lane == 0) s_tot = WarpTotals{0ull, 0.f};
 
   while (true) {
     const int item = cull_fetch(a.work_counter);
@@ -363,20 +388,24 @@ __global__ void __launch_bounds__(32, MINB) k_blend_bwd_tile(BlendArgs a, BwdIn 
     float T[kTileBlocks], gC[kTileBlocks], g0[kTileBlocks], g1[kTileBlocks], g2[kTileBlocks];
     int nc[kTileBlocks];
     int maxnc = 0;
+    {
+      unsigned long long pairs = 0;
+      float loss_acc = 0.f;
 #pragma unroll
-    for (int k = 0; k < kTileBlocks; ++k) {
-      load_pixel<L1>(in, cam, X0 + 8 * (k & 1) + lx, Y0 + 4 * (k >> 1) + ly, T[k], gC[k], g0[k], g1[k], g2[k], nc[k],
-                     pairs, loss_acc);
-      const int gm = (int)__reduce_max_sync(kAll, (unsigned)nc[k]);  // warp-uniform
-      if (lane == k) s_gmax[k] = gm;
-      maxnc = max(maxnc, gm);
+      for (int k = 0; k < kTileBlocks; ++k) {
+        load_pixel<L1>(in, cam, X0 + 8 * (k & 1) + lx, Y0 + 4 * (k >> 1) + ly, T[k], gC[k], g0[k], g1[k], g2[k],
+                       nc[k], pairs, loss_acc);
+        const int gm = (int)__reduce_max_sync(kAll, (unsigned)nc[k]);  // warp-uniform
+        if (lane == k) s_gmax[k] = gm;
+        maxnc = max(maxnc, gm);
+      }
+      item_counters<L1>(s_tot, pairs, loss_acc, lane);
     }
     __syncwarp();
     const uint2 range = a.ranges[item];
     const uint32_t end = range.x + (uint32_t)maxnc;  // no entry at or beyond maxnc is replayed
     const ProjRec* projv = a.proj + (size_t)v * a.n;
     GradRec* gradv = in.grad + (size_t)v * a.n;
-    uint32_t exec_groups = 0;
     int ns = 0;
 
     for (uint32_t b0 = range.x; b0 < end; b0 += CB) {
@@ -399,9 +428,9 @@ __global__ void __launch_bounds__(32, MINB) k_blend_bwd_tile(BlendArgs a, BwdIn 
       __syncwarp();
     }
     if (ns > 0) flush_deferred<IMP>(s_tab, s_fmeta, ns, gradv, in, lane);
-    executed += exec_groups;
   }
-  finish_counters<L1>(a, in, pairs, executed, loss_acc, lane);
+  __syncwarp();
+  finish_counters<L1>(a, in, s_tot, exec_groups, lane);
 }
 
 namespace {

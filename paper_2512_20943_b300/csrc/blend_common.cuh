@@ -55,9 +55,9 @@ struct __align__(16) StageMeta {
 // Stages the list entries [b0, b0 + nb) of a half-tile item into shared memory,
 // keeping only those whose block mask is non-zero, in list order; returns how
 // many were kept.  With LIVE (the backward) the mask is also restricted to the
-// blocks whose largest n_contrib (gmax) lies beyond the entry's position, and
-// `past` is set when an entry lies at or beyond maxnc (positions increase along
-// the list, so no later batch can contribute).  Half-list entries: the forward
+// blocks whose largest n_contrib (gmax, in shared memory) lies beyond the
+// entry's position, and `past` is set when an entry lies at or beyond maxnc
+// (positions increase along the list, so no later batch can contribute).  Half-list entries: the forward
 // computes each staged entry's exact block mask and stores it in the entry's
 // top bits; the backward reads it from there (every entry before maxnc was
 // staged by the forward of the same state).  Each lane adds to `groups` the
@@ -66,7 +66,7 @@ struct __align__(16) StageMeta {
 template <bool LIVE>
 __device__ __forceinline__ int stage_compact(const BlendArgs& a, bool use_hl, uint32_t b0, int nb, uint32_t list0,
                                              const ProjRec* projv, float log2_amin, float X0, float Y0,
-                                             const int (&gmax)[kBlocks], int maxnc, unsigned alive, float4* s_a,
+                                             const int* gmax, int maxnc, unsigned alive, float4* s_a,
                                              float4* s_b, StageMeta* s_meta, bool& past, uint32_t& groups) {
   const int lane = threadIdx.x & 31;
   int kept = 0;

@@ -24,12 +24,14 @@ __global__ void __launch_bounds__(32, MINB) k_blend_fwd(BlendArgs a, FwdOut out)
   __shared__ float4 s_a[FB];
   __shared__ float4 s_b[FB];
   __shared__ StageMeta s_meta[FB];
+  __shared__ unsigned long long s_pairs;  // the warp's definition pairs (no register holds them through the blend)
 
   const int lane = threadIdx.x;
   const float alpha_max = a.rp.alpha_max, alpha_min = a.rp.alpha_min, T_min = a.rp.T_min;
   const float log2_amin = log2f(alpha_min);
   const int lx = lane & 7, ly = lane >> 3;
-  unsigned long long pairs = 0, executed = 0;
+  uint32_t exec_groups = 0;  // per lane: blocks counted while staging
+  if (lane == 0) s_pairs = 0ull;
 
   while (true) {
     const int work = cull_fetch(a.work_counter);
@@ -61,7 +63,6 @@ __global__ void __launch_bounds__(32, MINB) k_blend_fwd(BlendArgs a, FwdOut out)
     uint2 er = range;
     if (use_hl) er = a.hranges[(int64_t)part * a.n_tiles + item];
     const ProjRec* projv = a.proj + (size_t)v * a.n;
-    uint32_t exec_groups = 0;  // per lane: blocks counted while staging
 
     for (uint32_t b0 = er.x; b0 < er.y; b0 += FB) {
       unsigned live = 0;
@@ -69,10 +70,9 @@ __global__ void __launch_bounds__(32, MINB) k_blend_fwd(BlendArgs a, FwdOut out)
       for (int k = 0; k < kBlocks; ++k)
         if (__any_sync(kAll, stop_at[k] < 0)) live |= 1u << k;
       if (live == 0) break;
-      const int none[kBlocks] = {};
       bool unused = false;
       const int nb = stage_compact<false>(a, use_hl, b0, (int)min((uint32_t)FB, er.y - b0), range.x, projv,
-                                          log2_amin, (float)X0, (float)Y0, none, 0, live, s_a, s_b, s_meta, unused,
+                                          log2_amin, (float)X0, (float)Y0, nullptr, 0, live, s_a, s_b, s_meta, unused,
                                           exec_groups);
       for (int j = 0; j < nb; ++j) {
         const StageMeta me = s_meta[j];
@@ -131,10 +131,10 @@ __global__ void __launch_bounds__(32, MINB) k_blend_fwd(BlendArgs a, FwdOut out)
       }
       __syncwarp();
     }
-    executed += exec_groups;
     const int64_t HW = (int64_t)cam.W * cam.H;
     float* rgb = out.rgb + 3 * cam.pix_base;
     const uint32_t len = range.y - range.x;
+    unsigned long long pairs = 0;
 #pragma unroll
     for (int k = 0; k < kBlocks; ++k) {
       const int x = X0 + 8 * (k & 1) + lx, y = Y0 + 4 * (k >> 1) + ly;
@@ -150,16 +150,18 @@ __global__ void __launch_bounds__(32, MINB) k_blend_fwd(BlendArgs a, FwdOut out)
         if (out.ncontrib_user) out.ncontrib_user[cam.pix_base + pix] = last[k];
       }
     }
+    for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(kAll, pairs, o);
+    if (lane == 0) s_pairs += pairs;
   }
-  for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(kAll, pairs, o);
+  unsigned long long executed = exec_groups;
   for (int o = 16; o > 0; o >>= 1) executed += __shfl_xor_sync(kAll, executed, o);
-  executed *= 32ull;  // 32 lane evaluations per block
+  __syncwarp();
   if (lane == 0) {
-    if (pairs) {
-      atomicAdd(a.pair_counter, pairs);
-      if (a.pair_total) atomicAdd(a.pair_total, pairs);
+    if (a.exec_total && executed) atomicAdd(a.exec_total, 32ull * executed);  // 32 lane evaluations per block
+    if (s_pairs) {
+      atomicAdd(a.pair_counter, s_pairs);
+      if (a.pair_total) atomicAdd(a.pair_total, s_pairs);
     }
-    if (a.exec_total && executed) atomicAdd(a.exec_total, executed);
   }
 }
 
