@@ -254,14 +254,11 @@ const char* airgs::shape_name(int shape) {
     char s[kShapes][48];
     Names() {
       const int fwd[kFwdShapes][2] = {{32, 32}, {16, 32}, {64, 32}, {32, 28}, {32, 24}};
-      // backward: staged entries per batch, warps per SM, item (0: half tile, 1: full tile)
-      const int bwd[kBwdShapes][3] = {{32, 28, 0}, {16, 28, 0}, {64, 28, 0}, {32, 24, 0},
-                                      {32, 32, 0}, {32, 20, 1}, {32, 24, 1}, {32, 16, 1}};
+      const int bwd[kBwdShapes][2] = {{32, 28}, {16, 28}, {64, 28}, {32, 24}, {32, 32}};
       for (int i = 0; i < kShapes; ++i) {
         const ShapeParts p = shape_parts(i);
-        snprintf(s[i], sizeof(s[i]), "fwd %d/%d bwd %s%d/%d keys %d run %d", fwd[p.fwd][0], fwd[p.fwd][1],
-                 bwd[p.bwd][2] ? "tile " : "", bwd[p.bwd][0], bwd[p.bwd][1], sort_keys_of(p.sort),
-                 emit_run_of(p.emit));
+        snprintf(s[i], sizeof(s[i]), "fwd %d/%d bwd %d/%d keys %d run %d", fwd[p.fwd][0], fwd[p.fwd][1],
+                 bwd[p.bwd][0], bwd[p.bwd][1], sort_keys_of(p.sort), emit_run_of(p.emit));
       }
     }
   };

@@ -8,16 +8,10 @@
 // chained through alpha = o G, G = exp(power) to the opacity, the 2D mean and
 // the conic; a clamped alpha (o G > alpha_max) passes no gradient to o or G.
 //
-// Two replays share the per-entry arithmetic (replay_entry):
-//  - k_blend_bwd: one warp per 16x8 half tile (four 8x4 blocks, a lane's four
-//    pixels), walking the half's compacted list with the forward's exact block
-//    masks stored in its entries;
-//  - k_blend_bwd_tile: one warp per 16x16 tile (eight 8x4 blocks, a lane's
-//    eight pixels), walking the tile's full list with each entry's exact block
-//    mask computed while staging; an entry reaching both halves of a tile is
-//    reduced once instead of twice.
-// Either way an entry's mask is restricted to the blocks whose largest
-// n_contrib lies beyond its position.  Each entry's ten per-lane sums, in five
+// One warp replays a 16x8 half tile (four 8x4 blocks, a lane's four pixels),
+// walking the half's compacted list with the forward's exact block masks
+// stored in its entries, restricted to the blocks whose largest n_contrib lies
+// beyond the entry's position.  Each entry's ten per-lane sums, in five
 // pairs
 //   (S_x = sum t dx, S_y = sum t dy), (sum t dx^2, sum t dy^2),
 //   (sum t, blend weight), (colour r, g), (colour b, sum t dx dy)
@@ -309,130 +303,6 @@ __global__ void __launch_bounds__(32, MINB) k_blend_bwd(BlendArgs a, BwdIn in) {
   finish_counters<L1>(a, in, s_tot, exec_groups, lane);
 }
 
-// ------------------------------------------------------------------ full-tile replay
-constexpr int kTileBlocks = 8;  // 8x4 blocks of a 16x16 tile, block k = 2 by + bx, by 0..3
-
-// Stages the full-list entries [b0, b0 + nb) of a tile, keeping in list order
-// those whose exact block mask, restricted to the blocks whose largest
-// n_contrib (s_gmax) lies beyond the entry's position, is non-zero.
-__device__ __forceinline__ int stage_tile(const BlendArgs& a, uint32_t b0, int nb, uint32_t list0,
-                                          const ProjRec* projv, float log2_amin, float X0, float Y0,
-                                          const int* s_gmax, float4* s_a, float4* s_b, StageMeta* s_meta,
-                                          uint32_t& groups) {
-  const int lane = threadIdx.x & 31;
-  int kept = 0;
-  for (int j0 = 0; j0 < nb; j0 += 32) {
-    const int j = j0 + lane;
-    unsigned msk = 0u;
-    float4 ga = make_float4(0.f, 0.f, 0.f, 0.f), gb = ga;
-    float gc = 0.f;
-    uint32_t id = 0u, pos = 0u;
-    if (j < nb) {
-      id = __ldg(a.ids + b0 + j);
-      pos = b0 + j - list0;
-      unsigned live = 0u;
-#pragma unroll
-      for (int k = 0; k < kTileBlocks; ++k) live |= ((int)pos < s_gmax[k] ? 1u : 0u) << k;
-      if (live) {
-        const ProjRec* r = projv + id;
-        ga = __ldg(&r->a);
-        gb = __ldg(&r->b);
-        gc = __ldg(&r->c.x);
-        msk = block_mask_exact(ga, gb, log2_amin, X0, Y0, live);
-      }
-    }
-    const unsigned bal = __ballot_sync(kAll, msk != 0u);
-    if (msk) {
-      const int d = kept + __popc(bal & ((1u << lane) - 1u));
-      s_a[d] = ga;
-      s_b[d] = gb;
-      s_meta[d] = StageMeta{pos + 1u, msk, gc, id};
-      groups += __popc(msk);
-    }
-    kept += __popc(bal);
-  }
-  __syncwarp();
-  return kept;
-}
-
-template <bool L1, bool IMP, int CB, int MINB>
-__global__ void __launch_bounds__(32, MINB) k_blend_bwd_tile(BlendArgs a, BwdIn in) {
-  __shared__ __align__(16) float2 s_tab[kPairRows][kPairStride];
-  __shared__ uint2 s_fmeta[kDeferG];  // (Gaussian id, blended pairs) of the deferred entries
-  __shared__ float4 s_a[CB];
-  __shared__ float4 s_b[CB];
-  __shared__ StageMeta s_meta[CB];
-  __shared__ int s_gmax[kTileBlocks];  // largest n_contrib of each block
-  __shared__ WarpTotals s_tot;
-
-  const int lane = threadIdx.x;
-  const int slot = table_slot(lane);
-  const float alpha_max = a.rp.alpha_max, alpha_min = a.rp.alpha_min;
-  const float log2_amin = log2f(alpha_min);
-  const int lx = lane & 7, ly = lane >> 3;
-  uint32_t exec_groups = 0;
-  if (lane == 0) s_tot = WarpTotals{0ull, 0.f};
-
-  while (true) {
-    const int item = cull_fetch(a.work_counter);
-    if (item >= a.n_tiles) break;
-    const int v = view_of_tile_cams(a.cams, a.n_views, item);
-    const CamDev& cam = a.cams[v];
-    const int lt = item - (int)__ldg(&a.cams[v].tile_base);
-    const int X0 = (lt % cam.TW) * kTile, Y0 = (lt / cam.TW) * kTile;
-    const float pxb[2] = {(float)(X0 + lx) + 0.5f, (float)(X0 + 8 + lx) + 0.5f};
-    float pyb[kTileBlocks / 2];
-#pragma unroll
-    for (int by = 0; by < kTileBlocks / 2; ++by) pyb[by] = (float)(Y0 + 4 * by + ly) + 0.5f;
-
-    float T[kTileBlocks], gC[kTileBlocks], g0[kTileBlocks], g1[kTileBlocks], g2[kTileBlocks];
-    int nc[kTileBlocks];
-    int maxnc = 0;
-    {
-      unsigned long long pairs = 0;
-      float loss_acc = 0.f;
-#pragma unroll
-      for (int k = 0; k < kTileBlocks; ++k) {
-        load_pixel<L1>(in, cam, X0 + 8 * (k & 1) + lx, Y0 + 4 * (k >> 1) + ly, T[k], gC[k], g0[k], g1[k], g2[k],
-                       nc[k], pairs, loss_acc);
-        const int gm = (int)__reduce_max_sync(kAll, (unsigned)nc[k]);  // warp-uniform
-        if (lane == k) s_gmax[k] = gm;
-        maxnc = max(maxnc, gm);
-      }
-      item_counters<L1>(s_tot, pairs, loss_acc, lane);
-    }
-    __syncwarp();
-    const uint2 range = a.ranges[item];
-    const uint32_t end = range.x + (uint32_t)maxnc;  // no entry at or beyond maxnc is replayed
-    const ProjRec* projv = a.proj + (size_t)v * a.n;
-    GradRec* gradv = in.grad + (size_t)v * a.n;
-    int ns = 0;
-
-    for (uint32_t b0 = range.x; b0 < end; b0 += CB) {
-      const int nb = stage_tile(a, b0, (int)min((uint32_t)CB, end - b0), range.x, projv, log2_amin, (float)X0,
-                                (float)Y0, s_gmax, s_a, s_b, s_meta, exec_groups);
-      for (int j = 0; j < nb; ++j) {
-        const StageMeta me = s_meta[j];
-        const float4 ga = s_a[j];
-        const float4 gb = s_b[j];
-        float2 acc[5];
-        int cnt;
-        replay_entry<kTileBlocks / 2, IMP>(ga, gb, me.c, (int)me.pos1, me.mask, pxb, pyb, alpha_max, alpha_min, T,
-                                           gC, g0, g1, g2, nc, acc, cnt);
-        defer_entry(s_tab, s_fmeta, ns, slot, acc, me.id, cnt);
-        if (++ns == kDeferG) {
-          flush_deferred<IMP>(s_tab, s_fmeta, ns, gradv, in, lane);
-          ns = 0;
-        }
-      }
-      __syncwarp();
-    }
-    if (ns > 0) flush_deferred<IMP>(s_tab, s_fmeta, ns, gradv, in, lane);
-  }
-  __syncwarp();
-  finish_counters<L1>(a, in, s_tot, exec_groups, lane);
-}
-
 namespace {
 
 template <class K>
@@ -447,38 +317,32 @@ cudaError_t launch_persistent(K kernel, int64_t items, cudaStream_t st, int num_
   return cudaGetLastError();
 }
 
-template <bool TILE, bool L1, bool IMP, int CB, int MINB>
+template <bool L1, bool IMP, int CB, int MINB>
 cudaError_t bwd_launch(cudaStream_t st, int num_sms, const BlendArgs& a, const BwdIn& in) {
-  if constexpr (TILE)
-    return launch_persistent(k_blend_bwd_tile<L1, IMP, CB, MINB>, a.n_tiles, st, num_sms, a, in);
-  else
-    return launch_persistent(k_blend_bwd<L1, IMP, CB, MINB>, a.n_tiles * 2, st, num_sms, a, in);
+  return launch_persistent(k_blend_bwd<L1, IMP, CB, MINB>, a.n_tiles * 2, st, num_sms, a, in);
 }
 
-template <bool TILE, int CB, int MINB>
+template <int CB, int MINB>
 cudaError_t bwd_dispatch(cudaStream_t st, int num_sms, const BlendArgs& a, const BwdIn& in) {
   const bool l1 = in.target != nullptr, imp = in.imp_w != nullptr;
   if (l1)
-    return imp ? bwd_launch<TILE, true, true, CB, MINB>(st, num_sms, a, in)
-               : bwd_launch<TILE, true, false, CB, MINB>(st, num_sms, a, in);
-  return imp ? bwd_launch<TILE, false, true, CB, MINB>(st, num_sms, a, in)
-             : bwd_launch<TILE, false, false, CB, MINB>(st, num_sms, a, in);
+    return imp ? bwd_launch<true, true, CB, MINB>(st, num_sms, a, in)
+               : bwd_launch<true, false, CB, MINB>(st, num_sms, a, in);
+  return imp ? bwd_launch<false, true, CB, MINB>(st, num_sms, a, in)
+             : bwd_launch<false, false, CB, MINB>(st, num_sms, a, in);
 }
 
 }  // namespace
 
-// The compiled backward shapes (kBwdShapes in kernels.h): item (half or full
-// tile), staged entries per batch and warps per SM (the register bound).
+// The compiled backward shapes (kBwdShapes in kernels.h): staged entries per
+// batch and warps per SM (the register bound).
 cudaError_t launch_blend_bwd(cudaStream_t st, int shape, int num_sms, const BlendArgs& a, const BwdIn& in) {
   switch (shape) {
-    case 1: return bwd_dispatch<false, 16, 28>(st, num_sms, a, in);
-    case 2: return bwd_dispatch<false, 64, 28>(st, num_sms, a, in);
-    case 3: return bwd_dispatch<false, 32, 24>(st, num_sms, a, in);
-    case 4: return bwd_dispatch<false, 32, 32>(st, num_sms, a, in);
-    case 5: return bwd_dispatch<true, 32, 20>(st, num_sms, a, in);
-    case 6: return bwd_dispatch<true, 32, 24>(st, num_sms, a, in);
-    case 7: return bwd_dispatch<true, 32, 16>(st, num_sms, a, in);
-    default: return bwd_dispatch<false, 32, 28>(st, num_sms, a, in);
+    case 1: return bwd_dispatch<16, 28>(st, num_sms, a, in);
+    case 2: return bwd_dispatch<64, 28>(st, num_sms, a, in);
+    case 3: return bwd_dispatch<32, 24>(st, num_sms, a, in);
+    case 4: return bwd_dispatch<32, 32>(st, num_sms, a, in);
+    default: return bwd_dispatch<32, 28>(st, num_sms, a, in);
   }
 }
 

@@ -54,7 +54,7 @@ def test_shape_table_without_gpu(lib_path):
     lib = _abi.load_library()
     n = lib.airgs_shape_count()
     names = [lib.airgs_shape_name(i).decode() for i in range(n)]
-    assert n == 360 and len(set(names)) == n
+    assert n == 225 and len(set(names)) == n
     assert names[0] == "fwd 32/32 bwd 32/28 keys 8 run 8"
     assert lib.airgs_shape_name(n) == b"" and lib.airgs_shape_name(-1) == b""
 
