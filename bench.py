@@ -90,12 +90,12 @@ _BLEND_SOURCES = ("paper_2512_20943_b300/csrc/blend_fwd.cu", "paper_2512_20943_b
 PROFILE_STEPS = 10  # steps of the per-stage profiling pass after the timed region
 
 NCU_TRAFFIC = {
-    "blend_bwd": {"bytes_per_launch": (657.595136 + 92.913920) * 1e6, "smem_bytes_per_launch": 426802375 * 128,
+    "blend_bwd": {"bytes_per_launch": (642.566400 + 89.244672) * 1e6, "smem_bytes_per_launch": 375140588 * 128,
                   "sources": _BLEND_SOURCES,
-                  "sha256": "265b0df977c4ade4acd766ce5bfe27e6c77b7b926ffe9a87442ba6b67bba0113"},
-    "blend_fwd": {"bytes_per_launch": (225.034752 + 233.092352) * 1e6, "smem_bytes_per_launch": 82761827 * 128,
+                  "sha256": "e2ca23a6eed809541225303b7ce0527e91470ce14d45fac6274a9f4d3299b02c"},
+    "blend_fwd": {"bytes_per_launch": (221.565184 + 230.910976) * 1e6, "smem_bytes_per_launch": 83946595 * 128,
                   "sources": _BLEND_SOURCES,
-                  "sha256": "265b0df977c4ade4acd766ce5bfe27e6c77b7b926ffe9a87442ba6b67bba0113"},
+                  "sha256": "e2ca23a6eed809541225303b7ce0527e91470ce14d45fac6274a9f4d3299b02c"},
 }
 
 
