@@ -92,10 +92,10 @@ PROFILE_STEPS = 10  # steps of the per-stage profiling pass after the timed regi
 NCU_TRAFFIC = {
     "blend_bwd": {"bytes_per_launch": (642.566400 + 89.244672) * 1e6, "smem_bytes_per_launch": 375140588 * 128,
                   "sources": _BLEND_SOURCES,
-                  "sha256": "e2ca23a6eed809541225303b7ce0527e91470ce14d45fac6274a9f4d3299b02c"},
+                  "sha256": "e34c3715ff8d6f0fb8c74de01f399d419c80a2371498566f6f3079b88f1c4ee8"},
     "blend_fwd": {"bytes_per_launch": (221.565184 + 230.910976) * 1e6, "smem_bytes_per_launch": 83946595 * 128,
                   "sources": _BLEND_SOURCES,
-                  "sha256": "e2ca23a6eed809541225303b7ce0527e91470ce14d45fac6274a9f4d3299b02c"},
+                  "sha256": "e34c3715ff8d6f0fb8c74de01f399d419c80a2371498566f6f3079b88f1c4ee8"},
 }
 
 

@@ -11,19 +11,18 @@
 // One warp replays a 16x8 half tile (four 8x4 blocks, a lane's four pixels),
 // walking the half's compacted list with the forward's exact block masks
 // stored in its entries, restricted to the blocks whose largest n_contrib lies
-// beyond the entry's position.  Each entry's ten per-lane sums, in five
-// pairs
+// beyond the entry's position.  Each entry's ten per-lane sums, in five pairs
 //   (S_x = sum t dx, S_y = sum t dy), (sum t dx^2, sum t dy^2),
 //   (sum t, blend weight), (colour r, g), (colour b, sum t dx dy)
 // (t = dL/dalpha G on unclamped pairs) are deferred into a per-warp
 // shared-memory table of three entries with one 8-byte store per pair, reduced
-// by two lanes per pair (a transpose through shared memory) and flushed with one
-// scalar red.global.add per sum into the Gaussian's gradient record (the
+// by two lanes per pair (a transpose through shared memory) and flushed with
+// one scalar red.global.add per sum into the Gaussian's gradient record (the
 // projection adjoint applies the 2D coefficients); the entry's blended-pair
-// count is a warp reduction of the lanes' counts.  With L1 the image gradient sign(C - target)/(3 sum H W) and the loss
-// are computed from the forward's image and the target in the kernel; with IMP
-// the blend weights and counts of the replay are the Gaussians' usage
-// frequency.
+// count is a warp reduction of the lanes' counts.  With L1 the image gradient
+// sign(C - target)/(3 sum H W) and the loss are computed from the forward's
+// image and the target in the kernel; with IMP the blend weights and counts of
+// the replay are the Gaussians' usage frequency.
 #include "blend_common.cuh"
 
 namespace airgs {
