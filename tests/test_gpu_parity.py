@@ -465,6 +465,41 @@ def test_large_gaussians_backward_counts_and_gradients(shape):
     res.state.release()
 
 
+def clamped_scene():
+    """Twelve opaque (o = 0.9975), wide Gaussians in front of a faint layer: in
+    20 of their 24 (view, Gaussian) projections some pixel has o G above
+    alpha_max = 0.99, so the replay meets clamped pairs (alpha = alpha_max, no
+    gradient to o or G) next to unclamped ones."""
+    g = synthetic.gaussians(150, 41, mean_mode="uniform", mean_scale=(1.3, 1.0, 0.8), log_scale=(-3.0, 0.4),
+                            sh_degree=1)
+    rng = np.random.default_rng(42)
+    g["opacity_logit"][:] = rng.normal(-1.0, 0.7, 150)
+    g["opacity_logit"][:12] = 6.0
+    g["log_scales"][:12] = rng.normal(-1.6, 0.15, (12, 3))
+    g["means"][:12, 2] -= 0.6
+    cams = [synthetic.camera((0.0, 0.0, -4.0), 96, 72, fov_x_deg=50.0),
+            synthetic.camera((0.5, 0.3, -3.8), 61, 45, fov_x_deg=55.0)]
+    return g, cams
+
+
+@pytest.mark.parametrize("shape", [0, 10])
+def test_clamped_alpha_gradients_match_oracle(shape):
+    """Gradients through pairs whose alpha is clamped at alpha_max (the replay
+    tells them from unclamped ones by ae == o G) match the oracle's."""
+    rast = rast_shape(shape)
+    g, cams = clamped_scene()
+    ref = oracle.render(synthetic.widen(g), cams)
+    dL = masked_dL(cams, ref, 43)
+    t, res = render_gpu(rast, g, cams, save=True)
+    flat = torch.from_numpy(np.concatenate([d.reshape(-1) for d in dL]).astype(np.float32)).cuda()
+    gr = rast.render_backward(res.state, flat)
+    torch.cuda.synchronize()
+    ref_g = oracle.render_backward(synthetic.widen(g), cams, dL)
+    for k in ("means", "log_scales", "quats", "opacity_logit", "sh"):
+        assert_grad_close(gr[k].cpu().numpy(), ref_g[k], k)
+    res.state.release()
+
+
 @pytest.mark.parametrize("shape", [0, 10])
 def test_needles_backward_matches_oracle(shape):
     rast = rast_shape(shape)
