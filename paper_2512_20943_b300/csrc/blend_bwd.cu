@@ -95,46 +95,54 @@ __device__ __forceinline__ void replay_entry(const float4 ga, const float4 gb, f
   const float dxb[2] = {__fsub_rn(ga.x, pxb[0]), __fsub_rn(ga.x, pxb[1])};
   float2 a01 = make_float2(0.f, 0.f), a24 = a01, a59 = a01, a67 = a01, a83 = a01;
   int lcnt = 0;
+  // one block: the lane's pixel of block k (column bx) against the entry
+  auto block = [&](int k, int bx, float dy, float b2dy, float c2dy2) {
+    const float dx = dxb[bx];
+    const float p2 = power2_of(dx, ga.z, b2dy, c2dy2);
+    const float G = ex2_approx(p2);
+    const float oG = __fmul_rn(gb.y, G);
+    const float alpha = alpha_of(gb.y, G, alpha_max);
+    // pair (pixel, entry) replayed iff pos1 <= n_contrib and the forward blended it
+    const bool valid = (pos1 <= nc[k]) && !(p2 > 0.f) && !(alpha < alpha_min);
+    const float ae = valid ? alpha : 0.f;
+    const float w = blend_weight(ae, T[k]);
+    const float gc = g0[k] * gb.z + g1[k] * gb.w + g2[k] * cb;
+    // independent sums in pairs: one packed FP32x2 operation each
+    a67 = __ffma2_rn(make_float2(w, w), make_float2(g0[k], g1[k]), a67);
+    a83.x = fmaf(w, g2[k], a83.x);
+    // gC[k] holds the colour still ahead of the replay, R = gC - gP
+    gC[k] = fmaf(-gc, w, gC[k]);
+    const float dL_dalpha = fmaf(-gC[k], rcp_approx_ftz(__fsub_rn(1.0f, ae)), T[k] * gc);
+    T[k] = transmit(T[k], w);
+    // t = dL/dalpha G on unclamped replayed pairs, whose ae equals o G
+    // exactly (a clamped pair has ae = alpha_max < o G, a skipped one 0)
+    const float tt = dL_dalpha * (ae == oG ? G : 0.f);
+    const float2 d2 = make_float2(dx, dy);
+    const float2 td = __fmul2_rn(make_float2(tt, tt), d2);  // (t dx, t dy)
+    a01 = __fadd2_rn(a01, td);
+    a24 = __ffma2_rn(td, d2, a24);                           // (t dx^2, t dy^2)
+    a83.y = fmaf(td.x, dy, a83.y);
+    if (IMP) {
+      a59 = __fadd2_rn(a59, make_float2(tt, w));
+      if (valid) ++lcnt;
+    } else {
+      a59.x += tt;
+    }
+  };
 #pragma unroll
   for (int by = 0; by < ROWS; ++by) {
-    if (!((m >> (2 * by)) & 3u)) continue;  // warp-uniform
+    // the row's live blocks (warp-uniform): both, or one of them
+    const unsigned rm = (m >> (2 * by)) & 3u;
+    if (!rm) continue;
     float dy, b2dy, c2dy2;  // shared by the row's two blocks
     row_terms(ga.y, pyb[by], ga.w, gb.x, dy, b2dy, c2dy2);
-#pragma unroll
-    for (int bx = 0; bx < 2; ++bx) {
-      const int k = 2 * by + bx;
-      if (!((m >> k) & 1u)) continue;  // warp-uniform
-      const float dx = dxb[bx];
-      const float p2 = power2_of(dx, ga.z, b2dy, c2dy2);
-      const float G = ex2_approx(p2);
-      const float oG = __fmul_rn(gb.y, G);
-      const float alpha = alpha_of(gb.y, G, alpha_max);
-      // pair (pixel, entry) replayed iff pos1 <= n_contrib and the forward blended it
-      const bool valid = (pos1 <= nc[k]) && !(p2 > 0.f) && !(alpha < alpha_min);
-      const float ae = valid ? alpha : 0.f;
-      const float w = blend_weight(ae, T[k]);
-      const float gc = g0[k] * gb.z + g1[k] * gb.w + g2[k] * cb;
-      // independent sums in pairs: one packed FP32x2 operation each
-      a67 = __ffma2_rn(make_float2(w, w), make_float2(g0[k], g1[k]), a67);
-      a83.x = fmaf(w, g2[k], a83.x);
-      // gC[k] holds the colour still ahead of the replay, R = gC - gP
-      gC[k] = fmaf(-gc, w, gC[k]);
-      const float dL_dalpha = fmaf(-gC[k], rcp_approx_ftz(__fsub_rn(1.0f, ae)), T[k] * gc);
-      T[k] = transmit(T[k], w);
-      // t = dL/dalpha G on unclamped replayed pairs, whose ae equals o G
-      // exactly (a clamped pair has ae = alpha_max < o G, a skipped one 0)
-      const float tt = dL_dalpha * (ae == oG ? G : 0.f);
-      const float2 d2 = make_float2(dx, dy);
-      const float2 td = __fmul2_rn(make_float2(tt, tt), d2);  // (t dx, t dy)
-      a01 = __fadd2_rn(a01, td);
-      a24 = __ffma2_rn(td, d2, a24);                           // (t dx^2, t dy^2)
-      a83.y = fmaf(td.x, dy, a83.y);
-      if (IMP) {
-        a59 = __fadd2_rn(a59, make_float2(tt, w));
-        if (valid) ++lcnt;
-      } else {
-        a59.x += tt;
-      }
+    if (rm == 3u) {
+      block(2 * by, 0, dy, b2dy, c2dy2);
+      block(2 * by + 1, 1, dy, b2dy, c2dy2);
+    } else if (rm == 1u) {
+      block(2 * by, 0, dy, b2dy, c2dy2);
+    } else {
+      block(2 * by + 1, 1, dy, b2dy, c2dy2);
     }
   }
   acc[0] = a01;

@@ -85,35 +85,43 @@ __global__ void __launch_bounds__(32, MINB) k_blend_fwd(BlendArgs a, FwdOut out)
         const float dxb[2] = {__fsub_rn(ga.x, pxb[0]), __fsub_rn(ga.x, pxb[1])};
         float wsum = 0.f;
         int bcount = 0;
+        // one block: the lane's pixel of block k (column bx) against the entry
+        auto block = [&](int k, int bx, float dy, float b2dy, float c2dy2) {
+          const float dx = dxb[bx];
+          const float p2 = power2_of(dx, ga.z, b2dy, c2dy2);
+          const float G = ex2_approx(p2);
+          const float alpha = alpha_of(gb.y, G, alpha_max);
+          const float w = blend_weight(alpha, T[k]);
+          const float Tn = transmit(T[k], w);
+          const bool valid = (stop_at[k] < 0) && !(p2 > 0.f) && !(alpha < alpha_min);
+          const bool stop = valid && (Tn < T_min);
+          const bool blend = valid && !stop;
+          if (blend) {
+            C01[k] = __ffma2_rn(make_float2(gb.z, gb.w), make_float2(w, w), C01[k]);
+            C2[k] = __fmaf_rn(cb, w, C2[k]);
+            T[k] = Tn;
+            last[k] = pos1;
+          }
+          if (stop) stop_at[k] = pos1;
+          if (IMP) {
+            wsum += blend ? w : 0.f;
+            bcount += blend ? 1 : 0;
+          }
+        };
 #pragma unroll
         for (int by = 0; by < 2; ++by) {
-          if (!((m >> (2 * by)) & 3u)) continue;  // warp-uniform
+          // the row's live blocks (warp-uniform): both, or one of them
+          const unsigned rm = (m >> (2 * by)) & 3u;
+          if (!rm) continue;
           float dy, b2dy, c2dy2;  // shared by the row's two blocks
           row_terms(ga.y, pyb[by], ga.w, gb.x, dy, b2dy, c2dy2);
-#pragma unroll
-          for (int bx = 0; bx < 2; ++bx) {
-            const int k = 2 * by + bx;
-            if (!((m >> k) & 1u)) continue;  // warp-uniform
-            const float dx = dxb[bx];
-            const float p2 = power2_of(dx, ga.z, b2dy, c2dy2);
-            const float G = ex2_approx(p2);
-            const float alpha = alpha_of(gb.y, G, alpha_max);
-            const float w = blend_weight(alpha, T[k]);
-            const float Tn = transmit(T[k], w);
-            const bool valid = (stop_at[k] < 0) && !(p2 > 0.f) && !(alpha < alpha_min);
-            const bool stop = valid && (Tn < T_min);
-            const bool blend = valid && !stop;
-            if (blend) {
-              C01[k] = __ffma2_rn(make_float2(gb.z, gb.w), make_float2(w, w), C01[k]);
-              C2[k] = __fmaf_rn(cb, w, C2[k]);
-              T[k] = Tn;
-              last[k] = pos1;
-            }
-            if (stop) stop_at[k] = pos1;
-            if (IMP) {
-              wsum += blend ? w : 0.f;
-              bcount += blend ? 1 : 0;
-            }
+          if (rm == 3u) {
+            block(2 * by, 0, dy, b2dy, c2dy2);
+            block(2 * by + 1, 1, dy, b2dy, c2dy2);
+          } else if (rm == 1u) {
+            block(2 * by, 0, dy, b2dy, c2dy2);
+          } else {
+            block(2 * by + 1, 1, dy, b2dy, c2dy2);
           }
         }
         if (IMP) {
