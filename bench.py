@@ -242,14 +242,18 @@ class Workload:
         return self.targets[s * n:(s + VIEWS_PER_STEP) * n]
 
 
-def train_step(rast, wl, frame, imp, map_tensor=None, target=None):
+def train_step(rast, wl, frame, imp, map_tensor=None, target=None, before_backward=None):
     """One step of the path: decode/apply frame `frame`, batched render of its
-    8 views, fused L1 backward with importance accumulation."""
+    8 views, fused L1 backward with importance accumulation (`before_backward`
+    is called between the render and the backward: the host feed's wait for
+    the targets)."""
     from paper_2512_20943_b300 import AIRGS_DELTA_PREV
     m = wl.maps[frame] if map_tensor is None else map_tensor
     rast.apply_frame_update(m, wl.lo, wl.hi, mode=AIRGS_DELTA_PREV, frame_id=frame)
     _, cams = wl.views(frame)
     res = rast.render(cams, save=True)
+    if before_backward is not None:
+        before_backward()
     tgt = wl.target_slice(frame) if target is None else target
     loss, grads = rast.render_backward_l1(res.state, tgt, importance=imp)
     res.state.release()
@@ -857,21 +861,23 @@ def run_e2e(rast, wl, args, device, stream, imp, world):
     update map and its 8 target images are copied from pinned host memory, and
     its loss is copied back and read on the host.  The copies go through the
     package's double-buffered HostFeed, so step k's inputs cross PCIe while step
-    k - 1 computes, and step k - 1's loss is read while step k runs; the timed
-    region ends when the last step's loss has been read."""
+    k - 1 computes, the targets (read only by the backward) are waited for after
+    the render, and step k - 1's loss is read while step k runs; the timed region
+    ends when the last step's loss has been read."""
     import torch
     from paper_2512_20943_b300.feed import HostFeed
     map_h = [torch.from_numpy(m.view(np.int16)).view(torch.uint16).pin_memory() for m in wl.maps_host]
     n = 3 * wl.view_px * VIEWS_PER_STEP
     tg_h = torch.from_numpy(wl.targets_host).pin_memory()
     feed = HostFeed({"map": (tuple(map_h[0].shape), torch.uint16), "target": ((n,), torch.float32)}, stream,
-                    device=device)
+                    device=device, late=("target",))
     losses = []
 
     def step(k, frame):
         s, _ = wl.views(frame)
         dev = feed.put(k, map=map_h[frame], target=tg_h[s * 3 * wl.view_px:s * 3 * wl.view_px + n])
-        loss, _ = train_step(rast, wl, frame, imp, map_tensor=dev["map"], target=dev["target"])
+        loss, _ = train_step(rast, wl, frame, imp, map_tensor=dev["map"], target=dev["target"],
+                             before_backward=lambda: feed.wait(k, "target"))
         feed.done(k, loss)
         if k:
             losses.append(float(feed.result(k - 1)[0]))
@@ -895,7 +901,8 @@ def run_e2e(rast, wl, args, device, stream, imp, world):
     value = world * VIEWS_PER_STEP * WIDTH * HEIGHT * args.steps / secs / 1e6
     return {"value": value, "unit": UNIT, "h2d_bytes_per_step": feed.h2d_bytes, "d2h_bytes_per_step": 4,
             "ms_per_step": 1e3 * secs / args.steps, "overlap": "double-buffered: inputs of step k copied while "
-                                                              "step k - 1 computes; every loss read back"}
+                                                              "step k - 1 computes, targets awaited before the "
+                                                              "backward; every loss read back"}
 
 
 def main(argv=None):

@@ -32,11 +32,16 @@ def test_feed_rejects_unknown_and_mismatched_buffers():
         feed.put(0, x=torch.zeros(5).pin_memory())
     with pytest.raises(KeyError):
         feed.result(0)
+    with pytest.raises(KeyError):
+        HostFeed({"x": ((4,), torch.float32)}, s, late=("y",))
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("depth", [1, 2, 3])
-def test_feed_training_matches_device_inputs(depth):
+@pytest.mark.parametrize("depth,late", [(1, False), (2, False), (3, False), (1, True), (2, True)])
+def test_feed_training_matches_device_inputs(depth, late):
+    """Losses of steps fed through the feed equal those of the same steps fed
+    from device copies, with the targets waited for at the start of the step or
+    (late) only before the backward."""
     import torch
     from paper_2512_20943_b300 import AIRGS_DELTA_PREV, Rasterizer
     from paper_2512_20943_b300.feed import HostFeed
@@ -53,7 +58,8 @@ def test_feed_training_matches_device_inputs(depth):
         rast.set_anchor(*anchor)
         losses = []
         feed = HostFeed({"map": (tuple(map_h[0].shape), torch.uint16), "target": ((tg_h[0].numel(),),
-                                                                              torch.float32)}, stream, depth=depth)
+                                                                              torch.float32)}, stream, depth=depth,
+                        late=("target",) if late else ())
         with torch.cuda.stream(stream):
             for k in range(n_frames):
                 if fed:
@@ -63,6 +69,8 @@ def test_feed_training_matches_device_inputs(depth):
                     m_d, t_d = map_h[k].cuda(), tg_h[k].cuda()
                 rast.apply_frame_update(m_d, lo, hi, mode=AIRGS_DELTA_PREV, frame_id=k)
                 res = rast.render(cams, save=True)
+                if fed and late:
+                    feed.wait(k, "target")
                 loss, _ = rast.render_backward_l1(res.state, t_d)
                 res.state.release()
                 if fed:
