@@ -90,12 +90,12 @@ _BLEND_SOURCES = ("paper_2512_20943_b300/csrc/blend_fwd.cu", "paper_2512_20943_b
 PROFILE_STEPS = 10  # steps of the per-stage profiling pass after the timed region
 
 NCU_TRAFFIC = {
-    "blend_bwd": {"bytes_per_launch": (642.566400 + 89.244672) * 1e6, "smem_bytes_per_launch": 375140588 * 128,
+    "blend_bwd": {"bytes_per_launch": (640.023552 + 85.096960) * 1e6, "smem_bytes_per_launch": 375530966 * 128,
                   "sources": _BLEND_SOURCES,
-                  "sha256": "e34c3715ff8d6f0fb8c74de01f399d419c80a2371498566f6f3079b88f1c4ee8"},
-    "blend_fwd": {"bytes_per_launch": (221.565184 + 230.910976) * 1e6, "smem_bytes_per_launch": 83946595 * 128,
+                  "sha256": "2c477c75e91c8631b3890b6bda9ca19956e839cd94d9b4c052fe6b989299c6af"},
+    "blend_fwd": {"bytes_per_launch": (220.214528 + 229.777664) * 1e6, "smem_bytes_per_launch": 83951196 * 128,
                   "sources": _BLEND_SOURCES,
-                  "sha256": "e34c3715ff8d6f0fb8c74de01f399d419c80a2371498566f6f3079b88f1c4ee8"},
+                  "sha256": "2c477c75e91c8631b3890b6bda9ca19956e839cd94d9b4c052fe6b989299c6af"},
 }
 
 
