@@ -57,12 +57,16 @@ struct __align__(16) StageMeta {
 // many were kept.  With LIVE (the backward) the mask is also restricted to the
 // blocks whose largest n_contrib (gmax, in shared memory) lies beyond the
 // entry's position, and `past` is set when an entry lies at or beyond maxnc
-// (positions increase along the list, so no later batch can contribute).  Half-list entries: the forward
-// computes each staged entry's exact block mask and stores it in the entry's
-// top bits; the backward reads it from there (every entry before maxnc was
-// staged by the forward of the same state).  Each lane adds to `groups` the
-// blocks its kept entries will evaluate (mask & alive, the blocks not yet
-// terminated at the batch's start), the issued-work statistic.
+// (positions increase along the list, so no later batch can contribute).  Without
+// LIVE (the forward) the exact test covers only the blocks in `alive` (some pixel
+// still blending at the batch's start), so entries that reach only finished
+// blocks are not staged.  Half-list entries: the forward stores each staged
+// entry's exact block mask (restricted to `alive`) in the entry's top bits; the
+// backward reads it from there (every entry before maxnc was staged by the
+// forward of the same state, and a block finished before the entry's batch has
+// no pixel whose n_contrib lies beyond the entry).  Each lane adds to `groups`
+// the blocks its kept entries will evaluate (mask & alive), the issued-work
+// statistic.
 template <bool LIVE>
 __device__ __forceinline__ int stage_compact(const BlendArgs& a, bool use_hl, uint32_t b0, int nb, uint32_t list0,
                                              const ProjRec* projv, float log2_amin, float X0, float Y0,
@@ -99,14 +103,16 @@ __device__ __forceinline__ int stage_compact(const BlendArgs& a, bool use_hl, ui
           for (int k = 0; k < kBlocks; ++k) live |= ((int)pos < gmax[k] ? 1u : 0u) << k;
           msk = have_mask ? (msk & live) : live;
         } else if (!have_mask) {
-          msk = (1u << kBlocks) - 1u;
+          msk = alive;
         }
         if (msk) {
           const ProjRec* r = projv + id;
           ga = __ldg(&r->a);
           gb = __ldg(&r->b);
           gc = __ldg(&r->c.x);
-          if (!have_mask) msk &= block_mask_exact(ga, gb, log2_amin, X0, Y0, (1u << kBlocks) - 1u);
+          if (!have_mask)
+            msk = LIVE ? (msk & block_mask_exact(ga, gb, log2_amin, X0, Y0, (1u << kBlocks) - 1u))
+                       : block_mask_exact(ga, gb, log2_amin, X0, Y0, msk);
         }
         if (!LIVE && use_hl) a.hl_mut[b0 + j].y = pos | (msk << kHlMaskShift);
       }

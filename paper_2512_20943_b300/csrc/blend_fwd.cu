@@ -76,8 +76,7 @@ __global__ void __launch_bounds__(32, MINB) k_blend_fwd(BlendArgs a, FwdOut out)
                                           exec_groups);
       for (int j = 0; j < nb; ++j) {
         const StageMeta me = s_meta[j];
-        const unsigned m = me.mask & live;
-        if (m == 0) continue;
+        const unsigned m = me.mask;  // staged against the blocks live at the batch's start: non-zero
         const float4 ga = s_a[j];
         const float4 gb = s_b[j];
         const float cb = me.c;
