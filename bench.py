@@ -90,12 +90,12 @@ _BLEND_SOURCES = ("paper_2512_20943_b300/csrc/blend_fwd.cu", "paper_2512_20943_b
 PROFILE_STEPS = 10  # steps of the per-stage profiling pass after the timed region
 
 NCU_TRAFFIC = {
-    "blend_bwd": {"bytes_per_launch": (640.023552 + 85.096960) * 1e6, "smem_bytes_per_launch": 375530966 * 128,
+    "blend_bwd": {"bytes_per_launch": (639.860224 + 85.680128) * 1e6, "smem_bytes_per_launch": 375525156 * 128,
                   "sources": _BLEND_SOURCES,
-                  "sha256": "2c477c75e91c8631b3890b6bda9ca19956e839cd94d9b4c052fe6b989299c6af"},
-    "blend_fwd": {"bytes_per_launch": (220.214528 + 229.777664) * 1e6, "smem_bytes_per_launch": 83951196 * 128,
+                  "sha256": "a9b0122b2c40acdadfa4675a46f15c363220af8b33f9fc36fe1e74a663ab8526"},
+    "blend_fwd": {"bytes_per_launch": (222.425600 + 231.676416) * 1e6, "smem_bytes_per_launch": 83382195 * 128,
                   "sources": _BLEND_SOURCES,
-                  "sha256": "2c477c75e91c8631b3890b6bda9ca19956e839cd94d9b4c052fe6b989299c6af"},
+                  "sha256": "a9b0122b2c40acdadfa4675a46f15c363220af8b33f9fc36fe1e74a663ab8526"},
 }
 
 
