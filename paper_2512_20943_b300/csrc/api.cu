@@ -84,12 +84,14 @@ struct airgs_state {
   uint2* hranges = nullptr;    // [2][tiles]
   GradRec* grad = nullptr;     // [V][N] blend-backward accumulators, zeroed during the render (saved states)
   bool grad_zeroed = false;    // grad holds zeros (not yet used by a backward)
-  // [4] device counters, 8 bytes each: forward pairs, forward work queue,
-  // backward pairs, backward work queue (int in the low half); the backward's
-  // two are adjacent, so one memset resets them
+  // [5] device counters, 8 bytes each: forward pairs, forward work queue,
+  // backward pairs, backward work queue (int in the low half; the backward's
+  // two are adjacent, so one memset resets them), tile instances
   unsigned long long* counters = nullptr;
   const float* rgb = nullptr;  // caller's forward output
-  int64_t n_inst = 0, n_tiles = 0, n_pixels = 0;
+  // tile instances; -1 while only the device counter holds the count (a render
+  // that did not wait for it: n_inst_bound bounds it)
+  int64_t n_inst = 0, n_inst_bound = 0, n_tiles = 0, n_pixels = 0;
   int shape = 0;               // kernel shape (shape_parts) the render ran and the backward runs
   std::vector<void*> owned;    // device allocations to free on release
 };
@@ -110,6 +112,10 @@ int fail(airgs_ctx* ctx, int code, const char* fmt, ...) {
 // Batches of at most this many (view, Gaussian) pairs take the per-tile ordering by default (sort_mode -1):
 // measured on a 2k-Gaussian, 128x128 render, 0.68 ms against 0.94 ms with the radix ordering.
 constexpr int64_t kSmallOrdering = 65536;
+// A per-tile ordering whose instance count is bounded by at most this many entries (every Gaussian of a view in
+// every tile of it) and whose lists cannot outgrow one CTA's sort (at most kTileSortBig Gaussians) sizes its
+// instance arrays by that bound instead of reading the count back: the render then never waits for the device.
+constexpr int64_t kNoWaitInstances = 1ll << 22;
 
 #define CK(expr)                                                                                  \
   do {                                                                                            \
@@ -339,7 +345,7 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
   ALLOC(s->proj, V * N);
   ALLOC(s->ranges, s->n_tiles);
   ALLOC(s->ncontrib, s->n_pixels);
-  ALLOC(s->counters, 4);
+  ALLOC(s->counters, 5);
   {
     const int slot = ctx->cam_slot;
     CK(cudaEventSynchronize(ctx->cam_copied[slot]));  // the slot's previous copy (complete unless just enqueued)
@@ -349,7 +355,7 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
     CK(cudaEventRecord(ctx->cam_copied[slot], st));
     ctx->cam_slot = slot ^ 1;
   }
-  CK(cudaMemsetAsync(s->counters, 0, 4 * sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(s->counters, 0, 5 * sizeof(unsigned long long), st));
   CK(cudaMemsetAsync(s->ranges, 0, s->n_tiles * sizeof(uint2), st));
   RasterParams rp = raster_params(ctx->cfg);
 
@@ -393,7 +399,46 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
                         n_views, rp, s->proj, dkeys, tiles, tile_counts, cull));
     }
     bool use_radix = !per_tile;
-    if (per_tile) {
+    // no wait for the instance count: an upper bound that keeps the arrays small, and lists that fit one CTA
+    int64_t bound = 0;
+    for (const CamDev& c : s->h_cams) bound += N * (int64_t)c.TW * c.TH;
+    const bool no_wait = per_tile && N <= kTileSortBig && bound <= kNoWaitInstances;
+    if (per_tile && no_wait) {
+      // per-tile lists as below, sized by the bound; the count stays on the device (counters[4])
+      const int64_t chunks = (int64_t)tile_offsets_chunks(s->n_tiles);
+      uint64_t* csum;
+      uint32_t *cursor, *big_list, *info;
+      TALLOC(csum, chunks + 1);
+      TALLOC(cursor, s->n_tiles);
+      TALLOC(big_list, s->n_tiles);
+      TALLOC(info, 4);
+      CK(cudaMemsetAsync(info, 0, 4 * sizeof(uint32_t), st));
+      {
+        StageScope sc(ctx, ST_EMIT);
+        CK(launch_tile_offsets(st, tile_counts, s->n_tiles, csum, s->ranges, cursor, big_list, info));
+      }
+      CK(cudaMemcpyAsync(s->counters + 4, csum + chunks, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+      PREFILL_GRAD();
+      s->n_inst = -1;
+      s->n_inst_bound = bound;
+      if (bound > 0) {
+        uint2* ipairs;
+        uint32_t* ivals;
+        TALLOC(ipairs, bound);
+        ALLOC(ivals, bound);
+        {
+          StageScope sc(ctx, ST_EMIT);
+          CK(launch_scatter(st, V * N, N, s->proj, s->d_cams, dkeys, cursor, ipairs));
+        }
+        {
+          StageScope sc(ctx, ST_TILE_SORT);
+          // lists longer than one 256-thread CTA's share: at most bound / kTileSortSmall of them
+          const int64_t big_max = std::min<int64_t>(s->n_tiles, bound / kTileSortSmall);
+          CK(launch_sort_tiles(st, s->n_tiles, s->ranges, big_list, big_max, ipairs, ivals, info + 1));
+        }
+        s->ids = ivals;
+      }
+    } else if (per_tile) {
       // per-tile lists: offsets from the counts, scatter, sort each list in shared memory
       const int64_t chunks = (int64_t)tile_offsets_chunks(s->n_tiles);
       uint64_t* csum;
@@ -432,7 +477,7 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
         }
         {
           StageScope sc(ctx, ST_TILE_SORT);
-          CK(launch_sort_tiles(st, s->n_tiles, s->ranges, big_list, n_big, ipairs, ivals));
+          CK(launch_sort_tiles(st, s->n_tiles, s->ranges, big_list, n_big, ipairs, ivals, nullptr));
         }
         s->ids = ivals;
       }
@@ -616,7 +661,7 @@ int backward_impl(airgs_ctx* ctx, airgs_state* s, const float* dL, const float* 
   in.grad = grad;
   in.imp_w = imp_w;
   in.imp_cnt = imp_cnt;
-  if (s->n_inst > 0) {
+  if (s->n_inst > 0 || (s->n_inst < 0 && s->n_inst_bound > 0)) {
     StageScope sc(ctx, ST_BLEND_BWD);
     CK(launch_blend_bwd(st, shape_parts(s->shape).bwd, ctx->num_sms, a, in));
   }
@@ -906,10 +951,10 @@ int airgs_release_state(airgs_ctx* ctx, airgs_state* state) {
 
 int airgs_state_stats(airgs_ctx* ctx, const airgs_state* s, airgs_stats* out) {
   if (!ctx || !s || !out) return AIRGS_E_ARG;
-  CK(cudaMemcpyAsync(ctx->h_pinned, s->counters, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+  CK(cudaMemcpyAsync(ctx->h_pinned, s->counters, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                      ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
-  out->n_instances = s->n_inst;
+  out->n_instances = s->n_inst >= 0 ? s->n_inst : (int64_t)ctx->h_pinned[4];
   out->n_tiles = s->n_tiles;
   out->n_pixels = s->n_pixels;
   out->pairs_forward = (int64_t)ctx->h_pinned[0];

@@ -37,8 +37,10 @@ cudaError_t launch_tile_offsets(cudaStream_t st, const uint32_t* counts, int64_t
 size_t tile_offsets_chunks(int64_t n_tiles);
 cudaError_t launch_scatter(cudaStream_t st, int64_t total, int64_t n, const ProjRec* proj, const CamDev* cams,
                            const uint32_t* depth_keys, uint32_t* cursor, uint2* pairs);
+// n_big: the number of long lists, or with n_big_dev (their count on the
+// device) an upper bound on it.
 cudaError_t launch_sort_tiles(cudaStream_t st, int64_t n_tiles, const uint2* ranges, const uint32_t* big_list,
-                              int64_t n_big, const uint2* pairs, uint32_t* vals);
+                              int64_t n_big, const uint2* pairs, uint32_t* vals, const uint32_t* n_big_dev);
 
 // keys: radix keys per thread (6, 8 or 12; 0 = the default for the segment
 // count); the scratch size and the sort must be given the same value.

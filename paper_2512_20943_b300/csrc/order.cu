@@ -166,11 +166,15 @@ __global__ void __launch_bounds__(256) k_sort_tiles_small(int64_t n_tiles, const
   }
 }
 
+// One CTA per long list; with n_big_dev (the count on the device, the grid an
+// upper bound) the CTAs beyond the count return at once.
 __global__ void __launch_bounds__(1024) k_sort_tiles_big(const uint32_t* __restrict__ big_list,
                                                         const uint2* __restrict__ ranges,
                                                         const uint2* __restrict__ pairs,
-                                                        uint32_t* __restrict__ vals) {
+                                                        uint32_t* __restrict__ vals,
+                                                        const uint32_t* __restrict__ n_big_dev) {
   extern __shared__ unsigned long long s_big[];
+  if (n_big_dev && blockIdx.x >= *n_big_dev) return;
   const uint2 r = ranges[big_list[blockIdx.x]];
   sort_segment<1024>(s_big, r.y - r.x, r.x, pairs, vals);
 }
@@ -198,7 +202,7 @@ cudaError_t launch_scatter(cudaStream_t st, int64_t total, int64_t n, const Proj
 }
 
 cudaError_t launch_sort_tiles(cudaStream_t st, int64_t n_tiles, const uint2* ranges, const uint32_t* big_list,
-                              int64_t n_big, const uint2* pairs, uint32_t* vals) {
+                              int64_t n_big, const uint2* pairs, uint32_t* vals, const uint32_t* n_big_dev) {
   if (n_tiles == 0) return cudaSuccess;
   const int grid = (int)(n_tiles < 65535 * 8 ? n_tiles : 65535 * 8);
   k_sort_tiles_small<<<grid, 256, 0, st>>>(n_tiles, ranges, pairs, vals);
@@ -207,7 +211,7 @@ cudaError_t launch_sort_tiles(cudaStream_t st, int64_t n_tiles, const uint2* ran
     const size_t smem = (size_t)kTileSortBig * sizeof(unsigned long long);
     cudaError_t e = cudaFuncSetAttribute(k_sort_tiles_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_sort_tiles_big<<<(unsigned)n_big, 1024, smem, st>>>(big_list, ranges, pairs, vals);
+    k_sort_tiles_big<<<(unsigned)n_big, 1024, smem, st>>>(big_list, ranges, pairs, vals, n_big_dev);
     count_launches(1);
   }
   return cudaGetLastError();
