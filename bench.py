@@ -92,10 +92,10 @@ PROFILE_STEPS = 10  # steps of the per-stage profiling pass after the timed regi
 NCU_TRAFFIC = {
     "blend_bwd": {"bytes_per_launch": (639.860224 + 85.680128) * 1e6, "smem_bytes_per_launch": 375525156 * 128,
                   "sources": _BLEND_SOURCES,
-                  "sha256": "a9b0122b2c40acdadfa4675a46f15c363220af8b33f9fc36fe1e74a663ab8526"},
+                  "sha256": "8184b66ddbe08f2361328862b187b8572e965f19ce04412d1f0ed584cff755d7"},
     "blend_fwd": {"bytes_per_launch": (222.425600 + 231.676416) * 1e6, "smem_bytes_per_launch": 83382195 * 128,
                   "sources": _BLEND_SOURCES,
-                  "sha256": "a9b0122b2c40acdadfa4675a46f15c363220af8b33f9fc36fe1e74a663ab8526"},
+                  "sha256": "8184b66ddbe08f2361328862b187b8572e965f19ce04412d1f0ed584cff755d7"},
 }
 
 

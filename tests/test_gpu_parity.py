@@ -767,17 +767,21 @@ def test_autograd_function_gradients_match_oracle(rast):
 @pytest.mark.parametrize("shape", [0, 20])
 def test_small_batch_default_ordering_equals_radix(shape):
     """The default ordering (sort_mode -1) sorts small batches per tile in
-    shared memory: images, T, n_contrib, importance and gradients equal the
-    radix ordering's (tile lists are identical, so the blend is too)."""
+    shared memory, with instance arrays sized by an upper bound (the render
+    does not wait for the count): images, T, n_contrib, importance, the
+    instance count and gradients equal the radix ordering's (tile lists are
+    identical, so the blend is too)."""
     from paper_2512_20943_b300 import RasterConfig, Rasterizer
     g, cams = small_sh3_scene()
-    out = []
+    out, n_inst = [], []
     for mode in (-1, 0):
         r = Rasterizer(RasterConfig(kernel_shape=shape, sort_mode=mode))
         t, res = render_gpu(r, g, cams, T=True, n_contrib=True, importance=True, save=True)
         gr = r.render_backward(res.state, torch.ones_like(res.rgb))
         torch.cuda.synchronize()
+        n_inst.append(r.stats(res.state)["n_instances"])
         out.append((res, {k: v.clone() for k, v in gr.items()}))
+    assert n_inst[0] == n_inst[1] > 0
     (a, ga), (b, gb) = out
     assert torch.equal(a.rgb, b.rgb) and torch.equal(a.T, b.T) and torch.equal(a.n_contrib, b.n_contrib)
     assert torch.equal(a.importance_cnt, b.importance_cnt)
