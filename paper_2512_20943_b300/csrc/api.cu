@@ -259,8 +259,8 @@ const char* airgs::shape_name(int shape) {
   struct Names {
     char s[kShapes][48];
     Names() {
-      const int fwd[kFwdShapes][2] = {{32, 32}, {16, 32}, {64, 32}, {32, 28}, {32, 24}};
-      const int bwd[kBwdShapes][2] = {{32, 28}, {16, 28}, {64, 28}, {32, 24}, {32, 32}};
+      const int fwd[kFwdShapes][2] = {{32, 28}, {16, 28}, {64, 28}, {32, 32}, {32, 24}};
+      const int bwd[kBwdShapes][2] = {{32, 32}, {16, 32}, {64, 32}, {32, 28}, {32, 24}};
       for (int i = 0; i < kShapes; ++i) {
         const ShapeParts p = shape_parts(i);
         snprintf(s[i], sizeof(s[i]), "fwd %d/%d bwd %d/%d keys %d run %d", fwd[p.fwd][0], fwd[p.fwd][1],

@@ -345,11 +345,11 @@ cudaError_t bwd_dispatch(cudaStream_t st, int num_sms, const BlendArgs& a, const
 // batch and warps per SM (the register bound).
 cudaError_t launch_blend_bwd(cudaStream_t st, int shape, int num_sms, const BlendArgs& a, const BwdIn& in) {
   switch (shape) {
-    case 1: return bwd_dispatch<16, 28>(st, num_sms, a, in);
-    case 2: return bwd_dispatch<64, 28>(st, num_sms, a, in);
-    case 3: return bwd_dispatch<32, 24>(st, num_sms, a, in);
-    case 4: return bwd_dispatch<32, 32>(st, num_sms, a, in);
-    default: return bwd_dispatch<32, 28>(st, num_sms, a, in);
+    case 1: return bwd_dispatch<16, 32>(st, num_sms, a, in);
+    case 2: return bwd_dispatch<64, 32>(st, num_sms, a, in);
+    case 3: return bwd_dispatch<32, 28>(st, num_sms, a, in);
+    case 4: return bwd_dispatch<32, 24>(st, num_sms, a, in);
+    default: return bwd_dispatch<32, 32>(st, num_sms, a, in);
   }
 }
 

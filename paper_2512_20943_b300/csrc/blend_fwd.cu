@@ -196,11 +196,11 @@ cudaError_t fwd_dispatch(cudaStream_t st, int num_sms, const BlendArgs& a, const
 // batch and warps per SM (the register bound).
 cudaError_t launch_blend_fwd(cudaStream_t st, int shape, int num_sms, const BlendArgs& a, const FwdOut& o) {
   switch (shape) {
-    case 1: return fwd_dispatch<16, 32>(st, num_sms, a, o);
-    case 2: return fwd_dispatch<64, 32>(st, num_sms, a, o);
-    case 3: return fwd_dispatch<32, 28>(st, num_sms, a, o);
+    case 1: return fwd_dispatch<16, 28>(st, num_sms, a, o);
+    case 2: return fwd_dispatch<64, 28>(st, num_sms, a, o);
+    case 3: return fwd_dispatch<32, 32>(st, num_sms, a, o);
     case 4: return fwd_dispatch<32, 24>(st, num_sms, a, o);
-    default: return fwd_dispatch<32, 32>(st, num_sms, a, o);
+    default: return fwd_dispatch<32, 28>(st, num_sms, a, o);
   }
 }
 

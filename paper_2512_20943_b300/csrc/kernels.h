@@ -140,8 +140,8 @@ struct BwdIn {
 // emission's instances per thread.  A shape index packs (forward f, backward
 // b, sort k, emission e) as f + kFwdShapes (b + kBwdShapes (k + kSortShapes e));
 // shape 0 (every part 0) is the default.
-constexpr int kFwdShapes = 5;   // forward (batch, warps): (32, 32) (16, 32) (64, 32) (32, 28) (32, 24)
-constexpr int kBwdShapes = 5;   // backward (batch, warps): (32, 28) (16, 28) (64, 28) (32, 24) (32, 32)
+constexpr int kFwdShapes = 5;   // forward (batch, warps): (32, 28) (16, 28) (64, 28) (32, 32) (32, 24)
+constexpr int kBwdShapes = 5;   // backward (batch, warps): (32, 32) (16, 32) (64, 32) (32, 28) (32, 24)
 constexpr int kSortShapes = 3;  // instance sort keys per thread: 8, 6, 12
 constexpr int kEmitShapes = 3;  // emission instances per thread and piece: 8, 4, 16
 constexpr int kShapes = kFwdShapes * kBwdShapes * kSortShapes * kEmitShapes;

@@ -55,7 +55,7 @@ def test_shape_table_without_gpu(lib_path):
     n = lib.airgs_shape_count()
     names = [lib.airgs_shape_name(i).decode() for i in range(n)]
     assert n == 225 and len(set(names)) == n
-    assert names[0] == "fwd 32/32 bwd 32/28 keys 8 run 8"
+    assert names[0] == "fwd 32/28 bwd 32/32 keys 8 run 8"
     assert lib.airgs_shape_name(n) == b"" and lib.airgs_shape_name(-1) == b""
 
 
