@@ -25,6 +25,8 @@
 // the replay are the Gaussians' usage frequency.
 #include "blend_common.cuh"
 
+#include <type_traits>
+
 namespace airgs {
 
 namespace {
@@ -80,23 +82,25 @@ __device__ __forceinline__ void defer_entry(float2 (*s_tab)[kPairStride], uint2*
   s_fmeta[ns] = make_uint2(id, (uint32_t)cnt);
 }
 
-// Replays one staged entry over the blocks of mask m (block k = 2 by + bx of
-// ROWS block rows; the lane's pixel of block k sits at (pxb[bx], pyb[by])) with
-// the forward's arithmetic: updates each pixel's T and colour still ahead (gC,
+// Replays one staged entry over the blocks of its mask m (non-zero; block k =
+// 2 by + bx, the lane's pixel of block k at (pxb[bx], pyb[by])) with the
+// forward's arithmetic: updates each pixel's T and colour still ahead (gC,
 // dotted with the image gradient g), returns the lane's ten sums in five pairs
 // (acc) and, with IMP, the warp's blended-pair count in cnt (warp-uniform).
-template <int ROWS, bool IMP>
+template <bool IMP>
 __device__ __forceinline__ void replay_entry(const float4 ga, const float4 gb, float cb, int pos1, unsigned m,
-                                             const float (&pxb)[2], const float (&pyb)[ROWS], float alpha_max,
-                                             float alpha_min, float (&T)[2 * ROWS], float (&gC)[2 * ROWS],
-                                             const float (&g0)[2 * ROWS], const float (&g1)[2 * ROWS],
-                                             const float (&g2)[2 * ROWS], const int (&nc)[2 * ROWS],
+                                             const float (&pxb)[2], const float (&pyb)[2], float alpha_max,
+                                             float alpha_min, float (&T)[kBlocks], float (&gC)[kBlocks],
+                                             const float (&g0)[kBlocks], const float (&g1)[kBlocks],
+                                             const float (&g2)[kBlocks], const int (&nc)[kBlocks],
                                              float2 (&acc)[5], int& cnt) {
   const float dxb[2] = {__fsub_rn(ga.x, pxb[0]), __fsub_rn(ga.x, pxb[1])};
-  float2 a01 = make_float2(0.f, 0.f), a24 = a01, a59 = a01, a67 = a01, a83 = a01;
-  int lcnt = 0;
-  // one block: the lane's pixel of block k (column bx) against the entry
-  auto block = [&](int k, int bx, float dy, float b2dy, float c2dy2) {
+  float2 a01, a24, a59, a67, a83;  // assigned by the entry's first block
+  int lcnt;
+  // one block: the lane's pixel of block k (column bx) against the entry; INIT:
+  // the entry's first block, which assigns the sums instead of adding to them
+  auto block = [&](auto init, int k, int bx, float dy, float b2dy, float c2dy2) {
+    constexpr bool INIT = decltype(init)::value;
     const float dx = dxb[bx];
     const float p2 = power2_of(dx, ga.z, b2dy, c2dy2);
     const float G = ex2_approx(p2);
@@ -108,8 +112,13 @@ __device__ __forceinline__ void replay_entry(const float4 ga, const float4 gb, f
     const float w = blend_weight(ae, T[k]);
     const float gc = g0[k] * gb.z + g1[k] * gb.w + g2[k] * cb;
     // independent sums in pairs: one packed FP32x2 operation each
-    a67 = __ffma2_rn(make_float2(w, w), make_float2(g0[k], g1[k]), a67);
-    a83.x = fmaf(w, g2[k], a83.x);
+    if (INIT) {
+      a67 = __fmul2_rn(make_float2(w, w), make_float2(g0[k], g1[k]));
+      a83.x = w * g2[k];
+    } else {
+      a67 = __ffma2_rn(make_float2(w, w), make_float2(g0[k], g1[k]), a67);
+      a83.x = fmaf(w, g2[k], a83.x);
+    }
     // gC[k] holds the colour still ahead of the replay, R = gC - gP
     gC[k] = fmaf(-gc, w, gC[k]);
     const float dL_dalpha = fmaf(-gC[k], rcp_approx_ftz(__fsub_rn(1.0f, ae)), T[k] * gc);
@@ -119,31 +128,53 @@ __device__ __forceinline__ void replay_entry(const float4 ga, const float4 gb, f
     const float tt = dL_dalpha * (ae == oG ? G : 0.f);
     const float2 d2 = make_float2(dx, dy);
     const float2 td = __fmul2_rn(make_float2(tt, tt), d2);  // (t dx, t dy)
-    a01 = __fadd2_rn(a01, td);
-    a24 = __ffma2_rn(td, d2, a24);                           // (t dx^2, t dy^2)
-    a83.y = fmaf(td.x, dy, a83.y);
-    if (IMP) {
-      a59 = __fadd2_rn(a59, make_float2(tt, w));
-      if (valid) ++lcnt;
+    if (INIT) {
+      a01 = td;
+      a24 = __fmul2_rn(td, d2);
+      a83.y = td.x * dy;
     } else {
-      a59.x += tt;
+      a01 = __fadd2_rn(a01, td);
+      a24 = __ffma2_rn(td, d2, a24);
+      a83.y = fmaf(td.x, dy, a83.y);
+    }
+    if (IMP) {
+      if (INIT) {
+        a59 = make_float2(tt, w);
+        lcnt = valid ? 1 : 0;
+      } else {
+        a59 = __fadd2_rn(a59, make_float2(tt, w));
+        if (valid) ++lcnt;
+      }
+    } else {
+      if (INIT) {
+        a59 = make_float2(tt, 0.f);
+        lcnt = 0;
+      } else {
+        a59.x += tt;
+      }
     }
   };
-#pragma unroll
-  for (int by = 0; by < ROWS; ++by) {
-    // the row's live blocks (warp-uniform): both, or one of them
-    const unsigned rm = (m >> (2 * by)) & 3u;
-    if (!rm) continue;
+  using First = std::integral_constant<bool, true>;
+  using Next = std::integral_constant<bool, false>;
+  // the row's live blocks (warp-uniform): both, or one of them; m != 0
+  auto row = [&](auto first, int by, unsigned rm) {
     float dy, b2dy, c2dy2;  // shared by the row's two blocks
     row_terms(ga.y, pyb[by], ga.w, gb.x, dy, b2dy, c2dy2);
     if (rm == 3u) {
-      block(2 * by, 0, dy, b2dy, c2dy2);
-      block(2 * by + 1, 1, dy, b2dy, c2dy2);
+      block(first, 2 * by, 0, dy, b2dy, c2dy2);
+      block(Next{}, 2 * by + 1, 1, dy, b2dy, c2dy2);
     } else if (rm == 1u) {
-      block(2 * by, 0, dy, b2dy, c2dy2);
+      block(first, 2 * by, 0, dy, b2dy, c2dy2);
     } else {
-      block(2 * by + 1, 1, dy, b2dy, c2dy2);
+      block(first, 2 * by + 1, 1, dy, b2dy, c2dy2);
     }
+  };
+  const unsigned r0 = m & 3u, r1 = (m >> 2) & 3u;
+  if (r0) {
+    row(First{}, 0, r0);
+    if (r1) row(Next{}, 1, r1);
+  } else {
+    row(First{}, 1, r1);
   }
   acc[0] = a01;
   acc[1] = a24;
@@ -293,8 +324,8 @@ __global__ void __launch_bounds__(32, MINB) k_blend_bwd(BlendArgs a, BwdIn in) {
         const float4 gb = s_b[j];
         float2 acc[5];
         int cnt;
-        replay_entry<2, IMP>(ga, gb, me.c, (int)me.pos1, me.mask, pxb, pyb, alpha_max, alpha_min, T, gC, g0, g1, g2,
-                             nc, acc, cnt);
+        replay_entry<IMP>(ga, gb, me.c, (int)me.pos1, me.mask, pxb, pyb, alpha_max, alpha_min, T, gC, g0, g1, g2, nc,
+                          acc, cnt);
         // every compacted entry has a live block: defer without a vote
         defer_entry(s_tab, s_fmeta, ns, slot, acc, me.id, cnt);
         if (++ns == kDeferG) {
