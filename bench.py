@@ -90,12 +90,12 @@ _BLEND_SOURCES = ("paper_2512_20943_b300/csrc/blend_fwd.cu", "paper_2512_20943_b
 PROFILE_STEPS = 10  # steps of the per-stage profiling pass after the timed region
 
 NCU_TRAFFIC = {
-    "blend_bwd": {"bytes_per_launch": (658.050560 + 88.083456) * 1e6, "smem_bytes_per_launch": 376116579 * 128,
+    "blend_bwd": {"bytes_per_launch": (656.552960 + 87.734016) * 1e6, "smem_bytes_per_launch": 376507427 * 128,
                   "sources": _BLEND_SOURCES,
-                  "sha256": "7795916ca57b2fd5a62f3f9cccb3f2f7b4066d88815d86f155f1fc9087a711f7"},
+                  "sha256": "bbf6ecd995f7ee78971aa56b55b9da582bca82b03d1ee0d7751def8c6da19d13"},
     "blend_fwd": {"bytes_per_launch": (217.441792 + 227.322368) * 1e6, "smem_bytes_per_launch": 81672641 * 128,
                   "sources": _BLEND_SOURCES,
-                  "sha256": "7795916ca57b2fd5a62f3f9cccb3f2f7b4066d88815d86f155f1fc9087a711f7"},
+                  "sha256": "bbf6ecd995f7ee78971aa56b55b9da582bca82b03d1ee0d7751def8c6da19d13"},
 }
 
 
