@@ -82,6 +82,7 @@ struct airgs_state {
   int32_t* ncontrib = nullptr; // [pixels]
   uint2* hl = nullptr;         // half-tile lists, nullable (lists of 2^28 entries or more: the full lists)
   uint2* hranges = nullptr;    // [2][tiles]
+  uint32_t* order = nullptr;   // [2 tiles] queue order of the blend kernels' half-tile items (with hl)
   GradRec* grad = nullptr;     // [V][N] blend-backward accumulators, zeroed during the render (saved states)
   bool grad_zeroed = false;    // grad holds zeros (not yet used by a backward)
   // [5] device counters, 8 bytes each: forward pairs, forward work queue,
@@ -562,6 +563,10 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
           StageScope sc(ctx, ST_RANGES);
           CK(launch_half_lists(st, skeys, s->ids, s->ranges, s->d_cams, n_views, s->proj, N, n_inst,
                                ctx->cfg.alpha_min, s->n_tiles, hflags, hsums, s->hl, s->hranges));
+          uint32_t* oscratch;
+          TALLOC(oscratch, 2 * kOrderBins);
+          ALLOC(s->order, 2 * s->n_tiles);
+          CK(launch_item_order(st, ctx->num_sms, s->hranges, s->n_tiles, oscratch, s->order));
         }
       }
     }
@@ -583,6 +588,7 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
   a.hl = s->hl;
   a.hl_mut = s->hl;
   a.hranges = s->hranges;
+  a.work_order = s->order;
   FwdOut o;
   o.rgb = rgb_out;
   o.T = T_out;
@@ -651,6 +657,7 @@ int backward_impl(airgs_ctx* ctx, airgs_state* s, const float* dL, const float* 
   a.hl = s->hl;
   a.hl_mut = s->hl;
   a.hranges = s->hranges;
+  a.work_order = s->order;
   BwdIn in;
   in.rgb = s->rgb;
   in.dL = dL;

@@ -31,6 +31,10 @@ __device__ __forceinline__ int cull_fetch(int* counter) {
   return __shfl_sync(kAll, it, 0);
 }
 
+// The work item at queue position q (< the item count): through the queue
+// order when there is one (every lane reads the same word).
+__device__ __forceinline__ int queue_item(const uint32_t* order, int q) { return order ? (int)__ldg(order + q) : q; }
+
 // View that owns a global tile id, from the cameras' tile bases (read through
 // the read-only cache).
 __device__ __forceinline__ int view_of_tile_cams(const CamDev* cams, int n_views, int tile) {

@@ -34,8 +34,9 @@ __global__ void __launch_bounds__(32, MINB) k_blend_fwd(BlendArgs a, FwdOut out)
   if (lane == 0) s_pairs = 0ull;
 
   while (true) {
-    const int work = cull_fetch(a.work_counter);
-    if (work >= a.n_tiles * 2) break;
+    const int q = cull_fetch(a.work_counter);
+    if (q >= a.n_tiles * 2) break;
+    const int work = queue_item(a.work_order, q);
     const int item = work >> 1, part = work & 1;
     const int v = view_of_tile_cams(a.cams, a.n_views, item);
     const CamDev& cam = a.cams[v];

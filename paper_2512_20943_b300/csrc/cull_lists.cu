@@ -178,4 +178,92 @@ cudaError_t launch_half_lists(cudaStream_t st, const uint32_t* keys, const uint3
   return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
+// ---------------------------------------------------------------- work order
+// The blend kernels take their (half tile) items from an atomic queue, one warp
+// per item.  Item costs vary by orders of magnitude (the half-list length), and
+// with the queue in tile order a long item taken near the end keeps its SM busy
+// while the others idle.  Ordering the queue by decreasing list length (longest
+// processing time first, in bins of half an octave) ends it on short items.
+
+// Bin of a half-list length L (descending order = decreasing bin): 0 for an
+// empty list, else 1 + 2 floor(log2 L) + the bit below the leading one.
+__device__ __forceinline__ int order_bin(uint32_t L) {
+  if (L == 0u) return 0;
+  const int msb = 31 - __clz(L);
+  const int sub = msb > 0 ? (int)((L >> (msb - 1)) & 1u) : 0;
+  return min(1 + 2 * msb + sub, kOrderBins - 1);
+}
+
+__device__ __forceinline__ uint32_t item_length(const uint2* hranges, int64_t n_tiles, int64_t w) {
+  const uint2 r = hranges[(w & 1) * n_tiles + (w >> 1)];
+  return r.y - r.x;
+}
+
+__global__ void __launch_bounds__(256) k_order_hist(const uint2* __restrict__ hranges, int64_t n_tiles,
+                                                    uint32_t* __restrict__ hist) {
+  wait_prior_grid();
+  __shared__ uint32_t sh[kOrderBins];
+  for (int i = threadIdx.x; i < kOrderBins; i += blockDim.x) sh[i] = 0u;
+  __syncthreads();
+  const int64_t n_work = 2 * n_tiles;
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_work; w += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&sh[order_bin(item_length(hranges, n_tiles, w))], 1u);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kOrderBins; i += blockDim.x)
+    if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+// Scatters each item to its bin's range (bins in decreasing order); within a
+// bin the order is that of the cursor's atomic increments (warp-aggregated).
+__global__ void __launch_bounds__(256) k_order_scatter(const uint2* __restrict__ hranges, int64_t n_tiles,
+                                                       const uint32_t* __restrict__ hist,
+                                                       uint32_t* __restrict__ cursor, uint32_t* __restrict__ order) {
+  wait_prior_grid();
+  __shared__ uint32_t base[kOrderBins];
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x < 32) {
+    // exclusive sum over the bins above: lane l owns bins 2l and 2l + 1
+    static_assert(kOrderBins == 64, "two bins per lane");
+    const uint32_t h0 = hist[2 * lane], h1 = hist[2 * lane + 1];
+    uint32_t x = h0 + h1;  // inclusive suffix sum over lanes >= l
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_down_sync(0xffffffffu, x, o);
+      if (lane + o < 32) x += y;
+    }
+    base[2 * lane + 1] = x - h0 - h1;  // bins above 2l + 1
+    base[2 * lane] = x - h0;
+  }
+  __syncthreads();
+  const int64_t n_work = 2 * n_tiles;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // every lane of a warp runs the same iterations (the shuffles take all lanes)
+  for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); w0 < n_work; w0 += stride) {
+    const int64_t w = w0 + lane;
+    const bool valid = w < n_work;
+    const int b = valid ? order_bin(item_length(hranges, n_tiles, w)) : kOrderBins;
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    const int leader = __ffs(peers) - 1;
+    uint32_t first = 0u;
+    if (lane == leader && valid) first = atomicAdd(&cursor[b], (uint32_t)__popc(peers));
+    first = __shfl_sync(0xffffffffu, first, leader);
+    if (valid) order[base[b] + first + (uint32_t)__popc(peers & ((1u << lane) - 1u))] = (uint32_t)w;
+  }
+}
+
+cudaError_t launch_item_order(cudaStream_t st, int num_sms, const uint2* hranges, int64_t n_tiles, uint32_t* scratch,
+                              uint32_t* order) {
+  if (n_tiles <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(scratch, 0, 2 * kOrderBins * sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = (2 * n_tiles + 255) / 256;
+  const unsigned grid = (unsigned)(blocks < 2 * (int64_t)num_sms ? blocks : 2 * (int64_t)num_sms);
+  e = launch_serialised(k_order_hist, dim3(grid), dim3(256), 0, st, hranges, n_tiles, scratch);
+  if (e == cudaSuccess)
+    e = launch_serialised(k_order_scatter, dim3(grid), dim3(256), 0, st, hranges, n_tiles,
+                          (const uint32_t*)scratch, scratch + kOrderBins, order);
+  count_launches(2);
+  return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
 }  // namespace airgs

@@ -94,6 +94,12 @@ cudaError_t launch_half_lists(cudaStream_t st, const uint32_t* keys, const uint3
                               const CamDev* cams, int n_views, const ProjRec* proj, int64_t n, int64_t n_inst,
                               float alpha_min, int64_t n_tiles, uint8_t* flags, uint64_t* sums, uint2* hl,
                               uint2* hranges);
+// Queue order of the blend kernels' 2 n_tiles half-tile items (work index
+// 2 tile + half): decreasing half-list length, in bins of half an octave.
+// scratch: 2 kOrderBins words (zeroed here); order: 2 n_tiles words.
+constexpr int kOrderBins = 64;
+cudaError_t launch_item_order(cudaStream_t st, int num_sms, const uint2* hranges, int64_t n_tiles, uint32_t* scratch,
+                              uint32_t* order);
 
 struct BlendArgs {
   const ProjRec* proj;  // [V][N]
@@ -111,6 +117,7 @@ struct BlendArgs {
   const uint2* hl;                 // nullable: half-tile lists of (Gaussian id, full-list position | block mask)
   uint2* hl_mut;                   // the same lists, written by the compacting forward (block masks)
   const uint2* hranges;            // [2][tiles] ranges into hl (top halves, then bottom halves)
+  const uint32_t* work_order;      // nullable: the queue's work indices in the order to hand them out
 };
 
 struct FwdOut {
