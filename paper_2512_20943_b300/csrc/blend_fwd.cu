@@ -17,14 +17,27 @@
 // the backward reproduces every decision bit for bit.
 #include "blend_common.cuh"
 
+#include <cstddef>
+
 namespace airgs {
 
 template <bool IMP, int FB, int MINB>
 __global__ void __launch_bounds__(32, MINB) k_blend_fwd(BlendArgs a, FwdOut out) {
-  __shared__ float4 s_a[FB];
-  __shared__ float4 s_b[FB];
-  __shared__ StageMeta s_meta[FB];
-  __shared__ unsigned long long s_pairs;  // the warp's definition pairs (no register holds them through the blend)
+  // the warp's shared memory as one block (16-byte records first)
+  struct __align__(16) WarpSmem {
+    float4 a[FB];
+    float4 b[FB];
+    StageMeta meta[FB];
+    unsigned long long pairs;  // the warp's definition pairs (no register holds them through the blend)
+  };
+  static_assert(offsetof(WarpSmem, a) % 16 == 0 && offsetof(WarpSmem, b) % 16 == 0 &&
+                    offsetof(WarpSmem, meta) % 16 == 0,
+                "16-byte shared loads need 16-byte aligned records");
+  __shared__ WarpSmem sw;
+  float4* s_a = sw.a;
+  float4* s_b = sw.b;
+  StageMeta* s_meta = sw.meta;
+  unsigned long long& s_pairs = sw.pairs;
 
   const int lane = threadIdx.x;
   const float alpha_max = a.rp.alpha_max, alpha_min = a.rp.alpha_min, T_min = a.rp.T_min;
