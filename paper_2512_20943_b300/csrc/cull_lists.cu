@@ -180,13 +180,16 @@ cudaError_t launch_half_lists(cudaStream_t st, const uint32_t* keys, const uint3
 
 // ---------------------------------------------------------------- work order
 // The blend kernels take their (half tile) items from an atomic queue, one warp
-// per item.  Item costs vary by orders of magnitude (the half-list length), and
-// with the queue in tile order a long item taken near the end keeps its SM busy
-// while the others idle.  Ordering the queue by decreasing list length (longest
-// processing time first, in bins of half an octave) ends it on short items.
+// per item.  Item costs vary several-fold (the half-list length), and with the
+// queue in tile order a long item taken near the end keeps its SM busy while
+// the others idle.  The order below hands out the items of each group of
+// consecutive views (work indices are view-major) longest list first (in bins
+// of half an octave): every group, the last one included, ends on short items,
+// and the items in flight together come from one group, whose Gaussian
+// records stay in L2.
 
-// Bin of a half-list length L (descending order = decreasing bin): 0 for an
-// empty list, else 1 + 2 floor(log2 L) + the bit below the leading one.
+// Bin of a half-list length L: 0 for an empty list, else 1 + 2 floor(log2 L)
+// + the bit below the leading one.
 __device__ __forceinline__ int order_bin(uint32_t L) {
   if (L == 0u) return 0;
   const int msb = 31 - __clz(L);
@@ -194,75 +197,104 @@ __device__ __forceinline__ int order_bin(uint32_t L) {
   return min(1 + 2 * msb + sub, kOrderBins - 1);
 }
 
-__device__ __forceinline__ uint32_t item_length(const uint2* hranges, int64_t n_tiles, int64_t w) {
-  const uint2 r = hranges[(w & 1) * n_tiles + (w >> 1)];
-  return r.y - r.x;
+struct OrderArgs {
+  const uint2* hranges;  // [2][tiles]
+  const CamDev* cams;
+  int n_views;
+  int views_per_group;
+  int n_groups;
+  int64_t n_tiles;
+};
+
+// Group-major bin index of work item w (group g, bin b: g kOrderBins + b).
+__device__ __forceinline__ int order_key(const OrderArgs& o, int64_t w) {
+  const int64_t tile = w >> 1;
+  const uint2 r = o.hranges[(w & 1) * o.n_tiles + tile];
+  int lo = 0, hi = o.n_views - 1;  // the view owning the tile
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((int64_t)__ldg(&o.cams[mid].tile_base) <= tile) lo = mid;
+    else hi = mid - 1;
+  }
+  const int g = min(lo / o.views_per_group, o.n_groups - 1);
+  return g * kOrderBins + order_bin(r.y - r.x);
 }
 
-__global__ void __launch_bounds__(256) k_order_hist(const uint2* __restrict__ hranges, int64_t n_tiles,
-                                                    uint32_t* __restrict__ hist) {
+// Adds one to counter[key] for every lane of the warp (one atomic per distinct
+// key, of the number of lanes holding it); returns the lane's rank among them
+// plus the counter's previous value.  Lanes with key < 0 take no part.
+__device__ __forceinline__ uint32_t warp_count(uint32_t* counter, int key, bool want_rank) {
+  const int lane = threadIdx.x & 31;
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  const int leader = __ffs(peers) - 1;
+  uint32_t first = 0u;
+  if (lane == leader && key >= 0) first = atomicAdd(&counter[key], (uint32_t)__popc(peers));
+  if (!want_rank) return 0u;
+  first = __shfl_sync(0xffffffffu, first, leader);
+  return first + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+}
+
+__global__ void __launch_bounds__(256) k_order_hist(OrderArgs o, uint32_t* __restrict__ hist) {
   wait_prior_grid();
-  __shared__ uint32_t sh[kOrderBins];
-  for (int i = threadIdx.x; i < kOrderBins; i += blockDim.x) sh[i] = 0u;
-  __syncthreads();
-  const int64_t n_work = 2 * n_tiles;
-  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_work; w += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(&sh[order_bin(item_length(hranges, n_tiles, w))], 1u);
-  __syncthreads();
-  for (int i = threadIdx.x; i < kOrderBins; i += blockDim.x)
-    if (sh[i]) atomicAdd(&hist[i], sh[i]);
+  const int64_t n_work = 2 * o.n_tiles, stride = (int64_t)gridDim.x * blockDim.x;
+  // every lane of a warp runs the same iterations (the warp votes take all lanes)
+  for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); w0 < n_work; w0 += stride) {
+    const int64_t w = w0 + (threadIdx.x & 31);
+    warp_count(hist, w < n_work ? order_key(o, w) : -1, false);
+  }
 }
 
-// Scatters each item to its bin's range (bins in decreasing order); within a
-// bin the order is that of the cursor's atomic increments (warp-aggregated).
-__global__ void __launch_bounds__(256) k_order_scatter(const uint2* __restrict__ hranges, int64_t n_tiles,
-                                                       const uint32_t* __restrict__ hist,
+// base[g][b]: the group's first work index plus the items of its bins above b.
+__global__ void __launch_bounds__(32) k_order_base(OrderArgs o, const uint32_t* __restrict__ hist,
+                                                   uint32_t* __restrict__ base) {
+  wait_prior_grid();
+  static_assert(kOrderBins == 64, "two bins per lane");
+  const int g = blockIdx.x, lane = threadIdx.x;
+  const uint32_t* h = hist + (size_t)g * kOrderBins;
+  const uint32_t h0 = h[2 * lane], h1 = h[2 * lane + 1];
+  uint32_t x = h0 + h1;  // inclusive suffix sum over lanes >= this one
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t y = __shfl_down_sync(0xffffffffu, x, off);
+    if (lane + off < 32) x += y;
+  }
+  const uint32_t start = 2u * __ldg(&o.cams[g * o.views_per_group].tile_base);
+  base[(size_t)g * kOrderBins + 2 * lane + 1] = start + x - h0 - h1;
+  base[(size_t)g * kOrderBins + 2 * lane] = start + x - h0;
+}
+
+__global__ void __launch_bounds__(256) k_order_scatter(OrderArgs o, const uint32_t* __restrict__ base,
                                                        uint32_t* __restrict__ cursor, uint32_t* __restrict__ order) {
   wait_prior_grid();
-  __shared__ uint32_t base[kOrderBins];
-  const int lane = threadIdx.x & 31;
-  if (threadIdx.x < 32) {
-    // exclusive sum over the bins above: lane l owns bins 2l and 2l + 1
-    static_assert(kOrderBins == 64, "two bins per lane");
-    const uint32_t h0 = hist[2 * lane], h1 = hist[2 * lane + 1];
-    uint32_t x = h0 + h1;  // inclusive suffix sum over lanes >= l
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_down_sync(0xffffffffu, x, o);
-      if (lane + o < 32) x += y;
-    }
-    base[2 * lane + 1] = x - h0 - h1;  // bins above 2l + 1
-    base[2 * lane] = x - h0;
-  }
-  __syncthreads();
-  const int64_t n_work = 2 * n_tiles;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  // every lane of a warp runs the same iterations (the shuffles take all lanes)
+  const int64_t n_work = 2 * o.n_tiles, stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); w0 < n_work; w0 += stride) {
-    const int64_t w = w0 + lane;
-    const bool valid = w < n_work;
-    const int b = valid ? order_bin(item_length(hranges, n_tiles, w)) : kOrderBins;
-    const unsigned peers = __match_any_sync(0xffffffffu, b);
-    const int leader = __ffs(peers) - 1;
-    uint32_t first = 0u;
-    if (lane == leader && valid) first = atomicAdd(&cursor[b], (uint32_t)__popc(peers));
-    first = __shfl_sync(0xffffffffu, first, leader);
-    if (valid) order[base[b] + first + (uint32_t)__popc(peers & ((1u << lane) - 1u))] = (uint32_t)w;
+    const int64_t w = w0 + (threadIdx.x & 31);
+    const int key = w < n_work ? order_key(o, w) : -1;
+    const uint32_t rank = warp_count(cursor, key, true);
+    if (key >= 0) order[base[key] + rank] = (uint32_t)w;
   }
 }
 
-cudaError_t launch_item_order(cudaStream_t st, int num_sms, const uint2* hranges, int64_t n_tiles, uint32_t* scratch,
-                              uint32_t* order) {
-  if (n_tiles <= 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(scratch, 0, 2 * kOrderBins * sizeof(uint32_t), st);
+size_t item_order_words(int n_views) { return (size_t)3 * kOrderBins * (n_views > 0 ? n_views : 1); }
+
+cudaError_t launch_item_order(cudaStream_t st, int num_sms, const uint2* hranges, const CamDev* cams, int n_views,
+                              int views_per_group, int64_t n_tiles, uint32_t* scratch, uint32_t* order) {
+  if (n_tiles <= 0 || n_views <= 0) return cudaSuccess;
+  if (views_per_group < 1) views_per_group = 1;
+  if (views_per_group > n_views) views_per_group = n_views;
+  OrderArgs o{hranges, cams, n_views, views_per_group, n_views / views_per_group, n_tiles};
+  const size_t words = (size_t)o.n_groups * kOrderBins;
+  uint32_t *hist = scratch, *cursor = scratch + words, *base = scratch + 2 * words;
+  cudaError_t e = cudaMemsetAsync(scratch, 0, 2 * words * sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
   const int64_t blocks = (2 * n_tiles + 255) / 256;
   const unsigned grid = (unsigned)(blocks < 2 * (int64_t)num_sms ? blocks : 2 * (int64_t)num_sms);
-  e = launch_serialised(k_order_hist, dim3(grid), dim3(256), 0, st, hranges, n_tiles, scratch);
+  e = launch_serialised(k_order_hist, dim3(grid), dim3(256), 0, st, o, hist);
   if (e == cudaSuccess)
-    e = launch_serialised(k_order_scatter, dim3(grid), dim3(256), 0, st, hranges, n_tiles,
-                          (const uint32_t*)scratch, scratch + kOrderBins, order);
-  count_launches(2);
+    e = launch_serialised(k_order_base, dim3((unsigned)o.n_groups), dim3(32), 0, st, o, (const uint32_t*)hist, base);
+  if (e == cudaSuccess)
+    e = launch_serialised(k_order_scatter, dim3(grid), dim3(256), 0, st, o, (const uint32_t*)base, cursor, order);
+  count_launches(3);
   return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
