@@ -124,19 +124,22 @@ constexpr int64_t kNoWaitInstances = 1ll << 22;
 // in flight together.
 constexpr int64_t kOrderMaxItemsPerWarp = 64;
 
-// Views per group of the blend queue's order: as many as keep the group's projection and gradient records within
-// half of L2, but enough that the last group holds at least kOrderGroupItemsPerWarp items per resident warp (the
-// longest lists are about three times the mean: the last group's longest items then start well before its end).
-// Streaming step (8 views of 300k Gaussians): groups of 4 views, backward 1.845 ms with 1.03 GB of DRAM traffic;
-// groups of 2 (4 items per warp) 1.855 ms, 0.78 GB; one group 1.845 ms, 1.32 GB.
+// Groups of the blend queue's order: as many views as keep a group's projection and gradient records within half
+// of L2, except the last group, which holds at least kOrderGroupItemsPerWarp items per resident warp (the longest
+// lists are about three times the mean: the last group's longest items then start well before its end).
+// Streaming step (8 views of 300k Gaussians): groups of 2, 2 and 4 views; with 2 groups of 4 views the backward took
+// 1.845 ms with 1.03 GB of DRAM traffic, with 4 groups of 2 (4 items per warp in the last) 1.855 ms and 0.78 GB,
+// with one group 1.845 ms and 1.32 GB.
 constexpr int64_t kOrderGroupItemsPerWarp = 8;
-int order_views_per_group(const airgs_ctx* ctx, int64_t n, int n_views, int64_t n_tiles) {
+void order_groups(const airgs_ctx* ctx, int64_t n, int n_views, int64_t n_tiles, int* views_per_group,
+                  int* last_views) {
   const int64_t per_view = n * (int64_t)(sizeof(ProjRec) + sizeof(GradRec));
-  int64_t vpg = per_view > 0 ? (int64_t)ctx->l2_bytes / 2 / per_view : n_views;
+  const int64_t vpg = per_view > 0 ? (int64_t)ctx->l2_bytes / 2 / per_view : n_views;
   const int64_t items_per_view = 2 * n_tiles / (n_views > 0 ? n_views : 1);
   const int64_t need = kOrderGroupItemsPerWarp * 32ll * ctx->num_sms;
-  if (items_per_view > 0 && vpg * items_per_view < need) vpg = (need + items_per_view - 1) / items_per_view;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(vpg, n_views));
+  const int64_t last = items_per_view > 0 ? (need + items_per_view - 1) / items_per_view : n_views;
+  *views_per_group = (int)std::max<int64_t>(1, std::min<int64_t>(vpg, n_views));
+  *last_views = (int)std::max<int64_t>(*views_per_group, std::min<int64_t>(last, n_views));
 }
 
 #define CK(expr)                                                                                  \
@@ -588,8 +591,10 @@ int render_impl(airgs_ctx* ctx, const airgs_gaussians* g, const airgs_camera* ca
             uint32_t* oscratch;
             TALLOC(oscratch, item_order_words(n_views));
             ALLOC(s->order, 2 * s->n_tiles);
-            CK(launch_item_order(st, ctx->num_sms, s->hranges, s->d_cams, n_views,
-                                 order_views_per_group(ctx, N, n_views, s->n_tiles), s->n_tiles, oscratch, s->order));
+            int vpg = 1, last_views = 1;
+            order_groups(ctx, N, n_views, s->n_tiles, &vpg, &last_views);
+            CK(launch_item_order(st, ctx->num_sms, s->hranges, s->d_cams, n_views, vpg, last_views, s->n_tiles,
+                                 oscratch, s->order));
           }
         }
       }

@@ -186,7 +186,8 @@ cudaError_t launch_half_lists(cudaStream_t st, const uint32_t* keys, const uint3
 // consecutive views (work indices are view-major) longest list first (in bins
 // of half an octave): every group, the last one included, ends on short items,
 // and the items in flight together come from one group, whose Gaussian
-// records stay in L2.
+// records stay in L2.  The last group may hold more views than the others (it
+// alone decides the kernel's end, so it needs enough items per warp).
 
 // Bin of a half-list length L: 0 for an empty list, else 1 + 2 floor(log2 L)
 // + the bit below the leading one.
@@ -278,11 +279,16 @@ __global__ void __launch_bounds__(256) k_order_scatter(OrderArgs o, const uint32
 size_t item_order_words(int n_views) { return (size_t)3 * kOrderBins * (n_views > 0 ? n_views : 1); }
 
 cudaError_t launch_item_order(cudaStream_t st, int num_sms, const uint2* hranges, const CamDev* cams, int n_views,
-                              int views_per_group, int64_t n_tiles, uint32_t* scratch, uint32_t* order) {
+                              int views_per_group, int last_views, int64_t n_tiles, uint32_t* scratch,
+                              uint32_t* order) {
   if (n_tiles <= 0 || n_views <= 0) return cudaSuccess;
   if (views_per_group < 1) views_per_group = 1;
   if (views_per_group > n_views) views_per_group = n_views;
-  OrderArgs o{hranges, cams, n_views, views_per_group, n_views / views_per_group, n_tiles};
+  if (last_views < views_per_group) last_views = views_per_group;
+  if (last_views > n_views) last_views = n_views;
+  // groups of views_per_group views before the last one, which takes the rest
+  // (at least last_views views)
+  OrderArgs o{hranges, cams, n_views, views_per_group, (n_views - last_views) / views_per_group + 1, n_tiles};
   const size_t words = (size_t)o.n_groups * kOrderBins;
   uint32_t *hist = scratch, *cursor = scratch + words, *base = scratch + 2 * words;
   cudaError_t e = cudaMemsetAsync(scratch, 0, 2 * words * sizeof(uint32_t), st);

@@ -95,14 +95,15 @@ cudaError_t launch_half_lists(cudaStream_t st, const uint32_t* keys, const uint3
                               float alpha_min, int64_t n_tiles, uint8_t* flags, uint64_t* sums, uint2* hl,
                               uint2* hranges);
 // Queue order of the blend kernels' 2 n_tiles half-tile items (work index
-// 2 tile + half): groups of views_per_group consecutive views in view order
-// (the last group also takes the remaining views), within a group decreasing
-// half-list length in bins of half an octave.  scratch: item_order_words
-// words; order: 2 n_tiles words.
+// 2 tile + half): groups of views_per_group consecutive views in view order,
+// the last group taking the remaining views (at least last_views), within a
+// group decreasing half-list length in bins of half an octave.  scratch:
+// item_order_words words; order: 2 n_tiles words.
 constexpr int kOrderBins = 64;
 size_t item_order_words(int n_views);
 cudaError_t launch_item_order(cudaStream_t st, int num_sms, const uint2* hranges, const CamDev* cams, int n_views,
-                              int views_per_group, int64_t n_tiles, uint32_t* scratch, uint32_t* order);
+                              int views_per_group, int last_views, int64_t n_tiles, uint32_t* scratch,
+                              uint32_t* order);
 
 struct BlendArgs {
   const ProjRec* proj;  // [V][N]
