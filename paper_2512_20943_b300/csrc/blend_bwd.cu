@@ -108,7 +108,7 @@ __device__ __forceinline__ void replay_entry(const float4 ga, const float4 gb, f
     const float oG = __fmul_rn(gb.y, G);
     const float alpha = alpha_of(gb.y, G, alpha_max);
     // pair (pixel, entry) replayed iff pos1 <= n_contrib and the forward blended it
-    const bool valid = (pos1 <= nc[k]) && !(p2 > 0.f) && !(alpha < alpha_min);
+    const bool valid = (pos1 <= nc[k]) && !(alpha < alpha_min);
     const float ae = valid ? alpha : 0.f;
     const float w = blend_weight(ae, T[k]);
     const float gc = g0[k] * gb.z + g1[k] * gb.w + g2[k] * cb;

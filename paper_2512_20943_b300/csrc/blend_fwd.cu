@@ -3,8 +3,10 @@
 // (view, half tile) items of a batch.
 //
 // Per pixel p (sampled at (u + 0.5, v + 0.5)) and list entry i in order:
-// d = p - mean2d_i, power = -1/2 (A dx^2 + C dy^2) - B dx dy; skip if power > 0;
-// alpha = min(alpha_max, o_i e^power); skip if alpha < alpha_min; stop (i not
+// d = p - mean2d_i, power = -1/2 (A dx^2 + C dy^2) - B dx dy (at most 0: the
+// projection keeps only positive-definite conics, so the kernels have no
+// power > 0 test, and a rounding excess near power = 0 blends as the exact
+// value does); alpha = min(alpha_max, o_i e^power); skip if alpha < alpha_min; stop (i not
 // blended) if T (1 - alpha) < T_min; else C += c_i alpha T, T <- T (1 - alpha).
 // The kernel stores C + T bg, T_final and n_contrib (position + 1 of the last
 // blended entry), and with IMP adds alpha T and 1 per blended pair to the
@@ -106,7 +108,7 @@ __global__ void __launch_bounds__(32, MINB) k_blend_fwd(BlendArgs a, FwdOut out)
           const float alpha = alpha_of(gb.y, G, alpha_max);
           const float w = blend_weight(alpha, T[k]);
           const float Tn = transmit(T[k], w);
-          const bool valid = (stop_at[k] < 0) && !(p2 > 0.f) && !(alpha < alpha_min);
+          const bool valid = (stop_at[k] < 0) && !(alpha < alpha_min);
           const bool stop = valid && (Tn < T_min);
           const bool blend = valid && !stop;
           if (blend) {
