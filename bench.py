@@ -93,15 +93,12 @@ _BLEND_SOURCES = ("paper_2512_20943_b300/csrc/blend_fwd.cu", "paper_2512_20943_b
 PROFILE_STEPS = 10  # steps of the per-stage profiling pass after the timed region
 
 NCU_TRAFFIC = {
-    # DRAM bytes from a --metrics capture of the current sources; shared-memory
-    # wavefronts from the --set full capture (the queue order does not change
-    # them)
-    "blend_bwd": {"bytes_per_launch": (793.038080 + 114.746880) * 1e6, "smem_bytes_per_launch": 376904566 * 128,
+    "blend_bwd": {"bytes_per_launch": (756.987136 + 108.916736) * 1e6, "smem_bytes_per_launch": 377169671 * 128,
                   "sources": _BLEND_SOURCES,
-                  "sha256": "a035c9e36bccd82f80a702d1420715dfd7e636acf73e730902d357329fd80db2"},
-    "blend_fwd": {"bytes_per_launch": (246.146304 + 228.430848) * 1e6, "smem_bytes_per_launch": 81671664 * 128,
+                  "sha256": "7dc876294e29a25a1044714f9bce53c080111211741cc5ec79e5e65ab708378f"},
+    "blend_fwd": {"bytes_per_launch": (244.283904 + 228.473856) * 1e6, "smem_bytes_per_launch": 81673612 * 128,
                   "sources": _BLEND_SOURCES,
-                  "sha256": "a035c9e36bccd82f80a702d1420715dfd7e636acf73e730902d357329fd80db2"},
+                  "sha256": "7dc876294e29a25a1044714f9bce53c080111211741cc5ec79e5e65ab708378f"},
 }
 
 
@@ -109,10 +106,10 @@ NCU_TRAFFIC = {
 # commands are in profiles/per_frame_200k_sh3_20x1352x1014_ncu.md and
 # profiles/plain_2k_sh0_128x128_ncu.md); the large workload is not captured
 CONFIG_TRAFFIC = {
-    ("per_frame", "blend_bwd"): {"bytes_per_launch": (1593.686784 + 208.404480) * 1e6, "sources": _BLEND_SOURCES,
-                                 "sha256": "a035c9e36bccd82f80a702d1420715dfd7e636acf73e730902d357329fd80db2"},
-    ("plain", "blend_fwd"): {"bytes_per_launch": 154.880e3, "sources": _BLEND_SOURCES,
-                             "sha256": "a035c9e36bccd82f80a702d1420715dfd7e636acf73e730902d357329fd80db2"},
+    ("per_frame", "blend_bwd"): {"bytes_per_launch": (1534.216192 + 199.067392) * 1e6, "sources": _BLEND_SOURCES,
+                                 "sha256": "7dc876294e29a25a1044714f9bce53c080111211741cc5ec79e5e65ab708378f"},
+    ("plain", "blend_fwd"): {"bytes_per_launch": 155.136e3, "sources": _BLEND_SOURCES,
+                             "sha256": "7dc876294e29a25a1044714f9bce53c080111211741cc5ec79e5e65ab708378f"},
 }
 
 

@@ -97,7 +97,7 @@ cudaError_t launch_half_lists(cudaStream_t st, const uint32_t* keys, const uint3
 // Queue order of the blend kernels' 2 n_tiles half-tile items (work index
 // 2 tile + half): groups of views_per_group consecutive views in view order,
 // the last group taking the remaining views (at least last_views), within a
-// group decreasing half-list length in bins of half an octave.  scratch:
+// group decreasing half-list length in bins of a quarter octave.  scratch:
 // item_order_words words; order: 2 n_tiles words.
 constexpr int kOrderBins = 64;
 size_t item_order_words(int n_views);
