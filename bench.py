@@ -633,6 +633,8 @@ def run_ours(args):
         line["e2e"] = e2e
     if not args.no_serving and world == 1:
         line["serving"] = run_serving(args, device)
+    if not args.no_next_rows and world == 1:
+        line["next_rows"] = run_next_rows(args, device)
     if not args.no_configs and world == 1:
         # the other workload shapes, each measured like the streaming step (plain 2k forward,
         # per-frame 200k x 20 views, large 2M x 16 x 4K with the kernel shape autotuned)
@@ -880,6 +882,168 @@ def run_serving(args, device):
     }
 
 
+NEXT_REPS = 20  # timed calls per kernel of the next_rows block (each after an L2 flush)
+SSIM_FLOPS_PER_VALUE = 5 * 44 + 3 * 44 + 40 + 6  # the D-SSIM loss and gradient, separable form
+
+
+def _timed_calls(stream, fn, reps, flush):
+    """Mean device time (ms) of fn() on the library's stream: reps calls, each
+    after writing a buffer larger than L2 (the write is outside the events)."""
+    import torch
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            fn()
+    stream.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    with torch.cuda.stream(stream):
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            fn()
+            b.record(stream)
+    stream.synchronize()
+    return statistics.mean(a.elapsed_time(b) for a, b in ev)
+
+
+def run_next_rows(args, device):
+    """The widened rows on the streaming workload's data (300k Gaussians SH3,
+    frame 0's update applied, the 8 views of step 0 at 1352x1014): usage-
+    frequency pruning of the frame delta (Sec. III-C), the pruning-level space
+    and Algorithm 1's choice, the densification statistics of keyframe
+    reconstruction (Sec. III-B) and the D-SSIM term of L_3DGS (Eq. 1).  Device
+    times from CUDA events, each call after an L2 flush; HBM-bound kernels as
+    algorithmic bytes over that time against the measured copy bandwidth."""
+    import torch
+    from paper_2512_20943_b300 import AIRGS_DELTA_ANCHOR, RasterConfig, Rasterizer
+    from paper_2512_20943_b300.pruning import pruning_level_space, select_pruning_level
+    peaks, _ = measured_peaks()
+    hbm = peaks["hbm_gbs"]
+    n = N_GAUSS
+    g, arc = synthetic.streaming_scene(n, 0)
+    cams = arc[:VIEWS_PER_STEP]
+    stream = torch.cuda.Stream()
+    rast = Rasterizer(RasterConfig(), stream=stream)
+    t = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in g.items() if k != "sh_degree"}
+    p = (t["means"], t["log_scales"], t["quats"], t["opacity_logit"], t["sh"])
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    n_px = VIEWS_PER_STEP * WIDTH * HEIGHT
+    target = torch.from_numpy(np.concatenate([x.reshape(-1) for x in synthetic.target_images(cams, 1)])).to(device)
+    out = {"workload": f"{n // 1000}k Gaussians SH3, {VIEWS_PER_STEP} views {WIDTH}x{HEIGHT} (the streaming step's)",
+           "timing": f"CUDA events around each call on the library's stream, mean of {NEXT_REPS}, a 256 MB write "
+                     "before each (inputs out of L2)", "hbm_peak_gbs": hbm}
+
+    def rate(bytes_, ms):
+        gbs = bytes_ / (ms * 1e-3) / 1e9
+        return {"ms": ms, "bytes": bytes_, "gbs": gbs, "frac_hbm": gbs / hbm}
+
+    with torch.cuda.stream(stream):
+        rast.set_anchor(*p)
+        w, _ = rast.gaussian_importance(cams)
+    stream.synchronize()
+    rng = np.random.default_rng(7)
+    D = torch.from_numpy(rng.normal(0, 0.01, (7, n)).astype(np.float32)).to(device)
+    D_sent = torch.zeros(7, n, dtype=torch.float32, device=device)
+
+    # f1: usage-frequency pruning p(D_t - D'_{t-1}) of 30 % of the Gaussians
+    n_prune = int(0.3 * n)
+    keep = rast.prune_mask(w, n_prune)
+    ms_mask = _timed_calls(stream, lambda: rast.prune_mask(w, n_prune), NEXT_REPS, flush)
+    ms_delta = _timed_calls(stream, lambda: rast.prune_delta(D, D_sent.clone(), keep), NEXT_REPS, flush)
+    ms_clone = _timed_calls(stream, lambda: D_sent.clone(), NEXT_REPS, flush)
+    d, _ = rast.prune_delta(D, D_sent.clone(), keep)
+    ms_apply = _timed_calls(stream, lambda: rast.apply_frame_delta(d, mode=AIRGS_DELTA_ANCHOR, quat_add=True),
+                            NEXT_REPS, flush)
+    out["pruning"] = {
+        "fraction": 0.3,
+        # mask: the weights read, the mask written (the sort inside is the implementation's)
+        "prune_mask": rate(n * (4 + 1), ms_mask),
+        # delta: D_t, the transmitted record and the mask read; the delta and the record written
+        "prune_delta": rate(n * (28 + 28 + 1 + 28 + 28), max(ms_delta - ms_clone, 1e-6)),
+        # apply: the delta and the anchor's means and quaternions read, the frame's written
+        "apply_frame_delta": rate(n * (28 + 28 + 28), ms_apply),
+    }
+
+    # f3: densification statistics (sum over views of |dL/d mean2d| and the view count) in the
+    # projection adjoint, and the selection
+    dg = torch.zeros(n, dtype=torch.float32, device=device)
+    dv = torch.zeros(n, dtype=torch.int32, device=device)
+
+    def bwd(dens):
+        res = rast.render_gaussians(*p, cams, save=True)
+        rast.render_backward_ex(res.state, target=target, densify=(dg, dv) if dens else None)
+        res.state.release()
+
+    ms_with = _timed_calls(stream, lambda: bwd(True), NEXT_REPS, flush)
+    ms_without = _timed_calls(stream, lambda: bwd(False), NEXT_REPS, flush)
+    ms_sel = _timed_calls(stream, lambda: rast.densify_select(dg, dv, 1e-4), NEXT_REPS, flush)
+    out["densification"] = {
+        "render_and_backward_ms_with_statistics": ms_with,
+        "render_and_backward_ms_without": ms_without,
+        "densify_select": rate(n * (4 + 4 + 1), ms_sel),
+    }
+
+    # f2: the pruning-level space S_t^d (11 levels: mask, delta, apply, render of the 8 views and
+    # its squared error against the unpruned render, per level) and Algorithm 1's choice at a
+    # budget of half the unpruned delta per frame (host wall time: the level loop reads each
+    # level's error and size back)
+    with torch.cuda.stream(stream):
+        pruning_level_space(rast, D, D_sent, w, cams)  # warm
+    stream.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        space = pruning_level_space(rast, D, D_sent, w, cams)
+    stream.synchronize()
+    ms_space = (time.perf_counter() - t0) * 1e3
+    levels = [(min(lv.quality, 200.0), lv.size) for lv in space]
+    t0 = time.perf_counter()
+    chosen = select_pruning_level(levels, 2.0, 0.5 * space[0].size, 1.0)
+    ms_select = (time.perf_counter() - t0) * 1e3
+    out["level_selection"] = {
+        "levels": len(space), "space_ms_wall": ms_space, "select_ms_host": ms_select, "chosen": chosen,
+        "budget": "B/R = half the unpruned delta's bytes", "psnr_db": [round(q, 2) for q, _ in levels],
+        "bytes": [sz for _, sz in levels],
+    }
+
+    # f4: L_3DGS = 0.8 L1 + 0.2 (1 - SSIM) and its image gradient over the 8 rendered views, and a
+    # training step with it (render, loss, explicit-gradient backward) beside the fused-L1 step
+    res = rast.render_gaussians(*p, cams)
+    rgb = res.rgb
+    ms_loss = _timed_calls(stream, lambda: rast.l3dgs_loss(cams, rgb, target, 0.2), NEXT_REPS, flush)
+    imp = (torch.zeros(n, dtype=torch.float32, device=device), torch.zeros(n, dtype=torch.int32, device=device))
+
+    def step_l3dgs():
+        r = rast.render_gaussians(*p, cams, save=True)
+        _, grad = rast.l3dgs_loss(cams, r.rgb, target, 0.2)
+        rast.render_backward(r.state, grad, importance=imp)
+        r.state.release()
+
+    def step_l1():
+        r = rast.render_gaussians(*p, cams, save=True)
+        rast.render_backward_l1(r.state, target, importance=imp)
+        r.state.release()
+
+    ms_step_ssim = _timed_calls(stream, step_l3dgs, NEXT_REPS, flush)
+    ms_step_l1 = _timed_calls(stream, step_l1, NEXT_REPS, flush)
+    # issue-bound: per value (pixel and channel) the separable 11-tap correlations of the five
+    # moments and of the three partials, each a horizontal and a vertical pass (11 FMAs each),
+    # the SSIM map and its partials, and the combination: 5 x 44 + 3 x 44 + 40 + 6 flops
+    n_sms = torch.cuda.get_device_properties(device).multi_processor_count
+    fp32_peak = n_sms * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
+    flops = n_px * 3 * SSIM_FLOPS_PER_VALUE
+    loss_rate = {"ms": ms_loss, "mpix_per_s": n_px / (ms_loss * 1e-3) / 1e6, "bound": "alu",
+                 "tflops_algorithmic": flops / (ms_loss * 1e-3) / 1e12,
+                 "frac_fp32": flops / (ms_loss * 1e-3) / 1e12 / fp32_peak, "fp32_peak_tflops": fp32_peak,
+                 "hbm_bytes": n_px * 3 * (4 + 4 + 4)}  # image and target read, gradient written
+    out["d_ssim"] = {
+        "lambda": 0.2, "loss_and_gradient": loss_rate,
+        "training_step_ms_l3dgs": ms_step_ssim, "training_step_ms_fused_l1": ms_step_l1,
+        "training_mpix_per_s_l3dgs": n_px / (ms_step_ssim * 1e-3) / 1e6,
+    }
+    del rast, flush
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_e2e(rast, wl, args, device, stream, imp, world):
     """Same step through the public API with host inputs: every step the frame's
     update map and its 8 target images are copied from pinned host memory, and
@@ -940,6 +1104,8 @@ def main(argv=None):
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the served request stream")
     ap.add_argument("--no-configs", action="store_true", help="skip the other workload shapes in the default line")
+    ap.add_argument("--no-next-rows", action="store_true",
+                    help="skip the pruning / level-selection / densification / D-SSIM timings")
     ap.add_argument("--autotune", action="store_true", help="search the kernel shapes first and keep the fastest")
     ap.add_argument("--shape", type=int, default=-1, help="kernel shape (-1: autotuned choice or shape 0)")
     ap.add_argument("--sort-mode", type=int, default=-1,

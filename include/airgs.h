@@ -266,7 +266,9 @@ int airgs_image_sse(airgs_ctx* ctx, const airgs_camera* cams, int n_views, const
  *   rgb, target   device float laid out like rgb_out
  *   loss_out      device double[3] (nullable): L, L1, SSIM
  *   dL_drgb_out   device float laid out like rgb_out (overwritten)
- * Synchronises on the stream (its host-side plane table must outlive the copy). */
+ * Returns once the work is queued on the context's stream (the per-plane table
+ * is staged from host memory before the call returns); the outputs are valid
+ * in stream order, like those of airgs_render. */
 int airgs_l3dgs_loss(airgs_ctx* ctx, const airgs_camera* cams, int n_views, const float* rgb, const float* target,
                      float lambda, double* loss_out, float* dL_drgb_out);
 

@@ -1244,7 +1244,7 @@ int airgs_l3dgs_loss(airgs_ctx* ctx, const airgs_camera* cams, int n_views, cons
   if (!rgb || !target || !dL_drgb_out) return fail(ctx, AIRGS_E_ARG, "null image pointer");
   if (!(lambda >= 0.f && lambda <= 1.f)) return fail(ctx, AIRGS_E_ARG, "lambda must be in [0, 1]");
   const int n_planes = 3 * n_views;
-  std::vector<int64_t> off(n_planes + 1, 0);
+  std::vector<int64_t> off(n_planes + 1, 0), tile_base(n_planes + 1, 0);
   std::vector<int> w(n_planes), h(n_planes);
   for (int v = 0; v < n_views; ++v)
     for (int c = 0; c < 3; ++c) {
@@ -1252,27 +1252,30 @@ int airgs_l3dgs_loss(airgs_ctx* ctx, const airgs_camera* cams, int n_views, cons
       w[p] = tmp[v].W;
       h[p] = tmp[v].H;
       off[p + 1] = off[p] + (int64_t)tmp[v].W * tmp[v].H;
+      tile_base[p + 1] = tile_base[p] + ssim_tiles(tmp[v].W, tmp[v].H);
     }
   const int64_t total = off[n_planes];
-  int64_t* d_off;
+  int64_t *d_off, *d_tb;
   int *d_w, *d_h;
-  float* scratch;
   double* sums;
-  if ((rc = dalloc(ctx, &d_off, n_planes + 1)) || (rc = dalloc(ctx, &d_w, n_planes)) ||
-      (rc = dalloc(ctx, &d_h, n_planes)) || (rc = dalloc(ctx, &scratch, 8 * total)) || (rc = dalloc(ctx, &sums, 5)))
+  if ((rc = dalloc(ctx, &d_off, n_planes + 1)) || (rc = dalloc(ctx, &d_tb, n_planes + 1)) ||
+      (rc = dalloc(ctx, &d_w, n_planes)) || (rc = dalloc(ctx, &d_h, n_planes)) || (rc = dalloc(ctx, &sums, 5)))
     return rc;
   cudaStream_t st = ctx->stream;
+  // pageable sources: each copy returns once its bytes are staged, so the host arrays may go after the calls
   cudaError_t e = cudaMemcpyAsync(d_off, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_tb, tile_base.data(), tile_base.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_w, w.data(), w.size() * sizeof(int), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_h, h.data(), h.size() * sizeof(int), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(sums, 0, 5 * sizeof(double), st);
   if (e == cudaSuccess)
-    e = launch_ssim_loss(st, d_off, d_w, d_h, n_planes, total, rgb, target, lambda, scratch, sums, dL_drgb_out);
+    e = launch_ssim_loss(st, d_off, d_w, d_h, d_tb, n_planes, total, tile_base[n_planes], rgb, target, lambda, sums,
+                         dL_drgb_out);
   if (e == cudaSuccess && loss_out)
     e = cudaMemcpyAsync(loss_out, sums + 2, 3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
-  // host arrays were copied (stream-ordered); device temporaries return to the pool
-  CK(cudaStreamSynchronize(st));
-  for (void* p : {(void*)d_off, (void*)d_w, (void*)d_h, (void*)scratch, (void*)sums}) dfree(ctx, p);
+  // device temporaries return to the pool in stream order
+  for (void* p : {(void*)d_off, (void*)d_tb, (void*)d_w, (void*)d_h, (void*)sums}) dfree(ctx, p);
   if (e != cudaSuccess) return fail(ctx, AIRGS_E_CUDA, "l3dgs_loss: %s", cudaGetErrorString(e));
   return AIRGS_OK;
 }

@@ -82,11 +82,14 @@ cudaError_t launch_densify_select(cudaStream_t st, int64_t n, const float* g, co
 cudaError_t launch_sq_err(cudaStream_t st, const float* a, const float* b, const int64_t* view_off, int n_views,
                           double* out);
 
-// L_3DGS = (1 - lambda) L1 + lambda (1 - SSIM) and its image gradient (ssim.cu).
-// scratch: 8 x total floats; sums: 5 doubles (zeroed; [2..4] receive L, L1, SSIM).
-cudaError_t launch_ssim_loss(cudaStream_t st, const int64_t* d_off, const int* d_w, const int* d_h, int n_planes,
-                             int64_t total, const float* x, const float* y, float lambda, float* scratch,
-                             double* sums, float* grad);
+// L_3DGS = (1 - lambda) L1 + lambda (1 - SSIM) and its image gradient (ssim.cu):
+// one CTA per 32x32 output tile of each (view, channel) plane; d_tile_base
+// [n_planes + 1] the planes' first tiles (ssim_tiles per plane), n_tiles their
+// total.  sums: 5 doubles (zeroed; [2..4] receive L, L1, SSIM).
+int64_t ssim_tiles(int w, int h);
+cudaError_t launch_ssim_loss(cudaStream_t st, const int64_t* d_off, const int* d_w, const int* d_h,
+                             const int64_t* d_tile_base, int n_planes, int64_t total, int64_t n_tiles, const float* x,
+                             const float* y, float lambda, double* sums, float* grad);
 
 // Half-tile blend lists (cull_lists.cu).
 size_t half_list_chunks(int64_t n_inst);
