@@ -95,10 +95,10 @@ PROFILE_STEPS = 10  # steps of the per-stage profiling pass after the timed regi
 NCU_TRAFFIC = {
     "blend_bwd": {"bytes_per_launch": (756.987136 + 108.916736) * 1e6, "smem_bytes_per_launch": 377169671 * 128,
                   "sources": _BLEND_SOURCES,
-                  "sha256": "7dc876294e29a25a1044714f9bce53c080111211741cc5ec79e5e65ab708378f"},
+                  "sha256": "fa334ab1a39d09c2bd6d8ebe7f979951cfdefe450482412bb954ede7f9b03588"},
     "blend_fwd": {"bytes_per_launch": (244.283904 + 228.473856) * 1e6, "smem_bytes_per_launch": 81673612 * 128,
                   "sources": _BLEND_SOURCES,
-                  "sha256": "7dc876294e29a25a1044714f9bce53c080111211741cc5ec79e5e65ab708378f"},
+                  "sha256": "fa334ab1a39d09c2bd6d8ebe7f979951cfdefe450482412bb954ede7f9b03588"},
 }
 
 
@@ -107,9 +107,9 @@ NCU_TRAFFIC = {
 # profiles/plain_2k_sh0_128x128_ncu.md); the large workload is not captured
 CONFIG_TRAFFIC = {
     ("per_frame", "blend_bwd"): {"bytes_per_launch": (1534.216192 + 199.067392) * 1e6, "sources": _BLEND_SOURCES,
-                                 "sha256": "7dc876294e29a25a1044714f9bce53c080111211741cc5ec79e5e65ab708378f"},
+                                 "sha256": "fa334ab1a39d09c2bd6d8ebe7f979951cfdefe450482412bb954ede7f9b03588"},
     ("plain", "blend_fwd"): {"bytes_per_launch": 155.136e3, "sources": _BLEND_SOURCES,
-                             "sha256": "7dc876294e29a25a1044714f9bce53c080111211741cc5ec79e5e65ab708378f"},
+                             "sha256": "fa334ab1a39d09c2bd6d8ebe7f979951cfdefe450482412bb954ede7f9b03588"},
 }
 
 
