@@ -100,15 +100,20 @@ def pruning_level_space(rast, D_t: torch.Tensor, D_sent: torch.Tensor, importanc
     rast.apply_frame_delta(D_t, mode=AIRGS_DELTA_ANCHOR, quat_add=quat_add)
     ref = rast.render(cams).rgb
     total_px = sum(3 * int(c["width"]) * int(c["height"]) for c in cams)
-    out = []
+    # every level is queued before any result is read back: one host wait for the space
+    pending = []
     for f in fractions:
         n_prune = int(round(f * n))
         keep = rast.prune_mask(importance, n_prune)
-        record = D_sent.clone()
+        with torch.cuda.stream(rast.stream):  # freed in the library's stream order, read back or not
+            record = D_sent.clone()
         _, nonzero = rast.prune_delta(D_t, record, keep)
         rast.apply_frame_delta(record, mode=AIRGS_DELTA_ANCHOR, quat_add=quat_add)
         img = rast.render(cams).rgb
-        sse = float(np.sum(rast.image_sse(cams, img, ref).cpu().numpy()))
+        pending.append((f, rast.image_sse(cams, img, ref), nonzero))
+    out = []
+    for f, sse_v, nonzero in pending:
+        sse = float(np.sum(sse_v.cpu().numpy()))
         sent = int(nonzero.cpu()[0])  # Gaussians with a non-zero transmitted delta
         out.append(Level(fraction=f, quality=psnr(sse, total_px), size=sent * BYTES_PER_GAUSSIAN))
     return out
