@@ -81,16 +81,36 @@ __global__ void k_apply_delta(int64_t n, const float* __restrict__ delta, int qu
 }
 
 // One block row of views: grid.y = view, partial sums in double.
+// Sum of squared differences in double-single arithmetic: each thread keeps a
+// (hi, lo) float pair, fed by error-free transformations (Knuth's TwoSum for
+// a - b and for the running sum, the FMA residual for the square), and the
+// threads' pairs are reduced in double.  The work stays on the FP32 pipe (the
+// FP64 pipe of this part is a small fraction of it) with a relative error far
+// below single precision.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
 __global__ void __launch_bounds__(256) k_sq_err(const float* __restrict__ a, const float* __restrict__ b,
                                                 const int64_t* __restrict__ view_off, double* __restrict__ out) {
   __shared__ double s[8];
   const int v = blockIdx.y;
   const int64_t o0 = view_off[v], o1 = view_off[v + 1];
-  double acc = 0.0;
+  float hi = 0.f, lo = 0.f;
   for (int64_t k = o0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < o1; k += (int64_t)gridDim.x * blockDim.x) {
-    const double d = (double)a[k] - (double)b[k];
-    acc += d * d;
+    float dh, dl;
+    two_sum(__ldg(a + k), -__ldg(b + k), dh, dl);  // a - b = dh + dl exactly
+    const float p = __fmul_rn(dh, dh);
+    const float pe = __fmaf_rn(dh, dh, -p);        // dh^2 = p + pe exactly
+    const float small = __fmaf_rn(2.f * dh, dl, __fmaf_rn(dl, dl, pe));
+    float sh, se;
+    two_sum(hi, p, sh, se);
+    hi = sh;
+    lo = __fadd_rn(lo, __fadd_rn(se, small));
   }
+  double acc = (double)hi + (double)lo;
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
   __syncthreads();
@@ -151,7 +171,7 @@ cudaError_t launch_apply_delta(cudaStream_t st, int64_t n, const float* delta, i
 cudaError_t launch_sq_err(cudaStream_t st, const float* a, const float* b, const int64_t* view_off, int n_views,
                           double* out) {
   if (n_views == 0) return cudaSuccess;
-  dim3 grid(64, (unsigned)n_views);
+  dim3 grid(256, (unsigned)n_views);  // one view alone still fills the SMs
   k_sq_err<<<grid, 256, 0, st>>>(a, b, view_off, out);
   count_launches(1);
   return cudaGetLastError();
