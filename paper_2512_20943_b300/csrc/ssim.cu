@@ -21,9 +21,12 @@
 // (52 rows x 42 columns), vertical moments, SSIM and partials on the 42x42
 // region the second correlation needs, horizontal partials (42 x 32), then the
 // vertical partials and the combination on the tile.  Each thread walks a strip
-// of 7 or 8 outputs along the pass direction, so that a loaded value serves the
-// strip's outputs from registers.  Global memory sees x and y once (plus the
-// halo, from L2) and the gradient written once.
+// of 4 to 8 outputs along the pass direction, so that a loaded value serves the
+// strip's outputs from registers.  Moments and partials are FP32x2 pairs
+// ((mu_x, mu_y), (m_xx, m_yy), (P1, P2)), so that a tap is two packed FMAs and
+// one scalar, and one reciprocal of C D per point gives 1/C and 1/D.  Global
+// memory sees x and y once (plus the halo, from L2) and the gradient written
+// once.
 #include "airgs_internal.cuh"
 #include "kernels.h"
 
