@@ -1067,12 +1067,14 @@ int airgs_sort_pairs(airgs_ctx* ctx, const uint32_t* keys_in, const uint32_t* va
     return fail(ctx, AIRGS_E_ARG, "bad sort arguments");
   if (n == 0) return AIRGS_OK;
   cudaStream_t st = ctx->stream;
-  uint32_t *ka, *va, *kb, *vb, *scr;
+  uint32_t *ka = nullptr, *va = nullptr, *kb = nullptr, *vb = nullptr, *scr = nullptr;
   int rc;
   if ((rc = dalloc(ctx, &ka, n)) || (rc = dalloc(ctx, &va, n)) || (rc = dalloc(ctx, &kb, n)) ||
       (rc = dalloc(ctx, &vb, n)) ||
-      (rc = dalloc(ctx, &scr, radix_scratch_bytes(n, 1, ctx->num_sms) / sizeof(uint32_t) + 1)))
+      (rc = dalloc(ctx, &scr, radix_scratch_bytes(n, 1, ctx->num_sms) / sizeof(uint32_t) + 1))) {
+    for (void* p : {(void*)ka, (void*)va, (void*)kb, (void*)vb}) dfree(ctx, p);
     return rc;
+  }
   bool in_b = false;
   cudaError_t e = cudaMemcpyAsync(ka, keys_in, 4 * n, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(va, vals_in, 4 * n, cudaMemcpyDeviceToDevice, st);
@@ -1106,12 +1108,12 @@ int airgs_autotune(airgs_ctx* ctx, const airgs_camera* cams, int n_views, int* s
       for (void* q : p) dfree(c, q);
     }
   } fr{ctx, {}};
-  if ((rc = dalloc(ctx, &rgb, 3 * np)) || (rc = dalloc(ctx, &target, 3 * np)) || (rc = dalloc(ctx, &gm, 3 * n)) ||
-      (rc = dalloc(ctx, &gl, 3 * n)) || (rc = dalloc(ctx, &gq, 4 * n)) || (rc = dalloc(ctx, &go, n)) ||
-      (rc = dalloc(ctx, &gs, (size_t)K * 3 * n)) || (rc = dalloc(ctx, &impw, n)) || (rc = dalloc(ctx, &impc, n)) ||
-      (rc = dalloc(ctx, &loss, 1)))
-    return rc;
-  fr.p = {rgb, target, gm, gl, gq, go, gs, impw, impc, loss};
+  const bool oom = (rc = dalloc(ctx, &rgb, 3 * np)) || (rc = dalloc(ctx, &target, 3 * np)) ||
+                  (rc = dalloc(ctx, &gm, 3 * n)) || (rc = dalloc(ctx, &gl, 3 * n)) || (rc = dalloc(ctx, &gq, 4 * n)) ||
+                  (rc = dalloc(ctx, &go, n)) || (rc = dalloc(ctx, &gs, (size_t)K * 3 * n)) ||
+                  (rc = dalloc(ctx, &impw, n)) || (rc = dalloc(ctx, &impc, n)) || (rc = dalloc(ctx, &loss, 1));
+  fr.p = {rgb, target, gm, gl, gq, go, gs, impw, impc, loss};  // the ones allocated return to the pool on any exit
+  if (oom) return rc;
   CK(cudaMemsetAsync(target, 0x3F, 12 * np, ctx->stream));  // every channel 0x3F3F3F3F = 0.747
   CK(cudaMemsetAsync(impw, 0, 4 * n, ctx->stream));
   CK(cudaMemsetAsync(impc, 0, 4 * n, ctx->stream));
@@ -1177,12 +1179,14 @@ int airgs_prune_mask(airgs_ctx* ctx, const float* importance, int64_t n, int64_t
   if (n < 0 || n >= (1ll << 32) || n_prune < 0 || n_prune > n || (n > 0 && (!importance || !keep_out)))
     return fail(ctx, AIRGS_E_ARG, "bad prune_mask arguments");
   if (n == 0) return AIRGS_OK;
-  uint32_t *ka, *va, *kb, *vb, *scr;
+  uint32_t *ka = nullptr, *va = nullptr, *kb = nullptr, *vb = nullptr, *scr = nullptr;
   int rc;
   if ((rc = dalloc(ctx, &ka, n)) || (rc = dalloc(ctx, &va, n)) || (rc = dalloc(ctx, &kb, n)) ||
       (rc = dalloc(ctx, &vb, n)) ||
-      (rc = dalloc(ctx, &scr, radix_scratch_bytes(n, 1, ctx->num_sms) / sizeof(uint32_t) + 1)))
+      (rc = dalloc(ctx, &scr, radix_scratch_bytes(n, 1, ctx->num_sms) / sizeof(uint32_t) + 1))) {
+    for (void* p : {(void*)ka, (void*)va, (void*)kb, (void*)vb}) dfree(ctx, p);
     return rc;
+  }
   cudaError_t e = launch_prune_mask(ctx->stream, ctx->num_sms, n, n_prune, importance, ka, va, kb, vb, scr, keep_out);
   for (void* p : {(void*)ka, (void*)va, (void*)kb, (void*)vb, (void*)scr}) dfree(ctx, p);
   if (e != cudaSuccess) return fail(ctx, AIRGS_E_CUDA, "prune_mask: %s", cudaGetErrorString(e));
@@ -1255,12 +1259,14 @@ int airgs_l3dgs_loss(airgs_ctx* ctx, const airgs_camera* cams, int n_views, cons
       tile_base[p + 1] = tile_base[p] + ssim_tiles(tmp[v].W, tmp[v].H);
     }
   const int64_t total = off[n_planes];
-  int64_t *d_off, *d_tb;
-  int *d_w, *d_h;
-  double* sums;
+  int64_t *d_off = nullptr, *d_tb = nullptr;
+  int *d_w = nullptr, *d_h = nullptr;
+  double* sums = nullptr;
   if ((rc = dalloc(ctx, &d_off, n_planes + 1)) || (rc = dalloc(ctx, &d_tb, n_planes + 1)) ||
-      (rc = dalloc(ctx, &d_w, n_planes)) || (rc = dalloc(ctx, &d_h, n_planes)) || (rc = dalloc(ctx, &sums, 5)))
+      (rc = dalloc(ctx, &d_w, n_planes)) || (rc = dalloc(ctx, &d_h, n_planes)) || (rc = dalloc(ctx, &sums, 5))) {
+    for (void* p : {(void*)d_off, (void*)d_tb, (void*)d_w, (void*)d_h, (void*)sums}) dfree(ctx, p);
     return rc;
+  }
   cudaStream_t st = ctx->stream;
   // pageable sources: each copy returns once its bytes are staged, so the host arrays may go after the calls
   cudaError_t e = cudaMemcpyAsync(d_off, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st);
