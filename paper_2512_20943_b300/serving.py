@@ -17,12 +17,17 @@ whole budget is rejected (status, not an abort).  Latency = GPU completion
 time of the request's batch - arrival time, both on the engine's clock.
 
 The plain loop renders the same request stream one view per call on one
-stream, in arrival order.
+stream, in arrival order.  Both hold Python's cyclic garbage collector off
+while they serve (collections_paused), as a latency-bound server does: a full
+collection over a heap of tensors and requests stalls the launching thread
+for tens of milliseconds, which shows up as a p99 outlier.
 
 Only host logic lives here; every rendering step runs in libairgs.
 """
 from __future__ import annotations
 
+import contextlib
+import gc
 import time
 from collections import deque
 from dataclasses import dataclass, field
@@ -204,12 +209,16 @@ class ServingEngine:
         once and each one's arrival is the moment the engine sees it."""
         reqs = sorted(requests, key=lambda r: r.arrival_s)
         pending = deque(reqs)
+        torch.cuda.synchronize()
+        with collections_paused():
+            return self._serve(reqs, pending, keep_images, realtime)
+
+    def _serve(self, reqs, pending, keep_images, realtime) -> ServeStats:
         queue = deque()
         inflight = []  # (event, bytes, requests)
         used = peak = 0
         batches = 0
         rr = 0
-        torch.cuda.synchronize()
         start = torch.cuda.Event(enable_timing=True)
         start.record()
         start.synchronize()
@@ -264,6 +273,17 @@ def run_plain_loop(anchor: dict, frames: FrameStream, requests, config: RasterCo
     ctx = Rasterizer(config, stream=stream)
     reqs = sorted(requests, key=lambda r: r.arrival_s)
     torch.cuda.synchronize()
+    with collections_paused():
+        start, events = _plain_serve(reqs, pub, stream, ctx, frames, keep_images, realtime)
+    torch.cuda.synchronize()
+    for ev, r in events:
+        r.status, r.done_s = "done", start.elapsed_time(ev) / 1e3
+    t_first = reqs[0].arrival_s if reqs else 0.0
+    return summarize(reqs, len(reqs), 0, t_first)
+
+
+def _plain_serve(reqs, pub, stream, ctx, frames, keep_images, realtime):
+    """The plain loop's launches: the start event and [(completion event, request)]."""
     start = torch.cuda.Event(enable_timing=True)
     start.record()
     start.synchronize()
@@ -286,11 +306,20 @@ def run_plain_loop(anchor: dict, frames: FrameStream, requests, config: RasterCo
         r.rgb = res.views()[0] if keep_images else None
         r.status, r.batch = "running", i
         events.append((ev, r))
-    torch.cuda.synchronize()
-    for ev, r in events:
-        r.status, r.done_s = "done", start.elapsed_time(ev) / 1e3
-    t_first = reqs[0].arrival_s if reqs else 0.0
-    return summarize(reqs, len(reqs), 0, t_first)
+    return start, events
+
+
+@contextlib.contextmanager
+def collections_paused():
+    """Automatic cyclic garbage collection off inside the block (objects are
+    still freed by reference counting); the collector's previous state after."""
+    was_enabled = gc.isenabled()
+    gc.disable()
+    try:
+        yield
+    finally:
+        if was_enabled:
+            gc.enable()
 
 
 def make_requests(stream_of_tuples):

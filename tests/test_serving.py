@@ -40,6 +40,27 @@ def test_summary_percentiles():
     assert abs(s.views_per_s - 1000.0) < 1e-6 and s.mean_batch == 10
 
 
+def test_collections_paused_restores_the_collector():
+    import gc
+    from paper_2512_20943_b300.serving import collections_paused
+    was = gc.isenabled()
+    try:
+        gc.enable()
+        with collections_paused():
+            assert not gc.isenabled()
+        assert gc.isenabled()
+        with pytest.raises(RuntimeError):  # restored on an exception too
+            with collections_paused():
+                raise RuntimeError("stop")
+        assert gc.isenabled()
+        gc.disable()  # a caller that had it off keeps it off
+        with collections_paused():
+            assert not gc.isenabled()
+        assert not gc.isenabled()
+    finally:
+        (gc.enable if was else gc.disable)()
+
+
 def _scene(n=20000):
     import torch
     g = synthetic.gaussians(n, 3, mean_scale=(0.7, 0.7, 0.7), log_scale=(-4.0, 0.6))
