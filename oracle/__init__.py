@@ -5,7 +5,8 @@ decode/apply of streamed updates (Sec. II Eq. 3, Sec. III-B Eq. 5, Sec. III-C),
 EWA projection and SH colour of the Gaussian primitive of Sec. II, 16x16 tile
 binning with a stable (tile, depth) order, front-to-back blending, the
 per-Gaussian blend weight behind usage-frequency pruning (Sec. III-C), the L1
-part of Eq. 1, and the analytic adjoint.  The arithmetic lives in
+part of Eq. 1, the analytic adjoint, and the clone / split / discard step of
+keyframe reconstruction (Sec. III-B).  The arithmetic lives in
 ``airgs_oracle.cpp``; this module only marshals numpy arrays.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
@@ -275,6 +276,73 @@ def apply_delta(base_means, base_quats, delta, quat_add=False):
                   w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2,
                   w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2], axis=1)
     return means, q / np.linalg.norm(q, axis=1, keepdims=True)
+
+
+def densify_classes(log_scales, opacity_logit, select, size_threshold, min_opacity=0.0):
+    """Per-Gaussian decisions of the densification step (see densify_apply):
+    (keep, clone, split) boolean arrays.  Both comparisons are taken in float32,
+    on the log scale and on the logit (monotone in the scale and the opacity),
+    against thresholds rounded once to float32 from float64:
+      large  <=>  max_k log_scale_k > float32(log size_threshold)
+      alive  <=>  logit >= float32(log(m / (1 - m))), m = min_opacity (always for m = 0)."""
+    ls = np.asarray(log_scales, np.float32).reshape(-1, 3)
+    lo = np.asarray(opacity_logit, np.float32).reshape(-1)
+    sel = np.asarray(select).reshape(-1) != 0
+    ls_thr = np.float32(np.log(np.float64(size_threshold)))
+    large = ls.max(axis=1) > ls_thr
+    if min_opacity > 0.0:
+        lo_thr = np.float32(np.log(np.float64(min_opacity) / (1.0 - np.float64(min_opacity))))
+        alive = lo >= lo_thr
+    else:
+        alive = np.ones(lo.shape[0], bool)
+    return alive & ~(sel & large), alive & sel & ~large, alive & sel & large
+
+
+def quat_to_rotation(q):
+    """Rotation matrices [n, 3, 3] of quaternions (w, x, y, z) [n, 4], normalised first."""
+    q = np.asarray(q, np.float64).reshape(-1, 4)
+    q = q / np.linalg.norm(q, axis=1, keepdims=True)
+    w, x, y, z = q[:, 0], q[:, 1], q[:, 2], q[:, 3]
+    return np.stack([
+        np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], axis=1),
+        np.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], axis=1),
+        np.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], axis=1)], axis=1)
+
+
+def densify_apply(g: dict, select, z, size_threshold, split_factor=1.6, min_opacity=0.0):
+    """The clone / split / discard step of keyframe reconstruction (Sec. III-B:
+    Gaussians in high-gradient regions are cloned or split, low-opacity ones are
+    discarded), with the clone and split rules of the adaptive density control
+    of 3D Gaussian Splatting, whose training the paper's keyframe step builds on:
+      selected and small (largest scale at most size_threshold): kept, and an
+        identical copy added;
+      selected and large: replaced by two children that sample the Gaussian as
+        a density: mean_j = mean + R(q/|q|) diag(exp(log_scale)) z[i, j],
+        log_scale_j = log_scale - log(split_factor) (the scale divided by
+        split_factor), quaternion, opacity logit and SH copied;
+      opacity below min_opacity: discarded, with its copy or children.
+    z [n, 2, 3] are the caller's standard normal samples.  Decisions as in
+    densify_classes.  Output (float64): the surviving originals in index order,
+    then the copies in index order, then the children (child 0, child 1 of
+    each split Gaussian) in index order; parent[j] = input index of output j."""
+    means = np.asarray(g["means"], np.float64).reshape(-1, 3)
+    n = means.shape[0]
+    log_s = np.asarray(g["log_scales"], np.float64).reshape(n, 3)
+    quats = np.asarray(g["quats"], np.float64).reshape(n, 4)
+    op = np.asarray(g["opacity_logit"], np.float64).reshape(n)
+    sh = np.asarray(g["sh"], np.float64).reshape(n, -1)
+    keep, clone, split = densify_classes(g["log_scales"], g["opacity_logit"], select, size_threshold, min_opacity)
+    ik, ic, isp = np.nonzero(keep)[0], np.nonzero(clone)[0], np.nonzero(split)[0]
+    zz = np.asarray(z, np.float64).reshape(n, 2, 3)[isp]                    # [m, 2, 3]
+    R = quat_to_rotation(quats[isp])                                          # [m, 3, 3]
+    offs = np.einsum("mab,mjb->mja", R, np.exp(log_s[isp])[:, None, :] * zz)  # R (s * z_j)
+    child_means = (means[isp][:, None, :] + offs).reshape(-1, 3)
+    parent = np.concatenate([ik, ic, np.repeat(isp, 2)])
+    out = dict(means=np.concatenate([means[ik], means[ic], child_means]),
+               log_scales=np.concatenate([log_s[ik], log_s[ic],
+                                          np.repeat(log_s[isp] - np.log(np.float64(split_factor)), 2, axis=0)]),
+               quats=quats[parent], opacity_logit=op[parent], sh=sh[parent], parent=parent.astype(np.int64))
+    return out
 
 
 def ssim_window(radius=5, sigma=1.5):
