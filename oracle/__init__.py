@@ -283,18 +283,19 @@ def densify_classes(log_scales, opacity_logit, select, size_threshold, min_opaci
     (keep, clone, split) boolean arrays.  Both comparisons are taken in float32,
     on the log scale and on the logit (monotone in the scale and the opacity),
     against thresholds rounded once to float32 from float64:
-      large  <=>  max_k log_scale_k > float32(log size_threshold)
-      alive  <=>  logit >= float32(log(m / (1 - m))), m = min_opacity (always for m = 0)."""
+      large  <=>  some log_scale_k > float32(log size_threshold)  (the largest scale above it)
+      alive  <=>  not logit < float32(log(m / (1 - m))), m = min_opacity (-inf for m = 0)
+    (written so that a NaN component or logit decides as a comparison with NaN does)."""
     ls = np.asarray(log_scales, np.float32).reshape(-1, 3)
     lo = np.asarray(opacity_logit, np.float32).reshape(-1)
     sel = np.asarray(select).reshape(-1) != 0
     ls_thr = np.float32(np.log(np.float64(size_threshold)))
-    large = ls.max(axis=1) > ls_thr
+    large = (ls > ls_thr).any(axis=1)
     if min_opacity > 0.0:
         lo_thr = np.float32(np.log(np.float64(min_opacity) / (1.0 - np.float64(min_opacity))))
-        alive = lo >= lo_thr
     else:
-        alive = np.ones(lo.shape[0], bool)
+        lo_thr = np.float32(-np.inf)
+    alive = ~(lo < lo_thr)
     return alive & ~(sel & large), alive & sel & ~large, alive & sel & large
 
 
