@@ -886,9 +886,15 @@ NEXT_REPS = 20  # timed calls per kernel of the next_rows block (each after an L
 SSIM_FLOPS_PER_VALUE = 5 * 44 + 3 * 44 + 40 + 6  # the D-SSIM loss and gradient, separable form
 
 
+SLEEP_CYCLES = 300_000  # about 0.15 ms of device spin before each timed call
+
+
 def _timed_calls(stream, fn, reps, flush):
     """Mean device time (ms) of fn() on the library's stream: reps calls, each
-    after writing a buffer larger than L2 (the write is outside the events)."""
+    after writing a buffer larger than L2 and a short device spin (both outside
+    the events), so that the call's kernels are all queued by the time the
+    stream reaches the first event and its host work (argument checks,
+    allocations) does not count as device time."""
     import torch
     with torch.cuda.stream(stream):
         for _ in range(3):
@@ -898,6 +904,7 @@ def _timed_calls(stream, fn, reps, flush):
     with torch.cuda.stream(stream):
         for a, b in ev:
             flush.zero_()
+            torch.cuda._sleep(SLEEP_CYCLES)
             a.record(stream)
             fn()
             b.record(stream)
@@ -930,7 +937,8 @@ def run_next_rows(args, device):
     target = torch.from_numpy(np.concatenate([x.reshape(-1) for x in synthetic.target_images(cams, 1)])).to(device)
     out = {"workload": f"{n // 1000}k Gaussians SH3, {VIEWS_PER_STEP} views {WIDTH}x{HEIGHT} (the streaming step's)",
            "timing": f"CUDA events around each call on the library's stream, mean of {NEXT_REPS}, a 256 MB write "
-                     "before each (inputs out of L2)", "hbm_peak_gbs": hbm}
+                     "(inputs out of L2) and a 0.15 ms device spin (the call's host work queued behind it) "
+                     "before each", "hbm_peak_gbs": hbm}
 
     def rate(bytes_, ms):
         gbs = bytes_ / (ms * 1e-3) / 1e9
@@ -976,10 +984,33 @@ def run_next_rows(args, device):
     ms_with = _timed_calls(stream, lambda: bwd(True), NEXT_REPS, flush)
     ms_without = _timed_calls(stream, lambda: bwd(False), NEXT_REPS, flush)
     ms_sel = _timed_calls(stream, lambda: rast.densify_select(dg, dv, 1e-4), NEXT_REPS, flush)
+    # the clone / split / discard step: the 10 % of the visible Gaussians with the largest mean
+    # screen-space gradient selected, size threshold at the median largest scale (about half the
+    # selected Gaussians split), opacity floor 0.005, standard normal samples
+    with torch.cuda.stream(stream):
+        vis = dv > 0
+        thr_g = float(torch.quantile((dg[vis] / dv[vis].float()).double(), 0.9)) if bool(vis.any()) else 1e-4
+        sel = rast.densify_select(dg, dv, thr_g)
+        size_thr = float(torch.exp(p[1].max(dim=1).values.median()).item())
+        z = torch.randn(n, 2, 3, generator=torch.Generator(device=device).manual_seed(31), device=device)
+        dens = rast.densify_apply(*p, sel, z, size_thr, 1.6, 0.005)
+    m_out, n_sel = int(dens["parent"].numel()), int(sel.sum().item())
+    # the split Gaussians (selected, alive, some log scale above the threshold; float32 compares)
+    lo_thr = float(np.log(0.005 / (1.0 - 0.005)))
+    n_split = int((sel.bool() & (p[1] > float(np.log(size_thr))).any(dim=1) & ~(p[3] < lo_thr)).sum().item())
+    del dens
+    ms_apply_dens = _timed_calls(stream, lambda: rast.densify_apply(*p, sel, z, size_thr, 1.6, 0.005, read_count=False),
+                                 NEXT_REPS, flush)
+    K3 = 3 * p[4].shape[1]
     out["densification"] = {
         "render_and_backward_ms_with_statistics": ms_with,
         "render_and_backward_ms_without": ms_without,
         "densify_select": rate(n * (4 + 4 + 1), ms_sel),
+        # apply: every input Gaussian and its selection byte read once, the split ones' samples,
+        # every output Gaussian and its parent index written
+        "densify_apply": dict(rate(n * (44 + 4 * K3 + 1) + n_split * 24 + m_out * (44 + 4 * K3 + 4), ms_apply_dens),
+                              n_in=n, selected=n_sel, split=n_split, n_out=m_out, size_threshold=size_thr,
+                              min_opacity=0.005),
     }
 
     # f2: the pruning-level space S_t^d (11 levels: mask, delta, apply, render of the 8 views and

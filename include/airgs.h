@@ -222,6 +222,45 @@ int airgs_render_backward_ex(airgs_ctx* ctx, airgs_state* saved, const airgs_bac
 int airgs_densify_select(airgs_ctx* ctx, const float* densify_grad, const uint32_t* densify_views, int64_t n,
                          float threshold, uint8_t* mask_out);
 
+/* Output of airgs_densify_apply: device buffers with room for `capacity`
+ * Gaussians each (capacity >= 2 n: every input Gaussian yields at most two
+ * outputs), laid out as airgs_gaussians with the same sh_degree. */
+typedef struct {
+  int64_t capacity;
+  float* means;          /* device [capacity][3] */
+  float* log_scales;     /* device [capacity][3] */
+  float* quats;          /* device [capacity][4], 16-byte aligned */
+  float* opacity_logit;  /* device [capacity] */
+  float* sh;             /* device [capacity][K][3] */
+  uint32_t* parent;      /* nullable device [capacity]: the input index of each output Gaussian */
+  int64_t* n_out;        /* device: the number of output Gaussians (written) */
+} airgs_densify_out;
+
+/* densify_apply: the clone / split / discard step of keyframe reconstruction
+ * (Sec. III-B: Gaussians in high-gradient regions are cloned or split, and
+ * Gaussians of low opacity are discarded), with the clone and split rules of
+ * the adaptive density control of 3D Gaussian Splatting.  For each input
+ * Gaussian i (g, device):
+ *   select[i] != 0 and every log_scale <= log(size_threshold): kept, plus an identical copy;
+ *   select[i] != 0 otherwise: replaced by two children j = 0, 1 with
+ *     mean = mean_i + R(q_i/|q_i|) diag(exp(log_scale_i)) z[i][j],
+ *     log_scale = log_scale_i - log(split_factor), quaternion, opacity logit and SH copied;
+ *   select[i] == 0: kept;
+ *   opacity_logit[i] < logit(min_opacity): discarded, with its copy or children
+ *     (min_opacity 0 discards nothing).
+ * The comparisons are float32, against log(size_threshold) and
+ * logit(min_opacity) rounded to float32 once.  select: device uint8 [n] (for
+ * example from airgs_densify_select); z: device float [n][2][3], standard normal
+ * samples the caller draws (only the rows of split Gaussians are read).
+ * Output rows: the kept originals, then the copies, then the children (two per
+ * split Gaussian), each group in input order; *out->n_out receives the count
+ * (asynchronously, like every output).  Arguments: size_threshold > 0,
+ * split_factor > 0, 0 <= min_opacity < 1 (else AIRGS_E_ARG);
+ * out->capacity < 2 n is AIRGS_E_CAPACITY.  The output buffers must not overlap
+ * the inputs. */
+int airgs_densify_apply(airgs_ctx* ctx, const airgs_gaussians* g, const uint8_t* select, const float* z,
+                        float size_threshold, float split_factor, float min_opacity, const airgs_densify_out* out);
+
 /* gaussian_importance: the per-Gaussian blend weight and blended-pair count of
  * the current frame over n_views cameras, without colour output (the usage
  * frequency of Sec. III-C).  w_out [n] float and cnt_out [n] uint32 are

@@ -102,6 +102,19 @@ class airgs_stats(ctypes.Structure):
     ]
 
 
+class airgs_densify_out(ctypes.Structure):
+    _fields_ = [
+        ("capacity", ctypes.c_int64),
+        ("means", ctypes.c_void_p),
+        ("log_scales", ctypes.c_void_p),
+        ("quats", ctypes.c_void_p),
+        ("opacity_logit", ctypes.c_void_p),
+        ("sh", ctypes.c_void_p),
+        ("parent", ctypes.c_void_p),
+        ("n_out", ctypes.c_void_p),
+    ]
+
+
 P = ctypes.c_void_p
 I = ctypes.c_int
 I64 = ctypes.c_int64
@@ -127,6 +140,8 @@ SIGNATURES = {
     "airgs_render_backward_l1": (I, [CTX, STATE, P, P, P, P, P, P, P, P, P]),
     "airgs_render_backward_ex": (I, [CTX, STATE, ctypes.POINTER(airgs_backward_args)]),
     "airgs_densify_select": (I, [CTX, P, P, I64, ctypes.c_float, P]),
+    "airgs_densify_apply": (I, [CTX, ctypes.POINTER(airgs_gaussians), P, P, ctypes.c_float, ctypes.c_float,
+                                ctypes.c_float, ctypes.POINTER(airgs_densify_out)]),
     "airgs_gaussian_importance": (I, [CTX, ctypes.POINTER(airgs_camera), I, P, P]),
     "airgs_prune_mask": (I, [CTX, P, I64, I64, P]),
     "airgs_prune_delta": (I, [CTX, I64, I, P, P, P, P, P]),

@@ -13,7 +13,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libairgs.so")
 SOURCES = ["api.cu", "project.cu", "sort.cu", "blend_fwd.cu", "blend_bwd.cu", "project_bwd.cu", "sort_noalloc.cu",
-           "order.cu", "cull_lists.cu", "prune.cu", "ssim.cu", "peak.cu"]
+           "order.cu", "cull_lists.cu", "prune.cu", "ssim.cu", "peak.cu", "densify.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 

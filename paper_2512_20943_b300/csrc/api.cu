@@ -958,6 +958,44 @@ int airgs_densify_select(airgs_ctx* ctx, const float* densify_grad, const uint32
   return AIRGS_OK;
 }
 
+int airgs_densify_apply(airgs_ctx* ctx, const airgs_gaussians* g, const uint8_t* select, const float* z,
+                        float size_threshold, float split_factor, float min_opacity, const airgs_densify_out* out) {
+  if (!ctx) return AIRGS_E_ARG;
+  int rc = check_gaussians(ctx, g);
+  if (rc) return rc;
+  if (!out || !out->n_out) return fail(ctx, AIRGS_E_ARG, "out and out->n_out are required");
+  if (!(size_threshold > 0.f) || !std::isfinite(size_threshold) || !(split_factor > 0.f) ||
+      !std::isfinite(split_factor) || !(min_opacity >= 0.f && min_opacity < 1.f))
+    return fail(ctx, AIRGS_E_ARG, "densify_apply: size_threshold > 0, split_factor > 0, 0 <= min_opacity < 1");
+  const int64_t n = g->n;
+  if (n > 0 && (!select || !z)) return fail(ctx, AIRGS_E_ARG, "densify_apply: select and z are required");
+  if (out->capacity < 2 * n)
+    return fail(ctx, AIRGS_E_CAPACITY, "densify_apply: capacity %lld below 2 n = %lld", (long long)out->capacity,
+                (long long)(2 * n));
+  if (n > 0 && (!out->means || !out->log_scales || !out->quats || !out->opacity_logit || !out->sh))
+    return fail(ctx, AIRGS_E_ARG, "densify_apply: null output pointer");
+  if (n > 0 && !aligned16(out->quats)) return fail(ctx, AIRGS_E_ARG, "densify_apply: out->quats must be 16-byte aligned");
+  const float ls_thr = (float)std::log((double)size_threshold);
+  const float ls_div = (float)std::log((double)split_factor);
+  const float lo_thr =
+      min_opacity > 0.f ? (float)std::log((double)min_opacity / (1.0 - (double)min_opacity)) : -INFINITY;
+  uint8_t* cls = nullptr;
+  uint3* tiles = nullptr;
+  uint32_t* totals = nullptr;
+  if (n > 0 && ((rc = dalloc(ctx, &cls, n)) || (rc = dalloc(ctx, &tiles, densify_tiles(n))) ||
+                (rc = dalloc(ctx, &totals, 4)))) {
+    for (void* p : {(void*)cls, (void*)tiles}) dfree(ctx, p);
+    return rc;
+  }
+  cudaError_t e = launch_densify_apply(ctx->stream, n, g->sh_degree, g->means, g->log_scales, g->quats,
+                                       g->opacity_logit, g->sh, select, z, ls_thr, ls_div, lo_thr, cls, tiles, totals,
+                                       out->means, out->log_scales, out->quats, out->opacity_logit, out->sh,
+                                       out->parent, out->n_out);
+  for (void* p : {(void*)cls, (void*)tiles, (void*)totals}) dfree(ctx, p);
+  if (e != cudaSuccess) return fail(ctx, AIRGS_E_CUDA, "densify_apply: %s", cudaGetErrorString(e));
+  return AIRGS_OK;
+}
+
 int airgs_gaussian_importance(airgs_ctx* ctx, const airgs_camera* cams, int n_views, float* w_out,
                               uint32_t* cnt_out) {
   if (!ctx) return AIRGS_E_ARG;

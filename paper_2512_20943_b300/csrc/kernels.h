@@ -82,6 +82,16 @@ cudaError_t launch_densify_select(cudaStream_t st, int64_t n, const float* g, co
 cudaError_t launch_sq_err(cudaStream_t st, const float* a, const float* b, const int64_t* view_off, int n_views,
                           double* out);
 
+// Clone / split / discard of keyframe densification (densify.cu): scratch cls
+// [n] bytes, tile_counts [densify_tiles(n)], totals [4].
+int64_t densify_tiles(int64_t n);
+cudaError_t launch_densify_apply(cudaStream_t st, int64_t n, int sh_degree, const float* means,
+                                 const float* log_scales, const float* quats, const float* opacity_logit,
+                                 const float* sh, const uint8_t* select, const float* z, float ls_thr, float ls_div,
+                                 float lo_thr, uint8_t* cls, uint3* tile_counts, uint32_t* totals, float* o_means,
+                                 float* o_log_scales, float* o_quats, float* o_opacity_logit, float* o_sh,
+                                 uint32_t* o_parent, int64_t* n_out);
+
 // L_3DGS = (1 - lambda) L1 + lambda (1 - SSIM) and its image gradient (ssim.cu):
 // one CTA per 32x32 output tile of each (view, channel) plane; d_tile_base
 // [n_planes + 1] the planes' first tiles (ssim_tiles per plane), n_tiles their

@@ -15,7 +15,7 @@ import torch
 
 from . import _abi
 from ._abi import (AIRGS_DELTA_ANCHOR, AIRGS_DELTA_PREV, AIRGS_QUAT_ADD, airgs_backward_args, airgs_camera,
-                   airgs_config, airgs_gaussians, airgs_stats, load_library)
+                   airgs_config, airgs_densify_out, airgs_gaussians, airgs_stats, load_library)
 
 
 class AirGSError(RuntimeError):
@@ -331,6 +331,41 @@ class Rasterizer:
         self._check(self.lib.airgs_densify_select(self.ctx, _ptr(grad_sum), _ptr(views), grad_sum.numel(),
                                                   float(threshold), _ptr(mask)))
         return mask
+
+    def densify_apply(self, means, log_scales, quats, opacity_logit, sh, select, z, size_threshold: float,
+                      split_factor: float = 1.6, min_opacity: float = 0.0, read_count: bool = True):
+        """Clone / split / discard step of keyframe densification (Sec. III-B),
+        airgs_densify_apply: selected Gaussians whose largest scale is at most
+        size_threshold gain an identical copy, larger selected ones become two
+        children sampled with the caller's standard normal z [n, 2, 3], and
+        Gaussians of opacity below min_opacity are discarded.  Returns a dict of
+        the output Gaussian set (means, log_scales, quats, opacity_logit, sh) and
+        `parent` (int32: input index of each output), sliced to the output
+        count, which is read back (one wait on the context's stream); with
+        read_count=False the buffers keep their capacity 2 n and `n_out` holds
+        the device count, with no wait."""
+        n, deg = self._check_params(means, log_scales, quats, opacity_logit, sh)
+        _check_cuda(select, "select", torch.uint8, (n,))
+        _check_cuda(z, "z", torch.float32, (n, 2, 3))
+        cap, K = 2 * n, (deg + 1) ** 2
+        out = dict(means=self._new((cap, 3), torch.float32), log_scales=self._new((cap, 3), torch.float32),
+                   quats=self._new((cap, 4), torch.float32), opacity_logit=self._new((cap,), torch.float32),
+                   sh=self._new((cap, K, 3), torch.float32), parent=self._new((cap,), torch.int32))
+        n_out = self._new((1,), torch.int64)
+        g = airgs_gaussians(n, deg, means.data_ptr(), log_scales.data_ptr(), quats.data_ptr(),
+                            opacity_logit.data_ptr(), sh.data_ptr())
+        d = airgs_densify_out(cap, out["means"].data_ptr(), out["log_scales"].data_ptr(), out["quats"].data_ptr(),
+                              out["opacity_logit"].data_ptr(), out["sh"].data_ptr(), out["parent"].data_ptr(),
+                              n_out.data_ptr())
+        self._check(self.lib.airgs_densify_apply(self.ctx, ctypes.byref(g), _ptr(select), _ptr(z),
+                                                 float(size_threshold), float(split_factor), float(min_opacity),
+                                                 ctypes.byref(d)))
+        if not read_count:
+            out["n_out"] = n_out
+            return out
+        self.stream.synchronize()
+        m = int(n_out.item())
+        return {k: v[:m] for k, v in out.items()}
 
     def gaussian_importance(self, cams):
         w = self._new((self.n,), torch.float32)
