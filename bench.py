@@ -95,10 +95,10 @@ PROFILE_STEPS = 10  # steps of the per-stage profiling pass after the timed regi
 NCU_TRAFFIC = {
     "blend_bwd": {"bytes_per_launch": (756.987136 + 108.916736) * 1e6, "smem_bytes_per_launch": 377169671 * 128,
                   "sources": _BLEND_SOURCES,
-                  "sha256": "7a3d657e2d5b8084546cbe041f6bb2673d307c732a4ead9b172085d5b2db8bac"},
+                  "sha256": "d906313092f121d20b8bec936683dbc8269322cf0b245db74be21831b3fff33e"},
     "blend_fwd": {"bytes_per_launch": (244.283904 + 228.473856) * 1e6, "smem_bytes_per_launch": 81673612 * 128,
                   "sources": _BLEND_SOURCES,
-                  "sha256": "7a3d657e2d5b8084546cbe041f6bb2673d307c732a4ead9b172085d5b2db8bac"},
+                  "sha256": "d906313092f121d20b8bec936683dbc8269322cf0b245db74be21831b3fff33e"},
 }
 
 
@@ -107,9 +107,9 @@ NCU_TRAFFIC = {
 # profiles/plain_2k_sh0_128x128_ncu.md); the large workload is not captured
 CONFIG_TRAFFIC = {
     ("per_frame", "blend_bwd"): {"bytes_per_launch": (1534.216192 + 199.067392) * 1e6, "sources": _BLEND_SOURCES,
-                                 "sha256": "7a3d657e2d5b8084546cbe041f6bb2673d307c732a4ead9b172085d5b2db8bac"},
+                                 "sha256": "d906313092f121d20b8bec936683dbc8269322cf0b245db74be21831b3fff33e"},
     ("plain", "blend_fwd"): {"bytes_per_launch": 155.136e3, "sources": _BLEND_SOURCES,
-                             "sha256": "7a3d657e2d5b8084546cbe041f6bb2673d307c732a4ead9b172085d5b2db8bac"},
+                             "sha256": "d906313092f121d20b8bec936683dbc8269322cf0b245db74be21831b3fff33e"},
 }
 
 
