@@ -25,6 +25,9 @@ namespace {
 #ifndef AIRGS_DS_ITEMS
 #define AIRGS_DS_ITEMS 2  // measured best of 1, 2, 4 (0.062, 0.057, 0.059 ms at 300k SH3)
 #endif
+#ifndef AIRGS_DS_SCATTER_MINB
+#define AIRGS_DS_SCATTER_MINB 1  // unbounded (100 registers); bounds for 3 or 4 CTAs per SM spill: 0.064, 0.074 against 0.056 ms
+#endif
 constexpr int DS_THREADS = 256;
 constexpr int DS_ITEMS = AIRGS_DS_ITEMS;  // Gaussians per thread
 constexpr int DS_TILE = DS_THREADS * DS_ITEMS;  // Gaussians per CTA
@@ -170,7 +173,7 @@ __device__ __forceinline__ void write_gaussian(const DensifyOutDev& o, uint32_t 
 }
 
 template <int SH3>
-__global__ void __launch_bounds__(DS_THREADS) k_densify_scatter(int64_t n, DensifyIn in, const uint8_t* __restrict__ cls,
+__global__ void __launch_bounds__(DS_THREADS, AIRGS_DS_SCATTER_MINB) k_densify_scatter(int64_t n, DensifyIn in, const uint8_t* __restrict__ cls,
                                                                 const uint3* __restrict__ tile_off,
                                                                 const uint32_t* __restrict__ totals,
                                                                 const float* __restrict__ z, float ls_div, bool sh_vec,
