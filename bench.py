@@ -882,7 +882,7 @@ def run_serving(args, device):
     }
 
 
-NEXT_REPS = 20  # timed calls per kernel of the next_rows block (each after an L2 flush)
+NEXT_REPS = 20  # timed calls per kernel of the next_rows block (each after an L2 flush and a device spin)
 SSIM_FLOPS_PER_VALUE = 5 * 44 + 3 * 44 + 40 + 6  # the D-SSIM loss and gradient, separable form
 
 
@@ -916,10 +916,11 @@ def run_next_rows(args, device):
     """The widened rows on the streaming workload's data (300k Gaussians SH3,
     frame 0's update applied, the 8 views of step 0 at 1352x1014): usage-
     frequency pruning of the frame delta (Sec. III-C), the pruning-level space
-    and Algorithm 1's choice, the densification statistics of keyframe
-    reconstruction (Sec. III-B) and the D-SSIM term of L_3DGS (Eq. 1).  Device
-    times from CUDA events, each call after an L2 flush; HBM-bound kernels as
-    algorithmic bytes over that time against the measured copy bandwidth."""
+    and Algorithm 1's choice, the densification statistics and the clone /
+    split / discard step of keyframe reconstruction (Sec. III-B) and the D-SSIM
+    term of L_3DGS (Eq. 1).  Device times from CUDA events, each call after an
+    L2 flush and a device spin (_timed_calls); HBM-bound kernels as algorithmic
+    bytes over that time against the measured copy bandwidth."""
     import torch
     from paper_2512_20943_b300 import AIRGS_DELTA_ANCHOR, RasterConfig, Rasterizer
     from paper_2512_20943_b300.pruning import pruning_level_space, select_pruning_level
