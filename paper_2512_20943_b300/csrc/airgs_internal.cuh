@@ -60,6 +60,11 @@ constexpr int kFlagGuardY = 32;
 struct __align__(16) GradRec {
   float4 a, b, c;
 };
+// Slots of a GradRec (as 12 floats) that carry the usage frequency of one
+// (view, Gaussian) from the blend backward to the projection adjoint: the sum
+// of blend weights, and the blended-pair count as a uint32.
+constexpr int kGradWeightSlot = 5;
+constexpr int kGradCountSlot = 10;
 
 // ------------------------------------------------------------------ exact-replay arithmetic
 // The forward and the backward evaluate every (pixel, Gaussian) pair through

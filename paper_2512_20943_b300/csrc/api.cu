@@ -704,7 +704,7 @@ int backward_impl(airgs_ctx* ctx, airgs_state* s, const float* dL, const float* 
   StageScope sc(ctx, ST_PROJECT_BWD);
   CK(launch_project_bwd(st, s->n, s->sh_degree, s->means, s->log_scales, s->quats, s->opacity, s->sh, s->d_cams,
                         s->n_views, s->proj, grad, g_means, g_log_scales, g_quats, g_opacity, g_sh, dens_grad,
-                        dens_views));
+                        dens_views, imp_w, imp_cnt));
   return AIRGS_OK;
 }
 

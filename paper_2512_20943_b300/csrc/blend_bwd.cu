@@ -22,7 +22,8 @@
 // count is a warp reduction of the lanes' counts.  With L1 the image gradient
 // sign(C - target)/(3 sum H W) and the loss are computed from the forward's
 // image and the target in the kernel; with IMP the blend weights and counts of
-// the replay are the Gaussians' usage frequency.
+// the replay, the Gaussians' usage frequency, go to the record's weight and
+// count slots, which the projection adjoint adds to the caller's accumulators.
 #include "blend_common.cuh"
 
 #include <cstddef>
@@ -39,8 +40,9 @@ namespace {
 // 16-byte loads touches 32 different banks).  In the flush lanes 2i and 2i+1
 // sum row i over lanes 0-15 and 16-31 (eight 16-byte loads each), trade the
 // component the other one owns with one shuffle, and send sum 2p + h (h = lane
-// parity) with one scalar reduction: sum q to the record's float q, except sum
-// 5 (the blend weight), which goes to the usage weight.
+// parity) with one scalar reduction to the record's float q; with IMP sum 5 is
+// the blend weight (the record's weight slot) and its lane also adds the
+// entry's blended-pair count to the count slot.
 constexpr int kDeferG = 3;
 constexpr int kPairRows = kDeferG * 5;
 constexpr int kPairStride = 36;  // float2 slots per row
@@ -49,7 +51,7 @@ __device__ __forceinline__ int table_slot(int lane) { return lane + ((lane >> 4)
 
 template <bool IMP>
 __device__ __forceinline__ void flush_deferred(float2 (*s_tab)[kPairStride], const uint2* s_fmeta, int nf,
-                                               GradRec* gradv, const BwdIn& in, int lane) {
+                                               GradRec* gradv, int lane) {
   __syncwarp();
   const int row = lane < 2 * kPairRows ? lane >> 1 : kPairRows - 1, h = lane & 1;
   const float4* rp = reinterpret_cast<const float4*>(&s_tab[row][18 * h]);
@@ -65,11 +67,13 @@ __device__ __forceinline__ void flush_deferred(float2 (*s_tab)[kPairStride], con
   const float other = __shfl_xor_sync(kAll, h ? ps.x : ps.y, 1);
   const float sum = (h ? ps.y : ps.x) + other;
   const int f = row / 5, q = 2 * (row - 5 * f) + h;
-  if (lane < 10 * nf && (IMP || q != 5)) {
+  static_assert(kGradWeightSlot == 5, "sum 5 of an entry is its blend weight");
+  if (lane < 10 * nf && (IMP || q != kGradWeightSlot)) {
     const uint2 fm = s_fmeta[f];  // (Gaussian id, blended pairs)
-    float* dst = q != 5 ? reinterpret_cast<float*>(gradv + fm.x) + q : in.imp_w + fm.x;
-    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(dst), "f"(sum) : "memory");
-    if (IMP && q == 5) asm volatile("red.global.add.u32 [%0], %1;" ::"l"(in.imp_cnt + fm.x), "r"(fm.y) : "memory");
+    float* rec = reinterpret_cast<float*>(gradv + fm.x);
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(rec + q), "f"(sum) : "memory");
+    if (IMP && q == kGradWeightSlot)
+      asm volatile("red.global.add.u32 [%0], %1;" ::"l"(rec + kGradCountSlot), "r"(fm.y) : "memory");
   }
   __syncwarp();  // the table is refilled after this
 }
@@ -347,13 +351,13 @@ __global__ void __launch_bounds__(32, MINB) k_blend_bwd(BlendArgs a, BwdIn in) {
         // every compacted entry has a live block: defer without a vote
         defer_entry(s_tab, s_fmeta, ns, slot, acc, me.id, cnt);
         if (++ns == kDeferG) {
-          flush_deferred<IMP>(s_tab, s_fmeta, ns, gradv, in, lane);
+          flush_deferred<IMP>(s_tab, s_fmeta, ns, gradv, lane);
           ns = 0;
         }
       }
       __syncwarp();
     }
-    if (ns > 0) flush_deferred<IMP>(s_tab, s_fmeta, ns, gradv, in, lane);
+    if (ns > 0) flush_deferred<IMP>(s_tab, s_fmeta, ns, gradv, lane);
   }
   __syncwarp();
   finish_counters<L1>(a, in, s_tot, exec_groups, lane);

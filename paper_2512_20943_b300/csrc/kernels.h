@@ -154,8 +154,8 @@ struct BwdIn {
   float* loss;          // L1 accumulator (nullable)
   const int32_t* ncontrib;
   GradRec* grad;        // [V][N]
-  float* imp_w;
-  uint32_t* imp_cnt;
+  float* imp_w;         // nullable: usage frequency requested (the replay fills the records' weight
+  uint32_t* imp_cnt;    // and count slots; the projection adjoint adds them here)
 };
 
 // Kernel shapes the autotuner searches: compiled instantiations of the blend
@@ -190,7 +190,8 @@ cudaError_t launch_project_bwd(cudaStream_t st, int64_t n, int sh_degree, const 
                                const float* log_scales, const float* quats, const float* opacity_logit,
                                const float* sh, const CamDev* cams, int n_views, const ProjRec* proj,
                                const GradRec* grad, float* g_means, float* g_log_scales, float* g_quats,
-                               float* g_opacity, float* g_sh, float* dens_grad, uint32_t* dens_views);
+                               float* g_opacity, float* g_sh, float* dens_grad, uint32_t* dens_views, float* imp_w,
+                               uint32_t* imp_cnt);
 
 cudaError_t measure_fp32_peak(cudaStream_t st, int num_sms, float* scratch, double* tflops);
 size_t fp32_probe_words(int num_sms);

@@ -87,7 +87,8 @@ __global__ void __launch_bounds__(PB_THREADS, AIRGS_PROJ_BWD_MINB) k_project_bwd
                                                      const GradRec* __restrict__ grad, float* __restrict__ g_means,
                                                      float* __restrict__ g_log_scales, float* __restrict__ g_quats,
                                                      float* __restrict__ g_opacity, float* __restrict__ g_sh,
-                                                     float* __restrict__ dens_grad, uint32_t* __restrict__ dens_views) {
+                                                     float* __restrict__ dens_grad, uint32_t* __restrict__ dens_views,
+                                                     float* __restrict__ imp_w, uint32_t* __restrict__ imp_cnt) {
   wait_prior_grid();
   constexpr int K = (DEG + 1) * (DEG + 1);
   constexpr int S = sh_tile_stride<DEG>();
@@ -122,6 +123,8 @@ __global__ void __launch_bounds__(PB_THREADS, AIRGS_PROJ_BWD_MINB) k_project_bwd
     float gop = 0.f;
     float dgrad = 0.f;   // sum over views of |dL/d mean2d| (densification statistic)
     uint32_t dviews = 0; // views in which the Gaussian is visible
+    float wimp = 0.f;    // usage frequency over the views: blend weight and blended pairs
+    uint32_t cimp = 0;
 
     for (int v = 0; v < n_views; ++v) {
       const size_t o = (size_t)v * n + i;
@@ -129,6 +132,9 @@ __global__ void __launch_bounds__(PB_THREADS, AIRGS_PROJ_BWD_MINB) k_project_bwd
       const int flags = __float_as_int(rec.c.w);
       if (!(flags & kFlagVisible)) continue;
       const GradRec gr = grad[o];
+      static_assert(kGradWeightSlot == 5 && kGradCountSlot == 10, "record slots read below");
+      wimp += gr.b.y;
+      cimp += __float_as_uint(gr.c.z);
       // the blend backward's sums -> gradients of the 2D mean, the conic and the opacity
       const float op2 = rec.b.y, lo = kLn2 * op2;
       const float gmx = lo * fmaf(2.f * rec.a.z, gr.a.x, rec.a.w * gr.a.y);
@@ -275,6 +281,10 @@ __global__ void __launch_bounds__(PB_THREADS, AIRGS_PROJ_BWD_MINB) k_project_bwd
       dens_grad[i] += dgrad;
       dens_views[i] += dviews;
     }
+    if (imp_w) {  // one thread per Gaussian: plain read-modify-write
+      imp_w[i] += wimp;
+      imp_cnt[i] += cimp;
+    }
   }
   __syncthreads();  // every thread has finished reading the coefficients
   if (t < nloc) {
@@ -289,14 +299,15 @@ cudaError_t launch_project_bwd(cudaStream_t st, int64_t n, int sh_degree, const 
                                const float* log_scales, const float* quats, const float* opacity_logit,
                                const float* sh, const CamDev* cams, int n_views, const ProjRec* proj,
                                const GradRec* grad, float* g_means, float* g_log_scales, float* g_quats,
-                               float* g_opacity, float* g_sh, float* dens_grad, uint32_t* dens_views) {
+                               float* g_opacity, float* g_sh, float* dens_grad, uint32_t* dens_views, float* imp_w,
+                               uint32_t* imp_cnt) {
   if (n == 0) return cudaSuccess;
   int blocks = (int)((n + PB_THREADS - 1) / PB_THREADS);
   cudaError_t e;
 #define AIRGS_PB(D)                                                                                                 \
   e = launch_serialised(k_project_bwd<D>, dim3(blocks), dim3(PB_THREADS), 0, st, n, means, log_scales, quats,       \
                         opacity_logit, sh, cams, n_views, proj, grad, g_means, g_log_scales, g_quats, g_opacity, g_sh, \
-                        dens_grad, dens_views)
+                        dens_grad, dens_views, imp_w, imp_cnt)
   switch (sh_degree) {
     case 0: AIRGS_PB(0); break;
     case 1: AIRGS_PB(1); break;
