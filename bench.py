@@ -93,12 +93,12 @@ _BLEND_SOURCES = ("paper_2512_20943_b300/csrc/blend_fwd.cu", "paper_2512_20943_b
 PROFILE_STEPS = 10  # steps of the per-stage profiling pass after the timed region
 
 NCU_TRAFFIC = {
-    "blend_bwd": {"bytes_per_launch": (756.987136 + 108.916736) * 1e6, "smem_bytes_per_launch": 377169671 * 128,
+    "blend_bwd": {"bytes_per_launch": (746.732032 + 104.579072) * 1e6, "smem_bytes_per_launch": 376582246 * 128,
                   "sources": _BLEND_SOURCES,
-                  "sha256": "d906313092f121d20b8bec936683dbc8269322cf0b245db74be21831b3fff33e"},
+                  "sha256": "8dc565fa118c57211fdc94d8b39c62f02c86fc2fc92abd0e75daa87d41ae8ee2"},
     "blend_fwd": {"bytes_per_launch": (244.283904 + 228.473856) * 1e6, "smem_bytes_per_launch": 81673612 * 128,
                   "sources": _BLEND_SOURCES,
-                  "sha256": "d906313092f121d20b8bec936683dbc8269322cf0b245db74be21831b3fff33e"},
+                  "sha256": "8dc565fa118c57211fdc94d8b39c62f02c86fc2fc92abd0e75daa87d41ae8ee2"},
 }
 
 
@@ -106,10 +106,10 @@ NCU_TRAFFIC = {
 # commands are in profiles/per_frame_200k_sh3_20x1352x1014_ncu.md and
 # profiles/plain_2k_sh0_128x128_ncu.md); the large workload is not captured
 CONFIG_TRAFFIC = {
-    ("per_frame", "blend_bwd"): {"bytes_per_launch": (1534.216192 + 199.067392) * 1e6, "sources": _BLEND_SOURCES,
-                                 "sha256": "d906313092f121d20b8bec936683dbc8269322cf0b245db74be21831b3fff33e"},
+    ("per_frame", "blend_bwd"): {"bytes_per_launch": (1521.957632 + 192.448256) * 1e6, "sources": _BLEND_SOURCES,
+                                 "sha256": "8dc565fa118c57211fdc94d8b39c62f02c86fc2fc92abd0e75daa87d41ae8ee2"},
     ("plain", "blend_fwd"): {"bytes_per_launch": 155.136e3, "sources": _BLEND_SOURCES,
-                             "sha256": "d906313092f121d20b8bec936683dbc8269322cf0b245db74be21831b3fff33e"},
+                             "sha256": "8dc565fa118c57211fdc94d8b39c62f02c86fc2fc92abd0e75daa87d41ae8ee2"},
 }
 
 
