@@ -70,7 +70,7 @@ __device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float* 
 }
 
 #ifndef AIRGS_PROJ_BWD_MINB
-#define AIRGS_PROJ_BWD_MINB 4  // 128 registers, 16 warps per SM (measured best of 1, 4, 5, 6)
+#define AIRGS_PROJ_BWD_MINB 4  // 128 registers, 16 warps per SM (measured best of 1, 3, 4, 5, 6)
 #endif
 constexpr int PB_THREADS = 128;
 
