@@ -16,9 +16,9 @@
 //   (sum t, blend weight), (colour r, g), (colour b, sum t dx dy)
 // (t = dL/dalpha G on unclamped pairs) are deferred into a per-warp
 // shared-memory table of three entries with one 8-byte store per pair, reduced
-// by two lanes per pair (a transpose through shared memory) and flushed with
-// one scalar red.global.add per sum into the Gaussian's gradient record (the
-// projection adjoint applies the 2D coefficients); the entry's blended-pair
+// by two lanes per pair (a transpose through shared memory), each adding its
+// half of the pair with one 8-byte vector reduction into the Gaussian's
+// gradient record (the projection adjoint applies the 2D coefficients); the entry's blended-pair
 // count is a warp reduction of the lanes' counts.  With L1 the image gradient
 // sign(C - target)/(3 sum H W) and the loss are computed from the forward's
 // image and the target in the kernel; with IMP the blend weights and counts of
@@ -38,11 +38,12 @@ namespace {
 // of 36 float2 = 72 words, 8 banks apart; the 16-byte gap before the upper
 // half puts the two halves 4 banks apart, so each 8-lane phase of the flush's
 // 16-byte loads touches 32 different banks).  In the flush lanes 2i and 2i+1
-// sum row i over lanes 0-15 and 16-31 (eight 16-byte loads each), trade the
-// component the other one owns with one shuffle, and send sum 2p + h (h = lane
-// parity) with one scalar reduction to the record's float q; with IMP sum 5 is
-// the blend weight (the record's weight slot) and its lane also adds the
-// entry's blended-pair count to the count slot.
+// sum row i over lanes 0-15 and 16-31 (eight 16-byte loads each) and each adds
+// its part of pair p to the record's floats 2p, 2p + 1 with one 8-byte vector
+// reduction (trading components by shuffle for one scalar reduction per sum
+// cost 2 % more time); with IMP pair 2 holds the blend weight in the record's
+// weight slot, and the even lane of that pair also adds the entry's
+// blended-pair count to the count slot.
 constexpr int kDeferG = 3;
 constexpr int kPairRows = kDeferG * 5;
 constexpr int kPairStride = 36;  // float2 slots per row
@@ -63,16 +64,14 @@ __device__ __forceinline__ void flush_deferred(float2 (*s_tab)[kPairStride], con
     s0 = __fadd2_rn(s0, make_float2(u.x, u.y));
     s1 = __fadd2_rn(s1, make_float2(u.z, u.w));
   }
-  const float2 ps = __fadd2_rn(s0, s1);
-  const float other = __shfl_xor_sync(kAll, h ? ps.x : ps.y, 1);
-  const float sum = (h ? ps.y : ps.x) + other;
-  const int f = row / 5, q = 2 * (row - 5 * f) + h;
-  static_assert(kGradWeightSlot == 5, "sum 5 of an entry is its blend weight");
-  if (lane < 10 * nf && (IMP || q != kGradWeightSlot)) {
+  const float2 ps = __fadd2_rn(s0, s1);  // this half row's part of sum pair p, both components
+  const int f = row / 5, p = row - 5 * f;
+  static_assert(kGradWeightSlot == 5, "pair 2 of an entry holds its blend weight");
+  if (lane < 10 * nf) {
     const uint2 fm = s_fmeta[f];  // (Gaussian id, blended pairs)
     float* rec = reinterpret_cast<float*>(gradv + fm.x);
-    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(rec + q), "f"(sum) : "memory");
-    if (IMP && q == kGradWeightSlot)
+    atomicAdd(reinterpret_cast<float2*>(rec) + p, ps);  // one 8-byte reduction per half row
+    if (IMP && p == 2 && h == 0)
       asm volatile("red.global.add.u32 [%0], %1;" ::"l"(rec + kGradCountSlot), "r"(fm.y) : "memory");
   }
   __syncwarp();  // the table is refilled after this
